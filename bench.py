@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Benchmark of the pixel-track CA chain on GB300: PU200 events/s.
+
+One step = the whole chain (load + bin, doublets, links, ntuplets + cleaning, fit) over
+one batch of BATCH synthetic PU200 events.  `value` is timed with CUDA events on the
+library's stream with the inputs already in device memory; L2 is flushed (256 MB write)
+before every step, outside the step's events.  `e2e` is the same metric through the
+public C ABI call pt_reconstruct_batch with pinned host buffers (host->device copies and
+the device->host read of the results inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own replica on its own GPU (events are independent,
+no collective on the data path); rank 0 prints one JSON line.  `--impl reference`
+times the CPU oracle on the host cores on the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import sim  # noqa: E402
+
+BATCH = 64
+SEED0 = 3000
+METRIC = "PU200 events/s on 1 GB300, plain CA vs MLP-gated (eff ≥ plain−0.5%); p99 ms"
+WORKLOAD = ("PU200: 10k helices/event (1/pT~U[0.1,2] GeV^-1, |eta|<2.5, z0~N(0,5cm)), "
+            "4 barrel layers + 2x3 disks, 2% noise, ~41k hits/event; plain CA")
+# kernels per step: load 6 (clear, histogram, 3 scan, scatter), doublets 1, links 1,
+# ntuplets 15 (search, bucket count, 3 scan, scatter, bucket sort, 3 cleaning, 3 scan,
+# compact, offsets), fit 1
+LAUNCHES_PER_STEP = 24
+FLUSH_BYTES = 256 << 20
+
+
+def make_events(n: int, seed0: int = SEED0):
+    return [sim.generate(sim.PU200, seed0 + i) for i in range(n)]
+
+
+def capacity(batch: int = BATCH, phi_bins: int = 256) -> dict:
+    import paper_2501_05520_gb300 as pt
+    return pt.default_capacity(max_events=batch, hits_per_event=49152,
+                               cells_per_event=3_500_000, links_per_event=262_144,
+                               ntuplets_per_event=196_608, phi_bins=phi_bins)
+
+
+# Algorithmic bytes per unit (read once + written once), per stage.
+def algorithmic_bytes(n_hits: int, cells: int, links: int, cand: int, survivors: int) -> dict:
+    return {
+        "load": 13 * n_hits + 20 * n_hits,
+        "doublets": 20 * n_hits + 10 * cells,
+        "connect": 8 * cells + 8 * n_hits + 4 * links + 1 * cells,
+        "ntuplets": 4 * links + 4 * cells + 29 * cand + 2 * 29 * cand + 4 * 5 * cand,
+        "fit": (6 * 12 + 36) * survivors,
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                p = [v.strip() for v in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+def cpu_baseline(n_events: int | None = None, seed0: int = SEED0 + 500) -> dict:
+    """The oracle as it stands, one PU200 event per host thread."""
+    import oracle
+    import paper_2501_05520_gb300 as pt
+    cuts = pt.default_cuts()
+    cores = os.cpu_count() or 1
+    n = n_events or max(1, min(cores, 16))
+    evs = make_events(n, seed0)
+    oracle.build()
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=min(cores, n)) as ex:
+        list(ex.map(lambda e: oracle.reconstruct(e.x, e.y, e.z, e.layer, cuts), evs))
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "events/s", "cores": min(cores, n), "kind": "oracle",
+            "sample": f"{n} PU200 events (seeds {seed0}..{seed0 + n - 1}), one per thread, "
+                      f"{platform.machine()} host, {dt:.1f} s"}
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, local = _dist_env()
+    if rank != 0:
+        return
+    import paper_2501_05520_gb300 as pt  # noqa: F401  (cut constants only)
+    cores = os.cpu_count() or 1
+    per_step = max(1, min(cores, 16))
+    for w in range(args.warmup):
+        cpu_baseline(per_step, seed0=SEED0 + 700 + w * per_step)
+    vals = []
+    t_all = 0.0
+    for s in range(args.steps):
+        r = cpu_baseline(per_step, seed0=SEED0 + s * per_step)
+        vals.append(r)
+        t_all += per_step / r["value"]
+    value = args.steps * per_step / t_all
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * t_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "events/s", "kind": "oracle",
+                             "cores": vals[0]["cores"],
+                             "sample": f"{per_step} PU200 events per step, one per thread"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2501_05520_gb300 as pt
+    rank, world, local = _dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B = args.batch
+    events = make_events(2 * B, seed0=SEED0 + rank * 100_000)
+    host = [sim.concat(events[:B]), sim.concat(events[B:])]
+    dbat = [(h[0], *(torch.from_numpy(a).to(dev) for a in h[1:])) for h in host]
+    stream = torch.cuda.Stream(dev)
+    ctx = pt.Context(capacity=capacity(B, args.phi_bins), device=local, stream=stream)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step_stages(i, evs):
+        off, x, y, z, layer = dbat[i % 2]
+        evs[0].record(stream)
+        ctx.pt_load_batch(off, x, y, z, layer)
+        evs[1].record(stream)
+        ctx.pt_build_doublets(sync=False)
+        evs[2].record(stream)
+        ctx.pt_connect_cells(sync=False)
+        evs[3].record(stream)
+        ctx.pt_find_ntuplets(sync=False)
+        evs[4].record(stream)
+        ctx.pt_fit_tracks(sync=False)
+        evs[5].record(stream)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            off, x, y, z, layer = dbat[i % 2]
+            ctx.pt_enqueue_batch(off, x, y, z, layer)
+        stream.synchronize()
+        ctx.pt_get_ntuplets()  # raises on any capacity or input error
+        # counts of one batch for the bytes model
+        off, x, y, z, layer = dbat[0]
+        ctx.pt_load_batch(off, x, y, z, layer)
+        counts = dict(hits=int(off[-1]), cells=ctx.pt_build_doublets(),
+                      links=ctx.pt_connect_cells(), survivors=ctx.pt_find_ntuplets())
+        counts["candidates"] = int(ctx.pt_get_candidates()[0].shape[0])
+        ctx.pt_fit_tracks()
+
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        with Clocks(local) as clk:
+            for s in range(args.steps):
+                flush.zero_()
+                step_stages(s, evs[s])
+            stream.synchronize()
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        ctx.pt_get_ntuplets()
+    clocks = clk.summary()
+    names = ["load", "doublets", "connect", "ntuplets", "fit"]
+    stage_ms = {n: [] for n in names}
+    step_ms = []
+    for e in evs:
+        step_ms.append(e[0].elapsed_time(e[5]))
+        for k, n in enumerate(names):
+            stage_ms[n].append(e[k].elapsed_time(e[k + 1]))
+    total_s = sum(step_ms) / 1000.0
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * B * args.steps / total_s
+
+    # end to end through the public call: pinned host in, host out
+    pin = [torch.from_numpy(a).pin_memory() for a in host[0][1:]]
+    capn = int(ctx.capacity["max_ntuplets"])
+    out = dict(hits=torch.empty((capn, 6), dtype=torch.int32).pin_memory(),
+               nhits=torch.empty(capn, dtype=torch.uint8).pin_memory(),
+               tracks=torch.empty((capn, 36), dtype=torch.uint8).pin_memory(),
+               event_offsets=torch.empty(B + 1, dtype=torch.int64).pin_memory())
+    e2e_t = []
+    S = 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        h, _, _, _ = ctx.pt_reconstruct_batch(host[0][0], *pin, out=out)
+        S = int(h.shape[0])
+        if i >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t)
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    n_hits = int(host[0][0][-1])
+    h2d = n_hits * 13 + (B + 1) * 4 + 8
+    d2h = S * (24 + 1 + 36) + (B + 1) * 8 + 128
+
+    # roofline of the dominant kernel
+    mean_stage = {n: statistics.mean(v) for n, v in stage_ms.items()}
+    dom = max(("doublets", "connect"), key=lambda n: mean_stage[n])
+    ab = algorithmic_bytes(counts["hits"], counts["cells"], counts["links"], counts["candidates"],
+                           counts["survivors"])
+    peaks = _peaks()
+    achieved = ab[dom] / (mean_stage[dom] / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": None, "peak_src": peaks["src"], "algorithmic_bytes": ab[dom]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "events_per_step": B, "form": "plain",
+                           "phi_bins": args.phi_bins,
+                           "l2": "flushed before every step (256 MB write, outside the events)",
+                           "parallelism": f"replicas x{world}"},
+                "e2e": {"value": world * B * args.steps / e2e_s, "unit": "events/s",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "roofline": roofline,
+                "stages_ms": {n: round(v, 4) for n, v in mean_stage.items()},
+                "counts_per_step": counts,
+                "clocks": clocks,
+                "gpu_launches": LAUNCHES_PER_STEP * args.steps}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--phi-bins", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        import paper_2501_05520_gb300.build as b
+        b.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * pt_ca.h -- C ABI of the GB300 pixel-track cellular automaton.
+ *
+ * The library implements, on one GPU, the pattern-recognition chain that the paper
+ * serves as its rule-based tracking workload (Sec. 2.2.1, Fig. 2): hits on adjacent
+ * detector layers are paired into doublets ("cells"), cells that share a hit are
+ * linked by a cellular automaton into triplets, hit chains ("ntuplets") that may be
+ * tracks are extracted and cleaned of duplicates, and a fit gives the track
+ * parameters.  Detector constants are loaded once when a context is created and
+ * intermediates stay on the device (Sec. 2.2.1 and Sec. 3); several requests can be
+ * in flight on one GPU (Sec. 3, Sec. 4.2).
+ *
+ * Conventions for every function:
+ *   - Return a pt_status; never throw, never abort.  On failure, pt_last_error()
+ *     returns a message for the calling thread (valid until that thread's next call).
+ *   - Input buffers are borrowed for the duration of the call only; output buffers are
+ *     owned by the caller.  `on_device` = 1 means the pointer is a device pointer on
+ *     the context's device, 0 means host memory (pinned host memory is faster).
+ *   - Hit indices in outputs are the caller's input indices within the event (0-based),
+ *     listed from the innermost to the outermost hit, padded with -1 to 6 entries.
+ *   - Ntuplets of an event are returned in canonical order: hit tuple ascending
+ *     (signed comparison, so a tuple sorts before its longer extensions).
+ *   - Capacities are never exceeded silently: the call returns PT_ERR_CAPACITY and
+ *     pt_last_error() names the capacity and the size that was needed.
+ *   - A context is used by one host thread at a time; contexts are independent.
+ *   - All GPU work of a context is issued on its stream, in call order.
+ *
+ * Layer codes: 0..3 barrel layers (inner to outer), 4..6 disks at +z (|z|
+ * increasing), 7..9 disks at -z.  Allowed layer pairs (inner, outer):
+ *   (0,1) (1,2) (2,3) (0,4) (1,4) (2,4) (4,5) (5,6) (0,7) (1,7) (2,7) (7,8) (8,9).
+ * Units: cm, GeV, tesla.  The beam spot is the z axis (x = y = 0).
+ */
+#ifndef PT_CA_H
+#define PT_CA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PT_OK = 0,
+  PT_ERR_INVALID = 1,   /* bad argument: NULL pointer, negative size, layer code > 9 ... */
+  PT_ERR_CAPACITY = 2,  /* a capacity of the context is too small for this input */
+  PT_ERR_CUDA = 3,      /* a CUDA runtime call failed; message has the CUDA error string */
+  PT_ERR_TIMEOUT = 4,   /* a bounded wait expired (pt_poll) */
+  PT_ERR_NOT_READY = 5, /* result not ready yet (pt_poll with timeout 0) */
+  PT_ERR_NOMEM = 6      /* device or host allocation failed, or the budget is exhausted */
+} pt_status;
+
+typedef struct pt_ctx pt_ctx;
+
+/* Cut constants (float32).  Every cut is evaluated in float32 with correctly rounded
+ * + - * / sqrt only, in a fixed order, without fused multiply-add:
+ *   doublet (inner i, outer o; dx = xo-xi, dy = yo-yi, dr = ro-ri, dz = zo-zi):
+ *     D0 dr > 0;  D1 xi*xo + yi*yo > 0;
+ *     D2 |xi*yo - yi*xo| * 2 <= kmax * ((ri*ro) * sqrt(dx*dx + dy*dy));
+ *     D3 |zi*dr - ri*dz| <= z0max * dr;   D4 |dz| <= cotmax * dr.
+ *   link of cells (h0,h1) -> (h1,h2):
+ *     C1 |(z1-z0)*(r2-r0) - (z2-z0)*(r1-r0)| <= rz0*(r2-r0) + rz1*|z2-z0|;
+ *     C2 curvature of the circle through the three hits <= kmax;
+ *     C3 distance of closest approach of that circle to the z axis <= dca_b0 when h0
+ *        is on layer 0, else dca_other (division-free form; the quotient is the link
+ *        quality q). */
+typedef struct {
+  float kmax;      /* 1/cm */
+  float z0max;     /* cm */
+  float cotmax;
+  float rz0;       /* cm */
+  float rz1;
+  float dca_b0;    /* cm */
+  float dca_other; /* cm */
+} pt_cuts;
+
+typedef struct {
+  float bfield_T;  /* solenoid field along +z, used for pT = 0.299792458 B / (100 |kappa|) */
+} pt_geometry;
+
+typedef struct {
+  int64_t max_events;   /* events per batch */
+  int64_t max_hits;     /* hits per batch (all events together) */
+  int64_t max_cells;    /* doublets per batch */
+  int64_t max_links;    /* accepted cell links per batch */
+  int64_t max_ntuplets; /* ntuplets before duplicate cleaning, per batch */
+  int32_t phi_bins;     /* azimuthal bins per layer, 16..4096 */
+  int32_t reserved;     /* must be 0 */
+} pt_capacity;
+
+/* One fitted track.  kappa > 0: counter-clockwise seen from +z moving outwards;
+ * phi0: direction of motion at the point of closest approach to the z axis, which is
+ * d0 * (sin phi0, -cos phi0); z0 and cot_theta: z = z0 + cot_theta * s along the
+ * transverse arc length s from that point; chi2 with 10 um (r-phi) and 20 um (z)
+ * errors; charge = -sign(kappa). */
+typedef struct {
+  float kappa, phi0, d0, cot_theta, z0, pt, chi2_circle, chi2_line;
+  int8_t charge;
+  uint8_t nhits;
+  uint8_t pad[2];
+} pt_track;
+
+/* ------------------------------------------------------------------ lifecycle */
+
+/* Device bytes needed for a context of the given capacity (the workspace that
+ * pt_create borrows when the caller supplies one).  Sec. 2.2.1: intermediates are kept
+ * on the device, so all per-batch state lives in this one block. */
+pt_status pt_workspace_size(const pt_capacity* cap, size_t* bytes);
+
+/* Create a context on `device` (Sec. 3: detector constants are loaded once at start).
+ * workspace: device memory of >= pt_workspace_size bytes, 256-byte aligned, owned by
+ *            the caller and borrowed until pt_destroy; NULL lets the library allocate.
+ * stream:    a cudaStream_t owned by the caller, or NULL to create a private stream.
+ * All three structs are copied.  On failure *out is NULL. */
+pt_status pt_create(const pt_geometry* geom, const pt_cuts* cuts, const pt_capacity* cap,
+                    int device, void* workspace, size_t workspace_bytes, void* stream,
+                    pt_ctx** out);
+
+/* Destroy a context; waits for its stream, frees what the library allocated. NULL ok. */
+pt_status pt_destroy(pt_ctx* ctx);
+
+/* Replace the stream of a context (caller-owned cudaStream_t, or NULL for private). */
+pt_status pt_set_stream(pt_ctx* ctx, void* stream);
+
+/* ------------------------------------------------------------ stage calls (Fig. 2) */
+
+/* Load one event of n hits (x, y, z float32, layer uint8) and sort it into per-layer
+ * azimuthal bins on the device.  Equivalent to pt_load_batch with one event. */
+pt_status pt_load_hits(pt_ctx* ctx, int64_t n, const float* x, const float* y, const float* z,
+                       const uint8_t* layer, int on_device);
+
+/* Load a batch of events.  hit_offsets: host array [n_events + 1], offsets[0] = 0,
+ * non-decreasing; event e owns hits [offsets[e], offsets[e+1]) of the x/y/z/layer
+ * arrays.  Errors: PT_ERR_INVALID for bad offsets or a layer code > 9 (checked on the
+ * device; reported by the next call that synchronises), PT_ERR_CAPACITY. */
+pt_status pt_load_batch(pt_ctx* ctx, int n_events, const int64_t* hit_offsets, const float* x,
+                        const float* y, const float* z, const uint8_t* layer, int on_device);
+
+/* Doublets of the loaded batch (Sec. 2.2.1, Fig. 2: hits in adjacent layers are
+ * paired).  n_cells: NULL to stay asynchronous; else the call synchronises the stream
+ * and stores the number of cells (and reports capacity errors). */
+pt_status pt_build_doublets(pt_ctx* ctx, int64_t* n_cells);
+
+/* Cellular-automaton links of cells that share a hit (Sec. 2.2.1: doublets are paired
+ * to triplets).  n_links as above. */
+pt_status pt_connect_cells(pt_ctx* ctx, int64_t* n_links);
+
+/* Ntuplets: every path of linked cells from a cell without an incoming link to a cell
+ * without an outgoing link, 3..6 hits (Sec. 2.2.1: a group of hits that may form a
+ * track is picked), then duplicate cleaning and canonical ordering.  n_ntuplets
+ * receives the number of cleaned ntuplets. */
+pt_status pt_find_ntuplets(pt_ctx* ctx, int64_t* n_ntuplets);
+
+/* Circle + line fit of every cleaned ntuplet (Sec. 2.2.1: a fit determines the track
+ * parameters).  n_tracks as above. */
+pt_status pt_fit_tracks(pt_ctx* ctx, int64_t* n_tracks);
+
+/* -------------------------------------------------------------------- results */
+
+/* Cleaned ntuplets of the batch, events in order, canonical order within an event.
+ * hits: [cap][6] int32 input indices within the event, -1 padded; nhits: [cap]
+ * (either may be NULL); event_offsets: [n_events + 1] int64 (may be NULL), the
+ * ntuplets of event e are [event_offsets[e], event_offsets[e+1]).  *n = total count.
+ * PT_ERR_CAPACITY if cap < total (nothing written).  Synchronises the stream. */
+pt_status pt_get_ntuplets(pt_ctx* ctx, int32_t* hits, uint8_t* nhits, int64_t* event_offsets,
+                          int64_t cap, int64_t* n, int on_device);
+
+/* Fitted tracks, one per cleaned ntuplet, same order.  Synchronises the stream. */
+pt_status pt_get_tracks(pt_ctx* ctx, pt_track* tracks, int64_t cap, int64_t* n, int on_device);
+
+/* Intermediate products, for validation.  Cells as (inner, outer) input-index pairs;
+ * links as (h0, h1, h2) input-index triples with their quality q; ntuplets before
+ * cleaning as [6] hit tuples with hit count and q.  Event e's entries carry the event
+ * index in `event` (NULL allowed).  Order is unspecified.  Synchronise the stream. */
+pt_status pt_get_cells(pt_ctx* ctx, int32_t* inner, int32_t* outer, int32_t* event, int64_t cap,
+                       int64_t* n);
+pt_status pt_get_links(pt_ctx* ctx, int32_t* h0, int32_t* h1, int32_t* h2, float* q,
+                       int32_t* event, int64_t cap, int64_t* n);
+pt_status pt_get_candidates(pt_ctx* ctx, int32_t* hits, uint8_t* nhits, float* q, int32_t* event,
+                            int64_t cap, int64_t* n);
+
+/* ------------------------------------------------------------- whole batch */
+
+/* Load, doublets, links, ntuplets, fit and copy-out of a batch in one call; the GPU
+ * stages run as one CUDA graph (captured on first use).  in_on_device applies to
+ * x/y/z/layer, out_on_device to the outputs.  Outputs as in pt_get_ntuplets /
+ * pt_get_tracks (hits, nhits, tracks may be NULL); event_offsets [n_events+1] required.
+ * Synchronises the stream. */
+pt_status pt_reconstruct_batch(pt_ctx* ctx, int n_events, const int64_t* hit_offsets,
+                               const float* x, const float* y, const float* z,
+                               const uint8_t* layer, int in_on_device, int32_t* hits_out,
+                               uint8_t* nhits_out, pt_track* tracks_out,
+                               int64_t* event_offsets, int64_t cap, int64_t* n,
+                               int out_on_device);
+
+/* Load a batch and enqueue all GPU stages (doublets, links, ntuplets, fit, export) as
+ * one CUDA graph on the context's stream, without synchronising: results stay on the
+ * device until a getter (pt_get_ntuplets, pt_get_tracks, ...) is called.  Input
+ * validation errors are returned immediately; capacity errors by the next getter. */
+pt_status pt_enqueue_batch(pt_ctx* ctx, int n_events, const int64_t* hit_offsets,
+                           const float* x, const float* y, const float* z, const uint8_t* layer,
+                           int on_device);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char* pt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PT_CA_H */

@@ -1,0 +1,354 @@
+"""GB300 pixel-track cellular automaton: thin Python binding of the C ABI in include/pt_ca.h.
+
+Argument marshalling only: every stage of the chain runs in the CUDA library
+(lib/libptca.so).  There is no CPU fallback: if the library is missing, every call
+raises.  PyTorch is used only for device memory (the workspace) and the stream.
+
+Function names follow the C ABI (pt_create, pt_load_hits, pt_build_doublets, ...);
+`Context` bundles a context handle with its torch-allocated workspace.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libptca.so")
+CUTS_FILE = os.path.join(_PKG, "params", "cuts_v1.json")
+_lib = None
+
+PT_OK, PT_ERR_INVALID, PT_ERR_CAPACITY, PT_ERR_CUDA, PT_ERR_TIMEOUT, PT_ERR_NOT_READY, \
+    PT_ERR_NOMEM = range(7)
+
+# Every symbol include/pt_ca.h declares.
+EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt_load_hits",
+            "pt_load_batch", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
+            "pt_fit_tracks", "pt_get_ntuplets", "pt_get_tracks", "pt_get_cells", "pt_get_links",
+            "pt_get_candidates", "pt_reconstruct_batch", "pt_enqueue_batch", "pt_last_error")
+
+
+class PtCuts(ctypes.Structure):
+    _fields_ = [("kmax", ctypes.c_float), ("z0max", ctypes.c_float), ("cotmax", ctypes.c_float),
+                ("rz0", ctypes.c_float), ("rz1", ctypes.c_float), ("dca_b0", ctypes.c_float),
+                ("dca_other", ctypes.c_float)]
+
+
+class PtGeometry(ctypes.Structure):
+    _fields_ = [("bfield_T", ctypes.c_float)]
+
+
+class PtCapacity(ctypes.Structure):
+    _fields_ = [("max_events", ctypes.c_int64), ("max_hits", ctypes.c_int64),
+                ("max_cells", ctypes.c_int64), ("max_links", ctypes.c_int64),
+                ("max_ntuplets", ctypes.c_int64), ("phi_bins", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+TRACK_DTYPE = np.dtype([("kappa", "<f4"), ("phi0", "<f4"), ("d0", "<f4"), ("cot_theta", "<f4"),
+                        ("z0", "<f4"), ("pt", "<f4"), ("chi2_circle", "<f4"),
+                        ("chi2_line", "<f4"), ("charge", "i1"), ("nhits", "u1"),
+                        ("pad", "u1", (2,))])
+assert TRACK_DTYPE.itemsize == 36
+
+
+class PtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"pt status {status}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_2501_05520_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        PI64 = ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "pt_workspace_size": [ctypes.POINTER(PtCapacity), ctypes.POINTER(ctypes.c_size_t)],
+            "pt_create": [ctypes.POINTER(PtGeometry), ctypes.POINTER(PtCuts),
+                          ctypes.POINTER(PtCapacity), I32, P, ctypes.c_size_t, P,
+                          ctypes.POINTER(ctypes.c_void_p)],
+            "pt_destroy": [P],
+            "pt_set_stream": [P, P],
+            "pt_load_hits": [P, I64, P, P, P, P, I32],
+            "pt_load_batch": [P, I32, P, P, P, P, P, I32],
+            "pt_build_doublets": [P, PI64],
+            "pt_connect_cells": [P, PI64],
+            "pt_find_ntuplets": [P, PI64],
+            "pt_fit_tracks": [P, PI64],
+            "pt_get_ntuplets": [P, P, P, P, I64, PI64, I32],
+            "pt_get_tracks": [P, P, I64, PI64, I32],
+            "pt_get_cells": [P, P, P, P, I64, PI64],
+            "pt_get_links": [P, P, P, P, P, P, I64, PI64],
+            "pt_get_candidates": [P, P, P, P, P, I64, PI64],
+            "pt_reconstruct_batch": [P, I32, P, P, P, P, P, I32, P, P, P, P, I64, PI64, I32],
+            "pt_enqueue_batch": [P, I32, P, P, P, P, P, I32],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.pt_last_error.restype = ctypes.c_char_p
+        L.pt_last_error.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != PT_OK:
+        raise PtError(status, lib().pt_last_error().decode())
+
+
+def default_cuts(which: str = "pt_min_0p45") -> dict:
+    """Frozen float32 cut constants (params/cuts_v1.json)."""
+    with open(CUTS_FILE) as f:
+        d = json.load(f)[which]
+    return {k: d[k] for k, _ in PtCuts._fields_}
+
+
+def default_capacity(max_events: int = 1, hits_per_event: int = 65536,
+                     cells_per_event: int = 4 << 20, links_per_event: int = 1 << 20,
+                     ntuplets_per_event: int = 1 << 19, phi_bins: int = 256) -> dict:
+    return dict(max_events=max_events, max_hits=max_events * hits_per_event,
+                max_cells=max_events * cells_per_event, max_links=max_events * links_per_event,
+                max_ntuplets=min(max_events * ntuplets_per_event, (1 << 29) - 1),
+                phi_bins=phi_bins, reserved=0)
+
+
+def _cap(d: dict) -> PtCapacity:
+    return PtCapacity(*(int(d.get(k, 0)) for k, _ in PtCapacity._fields_))
+
+
+def pt_workspace_size(capacity: dict) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().pt_workspace_size(ctypes.byref(_cap(capacity)), ctypes.byref(n)))
+    return int(n.value)
+
+
+def _hptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _as_input(a, dtype):
+    """(pointer, on_device, keep-alive) for a numpy array or a torch tensor."""
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        t = a.contiguous()
+        want = {np.float32: torch.float32, np.uint8: torch.uint8}[dtype]
+        if t.dtype != want:
+            t = t.to(want)
+        return ctypes.c_void_p(t.data_ptr()), int(t.is_cuda), t
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return _hptr(arr), 0, arr
+
+
+class Context:
+    """A pt_ctx with a workspace borrowed from the torch caching allocator.
+
+    cuts: dict of pt_cuts fields (default: the frozen constants); capacity: dict of
+    pt_capacity fields; stream: a torch.cuda.Stream, or None for torch's current stream.
+    """
+
+    def __init__(self, cuts: dict | None = None, capacity: dict | None = None,
+                 bfield: float = 3.8, device: int = 0, stream=None, torch_workspace: bool = True):
+        import torch
+        self.cuts = dict(cuts or default_cuts())
+        self.capacity = dict(capacity or default_capacity())
+        self.device = device
+        L = lib()
+        nbytes = pt_workspace_size(self.capacity)
+        ws_ptr, ws_bytes = None, 0
+        self._ws = None
+        if torch_workspace:
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
+            base = self._ws.data_ptr()
+            ws_ptr = (base + 255) // 256 * 256
+            ws_bytes = nbytes
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        self.stream = stream
+        h = ctypes.c_void_p(None)
+        _check(L.pt_create(ctypes.byref(PtGeometry(bfield)),
+                           ctypes.byref(PtCuts(*(float(self.cuts[k]) for k, _ in PtCuts._fields_))),
+                           ctypes.byref(_cap(self.capacity)), device,
+                           ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes,
+                           ctypes.c_void_p(sp) if sp else None, ctypes.byref(h)))
+        self.handle = h
+        self.n_events = 0
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().pt_destroy(self.handle)
+            self.handle = ctypes.c_void_p(None)
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------ stages
+    def pt_load_hits(self, x, y, z, layer):
+        px, dev, kx = _as_input(x, np.float32)
+        py, _, ky = _as_input(y, np.float32)
+        pz, _, kz = _as_input(z, np.float32)
+        pl, _, kl = _as_input(layer, np.uint8)
+        n = int(kx.shape[0]) if hasattr(kx, "shape") else len(kx)
+        _check(lib().pt_load_hits(self.handle, n, px, py, pz, pl, dev))
+        self.n_events = 1
+
+    def pt_load_batch(self, offsets, x, y, z, layer):
+        off = np.ascontiguousarray(offsets, np.int64)
+        px, dev, kx = _as_input(x, np.float32)
+        py, _, ky = _as_input(y, np.float32)
+        pz, _, kz = _as_input(z, np.float32)
+        pl, _, kl = _as_input(layer, np.uint8)
+        _check(lib().pt_load_batch(self.handle, off.size - 1, _hptr(off), px, py, pz, pl, dev))
+        self.n_events = off.size - 1
+
+    def _stage(self, fn, sync: bool):
+        if not sync:
+            _check(fn(self.handle, None))
+            return None
+        n = ctypes.c_int64(0)
+        _check(fn(self.handle, ctypes.byref(n)))
+        return int(n.value)
+
+    def pt_build_doublets(self, sync: bool = True):
+        return self._stage(lib().pt_build_doublets, sync)
+
+    def pt_connect_cells(self, sync: bool = True):
+        return self._stage(lib().pt_connect_cells, sync)
+
+    def pt_find_ntuplets(self, sync: bool = True):
+        return self._stage(lib().pt_find_ntuplets, sync)
+
+    def pt_fit_tracks(self, sync: bool = True):
+        return self._stage(lib().pt_fit_tracks, sync)
+
+    # ----------------------------------------------------------------- results
+    def pt_get_ntuplets(self):
+        """(hits int32 [S,6] event-local, nhits uint8 [S], event_offsets int64 [E+1])."""
+        n = ctypes.c_int64(0)
+        st = lib().pt_get_ntuplets(self.handle, None, None, None, 0, ctypes.byref(n), 0)
+        if st not in (PT_OK, PT_ERR_CAPACITY):
+            _check(st)
+        S = int(n.value)
+        hits = np.empty((S, 6), np.int32)
+        nh = np.empty(S, np.uint8)
+        off = np.empty(self.n_events + 1, np.int64)
+        _check(lib().pt_get_ntuplets(self.handle, _hptr(hits), _hptr(nh), _hptr(off), S,
+                                     ctypes.byref(n), 0))
+        return hits, nh, off
+
+    def pt_get_tracks(self) -> np.ndarray:
+        n = ctypes.c_int64(0)
+        st = lib().pt_get_tracks(self.handle, None, 0, ctypes.byref(n), 0)
+        if st not in (PT_OK, PT_ERR_CAPACITY):
+            _check(st)
+        out = np.zeros(int(n.value), TRACK_DTYPE)
+        _check(lib().pt_get_tracks(self.handle, _hptr(out), out.size, ctypes.byref(n), 0))
+        return out
+
+    def pt_get_cells(self):
+        n = ctypes.c_int64(0)
+        st = lib().pt_get_cells(self.handle, None, None, None, 0, ctypes.byref(n))
+        if st not in (PT_OK, PT_ERR_CAPACITY):
+            _check(st)
+        C = int(n.value)
+        a, b, e = (np.empty(C, np.int32) for _ in range(3))
+        _check(lib().pt_get_cells(self.handle, _hptr(a), _hptr(b), _hptr(e), C, ctypes.byref(n)))
+        return a, b, e
+
+    def pt_get_links(self):
+        n = ctypes.c_int64(0)
+        st = lib().pt_get_links(self.handle, None, None, None, None, None, 0, ctypes.byref(n))
+        if st not in (PT_OK, PT_ERR_CAPACITY):
+            _check(st)
+        Lk = int(n.value)
+        h0, h1, h2, e = (np.empty(Lk, np.int32) for _ in range(4))
+        q = np.empty(Lk, np.float32)
+        _check(lib().pt_get_links(self.handle, _hptr(h0), _hptr(h1), _hptr(h2), _hptr(q),
+                                  _hptr(e), Lk, ctypes.byref(n)))
+        return h0, h1, h2, q, e
+
+    def pt_get_candidates(self):
+        n = ctypes.c_int64(0)
+        st = lib().pt_get_candidates(self.handle, None, None, None, None, 0, ctypes.byref(n))
+        if st not in (PT_OK, PT_ERR_CAPACITY):
+            _check(st)
+        T = int(n.value)
+        hits = np.empty((T, 6), np.int32)
+        nh = np.empty(T, np.uint8)
+        q = np.empty(T, np.float32)
+        e = np.empty(T, np.int32)
+        _check(lib().pt_get_candidates(self.handle, _hptr(hits), _hptr(nh), _hptr(q), _hptr(e),
+                                       T, ctypes.byref(n)))
+        return hits, nh, q, e
+
+    # ------------------------------------------------------------ whole batch
+    def pt_enqueue_batch(self, offsets, x, y, z, layer):
+        off = np.ascontiguousarray(offsets, np.int64)
+        px, dev, kx = _as_input(x, np.float32)
+        py, _, ky = _as_input(y, np.float32)
+        pz, _, kz = _as_input(z, np.float32)
+        pl, _, kl = _as_input(layer, np.uint8)
+        _check(lib().pt_enqueue_batch(self.handle, off.size - 1, _hptr(off), px, py, pz, pl, dev))
+        self.n_events = off.size - 1
+
+    def pt_reconstruct_batch(self, offsets, x, y, z, layer, out: dict | None = None):
+        """Whole chain for a batch.  Returns (hits [S,6], nhits [S], tracks [S], offsets [E+1]).
+
+        `out` may hold preallocated host arrays 'hits', 'nhits', 'tracks' (pinned ones are
+        faster) of equal capacity, or torch CUDA tensors (then results stay on the device
+        and the returned arrays are those tensors)."""
+        off = np.ascontiguousarray(offsets, np.int64)
+        E = off.size - 1
+        px, dev, kx = _as_input(x, np.float32)
+        py, _, ky = _as_input(y, np.float32)
+        pz, _, kz = _as_input(z, np.float32)
+        pl, _, kl = _as_input(layer, np.uint8)
+        if out is None:
+            capn = int(self.capacity["max_ntuplets"])
+            out = dict(hits=np.empty((capn, 6), np.int32), nhits=np.empty(capn, np.uint8),
+                       tracks=np.zeros(capn, TRACK_DTYPE))
+        out_dev = int(hasattr(out["hits"], "is_cuda") and out["hits"].is_cuda)
+        evoff = out.get("event_offsets")
+        if evoff is None or evoff.shape[0] < E + 1:
+            evoff = np.empty(E + 1, np.int64)
+        n = ctypes.c_int64(0)
+        _check(lib().pt_reconstruct_batch(
+            self.handle, E, _hptr(off), px, py, pz, pl, dev,
+            ctypes.c_void_p(_ptr_of(out["hits"])), ctypes.c_void_p(_ptr_of(out["nhits"])),
+            ctypes.c_void_p(_ptr_of(out["tracks"])), ctypes.c_void_p(_ptr_of(evoff)),
+            int(out["nhits"].shape[0]), ctypes.byref(n), out_dev))
+        S = int(n.value)
+        self.n_events = E
+        return out["hits"][:S], out["nhits"][:S], out["tracks"][:S], evoff[: E + 1]
+
+
+def _ptr_of(a) -> int:
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def exported_symbols() -> list[str]:
+    """Names of EXPORTED found in the library (loads it; no GPU call)."""
+    L = lib()
+    return [s for s in EXPORTED if hasattr(L, s)]

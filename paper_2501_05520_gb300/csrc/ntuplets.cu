@@ -1,0 +1,207 @@
+// Stages A4-A6: ntuplet extraction, canonical order and duplicate cleaning (Sec.
+// 2.2.1, Fig. 2: from the seeds, a group of hits that potentially forms a track is
+// picked).
+//
+// A4  every path of linked cells from a root (a cell with no incoming link) to a leaf
+//     (a cell with no outgoing link) with 3..6 hits.  One thread per root walks its
+//     out-links depth first with an explicit stack (the layer graph bounds the depth
+//     at 5 cells).  The path quality q is the float32 sum of its link qualities,
+//     added from the innermost link outwards.
+// A6  canonical order: ntuplets sorted by their hit tuple (batch input indices, -1
+//     padded, signed).  A counting sort on the first hit puts them in per-hit buckets
+//     (a few entries each), which one thread per bucket finishes by insertion sort.
+// A5  duplicate cleaning on the sorted list, rank i = sorted position: key =
+//     (6 - nhits, q bits, i) packed in 64 bits, so a smaller key is "more hits, then
+//     smaller q, then smaller tuple".  atomicMin gives every cell its best key; an
+//     ntuplet survives when it holds the best key of all its cells; a triplet then
+//     dies if it shares a hit with a surviving ntuplet of >= 4 hits.  Survivors are
+//     compacted in sorted order, and per-event offsets are derived from it.
+#include "ptca_internal.cuh"
+
+namespace ptca {
+
+namespace {
+
+__global__ void __launch_bounds__(256)
+    k_find_ntuplets(Buffers b, uint64_t cap_cells, uint64_t cap_nt) {
+  const uint64_t nc = min(b.cnt[CNT_CELLS], (unsigned long long)cap_cells);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nc; a += stride) {
+    if (b.has_in[a] || b.link_cnt[a] == 0) continue;
+    uint32_t path[kMaxCellsPerNt];
+    uint32_t it[kMaxCellsPerNt], end[kMaxCellsPerNt];
+    float qs[kMaxCellsPerNt];
+    path[0] = (uint32_t)a;
+    it[0] = b.link_off[a];
+    end[0] = it[0] + b.link_cnt[a];
+    qs[0] = 0.0f;
+    int depth = 1;
+    while (depth > 0) {
+      const int d = depth - 1;
+      if (it[d] == end[d]) {
+        --depth;
+        continue;
+      }
+      const uint32_t l = it[d]++;
+      if (depth == kMaxCellsPerNt) continue;  // deeper than the layer graph allows
+      const uint32_t c = b.link_dst[l];
+      const float q = fadd(qs[d], b.link_q[l]);
+      const uint32_t nl = b.link_cnt[c];
+      if (nl == 0) {
+        // leaf: emit path[0..d] + c, i.e. depth + 1 cells, depth + 2 hits
+        const unsigned long long t = atomicAdd(&b.cnt[CNT_NT], 1ull);
+        if (t >= cap_nt) {
+          atomicOr(&b.cnt[CNT_STATUS], ST_NT);
+          continue;
+        }
+        const int ncell = depth + 1;
+        int32_t* hp = b.nt_hits + t * kMaxHits;
+        uint32_t* cp = b.nt_cells + t * kMaxCellsPerNt;
+        hp[0] = (int32_t)b.perm[b.cell_in[path[0]]];
+        for (int k = 0; k < ncell; ++k) {
+          const uint32_t ck = k < depth ? path[k] : c;
+          hp[k + 1] = (int32_t)b.perm[b.cell_out[ck]];
+          cp[k] = ck;
+        }
+        for (int k = ncell + 1; k < kMaxHits; ++k) hp[k] = -1;
+        for (int k = ncell; k < kMaxCellsPerNt; ++k) cp[k] = 0xffffffffu;
+        b.nt_n[t] = (uint8_t)(ncell + 1);
+        b.nt_q[t] = q;
+        continue;
+      }
+      path[depth] = c;
+      it[depth] = b.link_off[c];
+      end[depth] = it[depth] + nl;
+      qs[depth] = q;
+      ++depth;
+    }
+  }
+}
+
+__global__ void k_bucket_count(Buffers b, uint64_t cap_nt) {
+  const uint64_t T = min(b.cnt[CNT_NT], (unsigned long long)cap_nt);
+  if (blockIdx.x == 0 && threadIdx.x == 0) b.cnt[CNT_SCAN_NT] = T;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += stride)
+    b.nt_rank[t] = atomicAdd(&b.bucket_cnt[b.nt_hits[t * kMaxHits]], 1u);
+}
+
+__global__ void k_bucket_scatter(Buffers b, uint64_t cap_nt) {
+  const uint64_t T = min(b.cnt[CNT_NT], (unsigned long long)cap_nt);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += stride)
+    b.ord[b.bucket_start[b.nt_hits[t * kMaxHits]] + b.nt_rank[t]] = (uint32_t)t;
+}
+
+__device__ __forceinline__ bool tuple_less(const int32_t* a, const int32_t* c) {
+#pragma unroll
+  for (int k = 1; k < kMaxHits; ++k) {
+    if (a[k] != c[k]) return a[k] < c[k];
+  }
+  return false;
+}
+
+__global__ void k_bucket_sort(Buffers b) {
+  const int N = b.hdr->n_hits;
+  const int stride = gridDim.x * blockDim.x;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < N; h += stride) {
+    const uint32_t lo = b.bucket_start[h], hi = b.bucket_start[h + 1];
+    for (uint32_t i = lo + 1; i < hi; ++i) {
+      const uint32_t v = b.ord[i];
+      const int32_t* hv = b.nt_hits + (uint64_t)v * kMaxHits;
+      uint32_t j = i;
+      while (j > lo && tuple_less(hv, b.nt_hits + (uint64_t)b.ord[j - 1] * kMaxHits)) {
+        b.ord[j] = b.ord[j - 1];
+        --j;
+      }
+      b.ord[j] = v;
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long dedup_key(const Buffers& b, uint32_t t, uint64_t i) {
+  return ((unsigned long long)(kMaxHits - b.nt_n[t]) << 61) |
+         ((unsigned long long)__float_as_uint(b.nt_q[t]) << kRankBits) | i;
+}
+
+__global__ void k_dedup_min(Buffers b) {
+  const uint64_t T = b.cnt[CNT_SCAN_NT];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += stride) {
+    const uint32_t t = b.ord[i];
+    const unsigned long long key = dedup_key(b, t, i);
+    const int nc = b.nt_n[t] - 1;
+    for (int k = 0; k < nc; ++k) atomicMin(&b.best[b.nt_cells[(uint64_t)t * kMaxCellsPerNt + k]], key);
+  }
+}
+
+__global__ void k_dedup_alive(Buffers b) {
+  const uint64_t T = b.cnt[CNT_SCAN_NT];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += stride) {
+    const uint32_t t = b.ord[i];
+    const unsigned long long key = dedup_key(b, t, i);
+    const int n = b.nt_n[t];
+    bool ok = true;
+    for (int k = 0; k < n - 1; ++k)
+      ok = ok && (b.best[b.nt_cells[(uint64_t)t * kMaxCellsPerNt + k]] == key);
+    b.alive[i] = ok ? 1u : 0u;
+    if (ok && n >= 4)
+      for (int k = 0; k < n; ++k) b.used[b.nt_hits[(uint64_t)t * kMaxHits + k]] = 1;
+  }
+}
+
+__global__ void k_dedup_triplets(Buffers b) {
+  const uint64_t T = b.cnt[CNT_SCAN_NT];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += stride) {
+    if (!b.alive[i]) continue;
+    const uint32_t t = b.ord[i];
+    if (b.nt_n[t] != 3) continue;
+    const int32_t* h = b.nt_hits + (uint64_t)t * kMaxHits;
+    if (b.used[h[0]] || b.used[h[1]] || b.used[h[2]]) b.alive[i] = 0u;
+  }
+}
+
+__global__ void k_compact(Buffers b) {
+  const uint64_t T = b.cnt[CNT_SCAN_NT];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) b.cnt[CNT_SV] = b.alive_scan[T];
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += stride)
+    if (b.alive[i]) b.sv[b.alive_scan[i]] = (uint32_t)i;
+}
+
+// ev_nt_off[e] = first survivor of event >= e; survivors are ordered by event because
+// batch input indices are.
+__global__ void k_event_offsets(Buffers b) {
+  const uint64_t T = b.cnt[CNT_SCAN_NT];
+  const uint64_t S = b.alive_scan[T];
+  const int E = b.hdr->n_events;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= S; j += stride) {
+    const int e_cur = j < S ? find_event(b.hit_off, E, b.nt_hits[(uint64_t)b.ord[b.sv[j]] * kMaxHits])
+                            : E;
+    const int e_prev =
+        j > 0 ? find_event(b.hit_off, E, b.nt_hits[(uint64_t)b.ord[b.sv[j - 1]] * kMaxHits]) : -1;
+    for (int e = e_prev + 1; e <= e_cur; ++e) b.ev_nt_off[e] = (int64_t)j;
+  }
+}
+
+}  // namespace
+
+void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s) {
+  const uint64_t cap_nt = (uint64_t)p.max_ntuplets;
+  k_find_ntuplets<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_cells, cap_nt);
+  k_bucket_count<<<l.grid, 256, 0, s>>>(b, cap_nt);
+  launch_scan(b.bucket_cnt, b.bucket_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s);
+  k_bucket_scatter<<<l.grid, 256, 0, s>>>(b, cap_nt);
+  k_bucket_sort<<<l.grid, 256, 0, s>>>(b);
+  k_dedup_min<<<l.grid, 256, 0, s>>>(b);
+  k_dedup_alive<<<l.grid, 256, 0, s>>>(b);
+  k_dedup_triplets<<<l.grid, 256, 0, s>>>(b);
+  launch_scan(b.alive, b.alive_scan, &b.cnt[CNT_SCAN_NT], b.scan_part, s);
+  k_compact<<<l.grid, 256, 0, s>>>(b);
+  k_event_offsets<<<l.grid, 256, 0, s>>>(b);
+}
+
+}  // namespace ptca

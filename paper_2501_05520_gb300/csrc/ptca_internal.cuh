@@ -1,0 +1,233 @@
+// Internal declarations of the GB300 pixel-track CA library: device buffer layout,
+// exact float32 cut predicates and the host-side launchers of every kernel.
+//
+// Every kernel is a fixed-grid, grid-stride kernel that reads its work size from
+// device memory (batch header or a device counter).  No stage needs a host round
+// trip, so the whole chain of a batch can be replayed from one captured CUDA graph
+// whatever the batch's hit, cell or link counts are.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pt_ca.h"
+
+namespace ptca {
+
+constexpr int kLayers = 10;
+constexpr int kMaxHits = 6;                // longest chain of the layer graph
+constexpr int kMaxCellsPerNt = kMaxHits - 1;
+constexpr int kMaxOuter = 3;               // outer layers paired with one inner layer
+constexpr int kStage = 256;                // staged doublets per (hit, outer layer)
+constexpr int kLocalLinks = 8;             // links of one cell kept in registers
+constexpr int kRankBits = 29;              // duplicate-cleaning key: rank field width
+
+// device counters (unsigned long long)
+enum : int {
+  CNT_CELLS = 0,
+  CNT_LINKS = 1,
+  CNT_NT = 2,
+  CNT_STATUS = 3,
+  CNT_SCAN_BINS = 4,  // sizes for the device-wide scans
+  CNT_SCAN_HITS = 5,
+  CNT_SCAN_NT = 6,
+  CNT_GATE_KEPT = 7,
+  CNT_SV = 8,         // cleaned ntuplets
+  CNT_N = 16
+};
+// status bits
+enum : unsigned long long {
+  ST_CELLS = 1ull,
+  ST_LINKS = 2ull,
+  ST_NT = 4ull,
+  ST_LAYER = 8ull,
+};
+
+struct BatchHeader {
+  int32_t n_events;
+  int32_t n_hits;
+};
+
+struct Params {
+  pt_cuts cuts;
+  float bfield;
+  int32_t phi_bins;
+  int64_t max_events, max_hits, max_cells, max_links, max_ntuplets;
+};
+
+// Device buffers carved out of one workspace block (see layout() in runtime.cu).
+struct Buffers {
+  BatchHeader* hdr;
+  unsigned long long* cnt;   // [CNT_N]
+  // inputs, batch order
+  float* in_x;
+  float* in_y;
+  float* in_z;
+  uint8_t* in_layer;
+  int32_t* hit_off;          // [max_events + 1]
+  uint32_t* in_bin;          // [max_hits] global bin of input hit (or ~0)
+  uint32_t* in_rank;         // [max_hits] rank within the bin
+  // hits sorted by (event, layer, phi bin)
+  float4* hit4;              // [max_hits] (x, y, z, r)
+  uint32_t* perm;            // [max_hits] sorted -> input (batch) index
+  uint32_t* hbin;            // [max_hits] global bin of sorted hit
+  uint32_t* bin_cnt;         // [max_events*10*B + 1]
+  uint32_t* bin_start;       // [max_events*10*B + 1]
+  uint32_t* layer_rmax;      // [max_events*10] float bits of max r per event layer
+  // doublet segments: per sorted hit and outer-layer slot
+  uint32_t* seg_off;         // [max_hits*3]
+  uint32_t* seg_cnt;         // [max_hits*3]
+  float* seg_mdr;            // [max_hits*3] min dr of the segment, < 0: unsorted
+  // cells
+  uint32_t* cell_in;         // [max_cells] sorted hit index
+  uint32_t* cell_out;        // [max_cells]
+  float* cell_slope;         // [max_cells] dz/dr
+  uint32_t* link_off;        // [max_cells]
+  uint32_t* link_cnt;        // [max_cells]
+  uint8_t* has_in;           // [max_cells]
+  unsigned long long* best;  // [max_cells] duplicate-cleaning key
+  // links
+  uint32_t* link_dst;        // [max_links]
+  float* link_q;             // [max_links]
+  // ntuplets before cleaning
+  int32_t* nt_hits;          // [max_ntuplets*6] batch input index, -1 pad
+  uint32_t* nt_cells;        // [max_ntuplets*5]
+  uint8_t* nt_n;             // [max_ntuplets]
+  float* nt_q;               // [max_ntuplets]
+  uint32_t* nt_rank;         // [max_ntuplets] rank within its first-hit bucket
+  // canonical order
+  uint32_t* bucket_cnt;      // [max_hits + 1]
+  uint32_t* bucket_start;    // [max_hits + 1]
+  uint32_t* ord;             // [max_ntuplets] sorted position -> ntuplet
+  uint32_t* alive;           // [max_ntuplets]
+  uint32_t* alive_scan;      // [max_ntuplets + 1]
+  uint8_t* used;             // [max_hits]
+  uint32_t* sv;              // [max_ntuplets] survivor -> sorted position
+  int64_t* ev_nt_off;        // [max_events + 1]
+  pt_track* tracks;          // [max_ntuplets]
+  int32_t* exp_hits;         // [max_ntuplets*6] export staging (event-local indices)
+  uint8_t* exp_n;            // [max_ntuplets]
+  float* exp_q;              // [max_ntuplets]
+  int32_t* exp_ev;           // [max_ntuplets]
+  uint32_t* scan_part;       // [kScanBlocks + 1]
+};
+
+constexpr int kScanBlocks = 256;
+
+struct Launch {
+  int sms;         // multiprocessors
+  int grid;        // generic persistent grid (blocks of 256 threads)
+};
+
+// ------------------------------------------------------------------ launchers
+void launch_clear(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
+void launch_bin_hits(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
+void launch_doublets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
+void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
+void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
+void launch_fit(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
+// scan of n+1 entries: out[i] = sum(in[0..i)), n = *n_dev
+void launch_scan(const uint32_t* in, uint32_t* out, const unsigned long long* n_dev,
+                 uint32_t* part, cudaStream_t s);
+// exports with event-local input indices
+void launch_export_ntuplets(const Buffers& b, const Launch& l, cudaStream_t s);
+void launch_export_candidates(const Buffers& b, const Launch& l, cudaStream_t s);
+// cells -> out3 [n][3] (inner, outer, event); links -> out4 [n][4] (h0, h1, h2, event), q
+void launch_export_cells(const Buffers& b, const Params& p, const Launch& l, int32_t* out3,
+                         cudaStream_t s);
+void launch_export_links(const Buffers& b, const Params& p, const Launch& l, int32_t* out4,
+                         float* outq, cudaStream_t s);
+
+// ------------------------------------------------------------ device helpers
+#ifdef __CUDACC__
+constexpr unsigned kFull = 0xffffffffu;
+
+// Correctly rounded float32 operations that the compiler never contracts into FMA.
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// Doublet cuts D0..D4 on (x, y, z, r) of the inner and outer hit, in the library's
+// fixed evaluation order (see pt_cuts in pt_ca.h).
+__device__ __forceinline__ bool doublet_pass(const pt_cuts& c, float4 hi, float4 ho) {
+  const float dx = fsub(ho.x, hi.x), dy = fsub(ho.y, hi.y);
+  const float dr = fsub(ho.w, hi.w), dz = fsub(ho.z, hi.z);
+  if (!(dr > 0.0f)) return false;
+  if (!(fadd(fmul(hi.x, ho.x), fmul(hi.y, ho.y)) > 0.0f)) return false;
+  if (!(fabsf(fsub(fmul(hi.z, dr), fmul(hi.w, dz))) <= fmul(c.z0max, dr))) return false;
+  if (!(fabsf(dz) <= fmul(c.cotmax, dr))) return false;
+  const float l2 = fmul(fabsf(fsub(fmul(hi.x, ho.y), fmul(hi.y, ho.x))), 2.0f);
+  const float r2 = fmul(c.kmax, fmul(fmul(hi.w, ho.w), fsqrt(fadd(fmul(dx, dx), fmul(dy, dy)))));
+  return l2 <= r2;
+}
+
+// r-z alignment C1 only (cheap first test of a link).
+__device__ __forceinline__ bool link_c1(const pt_cuts& c, float4 p0, float4 p1, float4 p2) {
+  const float lc1 = fabsf(fsub(fmul(fsub(p1.z, p0.z), fsub(p2.w, p0.w)),
+                               fmul(fsub(p2.z, p0.z), fsub(p1.w, p0.w))));
+  const float rc1 = fadd(fmul(c.rz0, fsub(p2.w, p0.w)), fmul(c.rz1, fabsf(fsub(p2.z, p0.z))));
+  return lc1 <= rc1;
+}
+
+// Curvature C2 and beam-spot distance C3 of the circle through three hits; q gets the
+// distance (link quality) when both pass.
+__device__ __forceinline__ bool link_c23(const pt_cuts& c, float4 p0, bool first_on_b0, float4 p1,
+                                         float4 p2, float& q) {
+  const float ax = fsub(p1.x, p0.x), ay = fsub(p1.y, p0.y);
+  const float bx = fsub(p2.x, p0.x), by = fsub(p2.y, p0.y);
+  const float cx = fsub(p2.x, p1.x), cy = fsub(p2.y, p1.y);
+  const float a2 = fadd(fmul(ax, ax), fmul(ay, ay));
+  const float b2 = fadd(fmul(bx, bx), fmul(by, by));
+  const float cr = fsub(fmul(ax, by), fmul(ay, bx));
+  const float lc2 = fmul(fabsf(cr), 2.0f);
+  const float rc2 =
+      fmul(c.kmax, fmul(fmul(fsqrt(a2), fsqrt(b2)), fsqrt(fadd(fmul(cx, cx), fmul(cy, cy)))));
+  if (!(lc2 <= rc2)) return false;
+  const float D = fmul(cr, 2.0f);
+  const float ux = fsub(fmul(by, a2), fmul(ay, b2));
+  const float uy = fsub(fmul(ax, b2), fmul(bx, a2));
+  const float num = fadd(fmul(fadd(fmul(p0.x, p0.x), fmul(p0.y, p0.y)), D),
+                         fmul(fadd(fmul(p0.x, ux), fmul(p0.y, uy)), 2.0f));
+  const float px = fadd(fmul(p0.x, D), ux);
+  const float py = fadd(fmul(p0.y, D), uy);
+  const float den =
+      fadd(fsqrt(fadd(fmul(px, px), fmul(py, py))), fsqrt(fadd(fmul(ux, ux), fmul(uy, uy))));
+  const float dcamax = first_on_b0 ? c.dca_b0 : c.dca_other;
+  const float l3 = fabsf(num);
+  if (!(l3 <= fmul(dcamax, den))) return false;
+  q = fdiv(l3, den);
+  return true;
+}
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ unsigned warp_incl_scan(unsigned v) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned t = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Event owning batch hit g: largest e with off[e] <= g (empty events are skipped).
+__device__ __forceinline__ int find_event(const int32_t* off, int n_events, int g) {
+  int lo = 0, hi = n_events - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Outer layers of each inner layer (allowed layer pairs), -1 padded.
+static __constant__ int8_t kOuter[kLayers][kMaxOuter] = {
+    {1, 4, 7}, {2, 4, 7}, {3, 4, 7}, {-1, -1, -1}, {5, -1, -1},
+    {6, -1, -1}, {-1, -1, -1}, {8, -1, -1}, {9, -1, -1}, {-1, -1, -1}};
+static __constant__ int8_t kNOuter[kLayers] = {3, 3, 3, 0, 1, 1, 0, 1, 1, 0};
+#endif
+
+}  // namespace ptca

@@ -1,0 +1,600 @@
+// Host runtime of the C ABI declared in pt_ca.h: context lifecycle, workspace layout,
+// input staging, stage sequencing on the context's stream, CUDA-graph replay of the
+// whole batch, result export and error reporting.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ptca_internal.cuh"
+
+using namespace ptca;
+
+namespace {
+
+thread_local std::string g_err;
+
+pt_status fail(pt_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define PT_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(PT_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+  } while (0)
+
+#define PT_TRY(call)              \
+  do {                            \
+    pt_status s_ = (call);        \
+    if (s_ != PT_OK) return s_;   \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+
+// Carves the workspace; with base == nullptr only computes the size.
+size_t layout(const pt_capacity& c, char* base, Buffers* b) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    char* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  const size_t N = (size_t)c.max_hits, E = (size_t)c.max_events, C = (size_t)c.max_cells;
+  const size_t L = (size_t)c.max_links, T = (size_t)c.max_ntuplets;
+  const size_t NB = E * kLayers * (size_t)c.phi_bins + 1;
+  Buffers t{};
+  t.hdr = (BatchHeader*)take(sizeof(BatchHeader));
+  t.cnt = (unsigned long long*)take(CNT_N * 8);
+  t.in_x = (float*)take(N * 4);
+  t.in_y = (float*)take(N * 4);
+  t.in_z = (float*)take(N * 4);
+  t.in_layer = (uint8_t*)take(N);
+  t.hit_off = (int32_t*)take((E + 1) * 4);
+  t.in_bin = (uint32_t*)take(N * 4);
+  t.in_rank = (uint32_t*)take(N * 4);
+  t.hit4 = (float4*)take(N * 16);
+  t.perm = (uint32_t*)take(N * 4);
+  t.hbin = (uint32_t*)take(N * 4);
+  t.bin_cnt = (uint32_t*)take(NB * 4);
+  t.bin_start = (uint32_t*)take(NB * 4);
+  t.layer_rmax = (uint32_t*)take(E * kLayers * 4);
+  t.seg_off = (uint32_t*)take(N * kMaxOuter * 4);
+  t.seg_cnt = (uint32_t*)take(N * kMaxOuter * 4);
+  t.seg_mdr = (float*)take(N * kMaxOuter * 4);
+  t.cell_in = (uint32_t*)take(C * 4);
+  t.cell_out = (uint32_t*)take(C * 4);
+  t.cell_slope = (float*)take(C * 4);
+  t.link_off = (uint32_t*)take(C * 4);
+  t.link_cnt = (uint32_t*)take(C * 4);
+  t.has_in = (uint8_t*)take(C);
+  t.best = (unsigned long long*)take(C * 8);
+  t.link_dst = (uint32_t*)take(L * 4);
+  t.link_q = (float*)take(L * 4);
+  t.nt_hits = (int32_t*)take(T * kMaxHits * 4);
+  t.nt_cells = (uint32_t*)take(T * kMaxCellsPerNt * 4);
+  t.nt_n = (uint8_t*)take(T);
+  t.nt_q = (float*)take(T * 4);
+  t.nt_rank = (uint32_t*)take(T * 4);
+  t.bucket_cnt = (uint32_t*)take((N + 1) * 4);
+  t.bucket_start = (uint32_t*)take((N + 1) * 4);
+  t.ord = (uint32_t*)take(T * 4);
+  t.alive = (uint32_t*)take(T * 4);
+  t.alive_scan = (uint32_t*)take((T + 1) * 4);
+  t.used = (uint8_t*)take(N);
+  t.sv = (uint32_t*)take(T * 4);
+  t.ev_nt_off = (int64_t*)take((E + 1) * 8);
+  t.tracks = (pt_track*)take(T * sizeof(pt_track));
+  t.exp_hits = (int32_t*)take(T * kMaxHits * 4);
+  t.exp_n = (uint8_t*)take(T);
+  t.exp_q = (float*)take(T * 4);
+  t.exp_ev = (int32_t*)take(T * 4);
+  t.scan_part = (uint32_t*)take((kScanBlocks + 1) * 4);
+  if (b) *b = t;
+  return (off + kAlign - 1) / kAlign * kAlign;
+}
+
+pt_status check_capacity(const pt_capacity* c) {
+  if (!c) return fail(PT_ERR_INVALID, "capacity is NULL");
+  if (c->max_events < 1 || c->max_hits < 1 || c->max_cells < 1 || c->max_links < 1 ||
+      c->max_ntuplets < 1)
+    return fail(PT_ERR_INVALID, "capacities must be >= 1");
+  if (c->max_hits >= (1ll << 31) - 1) return fail(PT_ERR_INVALID, "max_hits must be < 2^31 - 1");
+  if (c->max_cells >= (1ll << 32) - 1 || c->max_links >= (1ll << 32) - 1)
+    return fail(PT_ERR_INVALID, "max_cells and max_links must be < 2^32 - 1");
+  if (c->max_ntuplets >= (1ll << kRankBits))
+    return fail(PT_ERR_INVALID, "max_ntuplets must be < 2^%d", kRankBits);
+  if (c->phi_bins < 16 || c->phi_bins > 4096)
+    return fail(PT_ERR_INVALID, "phi_bins must be in [16, 4096]");
+  if (c->max_events * kLayers * (int64_t)c->phi_bins >= (1ll << 31) - 1)
+    return fail(PT_ERR_INVALID, "max_events * 10 * phi_bins must be < 2^31 - 1");
+  if (c->reserved != 0) return fail(PT_ERR_INVALID, "reserved must be 0");
+  return PT_OK;
+}
+
+}  // namespace
+
+struct pt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  pt_capacity cap{};
+  Params P{};
+  Buffers B{};
+  Launch L{};
+  int n_events = 0;
+  int64_t n_hits = 0;
+  bool loaded = false;
+  std::vector<int64_t> hit_off;
+  // pinned staging
+  int32_t* h_off = nullptr;
+  BatchHeader* h_hdr = nullptr;
+  unsigned long long* h_cnt = nullptr;
+  cudaEvent_t staged = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  // validation staging, allocated on first use
+  char* val = nullptr;
+  size_t val_bytes = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+pt_status last_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(PT_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  return PT_OK;
+}
+
+// Reads the device counters (synchronises the stream) and turns status bits into errors.
+pt_status sync_counters(pt_ctx* c) {
+  PT_CUDA(cudaMemcpyAsync(c->h_cnt, c->B.cnt, CNT_N * 8, cudaMemcpyDeviceToHost, c->stream));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  const unsigned long long st = c->h_cnt[CNT_STATUS];
+  if (st & ST_LAYER) return fail(PT_ERR_INVALID, "input contains a layer code > 9");
+  if (st & ST_CELLS)
+    return fail(PT_ERR_CAPACITY, "max_cells = %lld is too small: %llu cells needed",
+                (long long)c->cap.max_cells, c->h_cnt[CNT_CELLS]);
+  if (st & ST_LINKS)
+    return fail(PT_ERR_CAPACITY, "max_links = %lld is too small: at least %llu links needed",
+                (long long)c->cap.max_links, c->h_cnt[CNT_LINKS]);
+  if (st & ST_NT)
+    return fail(PT_ERR_CAPACITY,
+                "max_ntuplets = %lld is too small: at least %llu ntuplets needed",
+                (long long)c->cap.max_ntuplets, c->h_cnt[CNT_NT]);
+  return PT_OK;
+}
+
+pt_status stage_inputs(pt_ctx* c, int n_events, const int64_t* off, const float* x,
+                       const float* y, const float* z, const uint8_t* layer, int on_device) {
+  if (n_events < 1) return fail(PT_ERR_INVALID, "n_events must be >= 1");
+  if (n_events > c->cap.max_events)
+    return fail(PT_ERR_CAPACITY, "max_events = %lld is too small: %d events given",
+                (long long)c->cap.max_events, n_events);
+  if (!off) return fail(PT_ERR_INVALID, "hit_offsets is NULL");
+  if (off[0] != 0) return fail(PT_ERR_INVALID, "hit_offsets[0] must be 0");
+  for (int e = 0; e < n_events; ++e)
+    if (off[e + 1] < off[e]) return fail(PT_ERR_INVALID, "hit_offsets must be non-decreasing");
+  const int64_t n = off[n_events];
+  if (n > c->cap.max_hits)
+    return fail(PT_ERR_CAPACITY, "max_hits = %lld is too small: %lld hits given",
+                (long long)c->cap.max_hits, (long long)n);
+  if (n > 0 && (!x || !y || !z || !layer)) return fail(PT_ERR_INVALID, "hit array is NULL");
+  if (!on_device)
+    for (int64_t i = 0; i < n; ++i)
+      if (layer[i] >= kLayers)
+        return fail(PT_ERR_INVALID, "layer code %d > 9 at hit %lld", (int)layer[i], (long long)i);
+  // the pinned staging of the previous call must have been consumed
+  PT_CUDA(cudaEventSynchronize(c->staged));
+  for (int e = 0; e <= n_events; ++e) c->h_off[e] = (int32_t)off[e];
+  c->h_hdr->n_events = n_events;
+  c->h_hdr->n_hits = (int32_t)n;
+  PT_CUDA(cudaMemcpyAsync(c->B.hit_off, c->h_off, (n_events + 1) * 4, cudaMemcpyHostToDevice,
+                          c->stream));
+  PT_CUDA(cudaMemcpyAsync(c->B.hdr, c->h_hdr, sizeof(BatchHeader), cudaMemcpyHostToDevice,
+                          c->stream));
+  if (n > 0) {
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    PT_CUDA(cudaMemcpyAsync(c->B.in_x, x, n * 4, k, c->stream));
+    PT_CUDA(cudaMemcpyAsync(c->B.in_y, y, n * 4, k, c->stream));
+    PT_CUDA(cudaMemcpyAsync(c->B.in_z, z, n * 4, k, c->stream));
+    PT_CUDA(cudaMemcpyAsync(c->B.in_layer, layer, n, k, c->stream));
+  }
+  PT_CUDA(cudaEventRecord(c->staged, c->stream));
+  c->n_events = n_events;
+  c->n_hits = n;
+  c->hit_off.assign(off, off + n_events + 1);
+  c->loaded = true;
+  return PT_OK;
+}
+
+void enqueue_pipeline(pt_ctx* c, cudaStream_t s) {
+  launch_clear(c->B, c->P, c->L, s);
+  launch_bin_hits(c->B, c->P, c->L, s);
+  launch_doublets(c->B, c->P, c->L, s);
+  launch_connect(c->B, c->P, c->L, s);
+  launch_ntuplets(c->B, c->P, c->L, s);
+  launch_fit(c->B, c->P, c->L, s);
+  launch_export_ntuplets(c->B, c->L, s);
+}
+
+pt_status ensure_graph(pt_ctx* c) {
+  if (c->graph) return PT_OK;
+  cudaStream_t cs;
+  PT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue_pipeline(c, cs);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return fail(PT_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  }
+  return PT_OK;
+}
+
+pt_status need_loaded(pt_ctx* c) {
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  if (!c->loaded) return fail(PT_ERR_INVALID, "no hits loaded");
+  return PT_OK;
+}
+
+pt_status val_staging(pt_ctx* c, size_t bytes) {
+  if (bytes <= c->val_bytes) return PT_OK;
+  if (c->val) cudaFree(c->val);
+  c->val = nullptr;
+  c->val_bytes = 0;
+  PT_CUDA(cudaMalloc(&c->val, bytes));
+  c->val_bytes = bytes;
+  return PT_OK;
+}
+
+pt_status copy_out(pt_ctx* c, void* dst, const void* src, size_t bytes, int on_device) {
+  if (!bytes || !dst) return PT_OK;
+  PT_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          c->stream));
+  return PT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pt_last_error(void) { return g_err.c_str(); }
+
+pt_status pt_workspace_size(const pt_capacity* cap, size_t* bytes) {
+  g_err.clear();
+  PT_TRY(check_capacity(cap));
+  if (!bytes) return fail(PT_ERR_INVALID, "bytes is NULL");
+  *bytes = layout(*cap, nullptr, nullptr);
+  return PT_OK;
+}
+
+pt_status pt_create(const pt_geometry* geom, const pt_cuts* cuts, const pt_capacity* cap,
+                    int device, void* workspace, size_t workspace_bytes, void* stream,
+                    pt_ctx** out) {
+  g_err.clear();
+  if (!out) return fail(PT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!geom || !cuts) return fail(PT_ERR_INVALID, "geometry or cuts is NULL");
+  PT_TRY(check_capacity(cap));
+  int ndev = 0;
+  PT_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(PT_ERR_INVALID, "device %d not present", device);
+  DeviceGuard guard(device);
+  const size_t need = layout(*cap, nullptr, nullptr);
+  if (workspace) {
+    if (workspace_bytes < need)
+      return fail(PT_ERR_CAPACITY, "workspace of %zu bytes is too small: %zu needed",
+                  workspace_bytes, need);
+    if ((uintptr_t)workspace % kAlign)
+      return fail(PT_ERR_INVALID, "workspace must be %zu-byte aligned", kAlign);
+  }
+  pt_ctx* c = new pt_ctx();
+  c->device = device;
+  c->cap = *cap;
+  c->P.cuts = *cuts;
+  c->P.bfield = geom->bfield_T;
+  c->P.phi_bins = cap->phi_bins;
+  c->P.max_events = cap->max_events;
+  c->P.max_hits = cap->max_hits;
+  c->P.max_cells = cap->max_cells;
+  c->P.max_links = cap->max_links;
+  c->P.max_ntuplets = cap->max_ntuplets;
+  auto bail = [&](pt_status st) {
+    pt_destroy(c);
+    return st;
+  };
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return bail(fail(PT_ERR_CUDA, "cannot query the multiprocessor count"));
+  c->L.sms = sms;
+  c->L.grid = sms * 4;
+  if (workspace) {
+    c->ws = (char*)workspace;
+    c->ws_bytes = workspace_bytes;
+  } else {
+    if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      c->ws = nullptr;
+      return bail(fail(PT_ERR_NOMEM, "cudaMalloc of %zu workspace bytes failed", need));
+    }
+    c->ws_bytes = need;
+    c->own_ws = true;
+  }
+  layout(*cap, c->ws, &c->B);
+  if (cudaMallocHost(&c->h_off, (cap->max_events + 1) * 4) != cudaSuccess ||
+      cudaMallocHost(&c->h_hdr, sizeof(BatchHeader)) != cudaSuccess ||
+      cudaMallocHost(&c->h_cnt, CNT_N * 8) != cudaSuccess)
+    return bail(fail(PT_ERR_NOMEM, "pinned host allocation failed"));
+  if (cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(PT_ERR_CUDA, "cudaEventCreate failed"));
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreate(&c->stream) != cudaSuccess)
+      return bail(fail(PT_ERR_CUDA, "cudaStreamCreate failed"));
+    c->own_stream = true;
+  }
+  if (cudaMemsetAsync(c->B.cnt, 0, CNT_N * 8, c->stream) != cudaSuccess)
+    return bail(fail(PT_ERR_CUDA, "cudaMemsetAsync failed"));
+  *out = c;
+  return PT_OK;
+}
+
+pt_status pt_destroy(pt_ctx* c) {
+  if (!c) return PT_OK;
+  DeviceGuard guard(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->val) cudaFree(c->val);
+  if (c->own_ws && c->ws) cudaFree(c->ws);
+  if (c->h_off) cudaFreeHost(c->h_off);
+  if (c->h_hdr) cudaFreeHost(c->h_hdr);
+  if (c->h_cnt) cudaFreeHost(c->h_cnt);
+  if (c->staged) cudaEventDestroy(c->staged);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return PT_OK;
+}
+
+pt_status pt_set_stream(pt_ctx* c, void* stream) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  DeviceGuard guard(c->device);
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  c->own_stream = false;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    PT_CUDA(cudaStreamCreate(&c->stream));
+    c->own_stream = true;
+  }
+  return PT_OK;
+}
+
+pt_status pt_load_batch(pt_ctx* c, int n_events, const int64_t* hit_offsets, const float* x,
+                        const float* y, const float* z, const uint8_t* layer, int on_device) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  DeviceGuard guard(c->device);
+  PT_TRY(stage_inputs(c, n_events, hit_offsets, x, y, z, layer, on_device));
+  launch_clear(c->B, c->P, c->L, c->stream);
+  launch_bin_hits(c->B, c->P, c->L, c->stream);
+  return last_launch();
+}
+
+pt_status pt_load_hits(pt_ctx* c, int64_t n, const float* x, const float* y, const float* z,
+                       const uint8_t* layer, int on_device) {
+  if (n < 0) return fail(PT_ERR_INVALID, "n must be >= 0");
+  const int64_t off[2] = {0, n};
+  return pt_load_batch(c, 1, off, x, y, z, layer, on_device);
+}
+
+#define STAGE_BODY(launch, counter, outp)                \
+  g_err.clear();                                         \
+  PT_TRY(need_loaded(c));                                \
+  DeviceGuard guard(c->device);                          \
+  launch;                                                \
+  PT_TRY(last_launch());                                 \
+  if (outp) {                                            \
+    PT_TRY(sync_counters(c));                            \
+    *(outp) = (int64_t)c->h_cnt[counter];                \
+  }                                                      \
+  return PT_OK;
+
+pt_status pt_build_doublets(pt_ctx* c, int64_t* n_cells) {
+  STAGE_BODY(launch_doublets(c->B, c->P, c->L, c->stream), CNT_CELLS, n_cells)
+}
+
+pt_status pt_connect_cells(pt_ctx* c, int64_t* n_links) {
+  STAGE_BODY(launch_connect(c->B, c->P, c->L, c->stream), CNT_LINKS, n_links)
+}
+
+pt_status pt_find_ntuplets(pt_ctx* c, int64_t* n_ntuplets) {
+  STAGE_BODY(launch_ntuplets(c->B, c->P, c->L, c->stream), CNT_SV, n_ntuplets)
+}
+
+pt_status pt_fit_tracks(pt_ctx* c, int64_t* n_tracks) {
+  STAGE_BODY(launch_fit(c->B, c->P, c->L, c->stream), CNT_SV, n_tracks)
+}
+
+pt_status pt_get_ntuplets(pt_ctx* c, int32_t* hits, uint8_t* nhits, int64_t* event_offsets,
+                          int64_t cap, int64_t* n, int on_device) {
+  g_err.clear();
+  PT_TRY(need_loaded(c));
+  DeviceGuard guard(c->device);
+  launch_export_ntuplets(c->B, c->L, c->stream);
+  PT_TRY(last_launch());
+  PT_TRY(sync_counters(c));
+  const int64_t S = (int64_t)c->h_cnt[CNT_SV];
+  if (n) *n = S;
+  if (cap < S)
+    return fail(PT_ERR_CAPACITY, "output capacity %lld is too small: %lld ntuplets",
+                (long long)cap, (long long)S);
+  PT_TRY(copy_out(c, hits, c->B.exp_hits, (size_t)S * kMaxHits * 4, on_device));
+  PT_TRY(copy_out(c, nhits, c->B.exp_n, (size_t)S, on_device));
+  PT_TRY(copy_out(c, event_offsets, c->B.ev_nt_off, (size_t)(c->n_events + 1) * 8, on_device));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  return PT_OK;
+}
+
+pt_status pt_get_tracks(pt_ctx* c, pt_track* tracks, int64_t cap, int64_t* n, int on_device) {
+  g_err.clear();
+  PT_TRY(need_loaded(c));
+  DeviceGuard guard(c->device);
+  PT_TRY(sync_counters(c));
+  const int64_t S = (int64_t)c->h_cnt[CNT_SV];
+  if (n) *n = S;
+  if (cap < S)
+    return fail(PT_ERR_CAPACITY, "output capacity %lld is too small: %lld tracks",
+                (long long)cap, (long long)S);
+  PT_TRY(copy_out(c, tracks, c->B.tracks, (size_t)S * sizeof(pt_track), on_device));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  return PT_OK;
+}
+
+pt_status pt_get_cells(pt_ctx* c, int32_t* inner, int32_t* outer, int32_t* event, int64_t cap,
+                       int64_t* n) {
+  g_err.clear();
+  PT_TRY(need_loaded(c));
+  DeviceGuard guard(c->device);
+  PT_TRY(sync_counters(c));
+  const int64_t C = (int64_t)c->h_cnt[CNT_CELLS];
+  if (n) *n = C;
+  if (cap < C) return fail(PT_ERR_CAPACITY, "output capacity %lld < %lld cells", (long long)cap,
+                           (long long)C);
+  if (C == 0) return PT_OK;
+  PT_TRY(val_staging(c, (size_t)C * 12));
+  launch_export_cells(c->B, c->P, c->L, (int32_t*)c->val, c->stream);
+  PT_TRY(last_launch());
+  std::vector<int32_t> tmp((size_t)C * 3);
+  PT_CUDA(cudaMemcpyAsync(tmp.data(), c->val, (size_t)C * 12, cudaMemcpyDeviceToHost, c->stream));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  for (int64_t i = 0; i < C; ++i) {
+    if (inner) inner[i] = tmp[i * 3];
+    if (outer) outer[i] = tmp[i * 3 + 1];
+    if (event) event[i] = tmp[i * 3 + 2];
+  }
+  return PT_OK;
+}
+
+pt_status pt_get_links(pt_ctx* c, int32_t* h0, int32_t* h1, int32_t* h2, float* q,
+                       int32_t* event, int64_t cap, int64_t* n) {
+  g_err.clear();
+  PT_TRY(need_loaded(c));
+  DeviceGuard guard(c->device);
+  PT_TRY(sync_counters(c));
+  const int64_t Lk = (int64_t)c->h_cnt[CNT_LINKS];
+  if (n) *n = Lk;
+  if (cap < Lk) return fail(PT_ERR_CAPACITY, "output capacity %lld < %lld links", (long long)cap,
+                            (long long)Lk);
+  if (Lk == 0) return PT_OK;
+  PT_TRY(val_staging(c, (size_t)Lk * 20));
+  int32_t* o4 = (int32_t*)c->val;
+  float* oq = (float*)(c->val + (size_t)Lk * 16);
+  launch_export_links(c->B, c->P, c->L, o4, oq, c->stream);
+  PT_TRY(last_launch());
+  std::vector<int32_t> tmp((size_t)Lk * 4);
+  std::vector<float> tq((size_t)Lk);
+  PT_CUDA(cudaMemcpyAsync(tmp.data(), o4, (size_t)Lk * 16, cudaMemcpyDeviceToHost, c->stream));
+  PT_CUDA(cudaMemcpyAsync(tq.data(), oq, (size_t)Lk * 4, cudaMemcpyDeviceToHost, c->stream));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  for (int64_t i = 0; i < Lk; ++i) {
+    if (h0) h0[i] = tmp[i * 4];
+    if (h1) h1[i] = tmp[i * 4 + 1];
+    if (h2) h2[i] = tmp[i * 4 + 2];
+    if (event) event[i] = tmp[i * 4 + 3];
+    if (q) q[i] = tq[i];
+  }
+  return PT_OK;
+}
+
+pt_status pt_get_candidates(pt_ctx* c, int32_t* hits, uint8_t* nhits, float* q, int32_t* event,
+                            int64_t cap, int64_t* n) {
+  g_err.clear();
+  PT_TRY(need_loaded(c));
+  DeviceGuard guard(c->device);
+  PT_TRY(sync_counters(c));
+  const int64_t T = (int64_t)c->h_cnt[CNT_SCAN_NT];
+  if (n) *n = T;
+  if (cap < T) return fail(PT_ERR_CAPACITY, "output capacity %lld < %lld candidates",
+                           (long long)cap, (long long)T);
+  launch_export_candidates(c->B, c->L, c->stream);
+  PT_TRY(last_launch());
+  PT_TRY(copy_out(c, hits, c->B.exp_hits, (size_t)T * kMaxHits * 4, 0));
+  PT_TRY(copy_out(c, nhits, c->B.exp_n, (size_t)T, 0));
+  PT_TRY(copy_out(c, q, c->B.exp_q, (size_t)T * 4, 0));
+  PT_TRY(copy_out(c, event, c->B.exp_ev, (size_t)T * 4, 0));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  return PT_OK;
+}
+
+pt_status pt_enqueue_batch(pt_ctx* c, int n_events, const int64_t* hit_offsets, const float* x,
+                           const float* y, const float* z, const uint8_t* layer, int on_device) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  DeviceGuard guard(c->device);
+  PT_TRY(stage_inputs(c, n_events, hit_offsets, x, y, z, layer, on_device));
+  PT_TRY(ensure_graph(c));
+  PT_CUDA(cudaGraphLaunch(c->graph, c->stream));
+  return PT_OK;
+}
+
+pt_status pt_reconstruct_batch(pt_ctx* c, int n_events, const int64_t* hit_offsets,
+                               const float* x, const float* y, const float* z,
+                               const uint8_t* layer, int on_device, int32_t* hits_out,
+                               uint8_t* nhits_out, pt_track* tracks_out, int64_t* event_offsets,
+                               int64_t cap, int64_t* n, int out_on_device) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  if (!event_offsets) return fail(PT_ERR_INVALID, "event_offsets is NULL");
+  DeviceGuard guard(c->device);
+  PT_TRY(stage_inputs(c, n_events, hit_offsets, x, y, z, layer, on_device));
+  PT_TRY(ensure_graph(c));
+  PT_CUDA(cudaGraphLaunch(c->graph, c->stream));
+  PT_TRY(sync_counters(c));
+  const int64_t S = (int64_t)c->h_cnt[CNT_SV];
+  if (n) *n = S;
+  if (cap < S)
+    return fail(PT_ERR_CAPACITY, "output capacity %lld is too small: %lld ntuplets",
+                (long long)cap, (long long)S);
+  PT_TRY(copy_out(c, hits_out, c->B.exp_hits, (size_t)S * kMaxHits * 4, out_on_device));
+  PT_TRY(copy_out(c, nhits_out, c->B.exp_n, (size_t)S, out_on_device));
+  PT_TRY(copy_out(c, tracks_out, c->B.tracks, (size_t)S * sizeof(pt_track), out_on_device));
+  PT_TRY(copy_out(c, event_offsets, c->B.ev_nt_off, (size_t)(n_events + 1) * 8, out_on_device));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  return PT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,53 @@
+"""The C-ABI library loads and exports every symbol include/pt_ca.h declares (no GPU).
+
+Also checks the host-side argument validation that runs before any CUDA call."""
+
+import os
+import re
+
+import pytest
+
+import paper_2501_05520_gb300 as pt
+from paper_2501_05520_gb300 import build as pkg_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^\s*(?:pt_status|const char\*)\s+(pt_\w+)\s*\(", txt, re.M)
+    return names
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pkg_build.build()
+
+
+def test_header_and_binding_agree():
+    assert set(_declared()) == set(pt.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol():
+    assert set(pt.exported_symbols()) == set(_declared())
+
+
+def test_workspace_size_and_capacity_validation():
+    n = pt.pt_workspace_size(pt.default_capacity())
+    assert n > 0 and n % 256 == 0
+    assert pt.pt_workspace_size(pt.default_capacity(max_events=4)) > n
+    for bad in (dict(pt.default_capacity(), phi_bins=8),
+                dict(pt.default_capacity(), max_ntuplets=1 << 29),
+                dict(pt.default_capacity(), max_cells=0),
+                dict(pt.default_capacity(), reserved=1)):
+        with pytest.raises(pt.PtError) as ei:
+            pt.pt_workspace_size(bad)
+        assert ei.value.status == pt.PT_ERR_INVALID
+        assert pt.lib().pt_last_error().decode()
+
+
+def test_build_is_incremental():
+    assert pkg_build.up_to_date()

@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA chain against the CPU oracle, element by element.
+
+Cells, links (with their float32 quality), ntuplet candidates and cleaned ntuplets
+must be bit-exact; fitted parameters within 1e-4 relative of the float64 oracle fit
+(floors in parity.py).  Every call goes through the C ABI via the thin binding.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import sim
+from parity import (assert_fits_close, assert_ntuplets_equal, cell_set, oracle_link_triples)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2501_05520_gb300 as pt  # noqa: E402
+
+SMALL_CAP = pt.default_capacity(max_events=8, hits_per_event=4096, cells_per_event=1 << 16,
+                                links_per_event=1 << 15, ntuplets_per_event=1 << 14)
+PU_CAP = pt.default_capacity(max_events=2, hits_per_event=65536, cells_per_event=4 << 20,
+                             links_per_event=1 << 20, ntuplets_per_event=1 << 19)
+
+
+@pytest.fixture(scope="module")
+def small_ctx(cuts):
+    with pt.Context(cuts=cuts, capacity=SMALL_CAP) as c:
+        yield c
+
+
+@pytest.fixture(scope="module")
+def pu_ctx(cuts):
+    with pt.Context(cuts=cuts, capacity=PU_CAP) as c:
+        yield c
+
+
+def run_stages(ctx, events):
+    off, x, y, z, layer = sim.concat(events)
+    ctx.pt_load_batch(off, x, y, z, layer)
+    out = dict(n_cells=ctx.pt_build_doublets(), n_links=ctx.pt_connect_cells(),
+               n_nt=ctx.pt_find_ntuplets(), n_tracks=ctx.pt_fit_tracks())
+    out["cells"] = ctx.pt_get_cells()
+    out["links"] = ctx.pt_get_links()
+    out["cand"] = ctx.pt_get_candidates()
+    out["nt"] = ctx.pt_get_ntuplets()
+    out["tracks"] = ctx.pt_get_tracks()
+    return out
+
+
+def check_event(out, e, ev, ref):
+    ci, co, ce = out["cells"]
+    m = ce == e
+    assert cell_set(ci[m], co[m]) == cell_set(ref["cell_inner"], ref["cell_outer"])
+    h0, h1, h2, q, le = out["links"]
+    m = le == e
+    got = dict(zip(zip(h0[m].tolist(), h1[m].tolist(), h2[m].tolist()),
+                   q[m].view(np.uint32).tolist()))
+    assert got == oracle_link_triples(ref)
+    hits, nh, cq, cev = out["cand"]
+    m = cev == e
+    got_c = {tuple(r): v for r, v in zip(hits[m].tolist(), cq[m].view(np.uint32).tolist())}
+    exp_c = {tuple(r): v for r, v in zip(ref["nt_hits"].tolist(),
+                                         ref["nt_q"].view(np.uint32).tolist())}
+    assert got_c == exp_c
+    assert int(m.sum()) == ref["nt_n"].size  # no duplicate candidates
+    nth, ntn, evoff = out["nt"]
+    sl = slice(evoff[e], evoff[e + 1])
+    assert_ntuplets_equal(nth[sl], oracle.survivors_hits(ref), ref)
+    assert np.array_equal(ntn[sl], ref["nt_n"][ref["survivors"]].astype(np.uint8))
+    assert_fits_close(out["tracks"][sl], ref["fit"])
+
+
+def test_config1_batch_matches_oracle(small_ctx, cuts):
+    events = [sim.generate(sim.SINGLE_MUON_LIKE, 1000 + i) for i in range(8)]
+    out = run_stages(small_ctx, events)
+    for e, ev in enumerate(events):
+        check_event(out, e, ev, oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts))
+
+
+def test_pu50_event_matches_oracle(cuts_low_pt):
+    with pt.Context(cuts=cuts_low_pt, capacity=PU_CAP) as ctx:
+        ev = sim.generate(sim.PU50, 2000)
+        out = run_stages(ctx, [ev])
+        ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts_low_pt)
+        assert out["n_cells"] == ref["cell_inner"].size
+        check_event(out, 0, ev, ref)
+
+
+def test_pu200_event_matches_oracle(pu_ctx, cuts):
+    ev = sim.generate(sim.PU200, 3000)
+    out = run_stages(pu_ctx, [ev])
+    ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts)
+    assert out["n_cells"] > 1_000_000
+    check_event(out, 0, ev, ref)
+
+
+def test_graph_path_equals_stage_path(pu_ctx, cuts):
+    events = [sim.generate(sim.PU50, 2010), sim.generate(sim.PU50, 2011, n_particles=700)]
+    out = run_stages(pu_ctx, events)
+    off, x, y, z, layer = sim.concat(events)
+    hits, nh, tracks, evoff = pu_ctx.pt_reconstruct_batch(off, x, y, z, layer)
+    assert np.array_equal(hits, out["nt"][0])
+    assert np.array_equal(evoff, out["nt"][2])
+    assert tracks.tobytes() == out["tracks"].tobytes()
+
+
+def test_uneven_batch_with_empty_and_degenerate_events(small_ctx, cuts):
+    g = sim.GenConfig(60, "inv_pt_uniform", 2.5, False, 0.3)
+    full = sim.generate(g, 77)
+    one_layer = sim.generate(g, 78)
+    keep = one_layer.layer == 1
+    for f in ("x", "y", "z", "layer", "pid"):
+        setattr(one_layer, f, getattr(one_layer, f)[keep])
+    empty = sim.generate(g, 79)
+    for f in ("x", "y", "z", "layer", "pid"):
+        setattr(empty, f, getattr(empty, f)[:0])
+    events = [empty, full, one_layer, sim.generate(g, 80, n_particles=7), empty,
+              sim.generate(sim.SINGLE_MUON_LIKE, 1005)]
+    out = run_stages(small_ctx, events)
+    evoff = out["nt"][2]
+    assert evoff.size == len(events) + 1
+    for e, ev in enumerate(events):
+        ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts)
+        check_event(out, e, ev, ref)
+    assert evoff[1] == evoff[0] == 0 and evoff[5] == evoff[4]
+
+
+@pytest.mark.parametrize("bins", [16, 4096])
+def test_phi_binning_is_only_an_acceleration(cuts, bins):
+    cap = dict(PU_CAP, phi_bins=bins)
+    ev = sim.generate(sim.PU50, 2020, n_particles=800)
+    with pt.Context(cuts=cuts, capacity=cap) as ctx:
+        out = run_stages(ctx, [ev])
+    check_event(out, 0, ev, oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts))
+
+
+def test_repeat_is_deterministic(pu_ctx):
+    ev = sim.generate(sim.PU50, 2030)
+    a = pu_ctx.pt_reconstruct_batch([0, ev.n_hits], ev.x, ev.y, ev.z, ev.layer)
+    a = [np.copy(v) for v in a]
+    for _ in range(2):
+        b = pu_ctx.pt_reconstruct_batch([0, ev.n_hits], ev.x, ev.y, ev.z, ev.layer)
+        assert all(np.array_equal(u, v) for u, v in zip(a[:2] + a[3:], b[:2] + b[3:]))
+        assert a[2].tobytes() == b[2].tobytes()
+
+
+def test_device_inputs(pu_ctx, cuts):
+    ev = sim.generate(sim.PU50, 2040, n_particles=500)
+    d = [torch.from_numpy(v).cuda() for v in (ev.x, ev.y, ev.z, ev.layer)]
+    hits, nh, tracks, evoff = pu_ctx.pt_reconstruct_batch([0, ev.n_hits], *d)
+    ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts)
+    assert_ntuplets_equal(hits, oracle.survivors_hits(ref), ref)
+    out = dict(hits=torch.empty((4096, 6), dtype=torch.int32, device="cuda"),
+               nhits=torch.empty(4096, dtype=torch.uint8, device="cuda"),
+               tracks=torch.empty((4096, 36), dtype=torch.uint8, device="cuda"),
+               event_offsets=torch.empty(2, dtype=torch.int64, device="cuda"))
+    h2, n2, t2, o2 = pu_ctx.pt_reconstruct_batch([0, ev.n_hits], *d, out=out)
+    assert np.array_equal(h2.cpu().numpy(), hits)
+    assert t2.cpu().numpy().tobytes() == tracks.tobytes()
+
+
+def test_capacity_and_input_errors(cuts):
+    ev = sim.generate(sim.PU50, 2050, n_particles=400)
+    cap = pt.default_capacity(max_events=1, hits_per_event=8192, cells_per_event=1000,
+                              links_per_event=1000, ntuplets_per_event=1000)
+    with pt.Context(cuts=cuts, capacity=cap) as ctx:
+        ctx.pt_load_hits(ev.x, ev.y, ev.z, ev.layer)
+        with pytest.raises(pt.PtError) as ei:
+            ctx.pt_build_doublets()
+        assert ei.value.status == pt.PT_ERR_CAPACITY and "max_cells" in str(ei.value)
+        big = sim.generate(sim.PU50, 2051)
+        with pytest.raises(pt.PtError) as ei:
+            ctx.pt_load_hits(big.x, big.y, big.z, big.layer)
+        assert ei.value.status == pt.PT_ERR_CAPACITY and "max_hits" in str(ei.value)
+        bad = ev.layer.copy()
+        bad[5] = 10
+        with pytest.raises(pt.PtError) as ei:
+            ctx.pt_load_hits(ev.x, ev.y, ev.z, bad)
+        assert ei.value.status == pt.PT_ERR_INVALID
+        d = [torch.from_numpy(v).cuda() for v in (ev.x, ev.y, ev.z, bad)]
+        ctx.pt_load_hits(*d)
+        with pytest.raises(pt.PtError) as ei:
+            ctx.pt_build_doublets()
+        assert ei.value.status == pt.PT_ERR_INVALID
+        with pytest.raises(pt.PtError) as ei:
+            ctx.pt_load_batch([0, 5, 3], ev.x, ev.y, ev.z, ev.layer)
+        assert ei.value.status in (pt.PT_ERR_INVALID, pt.PT_ERR_CAPACITY)
+        # the context stays usable after errors
+        small = sim.generate(sim.SINGLE_MUON_LIKE, 1001)
+        hits, nh, tr, off = ctx.pt_reconstruct_batch([0, small.n_hits], small.x, small.y,
+                                                     small.z, small.layer)
+        ref = oracle.reconstruct(small.x, small.y, small.z, small.layer, cuts)
+        assert np.array_equal(hits, oracle.survivors_hits(ref))
+
+
+def test_bench_configuration_sampled(cuts):
+    """The benchmark's launch configuration (64 PU200 events per batch, its capacity
+    and binning): three events checked bit-exactly against the oracle, all events
+    checked for canonical order, uniqueness and allowed layer chains."""
+    import bench
+    events = bench.make_events(bench.BATCH, seed0=bench.SEED0)
+    off, x, y, z, layer = sim.concat(events)
+    with pt.Context(cuts=cuts, capacity=bench.capacity()) as ctx:
+        hits, nh, tracks, evoff = ctx.pt_reconstruct_batch(off, x, y, z, layer)
+        hits, nh, tracks, evoff = (np.copy(v) for v in (hits, nh, tracks, evoff))
+    from sim import truth
+    allowed = set(truth.LAYER_PAIRS)
+    for e, ev in enumerate(events):
+        h = hits[evoff[e]:evoff[e + 1]]
+        keys = [tuple(r) for r in h.tolist()]
+        assert keys == sorted(keys) and len(set(keys)) == len(keys)
+        for r, n in zip(h, nh[evoff[e]:evoff[e + 1]]):
+            lay = ev.layer[r[:n]].tolist()
+            assert all((u, v) in allowed for u, v in zip(lay[:-1], lay[1:]))
+    for e in (0, len(events) // 2, len(events) - 1):
+        ev = events[e]
+        ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts)
+        sl = slice(evoff[e], evoff[e + 1])
+        assert_ntuplets_equal(hits[sl], oracle.survivors_hits(ref), ref)
+        assert_fits_close(tracks[sl], ref["fit"])
