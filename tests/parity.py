@@ -30,13 +30,13 @@ def drop_near(rows: np.ndarray, near: set) -> np.ndarray:
 
 
 def assert_ntuplets_equal(got: np.ndarray, exp: np.ndarray, ref: dict):
-    """Cleaned ntuplets: bit-exact in canonical order.  Ntuplets touching a
-    near-threshold decision are excluded first (their count is bounded at 0.1 %); the
+    """Cleaned ntuplets: bit-exact in canonical order.  Ntuplets sharing a hit with a
+    near-threshold decision are excluded first (their number is bounded at 0.5 %); the
     full sets are then also required to agree, since both sides evaluate the cuts in
     the same float32 order."""
     near = near_hits(ref)
     g2, e2 = drop_near(got, near), drop_near(exp, near)
-    assert e2.shape[0] >= exp.shape[0] - max(1, int(1e-3 * exp.shape[0]))
+    assert e2.shape[0] >= exp.shape[0] - max(2, int(5e-3 * exp.shape[0]))
     assert g2.shape == e2.shape and np.array_equal(g2, e2), "ntuplets differ (near excluded)"
     assert got.shape == exp.shape and np.array_equal(got, exp), "ntuplets differ"
 
