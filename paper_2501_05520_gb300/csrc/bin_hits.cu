@@ -19,7 +19,10 @@ __global__ void k_clear(Buffers b, int32_t phi_bins) {
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
   for (int i = t0; i <= nb; i += stride) b.bin_cnt[i] = 0;
   for (int i = t0; i < E * kLayers; i += stride) b.layer_rmax[i] = 0u;
-  for (int i = t0; i <= N; i += stride) b.bucket_cnt[i] = 0;
+  for (int i = t0; i <= N; i += stride) {
+    b.bucket_cnt[i] = 0;
+    b.in_cnt[i] = 0;
+  }
   for (int i = t0; i < N; i += stride) b.used[i] = 0;
   if (t0 == 0) {
     b.cnt[CNT_CELLS] = 0;
@@ -29,6 +32,9 @@ __global__ void k_clear(Buffers b, int32_t phi_bins) {
     b.cnt[CNT_GATE_KEPT] = 0;
     b.cnt[CNT_SCAN_NT] = 0;
     b.cnt[CNT_SV] = 0;
+    b.cnt[CNT_LKCELLS] = 0;
+    b.cnt[CNT_CELLS_USED] = 0;
+    b.cnt[CNT_LINKS_USED] = 0;
     b.cnt[CNT_SCAN_BINS] = (unsigned long long)nb;
     b.cnt[CNT_SCAN_HITS] = (unsigned long long)N;
   }

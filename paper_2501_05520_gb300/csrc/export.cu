@@ -47,6 +47,10 @@ __global__ void k_export_cells(Buffers b, uint64_t cap_cells, int32_t* out3) {
   const int E = b.hdr->n_events;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
+    if (b.cell_out[c] == kHole) {
+      out3[c * 3 + 0] = out3[c * 3 + 1] = out3[c * 3 + 2] = -1;
+      continue;
+    }
     const int32_t gi = (int32_t)b.perm[b.cell_in[c]], go = (int32_t)b.perm[b.cell_out[c]];
     const int e = find_event(b.hit_off, E, gi);
     out3[c * 3 + 0] = gi - b.hit_off[e];
@@ -60,8 +64,8 @@ __global__ void k_export_links(Buffers b, uint64_t cap_cells, int32_t* out4, flo
   const int E = b.hdr->n_events;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nc; a += stride) {
+    if (b.cell_out[a] == kHole || !b.has_out[a]) continue;  // allocation hole or no links
     const uint32_t n = b.link_cnt[a];
-    if (n == 0) continue;
     const int32_t g0 = (int32_t)b.perm[b.cell_in[a]], g1 = (int32_t)b.perm[b.cell_out[a]];
     const int e = find_event(b.hit_off, E, g0);
     const int32_t off = b.hit_off[e];

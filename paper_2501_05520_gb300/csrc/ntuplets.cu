@@ -3,9 +3,11 @@
 // picked).
 //
 // A4  every path of linked cells from a root (a cell with no incoming link) to a leaf
-//     (a cell with no outgoing link) with 3..6 hits.  One thread per root walks its
-//     out-links depth first with an explicit stack (the layer graph bounds the depth
-//     at 5 cells).  The path quality q is the float32 sum of its link qualities,
+//     (a cell with no outgoing link) with 3..6 hits.  Roots are taken from the compact
+//     list of cells with outgoing links (a root without one would give a 2-hit path,
+//     which is dropped).  One thread per root walks its out-links depth first with an
+//     explicit stack (the layer graph bounds the depth at 5 cells), once to count and,
+//     after one atomic per warp reserves the slots, once to write.  The path quality q is the float32 sum of its link qualities,
 //     added from the innermost link outwards.
 // A6  canonical order: ntuplets sorted by their hit tuple (batch input indices, -1
 //     padded, signed).  A counting sort on the first hit puts them in per-hit buckets
@@ -22,59 +24,84 @@ namespace ptca {
 
 namespace {
 
-__global__ void __launch_bounds__(256)
-    k_find_ntuplets(Buffers b, uint64_t cap_cells, uint64_t cap_nt) {
-  const uint64_t nc = min(b.cnt[CNT_CELLS], (unsigned long long)cap_cells);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nc; a += stride) {
-    if (b.has_in[a] || b.link_cnt[a] == 0) continue;
-    uint32_t path[kMaxCellsPerNt];
-    uint32_t it[kMaxCellsPerNt], end[kMaxCellsPerNt];
-    float qs[kMaxCellsPerNt];
-    path[0] = (uint32_t)a;
-    it[0] = b.link_off[a];
-    end[0] = it[0] + b.link_cnt[a];
-    qs[0] = 0.0f;
-    int depth = 1;
-    while (depth > 0) {
-      const int d = depth - 1;
-      if (it[d] == end[d]) {
-        --depth;
-        continue;
-      }
-      const uint32_t l = it[d]++;
-      if (depth == kMaxCellsPerNt) continue;  // deeper than the layer graph allows
-      const uint32_t c = b.link_dst[l];
-      const float q = fadd(qs[d], b.link_q[l]);
-      const uint32_t nl = b.link_cnt[c];
-      if (nl == 0) {
-        // leaf: emit path[0..d] + c, i.e. depth + 1 cells, depth + 2 hits
-        const unsigned long long t = atomicAdd(&b.cnt[CNT_NT], 1ull);
-        if (t >= cap_nt) {
-          atomicOr(&b.cnt[CNT_STATUS], ST_NT);
-          continue;
-        }
-        const int ncell = depth + 1;
-        int32_t* hp = b.nt_hits + t * kMaxHits;
-        uint32_t* cp = b.nt_cells + t * kMaxCellsPerNt;
-        hp[0] = (int32_t)b.perm[b.cell_in[path[0]]];
-        for (int k = 0; k < ncell; ++k) {
-          const uint32_t ck = k < depth ? path[k] : c;
-          hp[k + 1] = (int32_t)b.perm[b.cell_out[ck]];
-          cp[k] = ck;
-        }
-        for (int k = ncell + 1; k < kMaxHits; ++k) hp[k] = -1;
-        for (int k = ncell; k < kMaxCellsPerNt; ++k) cp[k] = 0xffffffffu;
-        b.nt_n[t] = (uint8_t)(ncell + 1);
-        b.nt_q[t] = q;
-        continue;
-      }
-      path[depth] = c;
-      it[depth] = b.link_off[c];
-      end[depth] = it[depth] + nl;
-      qs[depth] = q;
-      ++depth;
+// Depth-first walk from root a.  EMIT == false: returns the number of ntuplets;
+// EMIT == true: writes them at slots t0, t0 + 1, ... (slots >= cap_nt are dropped).
+template <bool EMIT>
+__device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, uint64_t cap_nt) {
+  uint32_t path[kMaxCellsPerNt];
+  uint32_t it[kMaxCellsPerNt], end[kMaxCellsPerNt];
+  float qs[kMaxCellsPerNt];
+  path[0] = a;
+  it[0] = b.link_off[a];
+  end[0] = it[0] + b.link_cnt[a];
+  qs[0] = 0.0f;
+  uint32_t found = 0;
+  int depth = 1;
+  while (depth > 0) {
+    const int d = depth - 1;
+    if (it[d] == end[d]) {
+      --depth;
+      continue;
     }
+    const uint32_t l = it[d]++;
+    if (depth == kMaxCellsPerNt) continue;  // deeper than the layer graph allows
+    const uint32_t c = b.link_dst[l];
+    const float q = fadd(qs[d], b.link_q[l]);
+    if (!b.has_out[c]) {
+      // leaf: path[0..d] + c, i.e. depth + 1 cells, depth + 2 hits
+      if (EMIT) {
+        const unsigned long long t = t0 + found;
+        if (t < cap_nt) {
+          const int ncell = depth + 1;
+          int32_t* hp = b.nt_hits + t * kMaxHits;
+          uint32_t* cp = b.nt_cells + t * kMaxCellsPerNt;
+          hp[0] = (int32_t)b.perm[b.cell_in[path[0]]];
+          for (int k = 0; k < ncell; ++k) {
+            const uint32_t ck = k < depth ? path[k] : c;
+            hp[k + 1] = (int32_t)b.perm[b.cell_out[ck]];
+            cp[k] = ck;
+            b.best[ck] = ~0ull;  // initial duplicate-cleaning key of a cell on an ntuplet
+          }
+          for (int k = ncell + 1; k < kMaxHits; ++k) hp[k] = -1;
+          for (int k = ncell; k < kMaxCellsPerNt; ++k) cp[k] = 0xffffffffu;
+          b.nt_n[t] = (uint8_t)(ncell + 1);
+          b.nt_q[t] = q;
+        }
+      }
+      ++found;
+      continue;
+    }
+    path[depth] = c;
+    it[depth] = b.link_off[c];
+    end[depth] = it[depth] + b.link_cnt[c];
+    qs[depth] = q;
+    ++depth;
+  }
+  return found;
+}
+
+// One thread per root; each warp counts its roots' ntuplets, reserves them with one
+// atomic and walks again to write them.
+__global__ void __launch_bounds__(256)
+    k_find_ntuplets(Buffers b, uint64_t cap_links, uint64_t cap_nt) {
+  const uint64_t nl = min(b.cnt[CNT_LKCELLS], (unsigned long long)cap_links);
+  const int lane = lane_id();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < nl;
+       i0 += stride) {
+    const uint64_t i = i0 + lane;
+    uint32_t a = kHole;
+    if (i < nl) a = b.lk_cells[i];
+    const bool root = a != kHole && !b.has_in[a];
+    const uint32_t n = root ? walk<false>(b, a, 0, cap_nt) : 0u;
+    const uint32_t inc = warp_incl_scan(n);
+    const uint32_t tot = __shfl_sync(kFull, inc, 31);
+    if (tot == 0) continue;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(&b.cnt[CNT_NT], (unsigned long long)tot);
+    base = __shfl_sync(kFull, base, 31);
+    if (base + tot > cap_nt && lane == 31) atomicOr(&b.cnt[CNT_STATUS], ST_NT);
+    if (n) walk<true>(b, a, base + inc - n, cap_nt);
   }
 }
 
@@ -191,7 +218,7 @@ __global__ void k_event_offsets(Buffers b) {
 
 void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s) {
   const uint64_t cap_nt = (uint64_t)p.max_ntuplets;
-  k_find_ntuplets<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_cells, cap_nt);
+  k_find_ntuplets<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links, cap_nt);
   k_bucket_count<<<l.grid, 256, 0, s>>>(b, cap_nt);
   launch_scan(b.bucket_cnt, b.bucket_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s);
   k_bucket_scatter<<<l.grid, 256, 0, s>>>(b, cap_nt);

@@ -33,6 +33,9 @@ enum : int {
   CNT_SCAN_NT = 6,
   CNT_GATE_KEPT = 7,
   CNT_SV = 8,         // cleaned ntuplets
+  CNT_LKCELLS = 9,    // slots reserved in the list of cells with outgoing links
+  CNT_CELLS_USED = 10,  // cells written (CNT_CELLS counts reserved slots incl. holes)
+  CNT_LINKS_USED = 11,  // links written (CNT_LINKS counts reserved slots incl. holes)
   CNT_N = 16
 };
 // status bits
@@ -41,6 +44,15 @@ enum : unsigned long long {
   ST_LINKS = 2ull,
   ST_NT = 4ull,
   ST_LAYER = 8ull,
+};
+
+// Cells leaving one hit towards one outer layer: [off, off + cnt) of the cell arrays,
+// sorted by r-z slope when mdr >= 0 (mdr = smallest dr in the segment).
+struct __align__(16) Segment {
+  uint32_t off;
+  uint32_t cnt;
+  float mdr;
+  uint32_t pad;
 };
 
 struct BatchHeader {
@@ -74,18 +86,24 @@ struct Buffers {
   uint32_t* bin_cnt;         // [max_events*10*B + 1]
   uint32_t* bin_start;       // [max_events*10*B + 1]
   uint32_t* layer_rmax;      // [max_events*10] float bits of max r per event layer
-  // doublet segments: per sorted hit and outer-layer slot
-  uint32_t* seg_off;         // [max_hits*3]
-  uint32_t* seg_cnt;         // [max_hits*3]
-  float* seg_mdr;            // [max_hits*3] min dr of the segment, < 0: unsorted
+  // doublet segments: per sorted hit and outer-layer slot (all 3 slots written)
+  Segment* seg;              // [max_hits*3]
   // cells
   uint32_t* cell_in;         // [max_cells] sorted hit index
   uint32_t* cell_out;        // [max_cells]
-  float* cell_slope;         // [max_cells] dz/dr
-  uint32_t* link_off;        // [max_cells]
-  uint32_t* link_cnt;        // [max_cells]
-  uint8_t* has_in;           // [max_cells]
-  unsigned long long* best;  // [max_cells] duplicate-cleaning key
+  uint32_t* cell_key;        // [max_cells] slope key: order-preserving bits of dz/dr,
+                             //   low 8 bits = position in the staging buffer
+  uint32_t* cell_inrank;     // [max_cells] rank among the cells ending on the same hit
+  uint8_t* cell_l0;          // [max_cells] layer of the inner hit
+  uint8_t* has_in;           // [max_cells] an accepted link ends on the cell
+  uint8_t* has_out;          // [max_cells] an accepted link starts from the cell
+  uint32_t* link_off;        // [max_cells] valid where has_out
+  uint32_t* link_cnt;        // [max_cells] valid where has_out
+  uint32_t* lk_cells;        // [max_links] cells with >= 1 outgoing link
+  unsigned long long* best;  // [max_cells] duplicate-cleaning key (cells on ntuplets)
+  uint32_t* in_cnt;          // [max_hits + 1] cells ending on each sorted hit
+  uint32_t* in_start;        // [max_hits + 1] exclusive scan of in_cnt
+  uint32_t* in_list;         // [max_cells] cells grouped by the hit they end on
   // links
   uint32_t* link_dst;        // [max_links]
   float* link_q;             // [max_links]
@@ -203,6 +221,16 @@ __device__ __forceinline__ bool link_c23(const pt_cuts& c, float4 p0, bool first
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// Order-preserving map float -> uint32 (monotone increasing, finite and infinite values).
+__device__ __forceinline__ uint32_t f2ord(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+constexpr uint32_t kKeyMask = 0xffffff00u;  // slope part of a cell key
+
 __device__ __forceinline__ unsigned warp_incl_scan(unsigned v) {
   const int lane = lane_id();
 #pragma unroll
@@ -211,6 +239,42 @@ __device__ __forceinline__ unsigned warp_incl_scan(unsigned v) {
     if (lane >= o) v += t;
   }
   return v;
+}
+
+constexpr uint32_t kHole = 0xffffffffu;  // marks a reserved but unused slot
+
+// Per-warp bump allocator over a global counter.  The first chunk is exactly the first
+// request (a warp that makes one request wastes nothing); later chunks double from
+// kChunkMin up to kChunkMax, so a busy warp takes a global atomic about once per
+// kChunkMax slots instead of once per request.  The unused tail of a chunk becomes a
+// hole that the owner marks.  All members are warp-uniform.
+struct WarpChunk {
+  unsigned long long next = 0, end = 0;
+  uint32_t size = 0;
+};
+constexpr uint32_t kChunkMin = 32;
+constexpr uint32_t kChunkMax = 2048;
+
+// Reserves n contiguous slots; returns the first.  The caller marks [old next, old end)
+// as a hole when a new chunk is taken (reported through *hole_lo / *hole_hi).
+__device__ __forceinline__ unsigned long long chunk_take(WarpChunk& ch, unsigned long long* counter,
+                                                         uint32_t n, unsigned long long* hole_lo,
+                                                         unsigned long long* hole_hi) {
+  *hole_lo = *hole_hi = 0;
+  if (ch.next + n > ch.end) {
+    *hole_lo = ch.next;
+    *hole_hi = ch.end;
+    const uint32_t want = ch.size == 0 ? n : (n > ch.size ? n : ch.size);
+    ch.size = ch.size == 0 ? (n > kChunkMin ? n : kChunkMin) : min(2 * ch.size, kChunkMax);
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == 0) base = atomicAdd(counter, (unsigned long long)want);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    ch.next = base;
+    ch.end = base + want;
+  }
+  const unsigned long long r = ch.next;
+  ch.next += n;
+  return r;
 }
 
 // Event owning batch hit g: largest e with off[e] <= g (empty events are skipped).

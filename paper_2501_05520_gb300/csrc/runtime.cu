@@ -68,16 +68,21 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b) {
   t.bin_cnt = (uint32_t*)take(NB * 4);
   t.bin_start = (uint32_t*)take(NB * 4);
   t.layer_rmax = (uint32_t*)take(E * kLayers * 4);
-  t.seg_off = (uint32_t*)take(N * kMaxOuter * 4);
-  t.seg_cnt = (uint32_t*)take(N * kMaxOuter * 4);
-  t.seg_mdr = (float*)take(N * kMaxOuter * 4);
+  t.seg = (Segment*)take(N * kMaxOuter * sizeof(Segment));
   t.cell_in = (uint32_t*)take(C * 4);
   t.cell_out = (uint32_t*)take(C * 4);
-  t.cell_slope = (float*)take(C * 4);
+  t.cell_key = (uint32_t*)take(C * 4);
+  t.cell_inrank = (uint32_t*)take(C * 4);
+  t.cell_l0 = (uint8_t*)take(C);
+  t.has_in = (uint8_t*)take(C);
+  t.has_out = (uint8_t*)take(C);
   t.link_off = (uint32_t*)take(C * 4);
   t.link_cnt = (uint32_t*)take(C * 4);
-  t.has_in = (uint8_t*)take(C);
+  t.lk_cells = (uint32_t*)take(L * 4);
   t.best = (unsigned long long*)take(C * 8);
+  t.in_cnt = (uint32_t*)take((N + 1) * 4);
+  t.in_start = (uint32_t*)take((N + 1) * 4);
+  t.in_list = (uint32_t*)take(C * 4);
   t.link_dst = (uint32_t*)take(L * 4);
   t.link_q = (float*)take(L * 4);
   t.nt_hits = (int32_t*)take(T * kMaxHits * 4);
@@ -176,11 +181,16 @@ pt_status sync_counters(pt_ctx* c) {
   const unsigned long long st = c->h_cnt[CNT_STATUS];
   if (st & ST_LAYER) return fail(PT_ERR_INVALID, "input contains a layer code > 9");
   if (st & ST_CELLS)
-    return fail(PT_ERR_CAPACITY, "max_cells = %lld is too small: %llu cells needed",
+    return fail(PT_ERR_CAPACITY,
+                "max_cells = %lld is too small: about %llu cell slots needed (cells plus "
+                "allocation slack)",
                 (long long)c->cap.max_cells, c->h_cnt[CNT_CELLS]);
   if (st & ST_LINKS)
-    return fail(PT_ERR_CAPACITY, "max_links = %lld is too small: at least %llu links needed",
-                (long long)c->cap.max_links, c->h_cnt[CNT_LINKS]);
+    return fail(PT_ERR_CAPACITY,
+                "max_links = %lld is too small: at least %llu link slots needed",
+                (long long)c->cap.max_links,
+                c->h_cnt[CNT_LINKS] > c->h_cnt[CNT_LKCELLS] ? c->h_cnt[CNT_LINKS]
+                                                            : c->h_cnt[CNT_LKCELLS]);
   if (st & ST_NT)
     return fail(PT_ERR_CAPACITY,
                 "max_ntuplets = %lld is too small: at least %llu ntuplets needed",
@@ -434,11 +444,11 @@ pt_status pt_load_hits(pt_ctx* c, int64_t n, const float* x, const float* y, con
   return PT_OK;
 
 pt_status pt_build_doublets(pt_ctx* c, int64_t* n_cells) {
-  STAGE_BODY(launch_doublets(c->B, c->P, c->L, c->stream), CNT_CELLS, n_cells)
+  STAGE_BODY(launch_doublets(c->B, c->P, c->L, c->stream), CNT_CELLS_USED, n_cells)
 }
 
 pt_status pt_connect_cells(pt_ctx* c, int64_t* n_links) {
-  STAGE_BODY(launch_connect(c->B, c->P, c->L, c->stream), CNT_LINKS, n_links)
+  STAGE_BODY(launch_connect(c->B, c->P, c->L, c->stream), CNT_LINKS_USED, n_links)
 }
 
 pt_status pt_find_ntuplets(pt_ctx* c, int64_t* n_ntuplets) {
@@ -490,21 +500,27 @@ pt_status pt_get_cells(pt_ctx* c, int32_t* inner, int32_t* outer, int32_t* event
   PT_TRY(need_loaded(c));
   DeviceGuard guard(c->device);
   PT_TRY(sync_counters(c));
-  const int64_t C = (int64_t)c->h_cnt[CNT_CELLS];
+  const int64_t C = (int64_t)c->h_cnt[CNT_CELLS_USED];
+  int64_t slots = (int64_t)c->h_cnt[CNT_CELLS];
+  if (slots > c->cap.max_cells) slots = c->cap.max_cells;
   if (n) *n = C;
   if (cap < C) return fail(PT_ERR_CAPACITY, "output capacity %lld < %lld cells", (long long)cap,
                            (long long)C);
   if (C == 0) return PT_OK;
-  PT_TRY(val_staging(c, (size_t)C * 12));
+  PT_TRY(val_staging(c, (size_t)slots * 12));
   launch_export_cells(c->B, c->P, c->L, (int32_t*)c->val, c->stream);
   PT_TRY(last_launch());
-  std::vector<int32_t> tmp((size_t)C * 3);
-  PT_CUDA(cudaMemcpyAsync(tmp.data(), c->val, (size_t)C * 12, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<int32_t> tmp((size_t)slots * 3);
+  PT_CUDA(cudaMemcpyAsync(tmp.data(), c->val, (size_t)slots * 12, cudaMemcpyDeviceToHost,
+                          c->stream));
   PT_CUDA(cudaStreamSynchronize(c->stream));
-  for (int64_t i = 0; i < C; ++i) {
-    if (inner) inner[i] = tmp[i * 3];
-    if (outer) outer[i] = tmp[i * 3 + 1];
-    if (event) event[i] = tmp[i * 3 + 2];
+  int64_t k = 0;
+  for (int64_t i = 0; i < slots && k < C; ++i) {
+    if (tmp[i * 3 + 2] < 0) continue;  // allocation hole
+    if (inner) inner[k] = tmp[i * 3];
+    if (outer) outer[k] = tmp[i * 3 + 1];
+    if (event) event[k] = tmp[i * 3 + 2];
+    ++k;
   }
   return PT_OK;
 }
@@ -515,27 +531,33 @@ pt_status pt_get_links(pt_ctx* c, int32_t* h0, int32_t* h1, int32_t* h2, float* 
   PT_TRY(need_loaded(c));
   DeviceGuard guard(c->device);
   PT_TRY(sync_counters(c));
-  const int64_t Lk = (int64_t)c->h_cnt[CNT_LINKS];
+  const int64_t Lk = (int64_t)c->h_cnt[CNT_LINKS_USED];
+  int64_t slots = (int64_t)c->h_cnt[CNT_LINKS];
+  if (slots > c->cap.max_links) slots = c->cap.max_links;
   if (n) *n = Lk;
   if (cap < Lk) return fail(PT_ERR_CAPACITY, "output capacity %lld < %lld links", (long long)cap,
                             (long long)Lk);
   if (Lk == 0) return PT_OK;
-  PT_TRY(val_staging(c, (size_t)Lk * 20));
+  PT_TRY(val_staging(c, (size_t)slots * 20));
   int32_t* o4 = (int32_t*)c->val;
-  float* oq = (float*)(c->val + (size_t)Lk * 16);
+  float* oq = (float*)(c->val + (size_t)slots * 16);
+  PT_CUDA(cudaMemsetAsync(o4, 0xff, (size_t)slots * 16, c->stream));
   launch_export_links(c->B, c->P, c->L, o4, oq, c->stream);
   PT_TRY(last_launch());
-  std::vector<int32_t> tmp((size_t)Lk * 4);
-  std::vector<float> tq((size_t)Lk);
-  PT_CUDA(cudaMemcpyAsync(tmp.data(), o4, (size_t)Lk * 16, cudaMemcpyDeviceToHost, c->stream));
-  PT_CUDA(cudaMemcpyAsync(tq.data(), oq, (size_t)Lk * 4, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<int32_t> tmp((size_t)slots * 4);
+  std::vector<float> tq((size_t)slots);
+  PT_CUDA(cudaMemcpyAsync(tmp.data(), o4, (size_t)slots * 16, cudaMemcpyDeviceToHost, c->stream));
+  PT_CUDA(cudaMemcpyAsync(tq.data(), oq, (size_t)slots * 4, cudaMemcpyDeviceToHost, c->stream));
   PT_CUDA(cudaStreamSynchronize(c->stream));
-  for (int64_t i = 0; i < Lk; ++i) {
-    if (h0) h0[i] = tmp[i * 4];
-    if (h1) h1[i] = tmp[i * 4 + 1];
-    if (h2) h2[i] = tmp[i * 4 + 2];
-    if (event) event[i] = tmp[i * 4 + 3];
-    if (q) q[i] = tq[i];
+  int64_t k = 0;
+  for (int64_t i = 0; i < slots && k < Lk; ++i) {
+    if (tmp[i * 4 + 3] < 0) continue;  // allocation hole
+    if (h0) h0[k] = tmp[i * 4];
+    if (h1) h1[k] = tmp[i * 4 + 1];
+    if (h2) h2[k] = tmp[i * 4 + 2];
+    if (event) event[k] = tmp[i * 4 + 3];
+    if (q) q[k] = tq[i];
+    ++k;
   }
   return PT_OK;
 }

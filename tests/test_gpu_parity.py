@@ -189,6 +189,19 @@ def test_capacity_and_input_errors(cuts):
         with pytest.raises(pt.PtError) as ei:
             ctx.pt_load_batch([0, 5, 3], ev.x, ev.y, ev.z, ev.layer)
         assert ei.value.status in (pt.PT_ERR_INVALID, pt.PT_ERR_CAPACITY)
+    # link and ntuplet capacities: the overflow is reported, never truncated silently
+    ev2 = sim.generate(sim.PU50, 2052)
+    for field, stage in (("max_links", "pt_connect_cells"), ("max_ntuplets", "pt_find_ntuplets")):
+        cap2 = dict(PU_CAP, **{field: 50})
+        with pt.Context(cuts=cuts, capacity=cap2) as c2:
+            c2.pt_load_hits(ev2.x, ev2.y, ev2.z, ev2.layer)
+            with pytest.raises(pt.PtError) as ei:
+                c2.pt_build_doublets()
+                c2.pt_connect_cells()
+                c2.pt_find_ntuplets()
+                c2.pt_fit_tracks()
+            assert ei.value.status == pt.PT_ERR_CAPACITY and field in str(ei.value)
+    with pt.Context(cuts=cuts, capacity=cap) as ctx:
         # the context stays usable after errors
         small = sim.generate(sim.SINGLE_MUON_LIKE, 1001)
         hits, nh, tr, off = ctx.pt_reconstruct_batch([0, small.n_hits], small.x, small.y,
