@@ -201,6 +201,30 @@ pt_status pt_enqueue_batch(pt_ctx* ctx, int n_events, const int64_t* hit_offsets
                            const float* x, const float* y, const float* z, const uint8_t* layer,
                            int on_device);
 
+/* Doublets of one event without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory -- code whose
+ * process hands all device memory to another allocator (a framework's caching pool
+ * that has reserved the GPU), or real-time loops that must not allocate after start-up
+ * -- and so cannot create a context.  Its scratch is a fixed array of about 2.7 MB
+ * compiled into the library, which every GPU that loads the library keeps until the
+ * process exits.
+ *   n <= 65536 hits, else PT_ERR_CAPACITY with no GPU work.  x, y, z (float32) and
+ *   layer (uint8): device pointers on the current device.  inner/outer: device arrays
+ *   of cap int32 entries receiving each accepted doublet as input hit indices (inner,
+ *   outer), in no particular order; the set equals the cells of pt_build_doublets with
+ *   the same cuts.  *n_out (host) receives the number of doublets; if it exceeds cap the
+ *   call returns PT_ERR_CAPACITY and only cap of them were written.
+ *   stream: cudaStream_t or NULL; the call synchronises it before returning.
+ * The first call on a device looks up the scratch array's device address (set-up done
+ * once per device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and each call clears what it reads as zero:
+ * calls whose GPU work overlaps (other threads, other streams) race and must not be
+ * issued concurrently.  No cudaMalloc, cudaFree or other allocating call is made. */
+pt_status pt_find_doublets_noalloc(const pt_cuts* cuts, int64_t n, const float* x,
+                                   const float* y, const float* z, const uint8_t* layer,
+                                   int32_t* inner, int32_t* outer, int64_t cap, int64_t* n_out,
+                                   void* stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char* pt_last_error(void);
 

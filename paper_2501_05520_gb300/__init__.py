@@ -28,7 +28,8 @@ PT_OK, PT_ERR_INVALID, PT_ERR_CAPACITY, PT_ERR_CUDA, PT_ERR_TIMEOUT, PT_ERR_NOT_
 EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt_load_hits",
             "pt_load_batch", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
             "pt_fit_tracks", "pt_get_ntuplets", "pt_get_tracks", "pt_get_cells", "pt_get_links",
-            "pt_get_candidates", "pt_reconstruct_batch", "pt_enqueue_batch", "pt_last_error")
+            "pt_get_candidates", "pt_reconstruct_batch", "pt_enqueue_batch",
+            "pt_find_doublets_noalloc", "pt_last_error")
 
 
 class PtCuts(ctypes.Structure):
@@ -90,6 +91,8 @@ def lib() -> ctypes.CDLL:
             "pt_get_candidates": [P, P, P, P, P, I64, PI64],
             "pt_reconstruct_batch": [P, I32, P, P, P, P, P, I32, P, P, P, P, I64, PI64, I32],
             "pt_enqueue_batch": [P, I32, P, P, P, P, P, I32],
+            "pt_find_doublets_noalloc": [ctypes.POINTER(PtCuts), I64, P, P, P, P, P, P, I64,
+                                         PI64, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)

@@ -137,6 +137,9 @@ struct Launch {
   int grid;        // generic persistent grid (blocks of 256 threads)
 };
 
+// Sets the calling thread's pt_last_error() message.
+void set_last_error(const char* msg);
+
 // ------------------------------------------------------------------ launchers
 void launch_clear(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
 void launch_bin_hits(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);

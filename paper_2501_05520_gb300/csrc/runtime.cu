@@ -297,6 +297,10 @@ pt_status copy_out(pt_ctx* c, void* dst, const void* src, size_t bytes, int on_d
 
 }  // namespace
 
+namespace ptca {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace ptca
+
 extern "C" {
 
 const char* pt_last_error(void) { return g_err.c_str(); }
