@@ -52,7 +52,7 @@ def make_events(n: int, seed0: int = SEED0):
     return [sim.generate(sim.PU200, seed0 + i) for i in range(n)]
 
 
-def capacity(batch: int = BATCH, phi_bins: int = 256) -> dict:
+def capacity(batch: int = BATCH, phi_bins: int = 1024) -> dict:
     import paper_2501_05520_gb300 as pt
     return pt.default_capacity(max_events=batch, hits_per_event=49152,
                                cells_per_event=3_500_000, links_per_event=262_144,
@@ -322,7 +322,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--batch", type=int, default=BATCH)
-    ap.add_argument("--phi-bins", type=int, default=256)
+    ap.add_argument("--phi-bins", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
