@@ -179,6 +179,46 @@ pt_status pt_get_links(pt_ctx* ctx, int32_t* h0, int32_t* h1, int32_t* h2, float
 pt_status pt_get_candidates(pt_ctx* ctx, int32_t* hits, uint8_t* nhits, float* q, int32_t* event,
                             int64_t cap, int64_t* n);
 
+/* ------------------------------------------------------------- learned gate */
+
+/* Learned link gate: an MLP 12 -> 64 -> 64 -> 1 (ReLU) scores every accepted cell link
+ * from 12 geometric features and links scoring below tau are removed before the ntuplet
+ * search; the exact cuts stay in force.  It is the library's analogue of the paper's
+ * edge-filtering MLP (Sec. 2.2.2: an MLP scores graph edges, a fixed threshold drops
+ * clearly fake ones).  Features of link (h0, h1, h2): C1, C2, C3 cut ratios,
+ * t_a/cotmax, 10 (t_b - t_a), r0/16, r1/16, r2/16, (z0 - r0 t_a)/z0max, layer0/9,
+ * layer1/9, layer2/9 (t = dz/dr of a cell).  Inference runs on the tensor cores with
+ * bf16 weights, features and hidden activations and float32 accumulation.
+ *
+ * w: host array of 5057 float32 parameters, row-major W1[64][12], b1[64], W2[64][64],
+ * b2[64], w3[64], b3; W1 and W2 are rounded to bf16 (nearest even) on upload, the rest
+ * stays float32.  tau: threshold on the score (logit).  w == NULL switches the gate off.
+ * Synchronises the stream; the next pt_reconstruct_batch re-captures its graph. */
+pt_status pt_set_gate(pt_ctx* ctx, const float* w, float tau);
+
+/* Current links with their float32 features [n][12], hits (event-local input indices),
+ * event and gate score (NaN when the gate is off); host outputs, any may be NULL.  With
+ * the gate on only the kept links are listed.  Synchronises the stream. */
+pt_status pt_get_link_features(pt_ctx* ctx, float* feat, int32_t* h0, int32_t* h1, int32_t* h2,
+                               int32_t* event, float* score, int64_t cap, int64_t* n);
+
+/* Scores of n feature rows with the context's gate (tensor-core path): feat device
+ * float32 [n][12], out device float32 [n]; n <= max_links.  Synchronises the stream. */
+pt_status pt_gate_score(pt_ctx* ctx, const float* feat, int64_t n, float* out);
+
+/* Training (Sec. 2.2.2 models are trained; here the gate is trained on the GPU): mean
+ * binary cross-entropy of sigmoid(score) against labels y in {0, 1} and its gradient
+ * with respect to the 5057 float32 parameters w.  All pointers are device pointers on
+ * the current device: w [5057], x [n][12], y [n], grad [5057] (overwritten), loss [1]
+ * (overwritten).  Asynchronous on `stream` (NULL: default stream). */
+pt_status pt_gate_loss_grad(const float* w, const float* x, const float* y, int64_t n,
+                            float* grad, float* loss, void* stream);
+
+/* One Adam step (bias-corrected, step >= 1) on n float32 parameters: device pointers w,
+ * first and second moment m and v (updated in place) and grad.  Asynchronous. */
+pt_status pt_gate_adam(float* w, float* m, float* v, const float* grad, int64_t n, float lr,
+                       float beta1, float beta2, float eps, int step, void* stream);
+
 /* ------------------------------------------------------------- whole batch */
 
 /* Load, doublets, links, ntuplets, fit and copy-out of a batch in one call; the GPU

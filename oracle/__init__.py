@@ -52,6 +52,9 @@ def _load():
         lib.orc_reconstruct.restype = P
         lib.orc_reconstruct.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.POINTER(Cuts),
                                         ctypes.c_double]
+        lib.orc_reconstruct_masked.restype = P
+        lib.orc_reconstruct_masked.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.POINTER(Cuts),
+                                               ctypes.c_double, P, ctypes.c_int64]
         for name in ("orc_sizes", "orc_get_radius", "orc_get_near"):
             getattr(lib, name).argtypes = [P, P]
         lib.orc_get_cells.argtypes = [P, P, P]
@@ -76,8 +79,11 @@ def make_cuts(d: dict) -> Cuts:
     return Cuts(*(float(np.float32(d[f])) for f, _ in Cuts._fields_))
 
 
-def reconstruct(x, y, z, layer, cuts: dict, bfield: float = 3.8) -> dict:
+def reconstruct(x, y, z, layer, cuts: dict, bfield: float = 3.8, link_keep=None) -> dict:
     """Run the whole chain on one event.  Hit arrays are float32 / uint8, input order.
+
+    link_keep: optional bool array, one entry per link of the plain run (its link order);
+    links with False are removed before the ntuplet search (a gate decision).
 
     Returns a dict of numpy arrays:
       r                      float32 [N]
@@ -96,8 +102,13 @@ def reconstruct(x, y, z, layer, cuts: dict, bfield: float = 3.8) -> dict:
     layer = np.ascontiguousarray(layer, np.uint8)
     n = x.shape[0]
     c = make_cuts(cuts)
-    h = lib.orc_reconstruct(n, _ptr(x), _ptr(y), _ptr(z), _ptr(layer), ctypes.byref(c),
-                            float(bfield))
+    if link_keep is None:
+        h = lib.orc_reconstruct(n, _ptr(x), _ptr(y), _ptr(z), _ptr(layer), ctypes.byref(c),
+                                float(bfield))
+    else:
+        keep = np.ascontiguousarray(link_keep, np.uint8)
+        h = lib.orc_reconstruct_masked(n, _ptr(x), _ptr(y), _ptr(z), _ptr(layer),
+                                       ctypes.byref(c), float(bfield), _ptr(keep), keep.size)
     try:
         sz = np.zeros(7, np.int64)
         lib.orc_sizes(h, _ptr(sz))

@@ -373,8 +373,22 @@ int64_t orc_dedup(int64_t T, const int32_t* hits, const int32_t* cells, const in
 }
 
 /* ----------------------------------------------------------------------- driver */
+/* link_keep (optional, may be NULL): one flag per link accepted by the cuts, in the
+ * order the plain run lists them (cell a major); links with flag 0 are removed before
+ * the ntuplet search (the learned gate's decision, computed by the caller). */
+orc_result* orc_reconstruct_masked(int64_t n, const float* x, const float* y, const float* z,
+                                   const uint8_t* layer, const orc_cuts* cuts, double bfield,
+                                   const uint8_t* link_keep, int64_t n_keep);
+
 orc_result* orc_reconstruct(int64_t n, const float* x, const float* y, const float* z,
                             const uint8_t* layer, const orc_cuts* cuts, double bfield) {
+  return orc_reconstruct_masked(n, x, y, z, layer, cuts, bfield, NULL, 0);
+}
+
+orc_result* orc_reconstruct_masked(int64_t n, const float* x, const float* y, const float* z,
+                                   const uint8_t* layer, const orc_cuts* cuts, double bfield,
+                                   const uint8_t* link_keep, int64_t n_keep) {
+  int64_t lidx = 0; /* index among all links accepted by the cuts */
   orc_result* R = (orc_result*)calloc(1, sizeof(orc_result));
   R->n_hits = n;
   R->r = (float*)malloc((size_t)(n > 0 ? n : 1) * sizeof(float));
@@ -433,6 +447,7 @@ orc_result* orc_reconstruct(int64_t n, const float* x, const float* y, const flo
       if (near) {
         iv_push(&R->near, 1); iv_push(&R->near, h0); iv_push(&R->near, h1); iv_push(&R->near, h2);
       }
+      if (ok && link_keep) ok = lidx < n_keep && link_keep[lidx++];
       if (ok) {
         iv_push(&R->link_a, (int32_t)a);
         iv_push(&R->link_b, b);

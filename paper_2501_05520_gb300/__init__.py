@@ -29,7 +29,8 @@ EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt
             "pt_load_batch", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
             "pt_fit_tracks", "pt_get_ntuplets", "pt_get_tracks", "pt_get_cells", "pt_get_links",
             "pt_get_candidates", "pt_reconstruct_batch", "pt_enqueue_batch",
-            "pt_find_doublets_noalloc", "pt_last_error")
+            "pt_find_doublets_noalloc", "pt_set_gate", "pt_get_link_features", "pt_gate_score",
+            "pt_gate_loss_grad", "pt_gate_adam", "pt_last_error")
 
 
 class PtCuts(ctypes.Structure):
@@ -93,6 +94,12 @@ def lib() -> ctypes.CDLL:
             "pt_enqueue_batch": [P, I32, P, P, P, P, P, I32],
             "pt_find_doublets_noalloc": [ctypes.POINTER(PtCuts), I64, P, P, P, P, P, P, I64,
                                          PI64, P],
+            "pt_set_gate": [P, P, ctypes.c_float],
+            "pt_get_link_features": [P, P, P, P, P, P, P, I64, PI64],
+            "pt_gate_score": [P, P, I64, P],
+            "pt_gate_loss_grad": [P, P, P, I64, P, P, P],
+            "pt_gate_adam": [P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, I32, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -304,6 +311,39 @@ class Context:
                                        T, ctypes.byref(n)))
         return hits, nh, q, e
 
+    # -------------------------------------------------------------- learned gate
+    def pt_set_gate(self, w, tau: float):
+        """Enable the gate with 5057 float32 parameters (host), or disable it (w=None)."""
+        if w is None:
+            _check(lib().pt_set_gate(self.handle, None, 0.0))
+            self.gate = None
+            return
+        arr = np.ascontiguousarray(w, np.float32)
+        assert arr.size == 5057
+        _check(lib().pt_set_gate(self.handle, _hptr(arr), float(tau)))
+        self.gate = (arr.copy(), float(tau))
+
+    def pt_get_link_features(self):
+        """(feat float32 [n,12], h0, h1, h2, event int32 [n], score float32 [n])."""
+        n = ctypes.c_int64(0)
+        st = lib().pt_get_link_features(self.handle, None, None, None, None, None, None, 0,
+                                        ctypes.byref(n))
+        if st not in (PT_OK, PT_ERR_CAPACITY):
+            _check(st)
+        L = int(n.value)
+        feat = np.empty((L, 12), np.float32)
+        h0, h1, h2, e = (np.empty(L, np.int32) for _ in range(4))
+        sc = np.empty(L, np.float32)
+        _check(lib().pt_get_link_features(self.handle, _hptr(feat), _hptr(h0), _hptr(h1),
+                                          _hptr(h2), _hptr(e), _hptr(sc), L, ctypes.byref(n)))
+        return feat, h0, h1, h2, e, sc
+
+    def pt_gate_score(self, feat_dev, out_dev):
+        """Scores of device feature rows (torch float32 [n,12]) into out_dev [n]."""
+        n = int(feat_dev.shape[0])
+        _check(lib().pt_gate_score(self.handle, ctypes.c_void_p(feat_dev.data_ptr()), n,
+                                   ctypes.c_void_p(out_dev.data_ptr())))
+
     # ------------------------------------------------------------ whole batch
     def pt_enqueue_batch(self, offsets, x, y, z, layer):
         off = np.ascontiguousarray(offsets, np.int64)
@@ -355,3 +395,22 @@ def exported_symbols() -> list[str]:
     """Names of EXPORTED found in the library (loads it; no GPU call)."""
     L = lib()
     return [s for s in EXPORTED if hasattr(L, s)]
+
+
+def pt_gate_loss_grad(w, x, y, grad, loss, stream=None):
+    """Mean BCE loss and gradient of the gate MLP; torch CUDA tensors (float32)."""
+    sp = stream.cuda_stream if stream is not None else 0
+    _check(lib().pt_gate_loss_grad(ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                   ctypes.c_void_p(y.data_ptr()), int(x.shape[0]),
+                                   ctypes.c_void_p(grad.data_ptr()),
+                                   ctypes.c_void_p(loss.data_ptr()),
+                                   ctypes.c_void_p(sp) if sp else None))
+
+
+def pt_gate_adam(w, m, v, grad, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One Adam step on torch CUDA float32 tensors (in place)."""
+    sp = stream.cuda_stream if stream is not None else 0
+    _check(lib().pt_gate_adam(ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(m.data_ptr()),
+                              ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                              int(w.numel()), float(lr), float(beta1), float(beta2), float(eps),
+                              int(step), ctypes.c_void_p(sp) if sp else None))

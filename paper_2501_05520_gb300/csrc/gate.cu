@@ -1,0 +1,424 @@
+// Learned link gate (optional stage after the cellular-automaton links): every accepted
+// link (h0 -> h1 -> h2) gets 12 geometric features, a 12 -> 64 -> 64 -> 1 MLP scores it
+// on the tensor cores, and links scoring below the threshold are removed before the
+// ntuplet search.  It plays the role of the edge-filtering MLP of the paper's ML
+// pipeline (Sec. 2.2.2: an MLP scores graph edges, a fixed threshold removes clearly
+// fake ones); the exact cuts stay in force, the gate only removes links.
+//
+// Features (float32 from the hit coordinates, rounded to bf16 for the MMA):
+//   C1, C2 and C3 cut ratios, t_a / cotmax, 10 (t_b - t_a), r0/16, r1/16, r2/16,
+//   (z0 - r0 t_a) / z0max, layer0/9, layer1/9, layer2/9; padded with 4 zeros to K = 16.
+//
+// Tensor-core MLP (one 128-thread CTA per SM slot, persistent over 128-link tiles):
+//   D1[128x64] = X[128x16] * W1^T      one tcgen05.mma (M=128, N=64, K=16), TMEM cols 0..63
+//   H1 = bf16(relu(D1 + b1))           tcgen05.ld by each warp's 32 TMEM lanes -> smem
+//   D2[128x64] = H1[128x64] * W2^T     four tcgen05.mma (K=16 each), TMEM cols 64..127
+//   score = relu(D2 + b2) . w3 + b3    tcgen05.ld + float32 dot in registers
+// Operands are bf16 in shared memory in the no-swizzle K-major layout of 8x8 core
+// matrices (16 bytes per row, 128 bytes per core matrix; LBO = 128 bytes between core
+// matrices along K, SBO = K/8 * 128 bytes between groups of 8 rows).  One thread issues
+// the MMAs and commits them to an mbarrier; every wait on it is bounded and sets an
+// error flag instead of hanging.
+#include <cuda_bf16.h>
+
+#include "ptca_internal.cuh"
+
+namespace ptca {
+
+namespace {
+
+constexpr int kTileM = 128;
+constexpr uint32_t kIdesc = (1u << 4)                          // D: float32
+                            | (1u << 7) | (1u << 10)            // A, B: bf16
+                            | ((uint32_t)(kGateHidden >> 3) << 17)  // N = 64
+                            | ((uint32_t)(kTileM >> 4) << 24);     // M = 128
+constexpr long long kWaitCycles = 1ll << 31;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor, no swizzle: start, LBO, SBO (bytes, >> 4), version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(mbar))
+               : "memory");
+}
+
+// Bounded wait for the mbarrier phase `parity` to complete; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes -> 32 registers per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+  return lo | (hi << 16);
+}
+
+// Shared-memory layout of the MLP kernel (bytes).
+constexpr int kOffX = 0;              // 128 x 16 bf16, SBO 256
+constexpr int kOffW1 = 4096;          // 64 x 16 bf16, SBO 256
+constexpr int kOffW2 = 6144;          // 64 x 64 bf16, SBO 1024
+constexpr int kOffH1 = 14336;         // 128 x 64 bf16, SBO 1024
+constexpr int kOffF = 30720;          // b1, b2, w3 (64 each), b3, tau
+constexpr int kOffBar = 31744;        // mbarrier
+constexpr int kOffTmem = 31752;       // TMEM base address
+constexpr int kOffFlag = 31756;       // wait status
+constexpr int kMlpSmem = 48 * 1024;   // requested: at most 4 CTAs per SM (TMEM 4 x 128 cols)
+
+__global__ void __launch_bounds__(kTileM, 1)
+    k_gate_mlp(const GateWeights* gw, const uint16_t* X, const unsigned long long* n_dev,
+               int64_t n_max, float* score, uint8_t* keep, unsigned long long* status) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  float* sb1 = (float*)(sm + kOffF);
+  float* sb2 = sb1 + kGateHidden;
+  float* sw3 = sb2 + kGateHidden;
+  float* sc = sw3 + kGateHidden;
+  uint64_t* mbar = (uint64_t*)(sm + kOffBar);
+  uint32_t* tslot = (uint32_t*)(sm + kOffTmem);
+  volatile uint32_t* flag = (volatile uint32_t*)(sm + kOffFlag);
+  // rows: n_max, or the device count clamped to n_max
+  const uint64_t n = n_dev ? min((uint64_t)*n_dev, (uint64_t)n_max) : (uint64_t)n_max;
+
+  // weights -> shared memory (already in the operand layout)
+  {
+    const uint4* w1 = (const uint4*)gw->w1;
+    const uint4* w2 = (const uint4*)gw->w2;
+    ((uint4*)(sm + kOffW1))[tid] = w1[tid];  // 128 x 16 B
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ((uint4*)(sm + kOffW2))[tid + 128 * i] = w2[tid + 128 * i];
+    if (tid < kGateHidden) {
+      sb1[tid] = gw->b1[tid];
+      sb2[tid] = gw->b2[tid];
+      sw3[tid] = gw->w3[tid];
+    }
+    if (tid == 0) {
+      sc[0] = gw->b3;
+      sc[1] = gw->tau;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      *flag = 0;
+    }
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                     smem_u32(tslot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t ax = smem_u32(sm + kOffX), aw1 = smem_u32(sm + kOffW1);
+  const uint32_t aw2 = smem_u32(sm + kOffW2), ah1 = smem_u32(sm + kOffH1);
+  uint32_t phase = 0;
+  bool pending = false;  // an MMA group was committed and not yet seen complete
+  const uint64_t n_tiles = (n + kTileM - 1) / kTileM;
+
+  for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const uint64_t row = t * kTileM + tid;
+    // X row -> core-matrix layout: k 0..7 at +0, k 8..15 at +128 within the row group
+    uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+    if (row < n) {
+      const uint4* src = (const uint4*)(X + row * kGateK1);
+      lo = src[0];
+      hi = src[1];
+    }
+    unsigned char* xr = sm + kOffX + (tid >> 3) * 256 + (tid & 7) * 16;
+    *(uint4*)xr = lo;
+    *(uint4*)(xr + 128) = hi;
+    fence_async_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0) {
+      mma_bf16(tmem, smem_desc(ax, 128, 256), smem_desc(aw1, 128, 256), 0u);
+      mma_commit(mbar);
+      pending = true;
+      if (!mbar_wait(mbar, phase)) *flag = 1;
+      else pending = false;
+    }
+    __syncthreads();
+    if (*flag) break;
+    phase ^= 1u;
+    tc_after_sync();
+    // epilogue 1: this thread's row of D1 -> relu(+b1) -> bf16 -> H1 (shared memory)
+    {
+      unsigned char* hr = sm + kOffH1 + (tid >> 3) * 1024 + (tid & 7) * 16;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float v[32];
+        tmem_ld32(tmem + lane_base + 32 * half, v);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {  // 4 core matrices of 8 columns per half
+          const int j0 = 32 * half + 8 * c;
+          uint4 pk;
+          pk.x = pack_bf16(fmaxf(v[8 * c + 0] + sb1[j0 + 0], 0.f), fmaxf(v[8 * c + 1] + sb1[j0 + 1], 0.f));
+          pk.y = pack_bf16(fmaxf(v[8 * c + 2] + sb1[j0 + 2], 0.f), fmaxf(v[8 * c + 3] + sb1[j0 + 3], 0.f));
+          pk.z = pack_bf16(fmaxf(v[8 * c + 4] + sb1[j0 + 4], 0.f), fmaxf(v[8 * c + 5] + sb1[j0 + 5], 0.f));
+          pk.w = pack_bf16(fmaxf(v[8 * c + 6] + sb1[j0 + 6], 0.f), fmaxf(v[8 * c + 7] + sb1[j0 + 7], 0.f));
+          *(uint4*)(hr + (j0 >> 3) * 128) = pk;
+        }
+      }
+    }
+    fence_async_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        mma_bf16(tmem + 64, smem_desc(ah1 + 256 * j, 128, 1024), smem_desc(aw2 + 256 * j, 128, 1024),
+                 j > 0 ? 1u : 0u);
+      mma_commit(mbar);
+      pending = true;
+      if (!mbar_wait(mbar, phase)) *flag = 1;
+      else pending = false;
+    }
+    __syncthreads();
+    if (*flag) break;
+    phase ^= 1u;
+    tc_after_sync();
+    // epilogue 2: relu(D2 + b2) . w3 + b3
+    float acc = sc[0];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      float v[32];
+      tmem_ld32(tmem + lane_base + 64 + 32 * half, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc += fmaxf(v[i] + sb2[32 * half + i], 0.f) * sw3[32 * half + i];
+    }
+    if (row < n) {
+      score[row] = acc;
+      if (keep) keep[row] = acc >= sc[1] ? 1 : 0;
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+  }
+  // teardown: report a timeout, let an MMA still in flight finish (bounded), free TMEM
+  if (tid == 0 && *flag) {
+    atomicOr(status, ST_GATE_TIMEOUT);
+    if (pending) mbar_wait(mbar, phase);
+  }
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
+// Features of one link from the hit coordinates and layers.
+__device__ __forceinline__ void link_features(const pt_cuts& c, float4 p0, float4 p1, float4 p2,
+                                              int L0, int L1, int L2, float (&f)[kGateFeat]) {
+  const float lc1 = fabsf((p1.z - p0.z) * (p2.w - p0.w) - (p2.z - p0.z) * (p1.w - p0.w));
+  const float rc1 = c.rz0 * (p2.w - p0.w) + c.rz1 * fabsf(p2.z - p0.z);
+  const float ax = p1.x - p0.x, ay = p1.y - p0.y, bx = p2.x - p0.x, by = p2.y - p0.y;
+  const float cx = p2.x - p1.x, cy = p2.y - p1.y;
+  const float a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
+  const float cr = ax * by - ay * bx;
+  const float kap = 2.0f * fabsf(cr) / (sqrtf(a2) * sqrtf(b2) * sqrtf(cx * cx + cy * cy));
+  const float D = 2.0f * cr;
+  const float ux = by * a2 - ay * b2, uy = ax * b2 - bx * a2;
+  const float num = (p0.x * p0.x + p0.y * p0.y) * D + 2.0f * (p0.x * ux + p0.y * uy);
+  const float px = p0.x * D + ux, py = p0.y * D + uy;
+  const float den = sqrtf(px * px + py * py) + sqrtf(ux * ux + uy * uy);
+  const float dmax = L0 == 0 ? c.dca_b0 : c.dca_other;
+  const float ta = (p1.z - p0.z) / (p1.w - p0.w);
+  const float tb = (p2.z - p1.z) / (p2.w - p1.w);
+  f[0] = lc1 / rc1;
+  f[1] = kap / c.kmax;
+  f[2] = fabsf(num) / den / dmax;
+  f[3] = ta / c.cotmax;
+  f[4] = 10.0f * (tb - ta);
+  f[5] = p0.w * (1.0f / 16.0f);
+  f[6] = p1.w * (1.0f / 16.0f);
+  f[7] = p2.w * (1.0f / 16.0f);
+  f[8] = (p0.z - p0.w * ta) / c.z0max;
+  f[9] = L0 * (1.0f / 9.0f);
+  f[10] = L1 * (1.0f / 9.0f);
+  f[11] = L2 * (1.0f / 9.0f);
+}
+
+// For every link of every cell with links: features -> bf16 row (or float32 row).
+template <bool F32>
+__global__ void k_gate_features(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap_links,
+                                float* out32) {
+  const uint64_t nl = min(b.cnt[CNT_LKCELLS], (unsigned long long)cap_links);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += stride) {
+    const uint32_t a = b.lk_cells[i];
+    if (a == kHole || !b.has_out[a]) continue;
+    const uint32_t h0 = b.cell_in[a], h1 = b.cell_out[a];
+    const float4 p0 = b.hit4[h0], p1 = b.hit4[h1];
+    const int L0 = b.cell_l0[a], L1 = (b.hbin[h1] / B) % kLayers;
+    const uint32_t off = b.link_off[a], cnt = b.link_cnt[a];
+    for (uint32_t l = off; l < off + cnt; ++l) {
+      const uint32_t h2 = b.cell_out[b.link_dst[l]];
+      float f[kGateFeat];
+      link_features(cuts, p0, p1, b.hit4[h2], L0, L1, (b.hbin[h2] / B) % kLayers, f);
+      if (F32) {
+#pragma unroll
+        for (int k = 0; k < kGateFeat; ++k) out32[(uint64_t)l * kGateFeat + k] = f[k];
+      } else {
+        uint4 lo, hi;
+        lo.x = pack_bf16(f[0], f[1]);
+        lo.y = pack_bf16(f[2], f[3]);
+        lo.z = pack_bf16(f[4], f[5]);
+        lo.w = pack_bf16(f[6], f[7]);
+        hi.x = pack_bf16(f[8], f[9]);
+        hi.y = pack_bf16(f[10], f[11]);
+        hi.z = 0;
+        hi.w = 0;
+        uint4* dst = (uint4*)(b.gate_x + (uint64_t)l * kGateK1);
+        dst[0] = lo;
+        dst[1] = hi;
+      }
+    }
+  }
+}
+
+// float32 feature rows -> bf16 rows padded to 16.
+__global__ void k_gate_pack(const float* feat, int64_t n, uint16_t* X) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const float* f = feat + r * kGateFeat;
+    uint4 lo, hi;
+    lo.x = pack_bf16(f[0], f[1]);
+    lo.y = pack_bf16(f[2], f[3]);
+    lo.z = pack_bf16(f[4], f[5]);
+    lo.w = pack_bf16(f[6], f[7]);
+    hi.x = pack_bf16(f[8], f[9]);
+    hi.y = pack_bf16(f[10], f[11]);
+    hi.z = 0;
+    hi.w = 0;
+    uint4* dst = (uint4*)(X + r * kGateK1);
+    dst[0] = lo;
+    dst[1] = hi;
+  }
+}
+
+// Clears the incoming-link flags of every current link target.
+__global__ void k_gate_clear_in(Buffers b, uint64_t cap_links) {
+  const uint64_t nl = min(b.cnt[CNT_LKCELLS], (unsigned long long)cap_links);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += stride) {
+    const uint32_t a = b.lk_cells[i];
+    if (a == kHole || !b.has_out[a]) continue;
+    const uint32_t off = b.link_off[a], cnt = b.link_cnt[a];
+    for (uint32_t l = off; l < off + cnt; ++l) b.has_in[b.link_dst[l]] = 0;
+  }
+}
+
+// Keeps, in order, the links that pass the gate; flags follow the kept links only.
+__global__ void k_gate_apply(Buffers b, uint64_t cap_links) {
+  const uint64_t nl = min(b.cnt[CNT_LKCELLS], (unsigned long long)cap_links);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  unsigned long long kept_total = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += stride) {
+    const uint32_t a = b.lk_cells[i];
+    if (a == kHole || !b.has_out[a]) continue;
+    const uint32_t off = b.link_off[a], cnt = b.link_cnt[a];
+    uint32_t k = 0;
+    for (uint32_t l = off; l < off + cnt; ++l) {
+      if (!b.gate_keep[l]) continue;
+      const uint32_t dst = b.link_dst[l];
+      b.link_dst[off + k] = dst;
+      b.link_q[off + k] = b.link_q[l];
+      b.gate_score[off + k] = b.gate_score[l];
+      b.has_in[dst] = 1;
+      ++k;
+    }
+    b.link_cnt[a] = k;
+    b.has_out[a] = k > 0;
+    kept_total += k;
+  }
+  if (kept_total) atomicAdd(&b.cnt[CNT_GATE_KEPT], kept_total);
+}
+
+}  // namespace
+
+cudaError_t gate_prepare() {
+  return cudaFuncSetAttribute(k_gate_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, kMlpSmem);
+}
+
+void launch_gate(const Buffers& b, const Params& p, const Launch& l, const GateWeights* w,
+                 cudaStream_t s) {
+  k_gate_features<false><<<l.grid, 256, 0, s>>>(b, p.cuts, p.phi_bins, (uint64_t)p.max_links,
+                                                 nullptr);
+  k_gate_mlp<<<l.sms * 4, kTileM, kMlpSmem, s>>>(w, b.gate_x, &b.cnt[CNT_LINKS], p.max_links,
+                                                   b.gate_score, b.gate_keep, &b.cnt[CNT_STATUS]);
+  k_gate_clear_in<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links);
+  k_gate_apply<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links);
+}
+
+void launch_gate_score(const GateWeights* w, const float* feat, int64_t n, float* out,
+                       uint16_t* xbuf, unsigned long long* status, int sms, cudaStream_t s) {
+  k_gate_pack<<<sms * 4, 256, 0, s>>>(feat, n, xbuf);
+  k_gate_mlp<<<sms * 4, kTileM, kMlpSmem, s>>>(w, xbuf, nullptr, n, out, nullptr, status);
+}
+
+void launch_export_link_features(const Buffers& b, const Params& p, const Launch& l,
+                                 float* out, cudaStream_t s) {
+  k_gate_features<true><<<l.grid, 256, 0, s>>>(b, p.cuts, p.phi_bins, (uint64_t)p.max_links, out);
+}
+
+}  // namespace ptca

@@ -44,6 +44,23 @@ enum : unsigned long long {
   ST_LINKS = 2ull,
   ST_NT = 4ull,
   ST_LAYER = 8ull,
+  ST_GATE_TIMEOUT = 16ull,  // a bounded wait in the gate kernel expired
+};
+
+// Gate parameters on the device: W1 and W2 as bf16 in the tensor-core operand layout,
+// biases and the last layer in float32.
+constexpr int kGateFeat = 12;
+constexpr int kGateK1 = 16;   // layer-1 K padded to the MMA K
+constexpr int kGateHidden = 64;
+constexpr int kGateParams = 5057;
+struct GateWeights {
+  uint16_t w1[kGateHidden * kGateK1];      // core-matrix layout, see gate.cu
+  uint16_t w2[kGateHidden * kGateHidden];  // core-matrix layout
+  float b1[kGateHidden];
+  float b2[kGateHidden];
+  float w3[kGateHidden];
+  float b3;
+  float tau;
 };
 
 // Cells leaving one hit towards one outer layer: [off, off + cnt) of the cell arrays,
@@ -123,6 +140,10 @@ struct Buffers {
   uint32_t* sv;              // [max_ntuplets] survivor -> sorted position
   int64_t* ev_nt_off;        // [max_events + 1]
   pt_track* tracks;          // [max_ntuplets]
+  // learned gate (valid when enabled)
+  uint16_t* gate_x;          // [max_links*16] bf16 features per link slot (12 used)
+  float* gate_score;         // [max_links] logit per link slot
+  uint8_t* gate_keep;        // [max_links] 1 where the link passes the gate
   int32_t* exp_hits;         // [max_ntuplets*6] export staging (event-local indices)
   uint8_t* exp_n;            // [max_ntuplets]
   float* exp_q;              // [max_ntuplets]
@@ -150,6 +171,22 @@ void launch_fit(const Buffers& b, const Params& p, const Launch& l, cudaStream_t
 // scan of n+1 entries: out[i] = sum(in[0..i)), n = *n_dev
 void launch_scan(const uint32_t* in, uint32_t* out, const unsigned long long* n_dev,
                  uint32_t* part, cudaStream_t s);
+// learned gate: features, tensor-core MLP and link pruning (enabled contexts only);
+// gate_prepare() sets the MLP kernel's shared-memory attribute (call before capture)
+cudaError_t gate_prepare();
+void launch_gate(const Buffers& b, const Params& p, const Launch& l, const GateWeights* w,
+                 cudaStream_t s);
+// scores of n feature rows (float32 [n][12], device) with the gate's MLP -> out [n]
+void launch_gate_score(const GateWeights* w, const float* feat, int64_t n, float* out,
+                       uint16_t* xbuf, unsigned long long* status, int sms, cudaStream_t s);
+// float32 features of the current links -> out [slots][12] (hole rows untouched)
+void launch_export_link_features(const Buffers& b, const Params& p, const Launch& l,
+                                 float* out, cudaStream_t s);
+// gate training: mean BCE loss and its gradient (zeroed first); Adam step
+cudaError_t launch_gate_grad(const float* w, const float* X, const float* y, int64_t n,
+                             float* grad, float* loss, int sms, cudaStream_t s);
+cudaError_t launch_gate_adam(float* w, float* m, float* v, const float* g, int64_t n, float lr,
+                             float b1, float b2, float eps, int step, cudaStream_t s);
 // exports with event-local input indices
 void launch_export_ntuplets(const Buffers& b, const Launch& l, cudaStream_t s);
 void launch_export_candidates(const Buffers& b, const Launch& l, cudaStream_t s);

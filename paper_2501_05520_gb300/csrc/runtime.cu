@@ -3,6 +3,7 @@
 // whole batch, result export and error reporting.
 #include <cstdarg>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -41,7 +42,7 @@ pt_status fail(pt_status st, const char* fmt, ...) {
 constexpr size_t kAlign = 256;
 
 // Carves the workspace; with base == nullptr only computes the size.
-size_t layout(const pt_capacity& c, char* base, Buffers* b) {
+size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate = nullptr) {
   size_t off = 0;
   auto take = [&](size_t bytes) -> char* {
     off = (off + kAlign - 1) / kAlign * kAlign;
@@ -99,11 +100,16 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b) {
   t.sv = (uint32_t*)take(T * 4);
   t.ev_nt_off = (int64_t*)take((E + 1) * 8);
   t.tracks = (pt_track*)take(T * sizeof(pt_track));
+  t.gate_x = (uint16_t*)take(L * 16 * 2);
+  t.gate_score = (float*)take(L * 4);
+  t.gate_keep = (uint8_t*)take(L);
   t.exp_hits = (int32_t*)take(T * kMaxHits * 4);
   t.exp_n = (uint8_t*)take(T);
   t.exp_q = (float*)take(T * 4);
   t.exp_ev = (int32_t*)take(T * 4);
   t.scan_part = (uint32_t*)take((kScanBlocks + 1) * 4);
+  if (gate) *gate = (GateWeights*)take(sizeof(GateWeights));
+  else take(sizeof(GateWeights));
   if (b) *b = t;
   return (off + kAlign - 1) / kAlign * kAlign;
 }
@@ -152,6 +158,9 @@ struct pt_ctx {
   // validation staging, allocated on first use
   char* val = nullptr;
   size_t val_bytes = 0;
+  // learned gate
+  GateWeights* gate = nullptr;  // device, inside the workspace
+  bool gate_on = false;
 };
 
 namespace {
@@ -180,6 +189,8 @@ pt_status sync_counters(pt_ctx* c) {
   PT_CUDA(cudaStreamSynchronize(c->stream));
   const unsigned long long st = c->h_cnt[CNT_STATUS];
   if (st & ST_LAYER) return fail(PT_ERR_INVALID, "input contains a layer code > 9");
+  if (st & ST_GATE_TIMEOUT)
+    return fail(PT_ERR_TIMEOUT, "a bounded wait of the gate's tensor-core kernel expired");
   if (st & ST_CELLS)
     return fail(PT_ERR_CAPACITY,
                 "max_cells = %lld is too small: about %llu cell slots needed (cells plus "
@@ -246,6 +257,7 @@ void enqueue_pipeline(pt_ctx* c, cudaStream_t s) {
   launch_bin_hits(c->B, c->P, c->L, s);
   launch_doublets(c->B, c->P, c->L, s);
   launch_connect(c->B, c->P, c->L, s);
+  if (c->gate_on) launch_gate(c->B, c->P, c->L, c->gate, s);
   launch_ntuplets(c->B, c->P, c->L, s);
   launch_fit(c->B, c->P, c->L, s);
   launch_export_ntuplets(c->B, c->L, s);
@@ -365,7 +377,7 @@ pt_status pt_create(const pt_geometry* geom, const pt_cuts* cuts, const pt_capac
     c->ws_bytes = need;
     c->own_ws = true;
   }
-  layout(*cap, c->ws, &c->B);
+  layout(*cap, c->ws, &c->B, &c->gate);
   if (cudaMallocHost(&c->h_off, (cap->max_events + 1) * 4) != cudaSuccess ||
       cudaMallocHost(&c->h_hdr, sizeof(BatchHeader)) != cudaSuccess ||
       cudaMallocHost(&c->h_cnt, CNT_N * 8) != cudaSuccess)
@@ -452,6 +464,11 @@ pt_status pt_build_doublets(pt_ctx* c, int64_t* n_cells) {
 }
 
 pt_status pt_connect_cells(pt_ctx* c, int64_t* n_links) {
+  if (c && c->gate_on) {
+    STAGE_BODY((launch_connect(c->B, c->P, c->L, c->stream),
+                launch_gate(c->B, c->P, c->L, c->gate, c->stream)),
+               CNT_GATE_KEPT, n_links)
+  }
   STAGE_BODY(launch_connect(c->B, c->P, c->L, c->stream), CNT_LINKS_USED, n_links)
 }
 
@@ -535,7 +552,7 @@ pt_status pt_get_links(pt_ctx* c, int32_t* h0, int32_t* h1, int32_t* h2, float* 
   PT_TRY(need_loaded(c));
   DeviceGuard guard(c->device);
   PT_TRY(sync_counters(c));
-  const int64_t Lk = (int64_t)c->h_cnt[CNT_LINKS_USED];
+  const int64_t Lk = c->gate_on ? (int64_t)c->h_cnt[CNT_GATE_KEPT] : (int64_t)c->h_cnt[CNT_LINKS_USED];
   int64_t slots = (int64_t)c->h_cnt[CNT_LINKS];
   if (slots > c->cap.max_links) slots = c->cap.max_links;
   if (n) *n = Lk;
@@ -583,6 +600,133 @@ pt_status pt_get_candidates(pt_ctx* c, int32_t* hits, uint8_t* nhits, float* q, 
   PT_TRY(copy_out(c, q, c->B.exp_q, (size_t)T * 4, 0));
   PT_TRY(copy_out(c, event, c->B.exp_ev, (size_t)T * 4, 0));
   PT_CUDA(cudaStreamSynchronize(c->stream));
+  return PT_OK;
+}
+
+pt_status pt_set_gate(pt_ctx* c, const float* w, float tau) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  DeviceGuard guard(c->device);
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  if (!w) {
+    c->gate_on = false;
+    return PT_OK;
+  }
+  for (int i = 0; i < kGateParams; ++i)
+    if (!std::isfinite(w[i])) return fail(PT_ERR_INVALID, "gate parameter %d is not finite", i);
+  if (!std::isfinite(tau)) return fail(PT_ERR_INVALID, "tau is not finite");
+  GateWeights h{};
+  const float* W1 = w;
+  const float* b1 = W1 + kGateHidden * kGateFeat;
+  const float* W2 = b1 + kGateHidden;
+  const float* b2 = W2 + kGateHidden * kGateHidden;
+  const float* w3 = b2 + kGateHidden;
+  const float b3 = w3[kGateHidden];
+  // bf16 (round to nearest even) in the core-matrix operand layout: element (row, k) of an
+  // R x K operand at ((row/8) * (K/8) + k/8) * 64 + (row%8) * 8 + k%8 (16-bit units)
+  auto bf16 = [](float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+  };
+  auto cm = [](int row, int k, int K) {
+    return (size_t)((row >> 3) * (K / 8) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+  };
+  for (int n = 0; n < kGateHidden; ++n) {
+    for (int k = 0; k < kGateK1; ++k)
+      h.w1[cm(n, k, kGateK1)] = k < kGateFeat ? bf16(W1[n * kGateFeat + k]) : (uint16_t)0;
+    for (int k = 0; k < kGateHidden; ++k) h.w2[cm(n, k, kGateHidden)] = bf16(W2[n * kGateHidden + k]);
+    h.b1[n] = b1[n];
+    h.b2[n] = b2[n];
+    h.w3[n] = w3[n];
+  }
+  h.b3 = b3;
+  h.tau = tau;
+  PT_CUDA(gate_prepare());
+  PT_CUDA(cudaMemcpy(c->gate, &h, sizeof(h), cudaMemcpyHostToDevice));
+  c->gate_on = true;
+  return PT_OK;
+}
+
+pt_status pt_get_link_features(pt_ctx* c, float* feat, int32_t* h0, int32_t* h1, int32_t* h2,
+                               int32_t* event, float* score, int64_t cap, int64_t* n) {
+  g_err.clear();
+  PT_TRY(need_loaded(c));
+  DeviceGuard guard(c->device);
+  PT_TRY(sync_counters(c));
+  const int64_t Lk = c->gate_on ? (int64_t)c->h_cnt[CNT_GATE_KEPT] : (int64_t)c->h_cnt[CNT_LINKS_USED];
+  int64_t slots = (int64_t)c->h_cnt[CNT_LINKS];
+  if (slots > c->cap.max_links) slots = c->cap.max_links;
+  if (n) *n = Lk;
+  if (cap < Lk) return fail(PT_ERR_CAPACITY, "output capacity %lld < %lld links", (long long)cap,
+                            (long long)Lk);
+  if (Lk == 0) return PT_OK;
+  PT_TRY(val_staging(c, (size_t)slots * (16 + 4 + 48)));
+  int32_t* o4 = (int32_t*)c->val;
+  float* oq = (float*)(c->val + (size_t)slots * 16);
+  float* of = (float*)(c->val + (size_t)slots * 20);
+  PT_CUDA(cudaMemsetAsync(o4, 0xff, (size_t)slots * 16, c->stream));
+  launch_export_links(c->B, c->P, c->L, o4, oq, c->stream);
+  launch_export_link_features(c->B, c->P, c->L, of, c->stream);
+  PT_TRY(last_launch());
+  std::vector<int32_t> t4((size_t)slots * 4);
+  std::vector<float> tf((size_t)slots * 12), ts((size_t)slots);
+  PT_CUDA(cudaMemcpyAsync(t4.data(), o4, (size_t)slots * 16, cudaMemcpyDeviceToHost, c->stream));
+  PT_CUDA(cudaMemcpyAsync(tf.data(), of, (size_t)slots * 48, cudaMemcpyDeviceToHost, c->stream));
+  if (c->gate_on)
+    PT_CUDA(cudaMemcpyAsync(ts.data(), c->B.gate_score, (size_t)slots * 4, cudaMemcpyDeviceToHost,
+                            c->stream));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  int64_t k = 0;
+  for (int64_t i = 0; i < slots && k < Lk; ++i) {
+    if (t4[i * 4 + 3] < 0) continue;  // hole or removed link
+    if (h0) h0[k] = t4[i * 4];
+    if (h1) h1[k] = t4[i * 4 + 1];
+    if (h2) h2[k] = t4[i * 4 + 2];
+    if (event) event[k] = t4[i * 4 + 3];
+    if (feat) std::memcpy(feat + k * 12, &tf[i * 12], 48);
+    if (score) score[k] = c->gate_on ? ts[i] : std::nanf("");
+    ++k;
+  }
+  return PT_OK;
+}
+
+pt_status pt_gate_score(pt_ctx* c, const float* feat, int64_t n, float* out) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  if (!c->gate_on) return fail(PT_ERR_INVALID, "no gate set (pt_set_gate)");
+  if (n < 0 || n > c->cap.max_links)
+    return fail(PT_ERR_CAPACITY, "n must be in [0, max_links = %lld]", (long long)c->cap.max_links);
+  if (n == 0) return PT_OK;
+  if (!feat || !out) return fail(PT_ERR_INVALID, "feat and out must not be NULL");
+  DeviceGuard guard(c->device);
+  launch_gate_score(c->gate, feat, n, out, c->B.gate_x, &c->B.cnt[CNT_STATUS], c->L.sms, c->stream);
+  PT_TRY(last_launch());
+  PT_TRY(sync_counters(c));
+  return PT_OK;
+}
+
+pt_status pt_gate_loss_grad(const float* w, const float* x, const float* y, int64_t n,
+                            float* grad, float* loss, void* stream) {
+  g_err.clear();
+  if (!w || !grad || !loss || (n > 0 && (!x || !y)) || n < 0)
+    return fail(PT_ERR_INVALID, "bad argument");
+  int dev = 0, sms = 0;
+  PT_CUDA(cudaGetDevice(&dev));
+  PT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PT_CUDA(launch_gate_grad(w, x, y, n, grad, loss, sms, (cudaStream_t)stream));
+  return PT_OK;
+}
+
+pt_status pt_gate_adam(float* w, float* m, float* v, const float* grad, int64_t n, float lr,
+                       float beta1, float beta2, float eps, int step, void* stream) {
+  g_err.clear();
+  if (!w || !m || !v || !grad || n < 0 || step < 1) return fail(PT_ERR_INVALID, "bad argument");
+  PT_CUDA(launch_gate_adam(w, m, v, grad, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream));
   return PT_OK;
 }
 

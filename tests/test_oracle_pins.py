@@ -326,3 +326,26 @@ def test_config1_efficiency(cuts):
         res = oracle.reconstruct(e.x, e.y, e.z, e.layer, cuts)
         eff.append(truth.rates(oracle.survivors_hits(res), e.pid, e.layer)["efficiency"])
     assert np.mean(eff) >= 0.99
+
+
+def test_masked_links_give_paths_of_the_kept_graph(cuts):
+    """With a link mask the ntuplets are the root-to-leaf paths of the graph of kept
+    links only (roots and leaves taken in that graph), and an all-true mask changes
+    nothing."""
+    e = sim.generate(sim.PU50, 2500, n_particles=500)
+    plain = oracle.reconstruct(e.x, e.y, e.z, e.layer, cuts)
+    same = oracle.reconstruct(e.x, e.y, e.z, e.layer, cuts,
+                              link_keep=np.ones(plain["link_a"].size, bool))
+    assert np.array_equal(oracle.survivors_hits(plain), oracle.survivors_hits(same))
+    keep = np.random.default_rng(1).random(plain["link_a"].size) < 0.6
+    res = oracle.reconstruct(e.x, e.y, e.z, e.layer, cuts, link_keep=keep)
+    assert res["link_a"].size == keep.sum()
+    G = nx.DiGraph()
+    G.add_nodes_from(range(plain["cell_inner"].size))
+    G.add_edges_from(zip(plain["link_a"][keep].tolist(), plain["link_b"][keep].tolist()))
+    leaves = [v for v in G if G.out_degree(v) == 0]
+    exp = set()
+    for root in (v for v in G if G.in_degree(v) == 0 and G.out_degree(v) > 0):
+        exp.update(tuple(p) for p in nx.all_simple_paths(G, root, leaves))
+    got = {tuple(res["nt_cells"][t][: res["nt_n"][t] - 1].tolist()) for t in range(res["nt_n"].size)}
+    assert got == exp and len(exp) > 50
