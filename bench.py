@@ -182,6 +182,53 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed(ctx, dbat, steps, flush, stream):
+    """K steps of the stage path with CUDA events between the stages; L2 flushed
+    before each step outside its events.  Returns per-step stage times (ms)."""
+    import torch
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(steps)]
+    for s_ in range(steps):
+        flush.zero_()
+        off, x, y, z, layer = dbat[s_ % 2]
+        e = evs[s_]
+        e[0].record(stream)
+        ctx.pt_load_batch(off, x, y, z, layer)
+        e[1].record(stream)
+        ctx.pt_build_doublets(sync=False)
+        e[2].record(stream)
+        ctx.pt_connect_cells(sync=False)
+        e[3].record(stream)
+        ctx.pt_find_ntuplets(sync=False)
+        e[4].record(stream)
+        ctx.pt_fit_tracks(sync=False)
+        e[5].record(stream)
+    stream.synchronize()
+    names = ["load", "doublets", "connect", "ntuplets", "fit"]
+    stage = {n: [e[k].elapsed_time(e[k + 1]) for e in evs] for k, n in enumerate(names)}
+    step = [e[0].elapsed_time(e[5]) for e in evs]
+    return step, stage
+
+
+def _physics(ctx, host, events):
+    """Efficiency, fake and duplicate rates of the cleaned ntuplets (generator truth)."""
+    from sim import truth
+    tot = dict(reco=0, matched=0.0, fake=0, nt=0, dup=0.0)
+    for bi, h in enumerate(host):
+        hits, nh, tr, eoff = ctx.pt_reconstruct_batch(*h)
+        for e in range(len(eoff) - 1):
+            ev = events[bi * (len(eoff) - 1) + e]
+            r = truth.rates_fast(hits[eoff[e]:eoff[e + 1]], ev.pid, ev.layer)
+            tot["reco"] += r["n_reconstructable"]
+            tot["matched"] += r["efficiency"] * r["n_reconstructable"]
+            tot["dup"] += r["duplicate_rate"] * r["n_reconstructable"]
+            tot["fake"] += r["n_fake"]
+            tot["nt"] += r["n_ntuplets"]
+    return {"efficiency": tot["matched"] / max(tot["reco"], 1),
+            "fake_rate": tot["fake"] / max(tot["nt"], 1),
+            "duplicate_rate": tot["dup"] / max(tot["reco"], 1),
+            "n_fake": tot["fake"], "n_ntuplets": tot["nt"], "events": len(events)}
+
+
 def run_ours(args):
     import torch
     import paper_2501_05520_gb300 as pt
@@ -199,89 +246,76 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)
     ctx = pt.Context(capacity=capacity(B, args.phi_bins), device=local, stream=stream)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-
-    def step_stages(i, evs):
-        off, x, y, z, layer = dbat[i % 2]
-        evs[0].record(stream)
-        ctx.pt_load_batch(off, x, y, z, layer)
-        evs[1].record(stream)
-        ctx.pt_build_doublets(sync=False)
-        evs[2].record(stream)
-        ctx.pt_connect_cells(sync=False)
-        evs[3].record(stream)
-        ctx.pt_find_ntuplets(sync=False)
-        evs[4].record(stream)
-        ctx.pt_fit_tracks(sync=False)
-        evs[5].record(stream)
-
-    with torch.cuda.stream(stream):
-        for i in range(args.warmup):
-            off, x, y, z, layer = dbat[i % 2]
-            ctx.pt_enqueue_batch(off, x, y, z, layer)
-        stream.synchronize()
-        ctx.pt_get_ntuplets()  # raises on any capacity or input error
-        # counts of one batch for the bytes model
-        off, x, y, z, layer = dbat[0]
-        ctx.pt_load_batch(off, x, y, z, layer)
-        counts = dict(hits=int(off[-1]), cells=ctx.pt_build_doublets(),
-                      links=ctx.pt_connect_cells(), survivors=ctx.pt_find_ntuplets())
-        counts["candidates"] = int(ctx.pt_get_candidates()[0].shape[0])
-        ctx.pt_fit_tracks()
-
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        with Clocks(local) as clk:
-            for s in range(args.steps):
-                flush.zero_()
-                step_stages(s, evs[s])
+    gw, gtau = pt.default_gate()
+    forms = {}
+    counts = None
+    clocks = None
+    for form in ("plain", "gated"):
+        ctx.pt_set_gate(gw if form == "gated" else None, gtau)
+        with torch.cuda.stream(stream):
+            for i in range(args.warmup):
+                off, x, y, z, layer = dbat[i % 2]
+                ctx.pt_enqueue_batch(off, x, y, z, layer)
             stream.synchronize()
-        torch.cuda.synchronize(dev)
+            ctx.pt_get_ntuplets()  # raises on any capacity or input error
+            if form == "plain":
+                off, x, y, z, layer = dbat[0]
+                ctx.pt_load_batch(off, x, y, z, layer)
+                counts = dict(hits=int(off[-1]), cells=ctx.pt_build_doublets(),
+                              links=ctx.pt_connect_cells(), survivors=ctx.pt_find_ntuplets())
+                counts["candidates"] = int(ctx.pt_get_candidates()[0].shape[0])
+                ctx.pt_fit_tracks()
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            if form == "plain":
+                with Clocks(local) as clk:
+                    step_ms, stage_ms = _timed(ctx, dbat, args.steps, flush, stream)
+                clocks = clk.summary()
+            else:
+                step_ms, stage_ms = _timed(ctx, dbat, args.steps, flush, stream)
+            torch.cuda.synchronize(dev)
+            if dist:
+                dist.barrier()
+            ctx.pt_get_ntuplets()
+        total_s = sum(step_ms) / 1000.0
         if dist:
-            dist.barrier()
-        ctx.pt_get_ntuplets()
-    clocks = clk.summary()
-    names = ["load", "doublets", "connect", "ntuplets", "fit"]
-    stage_ms = {n: [] for n in names}
-    step_ms = []
-    for e in evs:
-        step_ms.append(e[0].elapsed_time(e[5]))
-        for k, n in enumerate(names):
-            stage_ms[n].append(e[k].elapsed_time(e[k + 1]))
-    total_s = sum(step_ms) / 1000.0
-    if dist:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * B * args.steps / total_s
+            t = torch.tensor([total_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_s = float(t.item())
+        # end to end through the public call: pinned host in, host out
+        pin = [torch.from_numpy(a).pin_memory() for a in host[0][1:]]
+        capn = int(ctx.capacity["max_ntuplets"])
+        out = dict(hits=torch.empty((capn, 6), dtype=torch.int32).pin_memory(),
+                   nhits=torch.empty(capn, dtype=torch.uint8).pin_memory(),
+                   tracks=torch.empty((capn, 36), dtype=torch.uint8).pin_memory(),
+                   event_offsets=torch.empty(B + 1, dtype=torch.int64).pin_memory())
+        e2e_t = []
+        S = 0
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            h, _, _, _ = ctx.pt_reconstruct_batch(host[0][0], *pin, out=out)
+            S = int(h.shape[0])
+            if i >= args.warmup:
+                e2e_t.append(time.perf_counter() - t0)
+        e2e_s = sum(e2e_t)
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        forms[form] = dict(
+            value=world * B * args.steps / total_s, ms_per_step=1000.0 * total_s / args.steps,
+            p99_ms_per_step=float(np.percentile(step_ms, 99)),
+            stages_ms={n: round(statistics.mean(v), 4) for n, v in stage_ms.items()},
+            e2e={"value": world * B * args.steps / e2e_s, "unit": "events/s",
+                 "h2d_bytes_per_step": int(host[0][0][-1]) * 13 + (B + 1) * 4 + 8,
+                 "d2h_bytes_per_step": S * (24 + 1 + 36) + (B + 1) * 8 + 128},
+            physics=_physics(ctx, host, events) if not args.no_physics else None)
+    ctx.pt_set_gate(None, 0.0)
 
-    # end to end through the public call: pinned host in, host out
-    pin = [torch.from_numpy(a).pin_memory() for a in host[0][1:]]
-    capn = int(ctx.capacity["max_ntuplets"])
-    out = dict(hits=torch.empty((capn, 6), dtype=torch.int32).pin_memory(),
-               nhits=torch.empty(capn, dtype=torch.uint8).pin_memory(),
-               tracks=torch.empty((capn, 36), dtype=torch.uint8).pin_memory(),
-               event_offsets=torch.empty(B + 1, dtype=torch.int64).pin_memory())
-    e2e_t = []
-    S = 0
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        h, _, _, _ = ctx.pt_reconstruct_batch(host[0][0], *pin, out=out)
-        S = int(h.shape[0])
-        if i >= args.warmup:
-            e2e_t.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    n_hits = int(host[0][0][-1])
-    h2d = n_hits * 13 + (B + 1) * 4 + 8
-    d2h = S * (24 + 1 + 36) + (B + 1) * 8 + 128
-
-    # roofline of the dominant kernel
-    mean_stage = {n: statistics.mean(v) for n, v in stage_ms.items()}
+    # roofline of the dominant kernel of the plain form
+    plain = forms["plain"]
+    mean_stage = plain["stages_ms"]
     dom = max(("doublets", "connect"), key=lambda n: mean_stage[n])
     ab = algorithmic_bytes(counts["hits"], counts["cells"], counts["links"], counts["candidates"],
                            counts["survivors"])
@@ -292,18 +326,21 @@ def run_ours(args):
                 "traffic": None, "peak_src": peaks["src"], "algorithmic_bytes": ab[dom]}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+        line = {"metric": METRIC, "value": plain["value"], "unit": "events/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "ms_per_step": plain["ms_per_step"], "p99_ms_per_step": plain["p99_ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
                 "config": {"workload": WORKLOAD, "events_per_step": B, "form": "plain",
                            "phi_bins": args.phi_bins,
                            "l2": "flushed before every step (256 MB write, outside the events)",
                            "parallelism": f"replicas x{world}"},
-                "e2e": {"value": world * B * args.steps / e2e_s, "unit": "events/s",
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "e2e": plain["e2e"],
                 "roofline": roofline,
-                "stages_ms": {n: round(v, 4) for n, v in mean_stage.items()},
+                "stages_ms": plain["stages_ms"],
+                "gated": {k: forms["gated"][k] for k in ("value", "ms_per_step", "p99_ms_per_step",
+                                                         "stages_ms", "e2e")},
+                "physics": {"plain": plain["physics"], "gated": forms["gated"]["physics"]},
                 "counts_per_step": counts,
                 "clocks": clocks,
                 "gpu_launches": LAUNCHES_PER_STEP * args.steps}
@@ -324,6 +361,7 @@ def main():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--phi-bins", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-physics", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -123,6 +123,15 @@ def default_cuts(which: str = "pt_min_0p45") -> dict:
     return {k: d[k] for k, _ in PtCuts._fields_}
 
 
+GATE_FILE = os.path.join(_PKG, "params", "gate_v1.npz")
+
+
+def default_gate():
+    """(weights float32 [5057], tau) of the trained gate shipped with the library."""
+    d = np.load(GATE_FILE)
+    return d["w"].astype(np.float32), float(d["tau"])
+
+
 def default_capacity(max_events: int = 1, hits_per_event: int = 65536,
                      cells_per_event: int = 4 << 20, links_per_event: int = 1 << 20,
                      ntuplets_per_event: int = 1 << 19, phi_bins: int = 256) -> dict:

@@ -40,6 +40,7 @@ __global__ void k_in_scatter(Buffers b, uint64_t cap_cells) {
   }
 }
 
+template <bool GATE>
 __global__ void __launch_bounds__(kConnWarps * 32, 5)
     k_connect(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap_links) {
   __shared__ float4 st_p2[kConnWarps][kOutStage];
@@ -57,6 +58,10 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
   auto mark_hole = [&](unsigned long long lo, unsigned long long hi) {
     hi = min(hi, (unsigned long long)cap_links);
     for (unsigned long long i = lo + lane; i < hi; i += 32) b.lk_cells[i] = kHole;
+  };
+  auto mark_link_hole = [&](unsigned long long lo, unsigned long long hi) {
+    hi = min(hi, (unsigned long long)cap_links);
+    for (unsigned long long i = lo + lane; i < hi; i += 32) b.link_src[i] = kHole;
   };
 
   for (uint32_t h1 = blockIdx.x * kConnWarps + wib; h1 < n_sorted; h1 += nwarps) {
@@ -142,7 +147,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
             } else if (found >= kLocalLinks) {
               b.link_dst[wbase + found] = c;
               b.link_q[wbase + found] = q;
-              b.has_in[c] = 1;
+              if (GATE) b.link_src[wbase + found] = a;
+              else b.has_in[c] = 1;
             }
             ++found;
           }
@@ -158,6 +164,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
       if (tot > 0) {
         unsigned long long hlo, hhi;
         wbase = chunk_take(lch, &b.cnt[CNT_LINKS], tot, &hlo, &hhi);
+        if (GATE) mark_link_hole(hlo, hhi);
         lbase = chunk_take(kch, &b.cnt[CNT_LKCELLS], __popc(has), &hlo, &hhi);
         mark_hole(hlo, hhi);
         used += tot;
@@ -168,16 +175,19 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
         if (base + nlk > cap_links || li >= cap_links) {
           atomicOr(&b.cnt[CNT_STATUS], ST_LINKS);
           if (li < cap_links) b.lk_cells[li] = kHole;  // keep the list readable
+          if (GATE)
+            for (uint64_t i = base; i < base + nlk && i < cap_links; ++i) b.link_src[i] = kHole;
         } else {
           b.link_off[a] = (uint32_t)base;
           b.link_cnt[a] = nlk;
-          b.has_out[a] = 1;
+          if (!GATE) b.has_out[a] = 1;  // gated form: set by the gate for kept links
           b.lk_cells[li] = a;
           const uint32_t nl = nlk < kLocalLinks ? nlk : kLocalLinks;
           for (uint32_t i = 0; i < nl; ++i) {
             b.link_dst[base + i] = lb[i];
             b.link_q[base + i] = lq[i];
-            b.has_in[lb[i]] = 1;
+            if (GATE) b.link_src[base + i] = a;
+            else b.has_in[lb[i]] = 1;
           }
           if (nlk > kLocalLinks) scan(true, base);
         }
@@ -186,15 +196,22 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
     __syncwarp();
   }
   mark_hole(kch.next, kch.end);
+  if (GATE) mark_link_hole(lch.next, lch.end);
   if (lane == 0 && used) atomicAdd(&b.cnt[CNT_LINKS_USED], used);
 }
 
 }  // namespace
 
-void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s) {
+void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
+                    bool gated) {
   launch_scan(b.in_cnt, b.in_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s);
   k_in_scatter<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_cells);
-  k_connect<<<l.sms * 5, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins, (uint64_t)p.max_links);
+  if (gated)
+    k_connect<true><<<l.sms * 5, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
+                                                          (uint64_t)p.max_links);
+  else
+    k_connect<false><<<l.sms * 5, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
+                                                           (uint64_t)p.max_links);
 }
 
 }  // namespace ptca

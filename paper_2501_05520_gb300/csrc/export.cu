@@ -59,7 +59,8 @@ __global__ void k_export_cells(Buffers b, uint64_t cap_cells, int32_t* out3) {
   }
 }
 
-__global__ void k_export_links(Buffers b, uint64_t cap_cells, int32_t* out4, float* outq) {
+__global__ void k_export_links(Buffers b, uint64_t cap_cells, int32_t* out4, float* outq,
+                               bool gated) {
   const uint64_t nc = min(b.cnt[CNT_CELLS], (unsigned long long)cap_cells);
   const int E = b.hdr->n_events;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -72,6 +73,7 @@ __global__ void k_export_links(Buffers b, uint64_t cap_cells, int32_t* out4, flo
     const uint32_t l0 = b.link_off[a];
     for (uint32_t i = 0; i < n; ++i) {
       const uint32_t l = l0 + i;
+      if (gated && !b.gate_keep[l]) continue;
       const int32_t g2 = (int32_t)b.perm[b.cell_out[b.link_dst[l]]];
       out4[(uint64_t)l * 4 + 0] = g0 - off;
       out4[(uint64_t)l * 4 + 1] = g1 - off;
@@ -95,8 +97,8 @@ void launch_export_cells(const Buffers& b, const Params& p, const Launch& l, int
   k_export_cells<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_cells, out3);
 }
 void launch_export_links(const Buffers& b, const Params& p, const Launch& l, int32_t* out4,
-                         float* outq, cudaStream_t s) {
-  k_export_links<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_cells, out4, outq);
+                         float* outq, cudaStream_t s, bool gated) {
+  k_export_links<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_cells, out4, outq, gated);
 }
 
 }  // namespace ptca

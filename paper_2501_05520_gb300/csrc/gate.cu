@@ -1,7 +1,9 @@
 // Learned link gate (optional stage after the cellular-automaton links): every accepted
-// link (h0 -> h1 -> h2) gets 12 geometric features, a 12 -> 64 -> 64 -> 1 MLP scores it
-// on the tensor cores, and links scoring below the threshold are removed before the
-// ntuplet search.  It plays the role of the edge-filtering MLP of the paper's ML
+// link (h0 -> h1 -> h2) gets 12 geometric features (computed by the MLP kernel from the
+// link's three hits while it fills its operand tile), a 12 -> 64 -> 64 -> 1 MLP scores
+// it on the tensor cores, and
+// links scoring below the threshold are skipped by the ntuplet search: the MLP's
+// epilogue sets the in/out flags of the cells of kept links only.  It plays the role of the edge-filtering MLP of the paper's ML
 // pipeline (Sec. 2.2.2: an MLP scores graph edges, a fixed threshold removes clearly
 // fake ones); the exact cuts stay in force, the gate only removes links.
 //
@@ -103,12 +105,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
-  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
-  return lo | (hi << 16);
-}
-
 // Shared-memory layout of the MLP kernel (bytes).
 constexpr int kOffX = 0;              // 128 x 16 bf16, SBO 256
 constexpr int kOffW1 = 4096;          // 64 x 16 bf16, SBO 256
@@ -120,9 +116,14 @@ constexpr int kOffTmem = 31752;       // TMEM base address
 constexpr int kOffFlag = 31756;       // wait status
 constexpr int kMlpSmem = 48 * 1024;   // requested: at most 4 CTAs per SM (TMEM 4 x 128 cols)
 
+// PIPE = true: rows are link slots of the batch; each thread gathers its link's three
+// hits and computes the features; kept links set the flags the ntuplet search reads.
+// PIPE = false: rows are given bf16 feature rows X (standalone scoring).
+template <bool PIPE>
 __global__ void __launch_bounds__(kTileM, 1)
-    k_gate_mlp(const GateWeights* gw, const uint16_t* X, const unsigned long long* n_dev,
-               int64_t n_max, float* score, uint8_t* keep, unsigned long long* status) {
+    k_gate_mlp(const GateWeights* gw, Buffers b, pt_cuts cuts, int32_t B, const uint16_t* X,
+               const unsigned long long* n_dev, int64_t n_max, float* score, uint8_t* keep,
+               unsigned long long* status, unsigned long long* kept) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5;
   float* sb1 = (float*)(sm + kOffF);
@@ -176,15 +177,42 @@ __global__ void __launch_bounds__(kTileM, 1)
   for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const uint64_t row = t * kTileM + tid;
     // X row -> core-matrix layout: k 0..7 at +0, k 8..15 at +128 within the row group
-    uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
-    if (row < n) {
-      const uint4* src = (const uint4*)(X + row * kGateK1);
-      lo = src[0];
-      hi = src[1];
-    }
     unsigned char* xr = sm + kOffX + (tid >> 3) * 256 + (tid & 7) * 16;
-    *(uint4*)xr = lo;
-    *(uint4*)(xr + 128) = hi;
+    uint32_t src_cell = kHole;
+    if (PIPE) {
+      float f[kGateFeat];
+#pragma unroll
+      for (int k = 0; k < kGateFeat; ++k) f[k] = 0.0f;
+      if (row < n) {
+        src_cell = b.link_src[row];
+        if (src_cell != kHole) {
+          const uint32_t h0 = b.cell_in[src_cell], h1 = b.cell_out[src_cell];
+          const uint32_t h2 = b.cell_out[b.link_dst[row]];
+          gate_link_features(cuts, b.hit4[h0], b.hit4[h1], b.hit4[h2], b.cell_l0[src_cell],
+                             (b.hbin[h1] / B) % kLayers, (b.hbin[h2] / B) % kLayers, f);
+        }
+      }
+      uint4 lo, hi;
+      lo.x = pack_bf16x2(f[0], f[1]);
+      lo.y = pack_bf16x2(f[2], f[3]);
+      lo.z = pack_bf16x2(f[4], f[5]);
+      lo.w = pack_bf16x2(f[6], f[7]);
+      hi.x = pack_bf16x2(f[8], f[9]);
+      hi.y = pack_bf16x2(f[10], f[11]);
+      hi.z = 0;
+      hi.w = 0;
+      *(uint4*)xr = lo;
+      *(uint4*)(xr + 128) = hi;
+    } else {
+      uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+      if (row < n) {
+        const uint4* srcp = (const uint4*)(X + row * kGateK1);
+        lo = srcp[0];
+        hi = srcp[1];
+      }
+      *(uint4*)xr = lo;
+      *(uint4*)(xr + 128) = hi;
+    }
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
@@ -211,10 +239,10 @@ __global__ void __launch_bounds__(kTileM, 1)
         for (int c = 0; c < 4; ++c) {  // 4 core matrices of 8 columns per half
           const int j0 = 32 * half + 8 * c;
           uint4 pk;
-          pk.x = pack_bf16(fmaxf(v[8 * c + 0] + sb1[j0 + 0], 0.f), fmaxf(v[8 * c + 1] + sb1[j0 + 1], 0.f));
-          pk.y = pack_bf16(fmaxf(v[8 * c + 2] + sb1[j0 + 2], 0.f), fmaxf(v[8 * c + 3] + sb1[j0 + 3], 0.f));
-          pk.z = pack_bf16(fmaxf(v[8 * c + 4] + sb1[j0 + 4], 0.f), fmaxf(v[8 * c + 5] + sb1[j0 + 5], 0.f));
-          pk.w = pack_bf16(fmaxf(v[8 * c + 6] + sb1[j0 + 6], 0.f), fmaxf(v[8 * c + 7] + sb1[j0 + 7], 0.f));
+          pk.x = pack_bf16x2(fmaxf(v[8 * c + 0] + sb1[j0 + 0], 0.f), fmaxf(v[8 * c + 1] + sb1[j0 + 1], 0.f));
+          pk.y = pack_bf16x2(fmaxf(v[8 * c + 2] + sb1[j0 + 2], 0.f), fmaxf(v[8 * c + 3] + sb1[j0 + 3], 0.f));
+          pk.z = pack_bf16x2(fmaxf(v[8 * c + 4] + sb1[j0 + 4], 0.f), fmaxf(v[8 * c + 5] + sb1[j0 + 5], 0.f));
+          pk.w = pack_bf16x2(fmaxf(v[8 * c + 6] + sb1[j0 + 6], 0.f), fmaxf(v[8 * c + 7] + sb1[j0 + 7], 0.f));
           *(uint4*)(hr + (j0 >> 3) * 128) = pk;
         }
       }
@@ -246,9 +274,24 @@ __global__ void __launch_bounds__(kTileM, 1)
 #pragma unroll
       for (int i = 0; i < 32; ++i) acc += fmaxf(v[i] + sb2[32 * half + i], 0.f) * sw3[32 * half + i];
     }
+    // pipeline form (src != NULL): row = link slot; kept links set the flags the
+    // ntuplet search reads (a link slot that is a hole is never kept)
+    bool kp = row < n && acc >= sc[1];
     if (row < n) {
+      if (PIPE) {
+        if (src_cell == kHole) {
+          kp = false;
+        } else if (kp) {
+          b.has_in[b.link_dst[row]] = 1;
+          b.has_out[src_cell] = 1;
+        }
+      }
       score[row] = acc;
-      if (keep) keep[row] = acc >= sc[1] ? 1 : 0;
+      if (keep) keep[row] = kp ? 1 : 0;
+    }
+    if (kept) {
+      const unsigned bal = __ballot_sync(kFull, kp);
+      if ((tid & 31) == 0 && bal) atomicAdd(kept, (unsigned long long)__popc(bal));
     }
     tc_before_sync();
     __syncthreads();
@@ -266,72 +309,25 @@ __global__ void __launch_bounds__(kTileM, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
 }
 
-// Features of one link from the hit coordinates and layers.
-__device__ __forceinline__ void link_features(const pt_cuts& c, float4 p0, float4 p1, float4 p2,
-                                              int L0, int L1, int L2, float (&f)[kGateFeat]) {
-  const float lc1 = fabsf((p1.z - p0.z) * (p2.w - p0.w) - (p2.z - p0.z) * (p1.w - p0.w));
-  const float rc1 = c.rz0 * (p2.w - p0.w) + c.rz1 * fabsf(p2.z - p0.z);
-  const float ax = p1.x - p0.x, ay = p1.y - p0.y, bx = p2.x - p0.x, by = p2.y - p0.y;
-  const float cx = p2.x - p1.x, cy = p2.y - p1.y;
-  const float a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
-  const float cr = ax * by - ay * bx;
-  const float kap = 2.0f * fabsf(cr) / (sqrtf(a2) * sqrtf(b2) * sqrtf(cx * cx + cy * cy));
-  const float D = 2.0f * cr;
-  const float ux = by * a2 - ay * b2, uy = ax * b2 - bx * a2;
-  const float num = (p0.x * p0.x + p0.y * p0.y) * D + 2.0f * (p0.x * ux + p0.y * uy);
-  const float px = p0.x * D + ux, py = p0.y * D + uy;
-  const float den = sqrtf(px * px + py * py) + sqrtf(ux * ux + uy * uy);
-  const float dmax = L0 == 0 ? c.dca_b0 : c.dca_other;
-  const float ta = (p1.z - p0.z) / (p1.w - p0.w);
-  const float tb = (p2.z - p1.z) / (p2.w - p1.w);
-  f[0] = lc1 / rc1;
-  f[1] = kap / c.kmax;
-  f[2] = fabsf(num) / den / dmax;
-  f[3] = ta / c.cotmax;
-  f[4] = 10.0f * (tb - ta);
-  f[5] = p0.w * (1.0f / 16.0f);
-  f[6] = p1.w * (1.0f / 16.0f);
-  f[7] = p2.w * (1.0f / 16.0f);
-  f[8] = (p0.z - p0.w * ta) / c.z0max;
-  f[9] = L0 * (1.0f / 9.0f);
-  f[10] = L1 * (1.0f / 9.0f);
-  f[11] = L2 * (1.0f / 9.0f);
-}
-
-// For every link of every cell with links: features -> bf16 row (or float32 row).
-template <bool F32>
-__global__ void k_gate_features(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap_links,
-                                float* out32) {
+// float32 features of every current link (gated form: kept links only), row = link slot.
+__global__ void k_gate_features_f32(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap_links,
+                                    bool gated, float* out) {
   const uint64_t nl = min(b.cnt[CNT_LKCELLS], (unsigned long long)cap_links);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += stride) {
     const uint32_t a = b.lk_cells[i];
-    if (a == kHole || !b.has_out[a]) continue;
+    if (a == kHole) continue;
     const uint32_t h0 = b.cell_in[a], h1 = b.cell_out[a];
     const float4 p0 = b.hit4[h0], p1 = b.hit4[h1];
     const int L0 = b.cell_l0[a], L1 = (b.hbin[h1] / B) % kLayers;
     const uint32_t off = b.link_off[a], cnt = b.link_cnt[a];
     for (uint32_t l = off; l < off + cnt; ++l) {
+      if (gated && !b.gate_keep[l]) continue;
       const uint32_t h2 = b.cell_out[b.link_dst[l]];
       float f[kGateFeat];
-      link_features(cuts, p0, p1, b.hit4[h2], L0, L1, (b.hbin[h2] / B) % kLayers, f);
-      if (F32) {
+      gate_link_features(cuts, p0, p1, b.hit4[h2], L0, L1, (b.hbin[h2] / B) % kLayers, f);
 #pragma unroll
-        for (int k = 0; k < kGateFeat; ++k) out32[(uint64_t)l * kGateFeat + k] = f[k];
-      } else {
-        uint4 lo, hi;
-        lo.x = pack_bf16(f[0], f[1]);
-        lo.y = pack_bf16(f[2], f[3]);
-        lo.z = pack_bf16(f[4], f[5]);
-        lo.w = pack_bf16(f[6], f[7]);
-        hi.x = pack_bf16(f[8], f[9]);
-        hi.y = pack_bf16(f[10], f[11]);
-        hi.z = 0;
-        hi.w = 0;
-        uint4* dst = (uint4*)(b.gate_x + (uint64_t)l * kGateK1);
-        dst[0] = lo;
-        dst[1] = hi;
-      }
+      for (int k = 0; k < kGateFeat; ++k) out[(uint64_t)l * kGateFeat + k] = f[k];
     }
   }
 }
@@ -340,85 +336,43 @@ __global__ void k_gate_features(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap
 __global__ void k_gate_pack(const float* feat, int64_t n, uint16_t* X) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
-    const float* f = feat + r * kGateFeat;
-    uint4 lo, hi;
-    lo.x = pack_bf16(f[0], f[1]);
-    lo.y = pack_bf16(f[2], f[3]);
-    lo.z = pack_bf16(f[4], f[5]);
-    lo.w = pack_bf16(f[6], f[7]);
-    hi.x = pack_bf16(f[8], f[9]);
-    hi.y = pack_bf16(f[10], f[11]);
-    hi.z = 0;
-    hi.w = 0;
-    uint4* dst = (uint4*)(X + r * kGateK1);
-    dst[0] = lo;
-    dst[1] = hi;
+    float f[kGateFeat];
+#pragma unroll
+    for (int k = 0; k < kGateFeat; ++k) f[k] = feat[r * kGateFeat + k];
+    store_gate_row(X + r * kGateK1, f);
   }
-}
-
-// Clears the incoming-link flags of every current link target.
-__global__ void k_gate_clear_in(Buffers b, uint64_t cap_links) {
-  const uint64_t nl = min(b.cnt[CNT_LKCELLS], (unsigned long long)cap_links);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += stride) {
-    const uint32_t a = b.lk_cells[i];
-    if (a == kHole || !b.has_out[a]) continue;
-    const uint32_t off = b.link_off[a], cnt = b.link_cnt[a];
-    for (uint32_t l = off; l < off + cnt; ++l) b.has_in[b.link_dst[l]] = 0;
-  }
-}
-
-// Keeps, in order, the links that pass the gate; flags follow the kept links only.
-__global__ void k_gate_apply(Buffers b, uint64_t cap_links) {
-  const uint64_t nl = min(b.cnt[CNT_LKCELLS], (unsigned long long)cap_links);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  unsigned long long kept_total = 0;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += stride) {
-    const uint32_t a = b.lk_cells[i];
-    if (a == kHole || !b.has_out[a]) continue;
-    const uint32_t off = b.link_off[a], cnt = b.link_cnt[a];
-    uint32_t k = 0;
-    for (uint32_t l = off; l < off + cnt; ++l) {
-      if (!b.gate_keep[l]) continue;
-      const uint32_t dst = b.link_dst[l];
-      b.link_dst[off + k] = dst;
-      b.link_q[off + k] = b.link_q[l];
-      b.gate_score[off + k] = b.gate_score[l];
-      b.has_in[dst] = 1;
-      ++k;
-    }
-    b.link_cnt[a] = k;
-    b.has_out[a] = k > 0;
-    kept_total += k;
-  }
-  if (kept_total) atomicAdd(&b.cnt[CNT_GATE_KEPT], kept_total);
 }
 
 }  // namespace
 
 cudaError_t gate_prepare() {
-  return cudaFuncSetAttribute(k_gate_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, kMlpSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_gate_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kMlpSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gate_mlp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kMlpSmem);
+  return e;
 }
 
 void launch_gate(const Buffers& b, const Params& p, const Launch& l, const GateWeights* w,
                  cudaStream_t s) {
-  k_gate_features<false><<<l.grid, 256, 0, s>>>(b, p.cuts, p.phi_bins, (uint64_t)p.max_links,
-                                                 nullptr);
-  k_gate_mlp<<<l.sms * 4, kTileM, kMlpSmem, s>>>(w, b.gate_x, &b.cnt[CNT_LINKS], p.max_links,
-                                                   b.gate_score, b.gate_keep, &b.cnt[CNT_STATUS]);
-  k_gate_clear_in<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links);
-  k_gate_apply<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links);
+  k_gate_mlp<true><<<l.sms * 4, kTileM, kMlpSmem, s>>>(w, b, p.cuts, p.phi_bins, nullptr,
+                                                         &b.cnt[CNT_LINKS], p.max_links,
+                                                         b.gate_score, b.gate_keep,
+                                                         &b.cnt[CNT_STATUS], &b.cnt[CNT_GATE_KEPT]);
 }
 
 void launch_gate_score(const GateWeights* w, const float* feat, int64_t n, float* out,
                        uint16_t* xbuf, unsigned long long* status, int sms, cudaStream_t s) {
   k_gate_pack<<<sms * 4, 256, 0, s>>>(feat, n, xbuf);
-  k_gate_mlp<<<sms * 4, kTileM, kMlpSmem, s>>>(w, xbuf, nullptr, n, out, nullptr, status);
+  k_gate_mlp<false><<<sms * 4, kTileM, kMlpSmem, s>>>(w, Buffers{}, pt_cuts{}, 1, xbuf, nullptr, n,
+                                                        out, nullptr, status, nullptr);
 }
 
-void launch_export_link_features(const Buffers& b, const Params& p, const Launch& l,
+void launch_export_link_features(const Buffers& b, const Params& p, const Launch& l, bool gated,
                                  float* out, cudaStream_t s) {
-  k_gate_features<true><<<l.grid, 256, 0, s>>>(b, p.cuts, p.phi_bins, (uint64_t)p.max_links, out);
+  k_gate_features_f32<<<l.grid, 256, 0, s>>>(b, p.cuts, p.phi_bins, (uint64_t)p.max_links, gated,
+                                              out);
 }
 
 }  // namespace ptca

@@ -26,7 +26,7 @@ namespace {
 
 // Depth-first walk from root a.  EMIT == false: returns the number of ntuplets;
 // EMIT == true: writes them at slots t0, t0 + 1, ... (slots >= cap_nt are dropped).
-template <bool EMIT>
+template <bool EMIT, bool GATED>
 __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, uint64_t cap_nt) {
   uint32_t path[kMaxCellsPerNt];
   uint32_t it[kMaxCellsPerNt], end[kMaxCellsPerNt];
@@ -45,6 +45,7 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
     }
     const uint32_t l = it[d]++;
     if (depth == kMaxCellsPerNt) continue;  // deeper than the layer graph allows
+    if (GATED && !b.gate_keep[l]) continue;  // removed by the learned gate
     const uint32_t c = b.link_dst[l];
     const float q = fadd(qs[d], b.link_q[l]);
     if (!b.has_out[c]) {
@@ -82,6 +83,7 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
 
 // One thread per root; each warp counts its roots' ntuplets, reserves them with one
 // atomic and walks again to write them.
+template <bool GATED>
 __global__ void __launch_bounds__(256)
     k_find_ntuplets(Buffers b, uint64_t cap_links, uint64_t cap_nt) {
   const uint64_t nl = min(b.cnt[CNT_LKCELLS], (unsigned long long)cap_links);
@@ -92,8 +94,8 @@ __global__ void __launch_bounds__(256)
     const uint64_t i = i0 + lane;
     uint32_t a = kHole;
     if (i < nl) a = b.lk_cells[i];
-    const bool root = a != kHole && !b.has_in[a];
-    const uint32_t n = root ? walk<false>(b, a, 0, cap_nt) : 0u;
+    const bool root = a != kHole && b.has_out[a] && !b.has_in[a];
+    const uint32_t n = root ? walk<false, GATED>(b, a, 0, cap_nt) : 0u;
     const uint32_t inc = warp_incl_scan(n);
     const uint32_t tot = __shfl_sync(kFull, inc, 31);
     if (tot == 0) continue;
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(256)
     if (lane == 31) base = atomicAdd(&b.cnt[CNT_NT], (unsigned long long)tot);
     base = __shfl_sync(kFull, base, 31);
     if (base + tot > cap_nt && lane == 31) atomicOr(&b.cnt[CNT_STATUS], ST_NT);
-    if (n) walk<true>(b, a, base + inc - n, cap_nt);
+    if (n) walk<true, GATED>(b, a, base + inc - n, cap_nt);
   }
 }
 
@@ -216,9 +218,11 @@ __global__ void k_event_offsets(Buffers b) {
 
 }  // namespace
 
-void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s) {
+void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
+                     bool gated) {
   const uint64_t cap_nt = (uint64_t)p.max_ntuplets;
-  k_find_ntuplets<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links, cap_nt);
+  if (gated) k_find_ntuplets<true><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links, cap_nt);
+  else k_find_ntuplets<false><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links, cap_nt);
   k_bucket_count<<<l.grid, 256, 0, s>>>(b, cap_nt);
   launch_scan(b.bucket_cnt, b.bucket_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s);
   k_bucket_scatter<<<l.grid, 256, 0, s>>>(b, cap_nt);

@@ -7,6 +7,7 @@
 // whatever the batch's hit, cell or link counts are.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -144,6 +145,8 @@ struct Buffers {
   uint16_t* gate_x;          // [max_links*16] bf16 features per link slot (12 used)
   float* gate_score;         // [max_links] logit per link slot
   uint8_t* gate_keep;        // [max_links] 1 where the link passes the gate
+  uint32_t* link_src;        // [max_links] source cell of each link slot (gated form),
+                             //   kHole for unused slots
   int32_t* exp_hits;         // [max_ntuplets*6] export staging (event-local indices)
   uint8_t* exp_n;            // [max_ntuplets]
   float* exp_q;              // [max_ntuplets]
@@ -165,8 +168,12 @@ void set_last_error(const char* msg);
 void launch_clear(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
 void launch_bin_hits(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
 void launch_doublets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
-void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
-void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
+// gated = true: the link search also writes each link's gate features and source cell,
+// and leaves the in/out flags to the gate (launch_gate)
+void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
+                    bool gated = false);
+void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
+                     bool gated = false);
 void launch_fit(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
 // scan of n+1 entries: out[i] = sum(in[0..i)), n = *n_dev
 void launch_scan(const uint32_t* in, uint32_t* out, const unsigned long long* n_dev,
@@ -179,8 +186,8 @@ void launch_gate(const Buffers& b, const Params& p, const Launch& l, const GateW
 // scores of n feature rows (float32 [n][12], device) with the gate's MLP -> out [n]
 void launch_gate_score(const GateWeights* w, const float* feat, int64_t n, float* out,
                        uint16_t* xbuf, unsigned long long* status, int sms, cudaStream_t s);
-// float32 features of the current links -> out [slots][12] (hole rows untouched)
-void launch_export_link_features(const Buffers& b, const Params& p, const Launch& l,
+// float32 features of the current links (gated: kept only) -> out [slots][12]
+void launch_export_link_features(const Buffers& b, const Params& p, const Launch& l, bool gated,
                                  float* out, cudaStream_t s);
 // gate training: mean BCE loss and its gradient (zeroed first); Adam step
 cudaError_t launch_gate_grad(const float* w, const float* X, const float* y, int64_t n,
@@ -194,7 +201,7 @@ void launch_export_candidates(const Buffers& b, const Launch& l, cudaStream_t s)
 void launch_export_cells(const Buffers& b, const Params& p, const Launch& l, int32_t* out3,
                          cudaStream_t s);
 void launch_export_links(const Buffers& b, const Params& p, const Launch& l, int32_t* out4,
-                         float* outq, cudaStream_t s);
+                         float* outq, cudaStream_t s, bool gated = false);
 
 // ------------------------------------------------------------ device helpers
 #ifdef __CUDACC__
@@ -260,6 +267,62 @@ __device__ __forceinline__ bool link_c23(const pt_cuts& c, float4 p0, bool first
 }
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Learned-gate features of link (h0 -> h1 -> h2) from the hit coordinates (x, y, z, r)
+// and layers: C1, C2, C3 cut ratios, t_a/cotmax, 10 (t_b - t_a), r0/16, r1/16, r2/16,
+// (z0 - r0 t_a)/z0max, layer0/9, layer1/9, layer2/9.
+__device__ __forceinline__ void gate_link_features(const pt_cuts& c, float4 p0, float4 p1,
+                                                   float4 p2, int L0, int L1, int L2,
+                                                   float (&f)[12]) {
+  const float lc1 = fabsf((p1.z - p0.z) * (p2.w - p0.w) - (p2.z - p0.z) * (p1.w - p0.w));
+  const float rc1 = c.rz0 * (p2.w - p0.w) + c.rz1 * fabsf(p2.z - p0.z);
+  const float ax = p1.x - p0.x, ay = p1.y - p0.y, bx = p2.x - p0.x, by = p2.y - p0.y;
+  const float cx = p2.x - p1.x, cy = p2.y - p1.y;
+  const float a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
+  const float cr = ax * by - ay * bx;
+  const float kap = 2.0f * fabsf(cr) / (sqrtf(a2) * sqrtf(b2) * sqrtf(cx * cx + cy * cy));
+  const float D = 2.0f * cr;
+  const float ux = by * a2 - ay * b2, uy = ax * b2 - bx * a2;
+  const float num = (p0.x * p0.x + p0.y * p0.y) * D + 2.0f * (p0.x * ux + p0.y * uy);
+  const float px = p0.x * D + ux, py = p0.y * D + uy;
+  const float den = sqrtf(px * px + py * py) + sqrtf(ux * ux + uy * uy);
+  const float dmax = L0 == 0 ? c.dca_b0 : c.dca_other;
+  const float ta = (p1.z - p0.z) / (p1.w - p0.w);
+  const float tb = (p2.z - p1.z) / (p2.w - p1.w);
+  f[0] = lc1 / rc1;
+  f[1] = kap / c.kmax;
+  f[2] = fabsf(num) / den / dmax;
+  f[3] = ta / c.cotmax;
+  f[4] = 10.0f * (tb - ta);
+  f[5] = p0.w * (1.0f / 16.0f);
+  f[6] = p1.w * (1.0f / 16.0f);
+  f[7] = p2.w * (1.0f / 16.0f);
+  f[8] = (p0.z - p0.w * ta) / c.z0max;
+  f[9] = L0 * (1.0f / 9.0f);
+  f[10] = L1 * (1.0f / 9.0f);
+  f[11] = L2 * (1.0f / 9.0f);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+  return lo | (hi << 16);
+}
+
+// Writes the 12 features as one bf16 row of 16 (4 zeros) = 32 bytes.
+__device__ __forceinline__ void store_gate_row(uint16_t* row, const float (&f)[12]) {
+  uint4 lo, hi;
+  lo.x = pack_bf16x2(f[0], f[1]);
+  lo.y = pack_bf16x2(f[2], f[3]);
+  lo.z = pack_bf16x2(f[4], f[5]);
+  lo.w = pack_bf16x2(f[6], f[7]);
+  hi.x = pack_bf16x2(f[8], f[9]);
+  hi.y = pack_bf16x2(f[10], f[11]);
+  hi.z = 0;
+  hi.w = 0;
+  ((uint4*)row)[0] = lo;
+  ((uint4*)row)[1] = hi;
+}
 
 // Order-preserving map float -> uint32 (monotone increasing, finite and infinite values).
 __device__ __forceinline__ uint32_t f2ord(float f) {

@@ -103,6 +103,7 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.gate_x = (uint16_t*)take(L * 16 * 2);
   t.gate_score = (float*)take(L * 4);
   t.gate_keep = (uint8_t*)take(L);
+  t.link_src = (uint32_t*)take(L * 4);
   t.exp_hits = (int32_t*)take(T * kMaxHits * 4);
   t.exp_n = (uint8_t*)take(T);
   t.exp_q = (float*)take(T * 4);
@@ -256,9 +257,9 @@ void enqueue_pipeline(pt_ctx* c, cudaStream_t s) {
   launch_clear(c->B, c->P, c->L, s);
   launch_bin_hits(c->B, c->P, c->L, s);
   launch_doublets(c->B, c->P, c->L, s);
-  launch_connect(c->B, c->P, c->L, s);
+  launch_connect(c->B, c->P, c->L, s, c->gate_on);
   if (c->gate_on) launch_gate(c->B, c->P, c->L, c->gate, s);
-  launch_ntuplets(c->B, c->P, c->L, s);
+  launch_ntuplets(c->B, c->P, c->L, s, c->gate_on);
   launch_fit(c->B, c->P, c->L, s);
   launch_export_ntuplets(c->B, c->L, s);
 }
@@ -465,7 +466,7 @@ pt_status pt_build_doublets(pt_ctx* c, int64_t* n_cells) {
 
 pt_status pt_connect_cells(pt_ctx* c, int64_t* n_links) {
   if (c && c->gate_on) {
-    STAGE_BODY((launch_connect(c->B, c->P, c->L, c->stream),
+    STAGE_BODY((launch_connect(c->B, c->P, c->L, c->stream, true),
                 launch_gate(c->B, c->P, c->L, c->gate, c->stream)),
                CNT_GATE_KEPT, n_links)
   }
@@ -473,7 +474,7 @@ pt_status pt_connect_cells(pt_ctx* c, int64_t* n_links) {
 }
 
 pt_status pt_find_ntuplets(pt_ctx* c, int64_t* n_ntuplets) {
-  STAGE_BODY(launch_ntuplets(c->B, c->P, c->L, c->stream), CNT_SV, n_ntuplets)
+  STAGE_BODY(launch_ntuplets(c->B, c->P, c->L, c->stream, c->gate_on), CNT_SV, n_ntuplets)
 }
 
 pt_status pt_fit_tracks(pt_ctx* c, int64_t* n_tracks) {
@@ -563,7 +564,7 @@ pt_status pt_get_links(pt_ctx* c, int32_t* h0, int32_t* h1, int32_t* h2, float* 
   int32_t* o4 = (int32_t*)c->val;
   float* oq = (float*)(c->val + (size_t)slots * 16);
   PT_CUDA(cudaMemsetAsync(o4, 0xff, (size_t)slots * 16, c->stream));
-  launch_export_links(c->B, c->P, c->L, o4, oq, c->stream);
+  launch_export_links(c->B, c->P, c->L, o4, oq, c->stream, c->gate_on);
   PT_TRY(last_launch());
   std::vector<int32_t> tmp((size_t)slots * 4);
   std::vector<float> tq((size_t)slots);
@@ -670,8 +671,8 @@ pt_status pt_get_link_features(pt_ctx* c, float* feat, int32_t* h0, int32_t* h1,
   float* oq = (float*)(c->val + (size_t)slots * 16);
   float* of = (float*)(c->val + (size_t)slots * 20);
   PT_CUDA(cudaMemsetAsync(o4, 0xff, (size_t)slots * 16, c->stream));
-  launch_export_links(c->B, c->P, c->L, o4, oq, c->stream);
-  launch_export_link_features(c->B, c->P, c->L, of, c->stream);
+  launch_export_links(c->B, c->P, c->L, o4, oq, c->stream, c->gate_on);
+  launch_export_link_features(c->B, c->P, c->L, c->gate_on, of, c->stream);
   PT_TRY(last_launch());
   std::vector<int32_t> t4((size_t)slots * 4);
   std::vector<float> tf((size_t)slots * 12), ts((size_t)slots);

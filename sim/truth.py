@@ -92,3 +92,37 @@ def true_triplets(pid: np.ndarray, layer: np.ndarray):
                     and (int(layer[b]), int(layer[d])) in _ALLOWED):
                 tri.append((a, b, d))
     return np.asarray(tri, np.int64).reshape(-1, 3)
+
+
+def link_labels(pid: np.ndarray, h0, h1, h2) -> np.ndarray:
+    """Training label of a cell link: 1 if its three hits come from one particle."""
+    pid = np.asarray(pid)
+    p0, p1, p2 = pid[h0], pid[h1], pid[h2]
+    return ((p0 >= 0) & (p0 == p1) & (p1 == p2)).astype(np.float32)
+
+
+def match_fast(ntuplets: np.ndarray, pid: np.ndarray) -> np.ndarray:
+    """Vectorised `match` with frac = 1: particle of each all-one-particle ntuplet, else -1."""
+    nt = np.asarray(ntuplets)
+    if nt.shape[0] == 0:
+        return np.zeros(0, np.int64)
+    valid = nt >= 0
+    p = np.where(valid, np.asarray(pid)[np.where(valid, nt, 0)], -2)
+    first = p[:, 0]
+    same = np.all((p == first[:, None]) | ~valid, axis=1) & (first >= 0)
+    return np.where(same, first, -1).astype(np.int64)
+
+
+def rates_fast(ntuplets: np.ndarray, pid: np.ndarray, layer: np.ndarray) -> dict:
+    """`rates` with frac = 1, vectorised over ntuplets."""
+    chains = particle_chains(pid, layer)
+    reco = np.array([p for p, c in chains.items() if c["chain"].size >= 3], np.int64)
+    m = match_fast(ntuplets, pid)
+    matched, counts = np.unique(m[m >= 0], return_counts=True)
+    hit = np.isin(reco, matched)
+    cnt = dict(zip(matched.tolist(), counts.tolist()))
+    dup = sum(1 for p in reco.tolist() if cnt.get(p, 0) > 1)
+    n = max(reco.size, 1)
+    return dict(efficiency=float(hit.sum()) / n, fake_rate=float(np.mean(m < 0)) if m.size else 0.0,
+                duplicate_rate=dup / n, n_reconstructable=int(reco.size),
+                n_ntuplets=int(m.size), n_fake=int(np.sum(m < 0)))

@@ -159,3 +159,37 @@ def test_gated_pipeline_matches_oracle(cuts):
     assert np.array_equal(got_nt, exp_nt)
     # scores reported for kept links are >= tau
     assert np.all(gs >= tau)
+
+
+def test_trained_gate_gain(cuts):
+    """The shipped gate (trained on the GPU by pt_gate_loss_grad / pt_gate_adam on links
+    of PU200 events with seeds 4_000_000+) against the plain CA on held-out PU200
+    events: efficiency within 0.5 percentage points, fewer fakes, fewer links."""
+    from sim import truth
+    w, tau = pt.default_gate()
+    events = [sim.generate(sim.PU200, 3000 + i) for i in range(12)]
+    off, x, y, z, layer = sim.concat(events)
+    cap = pt.default_capacity(max_events=len(events), hits_per_event=49152,
+                              cells_per_event=3_500_000, links_per_event=262_144,
+                              ntuplets_per_event=196_608)
+    res = {}
+    with pt.Context(cuts=cuts, capacity=cap) as ctx:
+        for form in ("plain", "gated"):
+            ctx.pt_set_gate(w if form == "gated" else None, tau)
+            ctx.pt_load_batch(off, x, y, z, layer)
+            ctx.pt_build_doublets()
+            links = ctx.pt_connect_cells()
+            ctx.pt_find_ntuplets()
+            hits, nh, eoff = ctx.pt_get_ntuplets()
+            eff = fake = nf = nt = 0.0
+            for e, ev in enumerate(events):
+                r = truth.rates_fast(hits[eoff[e]:eoff[e + 1]], ev.pid, ev.layer)
+                eff += r["efficiency"] * r["n_reconstructable"]
+                nf += r["n_fake"]
+                nt += r["n_ntuplets"]
+                fake += r["n_reconstructable"]
+            res[form] = dict(eff=eff / fake, fake=nf / nt, n_fake=nf, links=links)
+    p, g = res["plain"], res["gated"]
+    assert g["eff"] >= p["eff"] - 0.005, res
+    assert g["fake"] < p["fake"] and g["n_fake"] < p["n_fake"], res
+    assert g["links"] < 0.8 * p["links"], res
