@@ -229,6 +229,57 @@ def _physics(ctx, host, events):
             "n_fake": tot["fake"], "n_ntuplets": tot["nt"], "events": len(events)}
 
 
+def _serving(pt, rate: float, seconds: float, gate=None, threads: int = 16,
+             budget: int = 2 << 30, slots: int = 4) -> dict:
+    """Poisson arrivals of PU 50-200 events at `rate` events/s from `threads` clients into
+    a pt_server with a `budget`-byte device budget: latency percentiles and sustained
+    events/s (server clock, submit to result ready)."""
+    import threading
+    pus = sim.serving_pileups(6000, 96, 50, 200)
+    pool = [sim.pileup_event(6000 + i, int(pu)) for i, pu in enumerate(pus)]
+    with pt.Server(budget_bytes=budget, slots=slots) as srv:
+        if gate is not None:
+            srv.pt_server_set_gate(*gate)
+        for t in [srv.pt_submit(e.x, e.y, e.z, e.layer) for e in pool[:32]]:
+            srv.pt_poll(t, -1)
+        srv.pt_server_reset_stats()
+        per = max(1, int(rate * seconds) // threads)
+        t0 = time.perf_counter() + 0.05
+
+        def client(k):
+            rng = np.random.default_rng(100 + k)
+            nxt = t0
+            pending = []
+            for i in range(per):
+                nxt += rng.exponential(threads / rate)
+                d = nxt - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                e = pool[(k * per + i) % len(pool)]
+                pending.append(srv.pt_submit(e.x, e.y, e.z, e.layer))
+                while pending:
+                    try:
+                        srv.pt_poll(pending[0], 0)
+                        pending.pop(0)
+                    except pt.PtError as err:
+                        if err.status != pt.PT_ERR_NOT_READY:
+                            raise
+                        break
+            for t in pending:
+                srv.pt_poll(t, -1)
+
+        ths = [threading.Thread(target=client, args=(k,)) for k in range(threads)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        st = srv.pt_server_stats()
+    return {"offered_events_per_s": rate, "sustained_events_per_s": st["events_per_s"],
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "events": st["n_done"],
+            "clients": threads, "slots": slots, "budget_bytes": budget,
+            "workload": "PU uniform in [50, 200], 50 particles per unit, 2% noise"}
+
+
 def run_ours(args):
     import torch
     import paper_2501_05520_gb300 as pt
@@ -344,6 +395,10 @@ def run_ours(args):
                 "counts_per_step": counts,
                 "clocks": clocks,
                 "gpu_launches": LAUNCHES_PER_STEP * args.steps}
+        if not args.no_serving:
+            line["serving"] = {"plain": _serving(pt, args.serve_rate, args.serve_seconds),
+                               "gated": _serving(pt, args.serve_rate, args.serve_seconds,
+                                                 gate=(gw, gtau))}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -362,6 +417,9 @@ def main():
     ap.add_argument("--phi-bins", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-physics", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -265,6 +265,50 @@ pt_status pt_find_doublets_noalloc(const pt_cuts* cuts, int64_t n, const float* 
                                    int32_t* inner, int32_t* outer, int64_t cap, int64_t* n_out,
                                    void* stream);
 
+/* ------------------------------------------------------------------ serving */
+
+/* In-process request server: the as-a-service pattern of the paper (Sec. 1 Fig. 1 and
+ * Sec. 3: clients send events, the server batches requests, runs them on the GPU and
+ * returns the results; several requests are in flight at once, Sec. 3.2/4.2), without
+ * network or inference server.  Continuous batching: the device budget is split into
+ * max_slots slots (contexts with their own stream and workspace); a dispatcher thread
+ * fills every free slot with the longest prefix of the FIFO of submitted events that
+ * fits it (event count, hits, estimated cells ~ 1.6e-3 * hits^2), runs the whole chain
+ * for it as one CUDA graph, and returns each event's ntuplets and tracks to its ticket.
+ * Slots run concurrently; a batch that overflows its slot is re-run event by event.
+ * Results are identical to running each event alone.  All functions are thread-safe. */
+typedef struct pt_server pt_server;
+
+/* device_budget_bytes: device memory the server may use for its workspaces (each slot
+ * gets budget / max_slots); PT_ERR_NOMEM if one PU200-sized event does not fit a slot. */
+pt_status pt_server_create(const pt_geometry* geom, const pt_cuts* cuts, int device,
+                           size_t device_budget_bytes, int max_slots, pt_server** out);
+
+/* Learned gate for all slots (pt_set_gate semantics); waits until no batch runs. */
+pt_status pt_server_set_gate(pt_server* s, const float* w, float tau);
+
+/* Queue one event (host arrays, copied before returning; never waits for the GPU).
+ * PT_ERR_CAPACITY if the event cannot fit a slot, PT_ERR_INVALID for bad input. */
+pt_status pt_submit(pt_server* s, int64_t n, const float* x, const float* y, const float* z,
+                    const uint8_t* layer, uint64_t* ticket);
+
+/* Result of a ticket: waits up to timeout_us (0: no wait -> PT_ERR_NOT_READY; < 0:
+ * wait indefinitely; else PT_ERR_TIMEOUT when it expires).  On success the ticket is
+ * released and hits [cap][6] / nhits [cap] / tracks [cap] (host, any may be NULL)
+ * receive the event's cleaned ntuplets (canonical order) and tracks; *n their number.
+ * PT_ERR_CAPACITY (ticket kept, *n set) if cap is too small. */
+pt_status pt_poll(pt_server* s, uint64_t ticket, int64_t timeout_us, int32_t* hits,
+                  uint8_t* nhits, pt_track* tracks, int64_t cap, int64_t* n);
+
+/* Submit-to-ready latency percentiles (ms) and sustained events/s (completed events over
+ * the time from the first submit to the last completion) since creation or reset. */
+pt_status pt_server_stats(pt_server* s, double* p50_ms, double* p99_ms, double* events_per_s,
+                          int64_t* n_done);
+pt_status pt_server_reset_stats(pt_server* s);
+
+/* Stop accepting work, finish what is queued, free everything.  NULL ok. */
+pt_status pt_server_destroy(pt_server* s);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char* pt_last_error(void);
 

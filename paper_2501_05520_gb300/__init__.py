@@ -30,7 +30,9 @@ EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt
             "pt_fit_tracks", "pt_get_ntuplets", "pt_get_tracks", "pt_get_cells", "pt_get_links",
             "pt_get_candidates", "pt_reconstruct_batch", "pt_enqueue_batch",
             "pt_find_doublets_noalloc", "pt_set_gate", "pt_get_link_features", "pt_gate_score",
-            "pt_gate_loss_grad", "pt_gate_adam", "pt_last_error")
+            "pt_gate_loss_grad", "pt_gate_adam", "pt_server_create", "pt_server_set_gate",
+            "pt_submit", "pt_poll", "pt_server_stats", "pt_server_reset_stats",
+            "pt_server_destroy", "pt_last_error")
 
 
 class PtCuts(ctypes.Structure):
@@ -100,6 +102,15 @@ def lib() -> ctypes.CDLL:
             "pt_gate_loss_grad": [P, P, P, I64, P, P, P],
             "pt_gate_adam": [P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              ctypes.c_float, I32, P],
+            "pt_server_create": [ctypes.POINTER(PtGeometry), ctypes.POINTER(PtCuts), I32,
+                                 ctypes.c_size_t, I32, ctypes.POINTER(ctypes.c_void_p)],
+            "pt_server_set_gate": [P, P, ctypes.c_float],
+            "pt_submit": [P, I64, P, P, P, P, ctypes.POINTER(ctypes.c_uint64)],
+            "pt_poll": [P, ctypes.c_uint64, I64, P, P, P, I64, PI64],
+            "pt_server_stats": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double), PI64],
+            "pt_server_reset_stats": [P],
+            "pt_server_destroy": [P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -423,3 +434,74 @@ def pt_gate_adam(w, m, v, grad, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stre
                               ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
                               int(w.numel()), float(lr), float(beta1), float(beta2), float(eps),
                               int(step), ctypes.c_void_p(sp) if sp else None))
+
+
+class Server:
+    """pt_server: continuous-batching request server (thread-safe)."""
+
+    def __init__(self, cuts: dict | None = None, budget_bytes: int = 2 << 30, slots: int = 2,
+                 bfield: float = 3.8, device: int = 0):
+        self.cuts = dict(cuts or default_cuts())
+        h = ctypes.c_void_p(None)
+        _check(lib().pt_server_create(
+            ctypes.byref(PtGeometry(bfield)),
+            ctypes.byref(PtCuts(*(float(self.cuts[k]) for k, _ in PtCuts._fields_))), device,
+            int(budget_bytes), int(slots), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().pt_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def pt_server_set_gate(self, w, tau: float):
+        arr = None if w is None else np.ascontiguousarray(w, np.float32)
+        _check(lib().pt_server_set_gate(self.handle, None if arr is None else _hptr(arr),
+                                        float(tau)))
+
+    def pt_submit(self, x, y, z, layer) -> int:
+        xs = [np.ascontiguousarray(a, t) for a, t in ((x, np.float32), (y, np.float32),
+                                                     (z, np.float32), (layer, np.uint8))]
+        t = ctypes.c_uint64(0)
+        _check(lib().pt_submit(self.handle, xs[0].shape[0], *(_hptr(a) for a in xs),
+                               ctypes.byref(t)))
+        return int(t.value)
+
+    def pt_poll(self, ticket: int, timeout_us: int = -1):
+        """(hits [S,6], nhits [S], tracks [S]); raises PtError (e.g. PT_ERR_NOT_READY)."""
+        n = ctypes.c_int64(0)
+        st = lib().pt_poll(self.handle, ticket, int(timeout_us), None, None, None, 0,
+                           ctypes.byref(n))
+        if st == PT_OK:  # empty result, ticket released
+            return (np.empty((0, 6), np.int32), np.empty(0, np.uint8), np.zeros(0, TRACK_DTYPE))
+        if st != PT_ERR_CAPACITY:
+            _check(st)
+        S = int(n.value)
+        hits = np.empty((S, 6), np.int32)
+        nh = np.empty(S, np.uint8)
+        tr = np.zeros(S, TRACK_DTYPE)
+        _check(lib().pt_poll(self.handle, ticket, 0, _hptr(hits), _hptr(nh), _hptr(tr), S,
+                             ctypes.byref(n)))
+        return hits, nh, tr
+
+    def pt_server_stats(self) -> dict:
+        p50, p99, eps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64(0)
+        _check(lib().pt_server_stats(self.handle, ctypes.byref(p50), ctypes.byref(p99),
+                                     ctypes.byref(eps), ctypes.byref(n)))
+        return dict(p50_ms=p50.value, p99_ms=p99.value, events_per_s=eps.value, n_done=n.value)
+
+    def pt_server_reset_stats(self):
+        _check(lib().pt_server_reset_stats(self.handle))

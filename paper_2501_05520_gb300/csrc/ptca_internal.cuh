@@ -164,6 +164,15 @@ struct Launch {
 // Sets the calling thread's pt_last_error() message.
 void set_last_error(const char* msg);
 
+// Asynchronous pieces of a batch for the request server (runtime.cu): read-back of the
+// counters, status check of that copy, and copies of the cleaned ntuplets, tracks and
+// per-event offsets into host memory, each completion recorded on `done`.
+cudaStream_t ctx_stream(pt_ctx* c);
+pt_status ctx_counters_async(pt_ctx* c, cudaEvent_t done);
+pt_status ctx_read_counters(pt_ctx* c, int64_t* n_ntuplets);
+pt_status ctx_results_async(pt_ctx* c, int64_t S, int32_t* hits, uint8_t* nhits,
+                            pt_track* tracks, int64_t* event_offsets, cudaEvent_t done);
+
 // ------------------------------------------------------------------ launchers
 void launch_clear(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
 void launch_bin_hits(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);

@@ -184,10 +184,17 @@ pt_status last_launch() {
   return PT_OK;
 }
 
+pt_status check_status(pt_ctx* c);
+
 // Reads the device counters (synchronises the stream) and turns status bits into errors.
 pt_status sync_counters(pt_ctx* c) {
   PT_CUDA(cudaMemcpyAsync(c->h_cnt, c->B.cnt, CNT_N * 8, cudaMemcpyDeviceToHost, c->stream));
   PT_CUDA(cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+// Status bits of the host copy of the counters -> error.
+pt_status check_status(pt_ctx* c) {
   const unsigned long long st = c->h_cnt[CNT_STATUS];
   if (st & ST_LAYER) return fail(PT_ERR_INVALID, "input contains a layer code > 9");
   if (st & ST_GATE_TIMEOUT)
@@ -312,6 +319,32 @@ pt_status copy_out(pt_ctx* c, void* dst, const void* src, size_t bytes, int on_d
 
 namespace ptca {
 void set_last_error(const char* msg) { g_err = msg; }
+
+cudaStream_t ctx_stream(pt_ctx* c) { return c->stream; }
+
+pt_status ctx_counters_async(pt_ctx* c, cudaEvent_t done) {
+  DeviceGuard guard(c->device);
+  PT_CUDA(cudaMemcpyAsync(c->h_cnt, c->B.cnt, CNT_N * 8, cudaMemcpyDeviceToHost, c->stream));
+  PT_CUDA(cudaEventRecord(done, c->stream));
+  return PT_OK;
+}
+
+pt_status ctx_read_counters(pt_ctx* c, int64_t* n_ntuplets) {
+  PT_TRY(check_status(c));
+  *n_ntuplets = (int64_t)c->h_cnt[CNT_SV];
+  return PT_OK;
+}
+
+pt_status ctx_results_async(pt_ctx* c, int64_t S, int32_t* hits, uint8_t* nhits,
+                            pt_track* tracks, int64_t* event_offsets, cudaEvent_t done) {
+  DeviceGuard guard(c->device);
+  PT_TRY(copy_out(c, hits, c->B.exp_hits, (size_t)S * kMaxHits * 4, 0));
+  PT_TRY(copy_out(c, nhits, c->B.exp_n, (size_t)S, 0));
+  PT_TRY(copy_out(c, tracks, c->B.tracks, (size_t)S * sizeof(pt_track), 0));
+  PT_TRY(copy_out(c, event_offsets, c->B.ev_nt_off, (size_t)(c->n_events + 1) * 8, 0));
+  PT_CUDA(cudaEventRecord(done, c->stream));
+  return PT_OK;
+}
 }  // namespace ptca
 
 extern "C" {
