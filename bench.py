@@ -153,6 +153,26 @@ def _dist_env():
     return rank, world, local
 
 
+def rank_seed0(rank: int) -> int:
+    """First event seed of a rank: the replicas process disjoint synthetic event streams."""
+    return SEED0 + rank * 100_000
+
+
+def max_over_ranks(seconds: float, dist=None, device="cpu") -> float:
+    """The job's time is its slowest rank's (no-op on one process)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, events_per_step: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's events over the slowest rank's time."""
+    return world * events_per_step * steps / seconds
+
+
 def run_reference(args):
     rank, world, local = _dist_env()
     if rank != 0:
@@ -291,11 +311,21 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B = args.batch
-    events = make_events(2 * B, seed0=SEED0 + rank * 100_000)
+    events = make_events(2 * B, seed0=rank_seed0(rank))
     host = [sim.concat(events[:B]), sim.concat(events[B:])]
     dbat = [(h[0], *(torch.from_numpy(a).to(dev) for a in h[1:])) for h in host]
     stream = torch.cuda.Stream(dev)
-    ctx = pt.Context(capacity=capacity(B, args.phi_bins), device=local, stream=stream)
+    # azimuthal bins and launch sizes: measured on this batch unless all three are given
+    launch = dict(phi_bins=args.phi_bins, blocks_per_sm=args.blocks_per_sm,
+                  search_blocks_per_sm=args.search_blocks_per_sm, source="command line")
+    if not all(launch[k] for k in ("phi_bins", "blocks_per_sm", "search_blocks_per_sm")):
+        from paper_2501_05520_gb300 import autotune
+        t = autotune.tuned(*host[0], capacity(B), device=local)
+        launch = {k: args.__dict__[k] or t[k]
+                  for k in ("phi_bins", "blocks_per_sm", "search_blocks_per_sm")}
+        launch.update(source=f"autotuned ({t['source']})", table=t["table"])
+    ctx = pt.Context(capacity=capacity(B, launch["phi_bins"]), device=local, stream=stream)
+    ctx.pt_set_launch(launch["blocks_per_sm"], launch["search_blocks_per_sm"])
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     gw, gtau = pt.default_gate()
     forms = {}
@@ -329,11 +359,7 @@ def run_ours(args):
             if dist:
                 dist.barrier()
             ctx.pt_get_ntuplets()
-        total_s = sum(step_ms) / 1000.0
-        if dist:
-            t = torch.tensor([total_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_s = float(t.item())
+        total_s = max_over_ranks(sum(step_ms) / 1000.0, dist, dev)
         # end to end through the public call: pinned host in, host out
         pin = [torch.from_numpy(a).pin_memory() for a in host[0][1:]]
         capn = int(ctx.capacity["max_ntuplets"])
@@ -349,16 +375,12 @@ def run_ours(args):
             S = int(h.shape[0])
             if i >= args.warmup:
                 e2e_t.append(time.perf_counter() - t0)
-        e2e_s = sum(e2e_t)
-        if dist:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(sum(e2e_t), dist, dev)
         forms[form] = dict(
-            value=world * B * args.steps / total_s, ms_per_step=1000.0 * total_s / args.steps,
+            value=job_rate(world, B, args.steps, total_s), ms_per_step=1000.0 * total_s / args.steps,
             p99_ms_per_step=float(np.percentile(step_ms, 99)),
             stages_ms={n: round(statistics.mean(v), 4) for n, v in stage_ms.items()},
-            e2e={"value": world * B * args.steps / e2e_s, "unit": "events/s",
+            e2e={"value": job_rate(world, B, args.steps, e2e_s), "unit": "events/s",
                  "h2d_bytes_per_step": int(host[0][0][-1]) * 13 + (B + 1) * 4 + 8,
                  "d2h_bytes_per_step": S * (24 + 1 + 36) + (B + 1) * 8 + 128},
             physics=_physics(ctx, host, events) if not args.no_physics else None)
@@ -383,7 +405,10 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "events_per_step": B, "form": "plain",
-                           "phi_bins": args.phi_bins,
+                           "phi_bins": launch["phi_bins"],
+                           "blocks_per_sm": launch["blocks_per_sm"],
+                           "search_blocks_per_sm": launch["search_blocks_per_sm"],
+                           "tuning": launch["source"],
                            "l2": "flushed before every step (256 MB write, outside the events)",
                            "parallelism": f"replicas x{world}"},
                 "e2e": plain["e2e"],
@@ -393,6 +418,7 @@ def run_ours(args):
                                                          "stages_ms", "e2e")},
                 "physics": {"plain": plain["physics"], "gated": forms["gated"]["physics"]},
                 "counts_per_step": counts,
+                "autotune": launch,
                 "clocks": clocks,
                 "gpu_launches": LAUNCHES_PER_STEP * args.steps}
         if not args.no_serving:
@@ -414,7 +440,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--batch", type=int, default=BATCH)
-    ap.add_argument("--phi-bins", type=int, default=1024)
+    ap.add_argument("--phi-bins", type=int, default=0, help="0: autotuned")
+    ap.add_argument("--blocks-per-sm", type=int, default=0, help="0: autotuned")
+    ap.add_argument("--search-blocks-per-sm", type=int, default=0, help="0: autotuned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-physics", action="store_true")
     ap.add_argument("--no-serving", action="store_true")

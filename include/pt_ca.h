@@ -265,6 +265,34 @@ pt_status pt_find_doublets_noalloc(const pt_cuts* cuts, int64_t n, const float* 
                                    int32_t* inner, int32_t* outer, int64_t cap, int64_t* n_out,
                                    void* stream);
 
+/* ------------------------------------------------------------------ tuning */
+
+/* Launch sizes of the persistent grid-stride kernels, in blocks per multiprocessor
+ * (each 1..32): blocks_per_sm for the 256-thread bookkeeping kernels (clear, binning,
+ * scans, ntuplet walk, dedup, fit, export; default 4) and search_blocks_per_sm for the
+ * warp-per-hit doublet and connect searches (default 5, their residency limit).  Any
+ * value gives the same results.  Synchronises the stream; the next whole-batch call
+ * re-captures its graph. */
+pt_status pt_set_launch(pt_ctx* ctx, int blocks_per_sm, int search_blocks_per_sm);
+
+/* Autotuner for the batched chain.  For every candidate azimuthal bin count
+ * phi_bins[i] (context capacity otherwise as `cap`) it creates a context on `device`,
+ * copies the caller's sample batch (HOST arrays, pt_load_batch layout) to it once, and
+ * for every pair (blocks_per_sm[jb], search_blocks_per_sm[js]) of pt_set_launch sizes
+ * launches the whole chain (the pt_enqueue_batch graph, plain form) once to warm up
+ * and `reps` more times, timing each launch with CUDA events on the context's stream.  best[3] receives the
+ * combination with the smallest median (phi_bins, blocks_per_sm, search_blocks_per_sm);
+ * results (optional, n_phi * n_bps * n_sbps floats, index (i * n_bps + jb) * n_sbps + js)
+ * each median in ms.  Every combination gives the same ntuplets: the binning and the
+ * launch sizes only change how the work is spread.  Errors: PT_ERR_INVALID for empty
+ * candidate lists or reps < 1, and any error of pt_create or of the batch itself. */
+pt_status pt_autotune(const pt_geometry* geom, const pt_cuts* cuts, const pt_capacity* cap,
+                      int device, int n_events, const int64_t* hit_offsets, const float* x,
+                      const float* y, const float* z, const uint8_t* layer,
+                      const int32_t* phi_bins, int n_phi, const int32_t* blocks_per_sm,
+                      int n_bps, const int32_t* search_blocks_per_sm, int n_sbps, int reps,
+                      int32_t* best, float* results);
+
 /* ------------------------------------------------------------------ serving */
 
 /* In-process request server: the as-a-service pattern of the paper (Sec. 1 Fig. 1 and

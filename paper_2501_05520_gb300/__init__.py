@@ -32,7 +32,7 @@ EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt
             "pt_find_doublets_noalloc", "pt_set_gate", "pt_get_link_features", "pt_gate_score",
             "pt_gate_loss_grad", "pt_gate_adam", "pt_server_create", "pt_server_set_gate",
             "pt_submit", "pt_poll", "pt_server_stats", "pt_server_reset_stats",
-            "pt_server_destroy", "pt_last_error")
+            "pt_server_destroy", "pt_set_launch", "pt_autotune", "pt_last_error")
 
 
 class PtCuts(ctypes.Structure):
@@ -111,6 +111,10 @@ def lib() -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_double), PI64],
             "pt_server_reset_stats": [P],
             "pt_server_destroy": [P],
+            "pt_set_launch": [P, I32, I32],
+            "pt_autotune": [ctypes.POINTER(PtGeometry), ctypes.POINTER(PtCuts),
+                            ctypes.POINTER(PtCapacity), I32, I32, P, P, P, P, P, P, I32, P, I32,
+                            P, I32, I32, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -331,6 +335,9 @@ class Context:
                                        T, ctypes.byref(n)))
         return hits, nh, q, e
 
+    def pt_set_launch(self, blocks_per_sm: int = 4, search_blocks_per_sm: int = 5):
+        _check(lib().pt_set_launch(self.handle, int(blocks_per_sm), int(search_blocks_per_sm)))
+
     # -------------------------------------------------------------- learned gate
     def pt_set_gate(self, w, tau: float):
         """Enable the gate with 5057 float32 parameters (host), or disable it (w=None)."""
@@ -505,3 +512,27 @@ class Server:
 
     def pt_server_reset_stats(self):
         _check(lib().pt_server_reset_stats(self.handle))
+
+
+def pt_autotune(offsets, x, y, z, layer, capacity: dict, phi_bins=(256, 512, 1024, 2048),
+                blocks_per_sm=(2, 4, 8), search_blocks_per_sm=(3, 5, 8), reps: int = 3,
+                cuts: dict | None = None, bfield: float = 3.8, device: int = 0) -> dict:
+    """Fastest (phi_bins, blocks_per_sm, search_blocks_per_sm) for a sample batch given
+    as host arrays; `table` maps "PxBxS" to the median chain time in ms (pt_ca.h)."""
+    cuts = dict(cuts or default_cuts())
+    off = np.ascontiguousarray(offsets, np.int64)
+    arrs = [np.ascontiguousarray(a, t) for a, t in ((x, np.float32), (y, np.float32),
+                                                    (z, np.float32), (layer, np.uint8))]
+    pb, bp, sp = (np.ascontiguousarray(v, np.int32)
+                  for v in (phi_bins, blocks_per_sm, search_blocks_per_sm))
+    res = np.zeros(pb.size * bp.size * sp.size, np.float32)
+    best = np.zeros(3, np.int32)
+    _check(lib().pt_autotune(ctypes.byref(PtGeometry(bfield)),
+                             ctypes.byref(PtCuts(*(float(cuts[k]) for k, _ in PtCuts._fields_))),
+                             ctypes.byref(_cap(capacity)), device, off.size - 1, _hptr(off),
+                             *(_hptr(a) for a in arrs), _hptr(pb), pb.size, _hptr(bp), bp.size,
+                             _hptr(sp), sp.size, int(reps), _hptr(best), _hptr(res)))
+    keys = [f"{int(p)}x{int(b)}x{int(q)}" for p in pb for b in bp for q in sp]
+    return dict(phi_bins=int(best[0]), blocks_per_sm=int(best[1]),
+                search_blocks_per_sm=int(best[2]),
+                table={k: round(float(v), 4) for k, v in zip(keys, res)})

@@ -207,10 +207,10 @@ void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStre
   launch_scan(b.in_cnt, b.in_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s);
   k_in_scatter<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_cells);
   if (gated)
-    k_connect<true><<<l.sms * 5, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
+    k_connect<true><<<l.sgrid, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
                                                           (uint64_t)p.max_links);
   else
-    k_connect<false><<<l.sms * 5, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
+    k_connect<false><<<l.sgrid, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
                                                            (uint64_t)p.max_links);
 }
 

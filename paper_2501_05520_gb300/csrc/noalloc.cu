@@ -192,7 +192,7 @@ extern "C" pt_status pt_find_doublets_noalloc(const pt_cuts* cuts, int64_t n, co
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return na_fail(PT_ERR_CUDA, "cannot query the multiprocessor count", e);
-  Launch l{sms, sms * 4};
+  Launch l{sms, sms * 4, sms * 5};
   k_na_header<<<1, 32, 0, s>>>(b, (int32_t)n);
   launch_clear(b, p, l, s);  // zeroes the counters and histograms the last call left
   launch_bin_hits(b, p, l, s);

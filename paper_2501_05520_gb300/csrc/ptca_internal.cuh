@@ -159,6 +159,7 @@ constexpr int kScanBlocks = 256;
 struct Launch {
   int sms;         // multiprocessors
   int grid;        // generic persistent grid (blocks of 256 threads)
+  int sgrid;       // grid of the doublet and connect searches (warp per hit)
 };
 
 // Sets the calling thread's pt_last_error() message.

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -399,6 +400,7 @@ pt_status pt_create(const pt_geometry* geom, const pt_cuts* cuts, const pt_capac
     return bail(fail(PT_ERR_CUDA, "cannot query the multiprocessor count"));
   c->L.sms = sms;
   c->L.grid = sms * 4;
+  c->L.sgrid = sms * 5;
   if (workspace) {
     c->ws = (char*)workspace;
     c->ws_bytes = workspace_bytes;
@@ -761,6 +763,80 @@ pt_status pt_gate_adam(float* w, float* m, float* v, const float* grad, int64_t 
   g_err.clear();
   if (!w || !m || !v || !grad || n < 0 || step < 1) return fail(PT_ERR_INVALID, "bad argument");
   PT_CUDA(launch_gate_adam(w, m, v, grad, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream));
+  return PT_OK;
+}
+
+pt_status pt_set_launch(pt_ctx* c, int blocks_per_sm, int search_blocks_per_sm) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  if (blocks_per_sm < 1 || blocks_per_sm > 32 || search_blocks_per_sm < 1 ||
+      search_blocks_per_sm > 32)
+    return fail(PT_ERR_INVALID, "blocks per multiprocessor must be in [1, 32]");
+  DeviceGuard guard(c->device);
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->L.grid = c->L.sms * blocks_per_sm;
+  c->L.sgrid = c->L.sms * search_blocks_per_sm;
+  return PT_OK;
+}
+
+pt_status pt_autotune(const pt_geometry* geom, const pt_cuts* cuts, const pt_capacity* cap,
+                      int device, int n_events, const int64_t* hit_offsets, const float* x,
+                      const float* y, const float* z, const uint8_t* layer,
+                      const int32_t* phi_bins, int n_phi, const int32_t* blocks_per_sm,
+                      int n_bps, const int32_t* search_blocks_per_sm, int n_sbps, int reps,
+                      int32_t* best, float* results) {
+  g_err.clear();
+  if (!cap || !phi_bins || !blocks_per_sm || !search_blocks_per_sm || n_phi < 1 || n_bps < 1 ||
+      n_sbps < 1 || reps < 1 || !best)
+    return fail(PT_ERR_INVALID, "bad autotune arguments");
+  DeviceGuard guard(device);
+  float best_ms = 0.0f;
+  bool have = false;
+  for (int i = 0; i < n_phi; ++i) {
+    pt_capacity c = *cap;
+    c.phi_bins = phi_bins[i];
+    pt_ctx* ctx = nullptr;
+    PT_TRY(pt_create(geom, cuts, &c, device, nullptr, 0, nullptr, &ctx));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    pt_status st = stage_inputs(ctx, n_events, hit_offsets, x, y, z, layer, 0);
+    for (int j = 0; j < n_bps * n_sbps && st == PT_OK; ++j) {
+      const int jb = j / n_sbps, js = j % n_sbps;
+      st = pt_set_launch(ctx, blocks_per_sm[jb], search_blocks_per_sm[js]);
+      if (st == PT_OK) st = ensure_graph(ctx);
+      std::vector<float> t;
+      for (int r = 0; r <= reps && st == PT_OK; ++r) {  // run 0 is the warm-up
+        cudaEventRecord(e0, ctx->stream);
+        if (cudaGraphLaunch(ctx->graph, ctx->stream) != cudaSuccess)
+          st = fail(PT_ERR_CUDA, "graph launch failed");
+        cudaEventRecord(e1, ctx->stream);
+        if (st == PT_OK) st = sync_counters(ctx);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) t.push_back(ms);
+      }
+      if (st != PT_OK) break;
+      std::sort(t.begin(), t.end());
+      const float med = t[t.size() / 2];
+      if (results) results[(int64_t)i * n_bps * n_sbps + j] = med;
+      if (!have || med < best_ms) {
+        have = true;
+        best_ms = med;
+        best[0] = phi_bins[i];
+        best[1] = blocks_per_sm[jb];
+        best[2] = search_blocks_per_sm[js];
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pt_destroy(ctx);
+    if (st != PT_OK) return st;
+  }
   return PT_OK;
 }
 
