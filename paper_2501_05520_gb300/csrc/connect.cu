@@ -4,23 +4,25 @@
 // triplets by the cellular automaton).
 //
 // One warp per middle hit h1.  The cells leaving h1 (up to three segments, one per
-// outer layer, each sorted by r-z slope) are staged once in shared memory with the
-// coordinates of their outer hits; the cells ending on h1 (grouped by the ranks the
-// doublet stage took) are spread over the lanes.  Writing t_a, t_b for the slopes of a
-// and b, C1 reads
+// outer layer) are staged once in shared memory: their r-z slopes and the coordinates
+// of their outer hits.  The cells ending on h1 come from a per-hit list of 8-byte
+// records (cell, inner hit | inner-layer flag) and are taken 32 at a time, one per
+// lane.  Writing t_a, t_b for the slopes of a and b, C1 reads
 //   (r1-r0)(r2-r1)|t_a - t_b| <= rz0 (r2-r0) + rz1 |z2-z0|,
 // and with |t_b| <= cotmax (D4) and m = the smallest r2-r1 of the segment this gives
-//   |t_a - t_b| <= (rz0 + rz1 cotmax)/(r1-r0) + (rz0 + rz1 |t_a|)/m,
-// a window that a binary search over the staged slope keys turns into a sub-range.
-// The window is widened by 1 % + 1e-3: float32 rounding of C1 moves its bound by at
-// most ~4e-7 |t_a| (r1-r0)/m + 1e-6 and the 8 dropped key bits move a slope by at most
-// 3e-5 relative, both far inside the margin.  Every candidate in the window gets the
-// exact cuts, so the window only skips pairs that cannot pass.  Segments that were too
-// large to sort are scanned whole.
-//
-// The links of one cell are written contiguously (one warp-aggregated atomic per
-// warp), which is the out-link list the ntuplet search walks; cells with at least one
-// link are appended to a compact list, the only cells that can start an ntuplet.
+//   |t_a - t_b| <= (rz0 + rz1 cotmax)/(r1-r0) + (rz0 + rz1 |t_a|)/m.
+// The window is widened by 1 % + 1e-3, far beyond the float32 rounding of C1 (about
+// 4e-7 |t_a| (r1-r0)/m + 1e-6) and of the approximate reciprocals used for it.  The
+// warp sweeps the staged slopes four at a time, every lane testing its own cell against
+// them, with no divergence; a lane whose window holds any of the four queues one entry
+// (lane, 4-bit mask, position).  The queue is drained 32 entries at a time through the
+// exact cuts, all lanes busy.  The links found for the 32 cells are collected in shared
+// memory and written with one warp-aggregated reservation: the links of one cell are
+// contiguous (the out-link list the ntuplet search walks), and cells with at least one
+// link are appended to a compact list, the only cells that can start an ntuplet.  If a
+// group finds more links than the collection holds, the sweep runs a second time and
+// writes the remainder directly.  Segments larger than the stage are swept piece by
+// piece.
 #include "ptca_internal.cuh"
 
 namespace ptca {
@@ -28,33 +30,117 @@ namespace ptca {
 namespace {
 
 constexpr int kConnWarps = 8;
-constexpr int kOutStage = 224;  // staged outgoing cells per warp
+constexpr int kOutStage = 160;  // staged outgoing cells per warp (multiple of 4)
+constexpr int kQueue = 128;     // candidate ring per warp (power of two, >= 31 + 32)
+constexpr int kFound = 64;      // links of one group kept in shared memory (rank < 256)
+constexpr uint32_t kNoBase = 0xffffffffu;
+constexpr uint32_t kHitChunk = 4;       // consecutive middle hits per warp chunk (<= 32)
+constexpr int kScatterBlocksPerSm = 4;  // fewer warps in flight keep the scatter local
+static_assert(kOutStage / 4 <= 128, "queue entries hold the staged position / 4 in 7 bits");
 
-// in_list[in_start[h] + rank] = cell, grouping the cells by the hit they end on.
-__global__ void k_in_scatter(Buffers b, uint64_t cap_cells) {
-  const uint64_t nc = min(b.cnt[CNT_CELLS], (unsigned long long)cap_cells);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
-    const uint32_t o = b.cell_out[c];
-    if (o != kHole) b.in_list[b.in_start[o] + b.cell_inrank[c]] = (uint32_t)c;
+__device__ __forceinline__ uint32_t round4(uint32_t n) { return (n + 3u) & ~3u; }
+
+// in_rec[in_start[h] + rank] = (cell, inner hit | inner layer is 0 << 31), grouping the
+// cells by the hit they end on.  One warp per inner hit, in sorted-hit order: the warps
+// running at one time cover a narrow azimuthal range of a layer, so their records land
+// in a narrow range of in_rec and partial sectors merge in L2 before write-back.
+__global__ void k_in_scatter(Buffers b, int32_t B) {
+  const int lane = lane_id();
+  const int E = b.hdr->n_events;
+  const uint32_t n_sorted = b.bin_start[E * kLayers * B];
+  const int wpb = blockDim.x >> 5;
+  const int nwarps = gridDim.x * wpb;
+  for (uint32_t h0 = blockIdx.x * wpb + (threadIdx.x >> 5); h0 < n_sorted; h0 += nwarps) {
+    const Segment* sgp = b.seg + (uint64_t)h0 * kMaxOuter;
+    const uint32_t n0 = sgp[0].cnt, n1 = sgp[1].cnt, n2 = sgp[2].cnt;
+    const uint32_t n = n0 + n1 + n2;
+    if (n == 0) continue;
+    const uint32_t o0 = sgp[0].off, o1 = sgp[1].off, o2 = sgp[2].off;
+    const uint32_t tag = h0 | ((b.hbin[h0] / (uint32_t)B) % kLayers == 0 ? 0x80000000u : 0u);
+    for (uint32_t i0 = 0; i0 < n; i0 += 64) {
+      uint32_t c[2], o[2], rk[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t i = i0 + u * 32 + lane;
+        o[u] = kHole;
+        if (i < n) {
+          c[u] = i < n0 ? o0 + i : (i < n0 + n1 ? o1 + (i - n0) : o2 + (i - n0 - n1));
+          o[u] = b.cell_out[c[u]];
+          rk[u] = b.cell_inrank[c[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (o[u] != kHole) b.in_rec[b.in_start[o[u]] + rk[u]] = make_uint2(c[u], tag);
+    }
   }
+}
+
+// Per-warp shared state.  Warp-uniform values live here rather than in registers, so
+// that the sweep keeps only a lane's slope and window live.
+struct ConnWarp {
+  float4 p2[kOutStage];      // staged outgoing cells: outer hit
+  float t[kOutStage];        //   slope (NaN padding)
+  float4 p0[32];             // lane's incoming cell: inner hit
+  float4 p1;                 // middle hit
+  Segment sg[kMaxOuter];     // outgoing segments of the middle hit
+  uint32_t pos[kMaxOuter];   // staged position of each segment / piece
+  uint32_t coff[kMaxOuter];  // cell of each staged position pos[k]
+  unsigned long long chunk_next[2], chunk_end[2], used;  // link slots, root slots
+  uint32_t chunk_size[2];
+  uint32_t b0;               // lanes whose incoming cell starts on layer 0
+  uint32_t a[32], cnt[32], base[32];
+  uint32_t hin0[32], hnin[32];  // incoming-cell list of each hit of the warp's chunk
+  uint16_t q[kQueue];        // candidates: lane << 11 | mask << 7 | staged position / 4
+  uint32_t fc[kFound];       // found links: target cell
+  float fq[kFound];          //   quality
+  uint16_t fa[kFound];       //   lane << 8 | rank among the lane cell's links
+};
+
+// Warp chunk reservation with the chunk state in shared memory, lane 0 acting.
+__device__ __forceinline__ unsigned long long chunk_take_shared(
+    ConnWarp& W, int which, unsigned long long* counter, uint32_t n, unsigned long long* hlo,
+    unsigned long long* hhi) {
+  unsigned long long r = 0, lo = 0, hi = 0;
+  if ((threadIdx.x & 31) == 0) {
+    unsigned long long next = W.chunk_next[which], end = W.chunk_end[which];
+    if (next + n > end) {
+      lo = next;
+      hi = end;
+      uint32_t size = W.chunk_size[which];
+      const uint32_t want = size == 0 ? n : (n > size ? n : size);
+      W.chunk_size[which] = size == 0 ? (n > kChunkMin ? n : kChunkMin) : min(2 * size, kChunkMax);
+      next = atomicAdd(counter, (unsigned long long)want);
+      end = next + want;
+    }
+    r = next;
+    W.chunk_next[which] = next + n;
+    W.chunk_end[which] = end;
+  }
+  r = __shfl_sync(kFull, r, 0);
+  *hlo = __shfl_sync(kFull, lo, 0);
+  *hhi = __shfl_sync(kFull, hi, 0);
+  return r;
 }
 
 template <bool GATE>
 __global__ void __launch_bounds__(kConnWarps * 32, 5)
     k_connect(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap_links) {
-  __shared__ float4 st_p2[kConnWarps][kOutStage];
-  __shared__ uint32_t st_key[kConnWarps][kOutStage];
-  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  __shared__ ConnWarp s_w[kConnWarps];
+  const int lane = lane_id();
+  ConnWarp& W = s_w[threadIdx.x >> 5];
   const unsigned lt_mask = (1u << lane) - 1u;
-  float4* sp2 = st_p2[wib];
-  uint32_t* skey = st_key[wib];
+  const float kNaN = __int_as_float(0x7fc00000);
+  const float kInf = __int_as_float(0x7f800000);
   const int E = b.hdr->n_events;
   const uint32_t n_sorted = b.bin_start[E * kLayers * B];
-  const float wconst = fadd(cuts.rz0, fmul(cuts.rz1, cuts.cotmax));
   const int nwarps = gridDim.x * kConnWarps;
-  WarpChunk lch, kch;  // link slots, root-candidate slots
-  unsigned long long used = 0;
+  if (lane < 2) {
+    W.chunk_next[lane] = W.chunk_end[lane] = 0;
+    W.chunk_size[lane] = 0;
+  }
+  if (lane == 0) W.used = 0;
+  __syncwarp();
   auto mark_hole = [&](unsigned long long lo, unsigned long long hi) {
     hi = min(hi, (unsigned long long)cap_links);
     for (unsigned long long i = lo + lane; i < hi; i += 32) b.lk_cells[i] = kHole;
@@ -63,141 +149,253 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
     hi = min(hi, (unsigned long long)cap_links);
     for (unsigned long long i = lo + lane; i < hi; i += 32) b.link_src[i] = kHole;
   };
+  auto write_link = [&](uint64_t slot, uint32_t a, uint32_t c, float q) {
+    b.link_dst[slot] = c;
+    b.link_q[slot] = q;
+    if (GATE) b.link_src[slot] = a;
+    else b.has_in[c] = 1;
+  };
+  // stages cells [c0, c0 + n) leaving the middle hit p1 at position p (padded to a
+  // multiple of 4 with NaN slopes)
+  auto stage = [&](uint32_t c0, uint32_t n, uint32_t p, float4 p1) {
+    for (uint32_t i = lane; i < round4(n); i += 32) {
+      float t = kNaN;
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < n) {
+        q = b.hit4[b.cell_out[c0 + i]];
+        t = fdiv(fsub(q.z, p1.z), fsub(q.w, p1.w));
+      }
+      W.t[p + i] = t;
+      W.p2[p + i] = q;
+    }
+  };
 
-  for (uint32_t h1 = blockIdx.x * kConnWarps + wib; h1 < n_sorted; h1 += nwarps) {
-    const uint32_t in0 = b.in_start[h1], nin = b.in_start[h1 + 1] - in0;
-    if (nin == 0) continue;
-    Segment sg[kMaxOuter];
-    uint32_t sbase[kMaxOuter];
-    uint32_t nout = 0;
+  // chunks of kHitChunk consecutive middle hits per warp; one round of loads finds the
+  // hits with both incoming and outgoing cells
+  for (uint32_t hc = (blockIdx.x * kConnWarps + (threadIdx.x >> 5)) * kHitChunk; hc < n_sorted;
+       hc += (uint32_t)nwarps * kHitChunk) {
+    bool work = false;
+    {
+      const uint32_t hl = hc + lane;
+      uint32_t in0 = 0, nin = 0;
+      if ((uint32_t)lane < kHitChunk && hl < n_sorted) {
+        in0 = b.in_start[hl];
+        nin = b.in_start[hl + 1] - in0;
+        if (nin) {
+          const Segment* sgp = b.seg + (uint64_t)hl * kMaxOuter;
+          work = (sgp[0].cnt | sgp[1].cnt | sgp[2].cnt) != 0;
+        }
+      }
+      __syncwarp();
+      W.hin0[lane] = in0;
+      W.hnin[lane] = nin;
+    }
+    unsigned todo = __ballot_sync(kFull, work);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t h1 = hc + src;
+      const uint32_t in0 = W.hin0[src], nin = W.hnin[src];
+      uint32_t tot = 0;
+      {
+        const Segment* sgp = b.seg + (uint64_t)h1 * kMaxOuter;
 #pragma unroll
-    for (int k = 0; k < kMaxOuter; ++k) {
-      sg[k] = b.seg[(uint64_t)h1 * kMaxOuter + k];
-      sbase[k] = nout;
-      nout += sg[k].cnt;
-    }
-    if (nout == 0) continue;
-    const bool staged = nout <= (uint32_t)kOutStage;
-    if (staged) {
-      for (uint32_t i = lane; i < nout; i += 32) {
-        const int k = i < sbase[1] ? 0 : (i < sbase[2] ? 1 : 2);
-        const uint32_t c = sg[k].off + (i - sbase[k]);
-        skey[i] = b.cell_key[c];
-        sp2[i] = b.hit4[b.cell_out[c]];
+        for (int k = 0; k < kMaxOuter; ++k) tot += round4(sgp[k].cnt);
+        __syncwarp();
+        if (lane < kMaxOuter) {
+          const Segment g = sgp[lane];
+          W.sg[lane] = g;
+          uint32_t p = 0;
+          for (int k = 0; k < lane; ++k) p += round4(sgp[k].cnt);
+          W.pos[lane] = p;
+          W.coff[lane] = g.off;
+        }
+        if (lane == 0) W.p1 = b.hit4[h1];
+        __syncwarp();
       }
-    }
-    __syncwarp();
-    const float4 p1 = b.hit4[h1];
+      const bool fits = tot <= (uint32_t)kOutStage;
+      if (fits) {
+#pragma unroll
+        for (int k = 0; k < kMaxOuter; ++k)
+          if (W.sg[k].cnt) stage(W.sg[k].off, W.sg[k].cnt, W.pos[k], W.p1);
+      }
 
-    for (uint32_t ib = 0; ib < nin; ib += 32) {
-      const bool active = ib + lane < nin;
-      uint32_t a = 0, nlk = 0;
-      uint32_t lb[kLocalLinks];
-      float lq[kLocalLinks];
-      float4 p0;
-      bool b0 = false;
-      float ta = 0.0f;
-      if (active) {
-        a = b.in_list[in0 + ib + lane];
-        p0 = b.hit4[b.cell_in[a]];
-        ta = ord2f(b.cell_key[a] & kKeyMask);
-        b0 = b.cell_l0[a] == 0;
-      }
-      // write == false: count, keep the first kLocalLinks in registers;
-      // write == true: store the links beyond the first kLocalLinks at wbase + index
-      auto scan = [&](bool write, uint64_t wbase) {
-        uint32_t found = 0;
-        const float inv_dr01 = 1.0f / (p1.w - p0.w);
-#pragma unroll 1
-        for (int k = 0; k < kMaxOuter; ++k) {
-          const uint32_t n = sg[k].cnt;
-          if (n == 0) continue;
-          uint32_t lo = 0;
-          uint32_t khi = 0xffffffffu;
-          if (sg[k].mdr > 0.0f) {
-            float w = wconst * inv_dr01 + (cuts.rz0 + cuts.rz1 * fabsf(ta)) / sg[k].mdr;
-            w = w * 1.01f + 1e-3f;
-            const uint32_t klo = f2ord(ta - w) & kKeyMask;
-            khi = f2ord(ta + w) | ~kKeyMask;
-            uint32_t h = n;  // first index whose key is >= klo
-            while (lo < h) {
-              const uint32_t mid = (lo + h) >> 1;
-              const uint32_t km = staged ? skey[sbase[k] + mid] : b.cell_key[sg[k].off + mid];
-              if (km < klo) lo = mid + 1; else h = mid;
-            }
+      for (uint32_t ib = 0; ib < nin; ib += 32) {
+        const bool active = ib + lane < nin;
+        float ta = kNaN;
+        float w[kMaxOuter];
+        {
+          uint2 r = make_uint2(0u, 0u);
+          float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 p1 = W.p1;
+          if (active) {
+            r = b.in_rec[in0 + ib + lane];
+            p0 = b.hit4[r.y & 0x7fffffffu];
+            ta = fdiv(fsub(p1.z, p0.z), fsub(p1.w, p0.w));  // the cell's slope dz/dr
           }
-          for (uint32_t j = lo; j < n; ++j) {
-            float4 p2;
-            if (staged) {
-              if (skey[sbase[k] + j] > khi) break;
-              p2 = sp2[sbase[k] + j];
-            } else {
-              if (b.cell_key[sg[k].off + j] > khi) break;
-              p2 = b.hit4[b.cell_out[sg[k].off + j]];
-            }
-            if (!link_c1(cuts, p0, p1, p2)) continue;
-            float q;
-            if (!link_c23(cuts, p0, b0, p1, p2, q)) continue;
-            const uint32_t c = sg[k].off + j;
-            if (!write) {
-              if (found < kLocalLinks) {
-                lb[found] = c;
-                lq[found] = q;
+          const unsigned b0 = __ballot_sync(kFull, (r.y >> 31) != 0);
+          __syncwarp();
+          W.p0[lane] = p0;
+          W.a[lane] = r.x;
+          if (lane == 0) W.b0 = b0;
+          const float wa = fadd(cuts.rz0, fmul(cuts.rz1, cuts.cotmax)) *
+                           __fdividef(1.0f, p1.w - p0.w);
+          const float wb = cuts.rz0 + cuts.rz1 * fabsf(ta);
+#pragma unroll
+          for (int k = 0; k < kMaxOuter; ++k) {
+            const float m = W.sg[k].mdr;
+            w[k] = m > 0.0f ? fmaf(wb, __fdividef(1.0f, m), wa) * 1.01f + 1e-3f : kInf;
+          }
+        }
+
+        uint32_t nfound = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+          if (pass == 1 && nfound <= (uint32_t)kFound) break;
+          __syncwarp();
+          W.cnt[lane] = 0;
+          __syncwarp();
+          uint32_t head = 0, tail = 0, nf = 0;
+          // exact cuts on up to 32 queued entries, all lanes busy (one round per set bit)
+          auto process = [&](uint32_t nt) {
+            __syncwarp();
+            const bool v = (uint32_t)lane < nt;
+            const uint32_t e = v ? W.q[(head + lane) & (kQueue - 1)] : 0u;
+            head += nt;
+            const uint32_t al = e >> 11, jb = (e & 0x7fu) << 2;
+            uint32_t mask = (e >> 7) & 0xfu;
+            const float4 p0 = W.p0[al];
+            const float4 p1 = W.p1;
+            const bool qb0 = (W.b0 >> al) & 1u;
+            while (__any_sync(kFull, mask != 0)) {
+              bool ok = false;
+              float q = 0.0f;
+              uint32_t jj = 0;
+              if (mask) {
+                jj = jb + (__ffs(mask) - 1);
+                mask &= mask - 1;
+                const float4 p2 = W.p2[jj];
+                ok = link_c1(cuts, p0, p1, p2) && link_c23(cuts, p0, qb0, p1, p2, q);
               }
-            } else if (found >= kLocalLinks) {
-              b.link_dst[wbase + found] = c;
-              b.link_q[wbase + found] = q;
-              if (GATE) b.link_src[wbase + found] = a;
-              else b.has_in[c] = 1;
+              const unsigned pm = __ballot_sync(kFull, ok);
+              if (pm) {
+                if (ok) {
+                  const unsigned peers = __match_any_sync(pm, al);
+                  const uint32_t c0 = W.cnt[al];
+                  const uint32_t rank = c0 + __popc(peers & lt_mask);
+                  const uint32_t seq = nf + __popc(pm & lt_mask);
+                  const int k = (jj >= W.pos[1]) + (jj >= W.pos[2]);
+                  const uint32_t c = W.coff[k] + (jj - W.pos[k]);
+                  __syncwarp(pm);
+                  if ((peers & lt_mask) == 0) W.cnt[al] = c0 + __popc(peers);
+                  if (pass == 0) {
+                    if (seq < (uint32_t)kFound) {
+                      W.fc[seq] = c;
+                      W.fq[seq] = q;
+                      W.fa[seq] = (uint16_t)((al << 8) | rank);
+                    }
+                  } else if (seq >= (uint32_t)kFound) {
+                    const uint32_t bs = W.base[al];
+                    if (bs != kNoBase) write_link((uint64_t)bs + rank, W.a[al], c, q);
+                  }
+                }
+                nf += __popc(pm);
+                __syncwarp();
+              }
             }
-            ++found;
+          };
+          // sweep of staged positions [p, p + n) with the lane's window wk
+          auto sweep = [&](uint32_t p, uint32_t n, float wk) {
+            for (uint32_t j = 0; j < n; j += 4) {
+              const float4 t4 = *reinterpret_cast<const float4*>(&W.t[p + j]);
+              const uint32_t m = (fabsf(t4.x - ta) <= wk ? 1u : 0u) | (fabsf(t4.y - ta) <= wk ? 2u : 0u) |
+                                 (fabsf(t4.z - ta) <= wk ? 4u : 0u) | (fabsf(t4.w - ta) <= wk ? 8u : 0u);
+              const unsigned bal = __ballot_sync(kFull, m != 0);
+              if (bal) {
+                if (m)
+                  W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] =
+                      (uint16_t)(((uint32_t)lane << 11) | (m << 7) | ((p + j) >> 2));
+                tail += __popc(bal);
+                if (tail - head >= 32u) process(32);
+              }
+            }
+          };
+          if (fits) {
+#pragma unroll
+            for (int k = 0; k < kMaxOuter; ++k)
+              if (W.sg[k].cnt) sweep(W.pos[k], round4(W.sg[k].cnt), w[k]);
+            if (tail != head) process(tail - head);
+          } else {
+#pragma unroll
+            for (int k = 0; k < kMaxOuter; ++k) {
+              const uint32_t cnt = W.sg[k].cnt, off = W.sg[k].off;
+              for (uint32_t j0 = 0; j0 < cnt; j0 += kOutStage) {
+                const uint32_t n = min(cnt - j0, (uint32_t)kOutStage);
+                __syncwarp();
+                stage(off + j0, n, 0, W.p1);
+                if (lane == 0) {
+                  W.pos[0] = 0;
+                  W.pos[1] = W.pos[2] = kOutStage;
+                  W.coff[0] = off + j0;
+                }
+                __syncwarp();
+                sweep(0, round4(n), w[k]);
+                if (tail != head) process(tail - head);
+              }
+            }
+          }
+          if (pass == 1) break;
+          nfound = nf;
+
+          // one reservation for the group's links and root candidates
+          const uint32_t nlk = active ? W.cnt[lane] : 0u;
+          const uint32_t inc = warp_incl_scan(nlk);
+          const uint32_t total = __shfl_sync(kFull, inc, 31);
+          const unsigned has = __ballot_sync(kFull, nlk > 0);
+          unsigned long long wbase = 0, lbase = 0;
+          if (total > 0) {
+            unsigned long long hlo, hhi;
+            wbase = chunk_take_shared(W, 0, &b.cnt[CNT_LINKS], total, &hlo, &hhi);
+            if (GATE) mark_link_hole(hlo, hhi);
+            lbase = chunk_take_shared(W, 1, &b.cnt[CNT_LKCELLS], __popc(has), &hlo, &hhi);
+            mark_hole(hlo, hhi);
+            if (lane == 0) W.used += total;
+          }
+          uint32_t mybase = kNoBase;
+          if (nlk > 0) {
+            const uint32_t a = W.a[lane];
+            const uint64_t base = wbase + inc - nlk;
+            const uint64_t li = lbase + __popc(has & lt_mask);
+            if (base + nlk > cap_links || li >= cap_links) {
+              atomicOr(&b.cnt[CNT_STATUS], ST_LINKS);
+              if (li < cap_links) b.lk_cells[li] = kHole;  // keep the list readable
+              if (GATE)
+                for (uint64_t i = base; i < base + nlk && i < cap_links; ++i) b.link_src[i] = kHole;
+            } else {
+              b.link_off[a] = (uint32_t)base;
+              b.link_cnt[a] = nlk;
+              if (!GATE) b.has_out[a] = 1;  // gated form: set by the gate for kept links
+              b.lk_cells[li] = a;
+              mybase = (uint32_t)base;
+            }
+          }
+          W.base[lane] = mybase;
+          __syncwarp();
+          const uint32_t nk = min(nf, (uint32_t)kFound);
+          for (uint32_t i = lane; i < nk; i += 32) {
+            const uint32_t e = W.fa[i];
+            const uint32_t bs = W.base[e >> 8];
+            if (bs != kNoBase) write_link((uint64_t)bs + (e & 0xffu), W.a[e >> 8], W.fc[i], W.fq[i]);
           }
         }
-        return found;
-      };
-      if (active) nlk = scan(false, 0);
-      // warp-aggregated reservation of the link slots and of the root-candidate list
-      const uint32_t inc = warp_incl_scan(nlk);
-      const uint32_t tot = __shfl_sync(kFull, inc, 31);
-      const unsigned has = __ballot_sync(kFull, nlk > 0);
-      unsigned long long wbase = 0, lbase = 0;
-      if (tot > 0) {
-        unsigned long long hlo, hhi;
-        wbase = chunk_take(lch, &b.cnt[CNT_LINKS], tot, &hlo, &hhi);
-        if (GATE) mark_link_hole(hlo, hhi);
-        lbase = chunk_take(kch, &b.cnt[CNT_LKCELLS], __popc(has), &hlo, &hhi);
-        mark_hole(hlo, hhi);
-        used += tot;
       }
-      if (active && nlk > 0) {
-        const uint64_t base = wbase + inc - nlk;
-        const uint64_t li = lbase + __popc(has & lt_mask);
-        if (base + nlk > cap_links || li >= cap_links) {
-          atomicOr(&b.cnt[CNT_STATUS], ST_LINKS);
-          if (li < cap_links) b.lk_cells[li] = kHole;  // keep the list readable
-          if (GATE)
-            for (uint64_t i = base; i < base + nlk && i < cap_links; ++i) b.link_src[i] = kHole;
-        } else {
-          b.link_off[a] = (uint32_t)base;
-          b.link_cnt[a] = nlk;
-          if (!GATE) b.has_out[a] = 1;  // gated form: set by the gate for kept links
-          b.lk_cells[li] = a;
-          const uint32_t nl = nlk < kLocalLinks ? nlk : kLocalLinks;
-          for (uint32_t i = 0; i < nl; ++i) {
-            b.link_dst[base + i] = lb[i];
-            b.link_q[base + i] = lq[i];
-            if (GATE) b.link_src[base + i] = a;
-            else b.has_in[lb[i]] = 1;
-          }
-          if (nlk > kLocalLinks) scan(true, base);
-        }
-      }
+      __syncwarp();
     }
     __syncwarp();
   }
-  mark_hole(kch.next, kch.end);
-  if (GATE) mark_link_hole(lch.next, lch.end);
-  if (lane == 0 && used) atomicAdd(&b.cnt[CNT_LINKS_USED], used);
+  __syncwarp();
+  mark_hole(W.chunk_next[1], W.chunk_end[1]);
+  if (GATE) mark_link_hole(W.chunk_next[0], W.chunk_end[0]);
+  if (lane == 0 && W.used) atomicAdd(&b.cnt[CNT_LINKS_USED], W.used);
 }
 
 }  // namespace
@@ -205,7 +403,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
 void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
                     bool gated) {
   launch_scan(b.in_cnt, b.in_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s);
-  k_in_scatter<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_cells);
+  k_in_scatter<<<l.sms * kScatterBlocksPerSm, 256, 0, s>>>(b, p.phi_bins);
   if (gated)
     k_connect<true><<<l.sgrid, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
                                                           (uint64_t)p.max_links);

@@ -8,16 +8,13 @@
 // ri < ro, so the window is that angle (ro = the largest radius seen on the outer
 // layer in this event) plus a safety margin and one bin each side.  The window is one
 // contiguous range of the sorted hits (two when it wraps).  Lanes stride over it,
-// test the exact float32 cuts, and stage the passing outer hits in shared memory.
-// The staged segment is sorted by its r-z slope dz/dr and appended with one atomic per
-// (hit, outer layer), so the cells leaving a hit towards one layer are contiguous and
-// slope-ordered; the link stage searches them by slope.  Slots are reserved through a
-// per-warp chunk allocator; unused slots are marked as holes.  The sort runs on single
-// 32-bit keys in registers (bitonic network over the warp): the order-preserving bits
-// of the slope with the low 8 bits replaced by the staging position, which both makes
-// the keys unique and locates the outer hit after sorting.  Each cell also takes its
-// rank among the cells ending on its outer hit, from which the link stage's per-hit
-// lists of incoming cells are built.
+// test the exact float32 cuts, and stage the passing outer hits in shared memory; the
+// segment is then appended with one reservation per
+// (hit, outer layer), so the cells leaving a hit towards one layer are contiguous.
+// Each segment records the smallest dr of its cells, which bounds the link stage's
+// slope window.  Slots are reserved through a per-warp chunk allocator; unused slots
+// are marked as holes.  Each cell also takes its rank among the cells ending on its
+// outer hit, from which the link stage's per-hit lists of incoming cells are built.
 #include "ptca_internal.cuh"
 
 namespace ptca {
@@ -37,79 +34,21 @@ __device__ __forceinline__ float phi_window(float kmax, float ri, float ro_max) 
   return fminf(asinf(a) - asinf(b) + 1e-4f, kHalfPi + 1e-3f);
 }
 
-// Bitonic sort of 32*E unique uint32 keys held in registers, element i = e*32 + lane,
-// ascending.  Partners closer than 32 elements are exchanged with xor shuffles, farther
-// ones live in the same lane.
-template <int E>
-__device__ __forceinline__ void warp_bitonic(uint32_t (&k)[E]) {
-  const int lane = lane_id();
-#pragma unroll
-  for (int size = 2; size <= 32 * E; size <<= 1) {
-#pragma unroll
-    for (int j = size >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int p = e ^ (j >> 5);
-          if (p > e) {
-            const bool up = ((e * 32 + lane) & size) == 0;
-            const uint32_t lo = min(k[e], k[p]), hi = max(k[e], k[p]);
-            k[e] = up ? lo : hi;
-            k[p] = up ? hi : lo;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const uint32_t o = __shfl_xor_sync(kFull, k[e], j);
-          const bool up = ((e * 32 + lane) & size) == 0;
-          const bool lower = (lane & j) == 0;
-          k[e] = (lower == up) ? min(k[e], o) : max(k[e], o);
-        }
-      }
-    }
-  }
-}
-
 // Writes one cell and takes its rank among the cells ending on the same outer hit.
 __device__ __forceinline__ void write_cell(const Buffers& b, uint64_t c, uint32_t s, uint32_t o,
-                                          uint32_t key, uint8_t L) {
+                                          uint8_t L) {
   b.cell_in[c] = s;
   b.cell_out[c] = o;
-  b.cell_key[c] = key;
   b.cell_l0[c] = L;
   b.has_in[c] = 0;
   b.has_out[c] = 0;
   b.cell_inrank[c] = atomicAdd(&b.in_cnt[o], 1u);
 }
 
-// Sorts the n staged keys (slope bits | staging position) and writes the cells
-// base..base+n in key order.
-template <int E>
-__device__ __forceinline__ void sort_and_write(const Buffers& b, const uint32_t* skey,
-                                               const uint32_t* sval, uint32_t n, uint64_t base,
-                                               uint32_t s, uint8_t L) {
-  const int lane = lane_id();
-  uint32_t k[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const uint32_t i = e * 32 + lane;
-    k[e] = i < n ? skey[i] : 0xffffffffu;
-  }
-  warp_bitonic<E>(k);
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const uint32_t i = e * 32 + lane;
-    if (i < n) write_cell(b, base + i, s, sval[k[e] & 0xffu], k[e], L);
-  }
-}
-
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
     k_doublets(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap_cells) {
-  __shared__ uint32_t st_key[kWarpsPerBlock][kStage];
   __shared__ uint32_t st_val[kWarpsPerBlock][kStage];
   const int lane = lane_id(), wib = threadIdx.x >> 5;
-  uint32_t* skey = st_key[wib];
   uint32_t* sval = st_val[wib];
   const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -171,23 +110,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
         for (uint32_t o0 = beg; o0 < end; o0 += 32) {
           const uint32_t o = o0 + lane;
           bool pass = false;
-          float slope = 0.0f;
           if (o < end) {
             const float4 ho = b.hit4[o];
             pass = doublet_pass(cuts, hi, ho);
-            if (pass) {
-              const float dr = fsub(ho.w, hi.w);
-              slope = fdiv(fsub(ho.z, hi.z), dr);
-              mdr = fminf(mdr, dr);
-            }
+            if (pass) mdr = fminf(mdr, fsub(ho.w, hi.w));
           }
           const unsigned bal = __ballot_sync(kFull, pass);
           if (pass) {
             const uint32_t pos = cnt + __popc(bal & lt_mask);
-            if (pos < kStage) {
-              skey[pos] = (f2ord(slope) & kKeyMask) | pos;
-              sval[pos] = o;
-            }
+            if (pos < kStage) sval[pos] = o;
           }
           cnt += __popc(bal);
         }
@@ -196,7 +127,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
       for (int off = 16; off > 0; off >>= 1) mdr = fminf(mdr, __shfl_xor_sync(kFull, mdr, off));
 
       uint32_t seg_off = 0, seg_cnt = 0;
-      float seg_mdr = -1.0f;
       if (cnt > 0) {
         unsigned long long hlo, hhi;
         const unsigned long long base = chunk_take(ch, &b.cnt[CNT_CELLS], cnt, &hlo, &hhi);
@@ -207,46 +137,36 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
           mark_hole(base, base + cnt);  // slots below the capacity stay readable
         } else if (cnt <= (uint32_t)kStage) {
           __syncwarp();
-          if (cnt <= 32) sort_and_write<1>(b, skey, sval, cnt, base, s, (uint8_t)L);
-          else if (cnt <= 64) sort_and_write<2>(b, skey, sval, cnt, base, s, (uint8_t)L);
-          else if (cnt <= 128) sort_and_write<4>(b, skey, sval, cnt, base, s, (uint8_t)L);
-          else sort_and_write<8>(b, skey, sval, cnt, base, s, (uint8_t)L);
+          for (uint32_t i = lane; i < cnt; i += 32)
+            write_cell(b, base + i, s, sval[i], (uint8_t)L);
           seg_off = (uint32_t)base;
           seg_cnt = cnt;
-          seg_mdr = mdr;
         } else {
-          // too many for the stage: recompute and write in test order (unsorted)
+          // too many for the stage: recompute and write in test order
           uint32_t pos0 = 0;
           for (int part = 0; part < 2; ++part) {
             const uint32_t beg = part ? r2 : r0, end = part ? r3 : r1;
             for (uint32_t o0 = beg; o0 < end; o0 += 32) {
               const uint32_t o = o0 + lane;
               bool pass = false;
-              float4 ho;
-              if (o < end) {
-                ho = b.hit4[o];
-                pass = doublet_pass(cuts, hi, ho);
-              }
+              if (o < end) pass = doublet_pass(cuts, hi, b.hit4[o]);
               const unsigned bal = __ballot_sync(kFull, pass);
               if (pass) {
                 const uint64_t c = base + pos0 + __popc(bal & lt_mask);
-                write_cell(b, c, s, o,
-                           f2ord(fdiv(fsub(ho.z, hi.z), fsub(ho.w, hi.w))) & kKeyMask,
-                           (uint8_t)L);
+                write_cell(b, c, s, o, (uint8_t)L);
               }
               pos0 += __popc(bal);
             }
           }
           seg_off = (uint32_t)base;
           seg_cnt = cnt;
-          seg_mdr = -1.0f;
         }
       }
       if (lane == 0) {
         Segment sg;
         sg.off = seg_off;
         sg.cnt = seg_cnt;
-        sg.mdr = seg_mdr;
+        sg.mdr = seg_cnt ? mdr : -1.0f;
         sg.pad = 0;
         b.seg[s * kMaxOuter + k] = sg;
       }

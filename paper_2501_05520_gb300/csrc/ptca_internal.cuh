@@ -64,8 +64,8 @@ struct GateWeights {
   float tau;
 };
 
-// Cells leaving one hit towards one outer layer: [off, off + cnt) of the cell arrays,
-// sorted by r-z slope when mdr >= 0 (mdr = smallest dr in the segment).
+// Cells leaving one hit towards one outer layer: [off, off + cnt) of the cell arrays;
+// mdr = the smallest dr (r_outer - r_inner) among them, -1 when the segment is empty.
 struct __align__(16) Segment {
   uint32_t off;
   uint32_t cnt;
@@ -109,8 +109,6 @@ struct Buffers {
   // cells
   uint32_t* cell_in;         // [max_cells] sorted hit index
   uint32_t* cell_out;        // [max_cells]
-  uint32_t* cell_key;        // [max_cells] slope key: order-preserving bits of dz/dr,
-                             //   low 8 bits = position in the staging buffer
   uint32_t* cell_inrank;     // [max_cells] rank among the cells ending on the same hit
   uint8_t* cell_l0;          // [max_cells] layer of the inner hit
   uint8_t* has_in;           // [max_cells] an accepted link ends on the cell
@@ -121,7 +119,8 @@ struct Buffers {
   unsigned long long* best;  // [max_cells] duplicate-cleaning key (cells on ntuplets)
   uint32_t* in_cnt;          // [max_hits + 1] cells ending on each sorted hit
   uint32_t* in_start;        // [max_hits + 1] exclusive scan of in_cnt
-  uint32_t* in_list;         // [max_cells] cells grouped by the hit they end on
+  uint2* in_rec;             // [max_cells] cells grouped by the hit they end on:
+                             //   (cell, inner sorted hit | inner layer is 0 << 31)
   // links
   uint32_t* link_dst;        // [max_links]
   float* link_q;             // [max_links]
@@ -333,16 +332,6 @@ __device__ __forceinline__ void store_gate_row(uint16_t* row, const float (&f)[1
   ((uint4*)row)[0] = lo;
   ((uint4*)row)[1] = hi;
 }
-
-// Order-preserving map float -> uint32 (monotone increasing, finite and infinite values).
-__device__ __forceinline__ uint32_t f2ord(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float ord2f(uint32_t k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
-}
-constexpr uint32_t kKeyMask = 0xffffff00u;  // slope part of a cell key
 
 __device__ __forceinline__ unsigned warp_incl_scan(unsigned v) {
   const int lane = lane_id();

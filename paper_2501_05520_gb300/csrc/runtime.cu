@@ -73,7 +73,6 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.seg = (Segment*)take(N * kMaxOuter * sizeof(Segment));
   t.cell_in = (uint32_t*)take(C * 4);
   t.cell_out = (uint32_t*)take(C * 4);
-  t.cell_key = (uint32_t*)take(C * 4);
   t.cell_inrank = (uint32_t*)take(C * 4);
   t.cell_l0 = (uint8_t*)take(C);
   t.has_in = (uint8_t*)take(C);
@@ -84,7 +83,7 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.best = (unsigned long long*)take(C * 8);
   t.in_cnt = (uint32_t*)take((N + 1) * 4);
   t.in_start = (uint32_t*)take((N + 1) * 4);
-  t.in_list = (uint32_t*)take(C * 4);
+  t.in_rec = (uint2*)take(C * 8);
   t.link_dst = (uint32_t*)take(L * 4);
   t.link_q = (float*)take(L * 4);
   t.nt_hits = (int32_t*)take(T * kMaxHits * 4);
