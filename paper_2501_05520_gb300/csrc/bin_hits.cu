@@ -80,9 +80,14 @@ __global__ void k_bin_count(Buffers b, int32_t B) {
   }
 }
 
-__global__ void k_bin_scatter(Buffers b) {
+__global__ void k_bin_scatter(Buffers b, float kmax) {
   const int N = b.hdr->n_hits;
   const int stride = gridDim.x * blockDim.x;
+  // per event layer: the outer-radius term of the doublet stage's azimuthal window
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.hdr->n_events * kLayers; i += stride) {
+    const float a = 0.5f * kmax * __uint_as_float(b.layer_rmax[i]);
+    b.layer_asin[i] = a >= 0.7f ? __int_as_float(0x7f800000) : asinf(a);
+  }
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += stride) {
     const uint32_t gb = b.in_bin[g];
     if (gb == 0xffffffffu) continue;
@@ -178,7 +183,7 @@ void launch_clear(const Buffers& b, const Params& p, const Launch& l, cudaStream
 void launch_bin_hits(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s) {
   k_bin_count<<<l.grid, 256, 0, s>>>(b, p.phi_bins);
   launch_scan(b.bin_cnt, b.bin_start, &b.cnt[CNT_SCAN_BINS], b.scan_part, s);
-  k_bin_scatter<<<l.grid, 256, 0, s>>>(b);
+  k_bin_scatter<<<l.grid, 256, 0, s>>>(b, p.cuts.kmax);
 }
 
 }  // namespace ptca

@@ -7,22 +7,25 @@
 // outer layer) are staged once in shared memory: their r-z slopes and the coordinates
 // of their outer hits.  The cells ending on h1 come from a per-hit list of 8-byte
 // records (cell, inner hit | inner-layer flag) and are taken 32 at a time, one per
-// lane.  Writing t_a, t_b for the slopes of a and b, C1 reads
-//   (r1-r0)(r2-r1)|t_a - t_b| <= rz0 (r2-r0) + rz1 |z2-z0|,
-// and with |t_b| <= cotmax (D4) and m = the smallest r2-r1 of the segment this gives
-//   |t_a - t_b| <= (rz0 + rz1 cotmax)/(r1-r0) + (rz0 + rz1 |t_a|)/m.
-// The window is widened by 1 % + 1e-3, far beyond the float32 rounding of C1 (about
-// 4e-7 |t_a| (r1-r0)/m + 1e-6) and of the approximate reciprocals used for it.  The
-// warp sweeps the staged slopes four at a time, every lane testing its own cell against
-// them, with no divergence; a lane whose window holds any of the four queues one entry
-// (lane, 4-bit mask, position).  The queue is drained 32 entries at a time through the
-// exact cuts, all lanes busy.  The links found for the 32 cells are collected in shared
-// memory and written with one warp-aggregated reservation: the links of one cell are
-// contiguous (the out-link list the ntuplet search walks), and cells with at least one
-// link are appended to a compact list, the only cells that can start an ntuplet.  If a
-// group finds more links than the collection holds, the sweep runs a second time and
-// writes the remainder directly.  Segments larger than the stage are swept piece by
-// piece.
+// lane.  With d1 = r1-r0, d2 = r2-r1 and t_a, t_b the slopes of a and b, C1 reads
+//   d1 d2 |t_a - t_b| <= rz0 (d1 + d2) + rz1 |t_a d1 + t_b d2|,
+// so |t_a - t_b| <= rz0 (1/d1 + 1/d2) + rz1 (|t_a|/d2 + |t_b|/d1).  Bounding |t_b| by
+// cotmax (D4), or by |t_a| + |t_a - t_b| and solving for |t_a - t_b|, and d2 by the
+// smallest r2-r1 of the segment, m, gives the window
+//   |t_a - t_b| <= min((rz0 + rz1 cotmax)/d1 + (rz0 + rz1 |t_a|)/m,
+//                      (rz0 + rz1 |t_a|)(1/d1 + 1/m) / (1 - rz1/d1)),
+// the second term only where d1 > rz1.  It is widened by 1 % + 1e-3, far beyond the
+// float32 rounding of C1 (about 4e-7 |t_a| d1/m + 1e-6) and of the approximate
+// reciprocals used for it.  The warp sweeps the staged slopes four at a time, every lane
+// testing its own cell against them, with no divergence; a lane whose window holds any
+// of the four queues one entry (lane, 4-bit mask, position).  The queue is drained 32
+// entries at a time through the exact cuts, all lanes busy.  The links found for the 32
+// cells are collected in shared memory and written with one warp-aggregated
+// reservation: the links of one cell are contiguous (the out-link list the ntuplet
+// search walks), and cells with at least one link are appended to a compact list, the
+// only cells that can start an ntuplet.  If a group finds more links than the
+// collection holds, the sweep runs a second time and writes the remainder directly.
+// Segments larger than the stage are swept piece by piece.
 #include "ptca_internal.cuh"
 
 namespace ptca {
@@ -81,20 +84,20 @@ __global__ void k_in_scatter(Buffers b, int32_t B) {
 struct ConnWarp {
   float4 p2[kOutStage];      // staged outgoing cells: outer hit
   float t[kOutStage];        //   slope (NaN padding)
-  float4 p0[32];             // lane's incoming cell: inner hit
   float4 p1;                 // middle hit
   Segment sg[kMaxOuter];     // outgoing segments of the middle hit
   uint32_t pos[kMaxOuter];   // staged position of each segment / piece
   uint32_t coff[kMaxOuter];  // cell of each staged position pos[k]
   unsigned long long chunk_next[2], chunk_end[2], used;  // link slots, root slots
   uint32_t chunk_size[2];
-  uint32_t b0;               // lanes whose incoming cell starts on layer 0
-  uint32_t a[32], cnt[32], base[32];
-  uint32_t hin0[32], hnin[32];  // incoming-cell list of each hit of the warp's chunk
-  uint16_t q[kQueue];        // candidates: lane << 11 | mask << 7 | staged position / 4
-  uint32_t fc[kFound];       // found links: target cell
+  uint32_t hin0[kHitChunk], hnin[kHitChunk];  // incoming-cell list of each hit of the chunk
+  uint32_t in0, nin;         // incoming-cell list of the middle hit
+  unsigned long long lbase;  // its link block
+  uint32_t lvalid;           //   (within the capacity)
+  uint2 q[kQueue];           // candidates: (incoming index, mask << 8 | staged position)
+  uint32_t fs[kFound];       // found links: source cell
+  uint32_t fd[kFound];       //   target cell
   float fq[kFound];          //   quality
-  uint16_t fa[kFound];       //   lane << 8 | rank among the lane cell's links
 };
 
 // Warp chunk reservation with the chunk state in shared memory, lane 0 acting.
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
   }
   if (lane == 0) W.used = 0;
   __syncwarp();
-  auto mark_hole = [&](unsigned long long lo, unsigned long long hi) {
+  auto mark_root_hole = [&](unsigned long long lo, unsigned long long hi) {
     hi = min(hi, (unsigned long long)cap_links);
     for (unsigned long long i = lo + lane; i < hi; i += 32) b.lk_cells[i] = kHole;
   };
@@ -150,10 +153,13 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
     for (unsigned long long i = lo + lane; i < hi; i += 32) b.link_src[i] = kHole;
   };
   auto write_link = [&](uint64_t slot, uint32_t a, uint32_t c, float q) {
+    b.link_src[slot] = a;
     b.link_dst[slot] = c;
     b.link_q[slot] = q;
-    if (GATE) b.link_src[slot] = a;
-    else b.has_in[c] = 1;
+    if (!GATE) {  // gated form: the gate sets the flags of the links it keeps
+      b.has_out[a] = 1;
+      b.has_in[c] = 1;
+    }
   };
   // stages cells [c0, c0 + n) leaving the middle hit p1 at position p (padded to a
   // multiple of 4 with NaN slopes)
@@ -187,15 +193,22 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
         }
       }
       __syncwarp();
-      W.hin0[lane] = in0;
-      W.hnin[lane] = nin;
+      if ((uint32_t)lane < kHitChunk) {
+        W.hin0[lane] = in0;
+        W.hnin[lane] = nin;
+      }
     }
     unsigned todo = __ballot_sync(kFull, work);
     while (todo) {
       const int src = __ffs(todo) - 1;
       todo &= todo - 1;
       const uint32_t h1 = hc + src;
-      const uint32_t in0 = W.hin0[src], nin = W.hnin[src];
+      __syncwarp();
+      if (lane == 0) {
+        W.in0 = W.hin0[src];
+        W.nin = W.hnin[src];
+        W.lvalid = 0;
+      }
       uint32_t tot = 0;
       {
         const Segment* sgp = b.seg + (uint64_t)h1 * kMaxOuter;
@@ -220,110 +233,103 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
           if (W.sg[k].cnt) stage(W.sg[k].off, W.sg[k].cnt, W.pos[k], W.p1);
       }
 
-      for (uint32_t ib = 0; ib < nin; ib += 32) {
-        const bool active = ib + lane < nin;
-        float ta = kNaN;
-        float w[kMaxOuter];
-        {
-          uint2 r = make_uint2(0u, 0u);
+      // Pass 0 finds the links of h1, keeps up to kFound of them in shared memory and
+      // counts all; if there were more, pass 1 repeats the search and writes the rest
+      // straight into the reserved block.
+      uint32_t nfound = 0;
+      for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1 && nfound <= (uint32_t)kFound) break;
+        uint32_t head = 0, tail = 0, nf = 0;
+        // exact cuts on up to 32 queued entries, all lanes busy (one round per set bit)
+        auto process = [&](uint32_t nt) {
+          __syncwarp();
+          const bool v = (uint32_t)lane < nt;
+          const uint2 e = v ? W.q[(head + lane) & (kQueue - 1)] : make_uint2(0u, 0u);
+          head += nt;
+          const uint32_t jb = e.y & 0xffu;
+          uint32_t mask = e.y >> 8;
+          uint32_t a = 0;
           float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f);
-          const float4 p1 = W.p1;
-          if (active) {
-            r = b.in_rec[in0 + ib + lane];
+          bool qb0 = false;
+          if (v) {
+            const uint2 r = b.in_rec[W.in0 + e.x];
+            a = r.x;
+            qb0 = (r.y >> 31) != 0;
             p0 = b.hit4[r.y & 0x7fffffffu];
-            ta = fdiv(fsub(p1.z, p0.z), fsub(p1.w, p0.w));  // the cell's slope dz/dr
           }
-          const unsigned b0 = __ballot_sync(kFull, (r.y >> 31) != 0);
-          __syncwarp();
-          W.p0[lane] = p0;
-          W.a[lane] = r.x;
-          if (lane == 0) W.b0 = b0;
-          const float wa = fadd(cuts.rz0, fmul(cuts.rz1, cuts.cotmax)) *
-                           __fdividef(1.0f, p1.w - p0.w);
-          const float wb = cuts.rz0 + cuts.rz1 * fabsf(ta);
-#pragma unroll
-          for (int k = 0; k < kMaxOuter; ++k) {
-            const float m = W.sg[k].mdr;
-            w[k] = m > 0.0f ? fmaf(wb, __fdividef(1.0f, m), wa) * 1.01f + 1e-3f : kInf;
-          }
-        }
-
-        uint32_t nfound = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-          if (pass == 1 && nfound <= (uint32_t)kFound) break;
-          __syncwarp();
-          W.cnt[lane] = 0;
-          __syncwarp();
-          uint32_t head = 0, tail = 0, nf = 0;
-          // exact cuts on up to 32 queued entries, all lanes busy (one round per set bit)
-          auto process = [&](uint32_t nt) {
-            __syncwarp();
-            const bool v = (uint32_t)lane < nt;
-            const uint32_t e = v ? W.q[(head + lane) & (kQueue - 1)] : 0u;
-            head += nt;
-            const uint32_t al = e >> 11, jb = (e & 0x7fu) << 2;
-            uint32_t mask = (e >> 7) & 0xfu;
-            const float4 p0 = W.p0[al];
-            const float4 p1 = W.p1;
-            const bool qb0 = (W.b0 >> al) & 1u;
-            while (__any_sync(kFull, mask != 0)) {
-              bool ok = false;
-              float q = 0.0f;
-              uint32_t jj = 0;
-              if (mask) {
-                jj = jb + (__ffs(mask) - 1);
-                mask &= mask - 1;
-                const float4 p2 = W.p2[jj];
-                ok = link_c1(cuts, p0, p1, p2) && link_c23(cuts, p0, qb0, p1, p2, q);
-              }
-              const unsigned pm = __ballot_sync(kFull, ok);
-              if (pm) {
-                if (ok) {
-                  const unsigned peers = __match_any_sync(pm, al);
-                  const uint32_t c0 = W.cnt[al];
-                  const uint32_t rank = c0 + __popc(peers & lt_mask);
-                  const uint32_t seq = nf + __popc(pm & lt_mask);
-                  const int k = (jj >= W.pos[1]) + (jj >= W.pos[2]);
-                  const uint32_t c = W.coff[k] + (jj - W.pos[k]);
-                  __syncwarp(pm);
-                  if ((peers & lt_mask) == 0) W.cnt[al] = c0 + __popc(peers);
-                  if (pass == 0) {
-                    if (seq < (uint32_t)kFound) {
-                      W.fc[seq] = c;
-                      W.fq[seq] = q;
-                      W.fa[seq] = (uint16_t)((al << 8) | rank);
-                    }
-                  } else if (seq >= (uint32_t)kFound) {
-                    const uint32_t bs = W.base[al];
-                    if (bs != kNoBase) write_link((uint64_t)bs + rank, W.a[al], c, q);
-                  }
+          const float4 p1 = W.p1;
+          while (__any_sync(kFull, mask != 0)) {
+            bool ok = false;
+            float q = 0.0f;
+            uint32_t jj = 0;
+            if (mask) {
+              jj = jb + (__ffs(mask) - 1);
+              mask &= mask - 1;
+              const float4 p2 = W.p2[jj];
+              ok = link_c1(cuts, p0, p1, p2) && link_c23(cuts, p0, qb0, p1, p2, q);
+            }
+            const unsigned pm = __ballot_sync(kFull, ok);
+            if (ok) {
+              const uint32_t seq = nf + __popc(pm & lt_mask);
+              const int k = (jj >= W.pos[1]) + (jj >= W.pos[2]);
+              const uint32_t c = W.coff[k] + (jj - W.pos[k]);
+              if (pass == 0) {
+                if (seq < (uint32_t)kFound) {
+                  W.fs[seq] = a;
+                  W.fd[seq] = c;
+                  W.fq[seq] = q;
                 }
-                nf += __popc(pm);
-                __syncwarp();
+              } else if (seq >= (uint32_t)kFound && W.lvalid) {
+                write_link(W.lbase + nfound + seq, a, c, q);
               }
             }
-          };
-          // sweep of staged positions [p, p + n) with the lane's window wk
-          auto sweep = [&](uint32_t p, uint32_t n, float wk) {
-            for (uint32_t j = 0; j < n; j += 4) {
-              const float4 t4 = *reinterpret_cast<const float4*>(&W.t[p + j]);
-              const uint32_t m = (fabsf(t4.x - ta) <= wk ? 1u : 0u) | (fabsf(t4.y - ta) <= wk ? 2u : 0u) |
-                                 (fabsf(t4.z - ta) <= wk ? 4u : 0u) | (fabsf(t4.w - ta) <= wk ? 8u : 0u);
-              const unsigned bal = __ballot_sync(kFull, m != 0);
-              if (bal) {
-                if (m)
-                  W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] =
-                      (uint16_t)(((uint32_t)lane << 11) | (m << 7) | ((p + j) >> 2));
-                tail += __popc(bal);
-                if (tail - head >= 32u) process(32);
-              }
+            nf += __popc(pm);
+          }
+        };
+        // sweep of staged positions [p, p + n) with the lane's window wk; ix = the
+        // lane's index in the incoming list
+        auto sweep = [&](uint32_t p, uint32_t n, float ta, float wk, uint32_t ix) {
+          for (uint32_t j = 0; j < n; j += 4) {
+            const float4 t4 = *reinterpret_cast<const float4*>(&W.t[p + j]);
+            const uint32_t m = (fabsf(t4.x - ta) <= wk ? 1u : 0u) | (fabsf(t4.y - ta) <= wk ? 2u : 0u) |
+                               (fabsf(t4.z - ta) <= wk ? 4u : 0u) | (fabsf(t4.w - ta) <= wk ? 8u : 0u);
+            const unsigned bal = __ballot_sync(kFull, m != 0);
+            if (bal) {
+              if (m) W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2(ix, (m << 8) | (p + j));
+              tail += __popc(bal);
+              if (tail - head >= 32u) process(32);
             }
-          };
+          }
+        };
+
+        for (uint32_t ib = 0; ib < W.nin; ib += 32) {
+          const uint32_t ix = ib + lane;
+          float ta = kNaN;
+          float w[kMaxOuter];
+          {
+            const float4 p1 = W.p1;
+            float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ix < W.nin) {
+              p0 = b.hit4[b.in_rec[W.in0 + ix].y & 0x7fffffffu];
+              ta = fdiv(fsub(p1.z, p0.z), fsub(p1.w, p0.w));  // the cell's slope dz/dr
+            }
+            const float id1 = __fdividef(1.0f, p1.w - p0.w);
+            const float wa = (cuts.rz0 + cuts.rz1 * cuts.cotmax) * id1;
+            const float ua = cuts.rz0 + cuts.rz1 * fabsf(ta);
+            const float shrink = 1.0f - cuts.rz1 * id1;
+#pragma unroll
+            for (int k = 0; k < kMaxOuter; ++k) {
+              const float m = W.sg[k].mdr;
+              const float im = __fdividef(1.0f, m);
+              float wk = fmaf(ua, im, wa);
+              if (shrink > 0.0f) wk = fminf(wk, __fdividef(ua * (id1 + im), shrink));
+              w[k] = m > 0.0f ? wk * 1.01f + 1e-3f : kInf;
+            }
+          }
           if (fits) {
 #pragma unroll
             for (int k = 0; k < kMaxOuter; ++k)
-              if (W.sg[k].cnt) sweep(W.pos[k], round4(W.sg[k].cnt), w[k]);
-            if (tail != head) process(tail - head);
+              if (W.sg[k].cnt) sweep(W.pos[k], round4(W.sg[k].cnt), ta, w[k], ix);
           } else {
 #pragma unroll
             for (int k = 0; k < kMaxOuter; ++k) {
@@ -338,54 +344,87 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
                   W.coff[0] = off + j0;
                 }
                 __syncwarp();
-                sweep(0, round4(n), w[k]);
-                if (tail != head) process(tail - head);
+                sweep(0, round4(n), ta, w[k], ix);
+                if (tail != head) process(tail - head);  // before the stage changes
               }
             }
           }
-          if (pass == 1) break;
-          nfound = nf;
+        }
+        if (tail != head) process(tail - head);
+        __syncwarp();
+        if (pass == 1) break;
+        nfound = nf;
+        if (nf == 0) break;
 
-          // one reservation for the group's links and root candidates
-          const uint32_t nlk = active ? W.cnt[lane] : 0u;
-          const uint32_t inc = warp_incl_scan(nlk);
-          const uint32_t total = __shfl_sync(kFull, inc, 31);
-          const unsigned has = __ballot_sync(kFull, nlk > 0);
-          unsigned long long wbase = 0, lbase = 0;
-          if (total > 0) {
-            unsigned long long hlo, hhi;
-            wbase = chunk_take_shared(W, 0, &b.cnt[CNT_LINKS], total, &hlo, &hhi);
-            if (GATE) mark_link_hole(hlo, hhi);
-            lbase = chunk_take_shared(W, 1, &b.cnt[CNT_LKCELLS], __popc(has), &hlo, &hhi);
-            mark_hole(hlo, hhi);
-            if (lane == 0) W.used += total;
+        // One reservation for the links of h1; with more than kFound of them, twice as
+        // many slots, the second half holding them in search order until they are sorted.
+        const uint32_t nres = nf <= (uint32_t)kFound ? nf : 2 * nf;
+        unsigned long long hlo, hhi;
+        const unsigned long long lbase = chunk_take_shared(W, 0, &b.cnt[CNT_LINKS], nres, &hlo, &hhi);
+        mark_link_hole(hlo, hhi);
+        const bool lvalid = lbase + nres <= cap_links;
+        if (lane == 0) {
+          W.used += nf;
+          W.lbase = lbase;
+          W.lvalid = lvalid;
+        }
+        if (!lvalid) {
+          if (lane == 0) atomicOr(&b.cnt[CNT_STATUS], ST_LINKS);
+          mark_link_hole(lbase, lbase + nres);  // slots below the capacity stay readable
+        } else if (nf > (uint32_t)kFound) {
+          for (uint32_t i = lane; i < (uint32_t)kFound; i += 32)
+            write_link(lbase + nf + i, W.fs[i], W.fd[i], W.fq[i]);
+        }
+      }
+
+      // The links of h1, sorted by source cell (stable), form one list per source:
+      // link_off / link_cnt of each source, which joins the list of possible roots.
+      __syncwarp();
+      if (nfound > 0 && W.lvalid) {
+        const unsigned long long lbase = W.lbase;
+        const bool big = nfound > (uint32_t)kFound;
+        const unsigned long long tmp = lbase + nfound;  // search-order copy when big
+        auto src_of = [&](uint32_t j) { return big ? b.link_src[tmp + j] : W.fs[j]; };
+        for (uint32_t i0 = 0; i0 < nfound; i0 += 32) {
+          const uint32_t i = i0 + lane;
+          uint32_t a = kHole, rank = 0, cnt = 0, c = 0;
+          float q = 0.0f;
+          bool first = false;
+          if (i < nfound) {
+            a = src_of(i);
+            first = true;
+            for (uint32_t j = 0; j < nfound; ++j) {
+              const uint32_t aj = src_of(j);
+              rank += (aj < a) || (aj == a && j < i);
+              cnt += aj == a;
+              first = first && !(aj == a && j < i);
+            }
+            c = big ? b.link_dst[tmp + i] : W.fd[i];
+            q = big ? b.link_q[tmp + i] : W.fq[i];
           }
-          uint32_t mybase = kNoBase;
-          if (nlk > 0) {
-            const uint32_t a = W.a[lane];
-            const uint64_t base = wbase + inc - nlk;
-            const uint64_t li = lbase + __popc(has & lt_mask);
-            if (base + nlk > cap_links || li >= cap_links) {
-              atomicOr(&b.cnt[CNT_STATUS], ST_LINKS);
-              if (li < cap_links) b.lk_cells[li] = kHole;  // keep the list readable
-              if (GATE)
-                for (uint64_t i = base; i < base + nlk && i < cap_links; ++i) b.link_src[i] = kHole;
-            } else {
-              b.link_off[a] = (uint32_t)base;
-              b.link_cnt[a] = nlk;
-              if (!GATE) b.has_out[a] = 1;  // gated form: set by the gate for kept links
-              b.lk_cells[li] = a;
-              mybase = (uint32_t)base;
+          __syncwarp();
+          if (i < nfound) {
+            write_link(lbase + rank, a, c, q);
+            if (first) {
+              b.link_off[a] = (uint32_t)(lbase + rank);
+              b.link_cnt[a] = cnt;
             }
           }
-          W.base[lane] = mybase;
-          __syncwarp();
-          const uint32_t nk = min(nf, (uint32_t)kFound);
-          for (uint32_t i = lane; i < nk; i += 32) {
-            const uint32_t e = W.fa[i];
-            const uint32_t bs = W.base[e >> 8];
-            if (bs != kNoBase) write_link((uint64_t)bs + (e & 0xffu), W.a[e >> 8], W.fc[i], W.fq[i]);
+          const unsigned fm = __ballot_sync(kFull, first);
+          if (fm) {
+            unsigned long long rlo, rhi;
+            const unsigned long long rb = chunk_take_shared(W, 1, &b.cnt[CNT_LKCELLS], __popc(fm), &rlo, &rhi);
+            mark_root_hole(rlo, rhi);
+            const unsigned long long ri = rb + __popc(fm & lt_mask);
+            if (first) {
+              if (ri < cap_links) b.lk_cells[ri] = a;
+              else atomicOr(&b.cnt[CNT_STATUS], ST_LINKS);
+            }
           }
+        }
+        if (big) {
+          __syncwarp();
+          mark_link_hole(tmp, tmp + nfound);
         }
       }
       __syncwarp();
@@ -393,8 +432,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
     __syncwarp();
   }
   __syncwarp();
-  mark_hole(W.chunk_next[1], W.chunk_end[1]);
-  if (GATE) mark_link_hole(W.chunk_next[0], W.chunk_end[0]);
+  mark_root_hole(W.chunk_next[1], W.chunk_end[1]);
+  mark_link_hole(W.chunk_next[0], W.chunk_end[0]);
   if (lane == 0 && W.used) atomicAdd(&b.cnt[CNT_LINKS_USED], W.used);
 }
 

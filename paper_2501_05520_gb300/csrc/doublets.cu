@@ -26,12 +26,12 @@ constexpr float kHalfPi = 1.57079632679489661923f;
 constexpr int kWarpsPerBlock = 8;
 
 // Largest azimuth difference (radians) between an inner hit at ri and any outer hit
-// at radius <= ro_max that can pass D1 (same hemisphere) and D2 (curvature <= kmax).
-__device__ __forceinline__ float phi_window(float kmax, float ri, float ro_max) {
-  const float a = 0.5f * kmax * ro_max;
-  if (a >= 0.7f) return kHalfPi + 1e-3f;  // only D1 bounds the angle
-  const float b = fminf(0.5f * kmax * ri, a);
-  return fminf(asinf(a) - asinf(b) + 1e-4f, kHalfPi + 1e-3f);
+// at radius <= ro_max that can pass D1 (same hemisphere) and D2 (curvature <= kmax):
+// asin(kmax*ro_max/2) - asin(kmax*ri/2), given the first term (asin_o, +inf when
+// kmax*ro_max/2 >= 0.7, where only D1 bounds the angle) and the second (asin_i).
+__device__ __forceinline__ float phi_window(float asin_o, float asin_i) {
+  if (asin_o == __int_as_float(0x7f800000)) return kHalfPi + 1e-3f;
+  return fminf(asin_o - asin_i + 1e-4f, kHalfPi + 1e-3f);
 }
 
 // Writes one cell and takes its rank among the cells ending on the same outer hit.
@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
     const int bin = gb - el * B;
     const float4 hi = b.hit4[s];
     const int nout = kNOuter[L];
+    const float asin_i = asinf(0.5f * cuts.kmax * hi.w);  // unused where the outer term is +inf
     for (int k = 0; k < nout; ++k) {
       const int Lo = kOuter[L][k];
       const float ro_max = __uint_as_float(b.layer_rmax[e * kLayers + Lo]);
@@ -81,7 +82,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
       float mdr = __int_as_float(0x7f800000);
       uint32_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;  // up to two sorted-hit ranges
       if (ro_max > hi.w) {
-        const int w = (int)ceilf(phi_window(cuts.kmax, hi.w, ro_max) * bins_per_rad) + 1;
+        const int w =
+            (int)ceilf(phi_window(b.layer_asin[e * kLayers + Lo], asin_i) * bins_per_rad) + 1;
         const uint32_t base = (uint32_t)(e * kLayers + Lo) * (uint32_t)B;
         if (2 * w + 1 >= B) {
           r0 = b.bin_start[base];

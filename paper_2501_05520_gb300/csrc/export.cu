@@ -59,28 +59,23 @@ __global__ void k_export_cells(Buffers b, uint64_t cap_cells, int32_t* out3) {
   }
 }
 
-__global__ void k_export_links(Buffers b, uint64_t cap_cells, int32_t* out4, float* outq,
+__global__ void k_export_links(Buffers b, uint64_t cap_links, int32_t* out4, float* outq,
                                bool gated) {
-  const uint64_t nc = min(b.cnt[CNT_CELLS], (unsigned long long)cap_cells);
+  const uint64_t nl = min(b.cnt[CNT_LINKS], (unsigned long long)cap_links);
   const int E = b.hdr->n_events;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nc; a += stride) {
-    if (b.cell_out[a] == kHole || !b.has_out[a]) continue;  // allocation hole or no links
-    const uint32_t n = b.link_cnt[a];
+  for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += stride) {
+    const uint32_t a = b.link_src[l];
+    if (a == kHole || (gated && !b.gate_keep[l])) continue;  // hole or removed link
     const int32_t g0 = (int32_t)b.perm[b.cell_in[a]], g1 = (int32_t)b.perm[b.cell_out[a]];
+    const int32_t g2 = (int32_t)b.perm[b.cell_out[b.link_dst[l]]];
     const int e = find_event(b.hit_off, E, g0);
     const int32_t off = b.hit_off[e];
-    const uint32_t l0 = b.link_off[a];
-    for (uint32_t i = 0; i < n; ++i) {
-      const uint32_t l = l0 + i;
-      if (gated && !b.gate_keep[l]) continue;
-      const int32_t g2 = (int32_t)b.perm[b.cell_out[b.link_dst[l]]];
-      out4[(uint64_t)l * 4 + 0] = g0 - off;
-      out4[(uint64_t)l * 4 + 1] = g1 - off;
-      out4[(uint64_t)l * 4 + 2] = g2 - off;
-      out4[(uint64_t)l * 4 + 3] = e;
-      outq[l] = b.link_q[l];
-    }
+    out4[l * 4 + 0] = g0 - off;
+    out4[l * 4 + 1] = g1 - off;
+    out4[l * 4 + 2] = g2 - off;
+    out4[l * 4 + 3] = e;
+    outq[l] = b.link_q[l];
   }
 }
 
@@ -98,7 +93,7 @@ void launch_export_cells(const Buffers& b, const Params& p, const Launch& l, int
 }
 void launch_export_links(const Buffers& b, const Params& p, const Launch& l, int32_t* out4,
                          float* outq, cudaStream_t s, bool gated) {
-  k_export_links<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_cells, out4, outq, gated);
+  k_export_links<<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links, out4, outq, gated);
 }
 
 }  // namespace ptca

@@ -312,23 +312,18 @@ __global__ void __launch_bounds__(kTileM, 1)
 // float32 features of every current link (gated form: kept links only), row = link slot.
 __global__ void k_gate_features_f32(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap_links,
                                     bool gated, float* out) {
-  const uint64_t nl = min(b.cnt[CNT_LKCELLS], (unsigned long long)cap_links);
+  const uint64_t nl = min(b.cnt[CNT_LINKS], (unsigned long long)cap_links);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += stride) {
-    const uint32_t a = b.lk_cells[i];
-    if (a == kHole) continue;
+  for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += stride) {
+    const uint32_t a = b.link_src[l];
+    if (a == kHole || (gated && !b.gate_keep[l])) continue;
     const uint32_t h0 = b.cell_in[a], h1 = b.cell_out[a];
-    const float4 p0 = b.hit4[h0], p1 = b.hit4[h1];
-    const int L0 = b.cell_l0[a], L1 = (b.hbin[h1] / B) % kLayers;
-    const uint32_t off = b.link_off[a], cnt = b.link_cnt[a];
-    for (uint32_t l = off; l < off + cnt; ++l) {
-      if (gated && !b.gate_keep[l]) continue;
-      const uint32_t h2 = b.cell_out[b.link_dst[l]];
-      float f[kGateFeat];
-      gate_link_features(cuts, p0, p1, b.hit4[h2], L0, L1, (b.hbin[h2] / B) % kLayers, f);
+    const uint32_t h2 = b.cell_out[b.link_dst[l]];
+    float f[kGateFeat];
+    gate_link_features(cuts, b.hit4[h0], b.hit4[h1], b.hit4[h2], b.cell_l0[a],
+                       (b.hbin[h1] / B) % kLayers, (b.hbin[h2] / B) % kLayers, f);
 #pragma unroll
-      for (int k = 0; k < kGateFeat; ++k) out[(uint64_t)l * kGateFeat + k] = f[k];
-    }
+    for (int k = 0; k < kGateFeat; ++k) out[l * kGateFeat + k] = f[k];
   }
 }
 

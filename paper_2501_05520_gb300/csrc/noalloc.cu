@@ -18,13 +18,25 @@ constexpr size_t kNaAlign = 256;
 
 constexpr size_t na_round(size_t x) { return (x + kNaAlign - 1) / kNaAlign * kNaAlign; }
 constexpr size_t kNaNb = (size_t)kLayers * kNaBins + 1;
-constexpr size_t kNaBytes =
-    na_round(sizeof(BatchHeader)) + na_round(CNT_N * 8) + na_round(2 * 4) +      // hdr, cnt, off
-    2 * na_round(kNaMaxHits * 4) +                                                // in_bin, rank
-    na_round(kNaMaxHits * 16) + 2 * na_round(kNaMaxHits * 4) +                    // hit4, perm, hbin
-    2 * na_round(kNaNb * 4) + na_round(kLayers * 4) +                             // bins, rmax
-    2 * na_round((kNaMaxHits + 1) * 4) + na_round(kNaMaxHits) +                   // cleared arrays
-    na_round((kScanBlocks + 1) * 4);                                              // scan partials
+// Bytes of each scratch buffer, in the order na_layout carves them.
+enum NaPart {
+  NA_HDR, NA_CNT, NA_OFF, NA_IN_BIN, NA_IN_RANK, NA_HIT4, NA_PERM, NA_HBIN, NA_BIN_CNT,
+  NA_BIN_START, NA_RMAX, NA_ASIN, NA_BUCKET_CNT, NA_IN_CNT, NA_USED, NA_SCAN,
+  NA_PARTS
+};
+constexpr size_t kNaPart[NA_PARTS] = {
+    sizeof(BatchHeader), CNT_N * 8, 2 * 4,                   // header, counters, offsets
+    kNaMaxHits * 4, kNaMaxHits * 4,                          // in_bin, in_rank
+    kNaMaxHits * 16, kNaMaxHits * 4, kNaMaxHits * 4,         // hit4, perm, hbin
+    kNaNb * 4, kNaNb * 4, kLayers * 4, kLayers * 4,          // bins, layer r max, layer asin
+    (kNaMaxHits + 1) * 4, (kNaMaxHits + 1) * 4, kNaMaxHits,  // cleared: bucket, in, used
+    (kScanBlocks + 1) * 4};                                  // scan partials
+constexpr size_t na_offset(int part) {
+  size_t off = 0;
+  for (int i = 0; i < part; ++i) off += na_round(kNaPart[i]);
+  return off;
+}
+constexpr size_t kNaBytes = na_offset(NA_PARTS);
 
 // The scratch.  Every GPU that loads the library holds it until the process exits.
 static __device__ __align__(256) unsigned char g_scratch[kNaBytes];
@@ -32,28 +44,24 @@ static __device__ __align__(256) unsigned char g_scratch[kNaBytes];
 // Carves the scratch (device address `base`) into the buffers the binning kernels use.
 Buffers na_layout(char* base, const float* x, const float* y, const float* z,
                   const uint8_t* layer) {
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    char* p = base + off;
-    off += na_round(bytes);
-    return p;
-  };
+  auto at = [&](int part) { return base + na_offset(part); };
   Buffers b{};
-  b.hdr = (BatchHeader*)take(sizeof(BatchHeader));
-  b.cnt = (unsigned long long*)take(CNT_N * 8);
-  b.hit_off = (int32_t*)take(2 * 4);
-  b.in_bin = (uint32_t*)take(kNaMaxHits * 4);
-  b.in_rank = (uint32_t*)take(kNaMaxHits * 4);
-  b.hit4 = (float4*)take(kNaMaxHits * 16);
-  b.perm = (uint32_t*)take(kNaMaxHits * 4);
-  b.hbin = (uint32_t*)take(kNaMaxHits * 4);
-  b.bin_cnt = (uint32_t*)take(kNaNb * 4);
-  b.bin_start = (uint32_t*)take(kNaNb * 4);
-  b.layer_rmax = (uint32_t*)take(kLayers * 4);
-  b.bucket_cnt = (uint32_t*)take((kNaMaxHits + 1) * 4);
-  b.in_cnt = (uint32_t*)take((kNaMaxHits + 1) * 4);
-  b.used = (uint8_t*)take(kNaMaxHits);
-  b.scan_part = (uint32_t*)take((kScanBlocks + 1) * 4);
+  b.hdr = (BatchHeader*)at(NA_HDR);
+  b.cnt = (unsigned long long*)at(NA_CNT);
+  b.hit_off = (int32_t*)at(NA_OFF);
+  b.in_bin = (uint32_t*)at(NA_IN_BIN);
+  b.in_rank = (uint32_t*)at(NA_IN_RANK);
+  b.hit4 = (float4*)at(NA_HIT4);
+  b.perm = (uint32_t*)at(NA_PERM);
+  b.hbin = (uint32_t*)at(NA_HBIN);
+  b.bin_cnt = (uint32_t*)at(NA_BIN_CNT);
+  b.bin_start = (uint32_t*)at(NA_BIN_START);
+  b.layer_rmax = (uint32_t*)at(NA_RMAX);
+  b.layer_asin = (float*)at(NA_ASIN);
+  b.bucket_cnt = (uint32_t*)at(NA_BUCKET_CNT);
+  b.in_cnt = (uint32_t*)at(NA_IN_CNT);
+  b.used = (uint8_t*)at(NA_USED);
+  b.scan_part = (uint32_t*)at(NA_SCAN);
   b.in_x = (float*)x;
   b.in_y = (float*)y;
   b.in_z = (float*)z;

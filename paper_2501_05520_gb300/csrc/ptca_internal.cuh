@@ -104,6 +104,8 @@ struct Buffers {
   uint32_t* bin_cnt;         // [max_events*10*B + 1]
   uint32_t* bin_start;       // [max_events*10*B + 1]
   uint32_t* layer_rmax;      // [max_events*10] float bits of max r per event layer
+  float* layer_asin;         // [max_events*10] asin(kmax r_max / 2) per event layer,
+                             //   +inf when kmax r_max / 2 >= 0.7
   // doublet segments: per sorted hit and outer-layer slot (all 3 slots written)
   Segment* seg;              // [max_hits*3]
   // cells
@@ -113,8 +115,8 @@ struct Buffers {
   uint8_t* cell_l0;          // [max_cells] layer of the inner hit
   uint8_t* has_in;           // [max_cells] an accepted link ends on the cell
   uint8_t* has_out;          // [max_cells] an accepted link starts from the cell
-  uint32_t* link_off;        // [max_cells] valid where has_out
-  uint32_t* link_cnt;        // [max_cells] valid where has_out
+  uint32_t* link_off;        // [max_cells] first slot of the cell's links (valid where it
+  uint32_t* link_cnt;        //   has links) and their number
   uint32_t* lk_cells;        // [max_links] cells with >= 1 outgoing link
   unsigned long long* best;  // [max_cells] duplicate-cleaning key (cells on ntuplets)
   uint32_t* in_cnt;          // [max_hits + 1] cells ending on each sorted hit
@@ -144,8 +146,8 @@ struct Buffers {
   uint16_t* gate_x;          // [max_links*16] bf16 features per link slot (12 used)
   float* gate_score;         // [max_links] logit per link slot
   uint8_t* gate_keep;        // [max_links] 1 where the link passes the gate
-  uint32_t* link_src;        // [max_links] source cell of each link slot (gated form),
-                             //   kHole for unused slots
+  uint32_t* link_src;        // [max_links] source cell of each link slot, kHole for unused
+                             //   slots
   int32_t* exp_hits;         // [max_ntuplets*6] export staging (event-local indices)
   uint8_t* exp_n;            // [max_ntuplets]
   float* exp_q;              // [max_ntuplets]

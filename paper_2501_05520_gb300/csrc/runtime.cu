@@ -70,6 +70,7 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.bin_cnt = (uint32_t*)take(NB * 4);
   t.bin_start = (uint32_t*)take(NB * 4);
   t.layer_rmax = (uint32_t*)take(E * kLayers * 4);
+  t.layer_asin = (float*)take(E * kLayers * 4);
   t.seg = (Segment*)take(N * kMaxOuter * sizeof(Segment));
   t.cell_in = (uint32_t*)take(C * 4);
   t.cell_out = (uint32_t*)take(C * 4);

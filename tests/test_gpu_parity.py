@@ -235,3 +235,53 @@ def test_bench_configuration_sampled(cuts):
         sl = slice(evoff[e], evoff[e + 1])
         assert_ntuplets_equal(hits[sl], oracle.survivors_hits(ref), ref)
         assert_fits_close(tracks[sl], ref["fit"])
+
+
+class _Hits:
+    """Bare hit arrays in the Event layout that sim.concat reads."""
+
+    def __init__(self, x, y, z, layer):
+        self.x, self.y, self.z = (np.asarray(v, np.float32) for v in (x, y, z))
+        self.layer = np.asarray(layer, np.uint8)
+        self.n_hits = self.x.size
+
+
+def _fan_event(sizes, seed=0):
+    """Middle hits on layer 1, each crossed by n x n nearly collinear radial lines: n hits
+    on layer 0 and n on layer 2 whose r-z slopes differ by 1e-4, so every (inner, outer)
+    pair through the middle hit passes C1-C3 and the middle hit carries n*n links."""
+    rng = np.random.default_rng(seed)
+    x, y, z, lay = [], [], [], []
+    for k, n in enumerate(sizes):
+        phi = 0.4 + 0.9 * k
+        z1 = -10.0 + 7.0 * k
+        t0 = rng.uniform(-1, 1)
+        pts = [(6.8, z1, 1)]
+        for i in range(n):
+            t = t0 + 1e-4 * i
+            pts.append((2.9, z1 - t * (6.8 - 2.9), 0))
+            pts.append((10.9, z1 + t * (10.9 - 6.8), 2))
+        for r, zz, L in pts:
+            x.append(r * np.cos(phi))
+            y.append(r * np.sin(phi))
+            z.append(zz)
+            lay.append(L)
+    return _Hits(x, y, z, lay)
+
+
+def test_dense_middle_hits_many_links(cuts):
+    """Middle hits with 64 (the in-kernel collection), 81 and 144 links: the second search
+    pass, the per-source sort of a hit's links and the temporary copy it uses."""
+    ev = _fan_event([8, 9, 12, 3])
+    ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts)
+    h1 = ref["cell_outer"][ref["link_a"]]
+    assert sorted(np.bincount(h1)[np.bincount(h1) > 0].tolist()) == [9, 64, 81, 144]
+    with pt.Context(cuts=cuts, capacity=SMALL_CAP) as ctx:
+        out = run_stages(ctx, [ev, sim.generate(sim.SINGLE_MUON_LIKE, 1100)])
+        check_event(out, 0, ev, ref)
+        n_links = out["n_links"]
+        # the same batch through the captured whole-chain graph
+        hits, nh, tr, eoff = ctx.pt_reconstruct_batch(*sim.concat(
+            [ev, sim.generate(sim.SINGLE_MUON_LIKE, 1100)]))
+    assert n_links == ref["link_a"].size + out["links"][0][out["links"][4] == 1].size
+    assert_ntuplets_equal(hits[eoff[0]:eoff[1]], oracle.survivors_hits(ref), ref)
