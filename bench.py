@@ -41,11 +41,19 @@ SEED0 = 3000
 METRIC = "PU200 events/s on 1 GB300, plain CA vs MLP-gated (eff ≥ plain−0.5%); p99 ms"
 WORKLOAD = ("PU200: 10k helices/event (1/pT~U[0.1,2] GeV^-1, |eta|<2.5, z0~N(0,5cm)), "
             "4 barrel layers + 2x3 disks, 2% noise, ~41k hits/event; plain CA")
-# kernels per step: load 6 (clear, histogram, 3 scan, scatter), doublets 1, links 1,
-# ntuplets 15 (search, bucket count, 3 scan, scatter, bucket sort, 3 cleaning, 3 scan,
-# compact, offsets), fit 1
-LAUNCHES_PER_STEP = 24
 FLUSH_BYTES = 256 << 20
+TRACE_STEPS = 5      # extra stage-path steps with per-kernel CUDA events (after the timing)
+CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped to [20, 250]
+
+# DRAM traffic per event of the main kernels from one ncu capture (8 PU200 events per
+# launch, profiles/), valid only while the kernel's sources hash to the recorded value.
+NCU_TRAFFIC = {
+    "k_doublets": {"bytes_per_event": 41678208, "issue_active_pct": 72.1, "sha": "ef12f61da283"},
+    "k_in_scatter": {"bytes_per_event": 38948448, "issue_active_pct": 23.8, "sha": "08f4ef1d7a25"},
+    "k_connect": {"bytes_per_event": 36949760, "issue_active_pct": 64.6, "sha": "08f4ef1d7a25"},
+    "k_find_ntuplets": {"bytes_per_event": 59041664, "issue_active_pct": 11.8,
+                        "sha": "fd6594bb0d0b"},
+}
 
 
 def make_events(n: int, seed0: int = SEED0):
@@ -59,15 +67,36 @@ def capacity(batch: int = BATCH, phi_bins: int = 1024) -> dict:
                                ntuplets_per_event=196_608, phi_bins=phi_bins)
 
 
-# Algorithmic bytes per unit (read once + written once), per stage.
-def algorithmic_bytes(n_hits: int, cells: int, links: int, cand: int, survivors: int) -> dict:
+# Algorithmic bytes of one launch of each main kernel (every array the kernel must touch,
+# read once or written once, in this library's layout): N hits, C cells, Lk links,
+# T ntuplet candidates.
+def kernel_bytes(kernel: str, c: dict) -> int | None:
+    N, C, Lk, T = c["hits"], c["cells"], c["links"], c["candidates"]
     return {
-        "load": 13 * n_hits + 20 * n_hits,
-        "doublets": 20 * n_hits + 10 * cells,
-        "connect": 8 * cells + 8 * n_hits + 4 * links + 1 * cells,
-        "ntuplets": 4 * links + 4 * cells + 29 * cand + 2 * 29 * cand + 4 * 5 * cand,
-        "fit": (6 * 12 + 36) * survivors,
-    }
+        # hit (x,y,z,r) 16 N; segments 48 N; in-degree counters 8 N (atomic read+write);
+        # cells (inner, outer, rank, layer, 2 flags) 15 C
+        "k_doublets": 16 * N + 48 * N + 8 * N + 15 * C,
+        # segments 48 N, layer tag 4 N, in_start 4 N; cell outer + rank 8 C; records 8 C
+        "k_in_scatter": 56 * N + 16 * C,
+        # in_start 4 N, segments 48 N, hits 16 N; records 8 C, outer hit of staged cells
+        # 4 C; links (source, target, quality) 12 Lk, per-cell lists and flags <= 14 Lk
+        "k_connect": 68 * N + 12 * C + 26 * Lk,
+        # roots and their flags and lists <= 14 Lk, link targets and qualities 8 Lk;
+        # candidates (6 hits, 5 cells, n, q) 49 T
+        "k_find_ntuplets": 22 * Lk + 49 * T,
+    }.get(kernel)
+
+
+def kernel_sources_sha(kernel: str) -> str:
+    import hashlib
+    src = {"k_doublets": "doublets.cu", "k_in_scatter": "connect.cu", "k_connect": "connect.cu",
+           "k_find_ntuplets": "ntuplets.cu"}[kernel]
+    d = os.path.join(ROOT, "paper_2501_05520_gb300", "csrc")
+    h = hashlib.sha1()
+    for f in (src, "ptca_internal.cuh"):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
 
 
 class Clocks:
@@ -229,6 +258,34 @@ def _timed(ctx, dbat, steps, flush, stream):
     return step, stage
 
 
+def _config4(ctx, dev, flush, stream, steps, warmup, n_events):
+    """The batch workload through the whole-chain CUDA graph (pt_enqueue_batch), inputs in
+    device memory, L2 flushed before every step outside its events."""
+    import torch
+    pus = sim.batch_pileups(CONFIG4_SEED0, n_events)
+    evs = [sim.pileup_event(CONFIG4_SEED0 + i, int(p)) for i, p in enumerate(pus)]
+    off, *arrs = sim.concat(evs)
+    d = [torch.from_numpy(a).to(dev) for a in arrs]
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            ctx.pt_enqueue_batch(off, *d)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            ctx.pt_enqueue_batch(off, *d)
+            e1.record(stream)
+    stream.synchronize()
+    ctx.pt_get_ntuplets()  # raises on any capacity or input error
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return {"value": n_events * steps / (sum(ms) / 1000.0), "unit": "events/s",
+            "ms_per_step": statistics.mean(ms), "events_per_step": n_events,
+            "hits_per_step": int(off[-1]),
+            "workload": f"pileup ~ Poisson(140) in [20, 250], seeds {CONFIG4_SEED0}+i",
+            "path": "whole-chain CUDA graph, device inputs"}
+
+
 def _physics(ctx, host, events):
     """Efficiency, fake and duplicate rates of the cleaned ntuplets (generator truth)."""
     from sim import truth
@@ -331,6 +388,7 @@ def run_ours(args):
     forms = {}
     counts = None
     clocks = None
+    kernels, launches = {}, {}
     for form in ("plain", "gated"):
         ctx.pt_set_gate(gw if form == "gated" else None, gtau)
         with torch.cuda.stream(stream):
@@ -359,6 +417,14 @@ def run_ours(args):
             if dist:
                 dist.barrier()
             ctx.pt_get_ntuplets()
+            # per-kernel device times, on extra steps after the timed region
+            ctx.pt_set_tracing(True)
+            _timed(ctx, dbat, TRACE_STEPS, flush, stream)
+            trace = ctx.pt_get_trace()
+            ctx.pt_set_tracing(False)
+            kernels[form] = {k: round(ms / n, 4) for k, (ms, n) in trace.items()}
+            launches[form] = sum(n * (3 if k == "scan" else 1)
+                                 for k, (_, n) in trace.items()) // TRACE_STEPS
         total_s = max_over_ranks(sum(step_ms) / 1000.0, dist, dev)
         # end to end through the public call: pinned host in, host out
         pin = [torch.from_numpy(a).pin_memory() for a in host[0][1:]]
@@ -385,18 +451,22 @@ def run_ours(args):
                  "d2h_bytes_per_step": S * (24 + 1 + 36) + (B + 1) * 8 + 128},
             physics=_physics(ctx, host, events) if not args.no_physics else None)
     ctx.pt_set_gate(None, 0.0)
+    config4 = _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)
 
-    # roofline of the dominant kernel of the plain form
+    # roofline of the dominant kernel of the plain form (mean traced launch duration)
     plain = forms["plain"]
-    mean_stage = plain["stages_ms"]
-    dom = max(("doublets", "connect"), key=lambda n: mean_stage[n])
-    ab = algorithmic_bytes(counts["hits"], counts["cells"], counts["links"], counts["candidates"],
-                           counts["survivors"])
+    km = kernels["plain"]
+    dom = max((k for k in km if kernel_bytes(k, counts) is not None), key=lambda k: km[k])
+    ab = kernel_bytes(dom, counts)
     peaks = _peaks()
-    achieved = ab[dom] / (mean_stage[dom] / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved,
+    achieved = ab / (km[dom] / 1000.0) / 1e9
+    rec = NCU_TRAFFIC.get(dom)
+    fresh = rec is not None and rec["sha"] == kernel_sources_sha(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": None, "peak_src": peaks["src"], "algorithmic_bytes": ab[dom]}
+                "traffic": int(rec["bytes_per_event"] * B) if fresh else None,
+                "peak_src": peaks["src"], "algorithmic_bytes": ab, "launch_ms": km[dom],
+                "issue_active_pct": rec["issue_active_pct"] if fresh else None}
 
     if rank == 0:
         line = {"metric": METRIC, "value": plain["value"], "unit": "events/s", "n_gpus": world,
@@ -414,13 +484,17 @@ def run_ours(args):
                 "e2e": plain["e2e"],
                 "roofline": roofline,
                 "stages_ms": plain["stages_ms"],
-                "gated": {k: forms["gated"][k] for k in ("value", "ms_per_step", "p99_ms_per_step",
-                                                         "stages_ms", "e2e")},
+                "kernels_ms": kernels["plain"],
+                "gated": dict({k: forms["gated"][k] for k in ("value", "ms_per_step",
+                                                              "p99_ms_per_step", "stages_ms",
+                                                              "e2e")},
+                              kernels_ms=kernels["gated"]),
                 "physics": {"plain": plain["physics"], "gated": forms["gated"]["physics"]},
                 "counts_per_step": counts,
+                "batch_workload": config4,
                 "autotune": launch,
                 "clocks": clocks,
-                "gpu_launches": LAUNCHES_PER_STEP * args.steps}
+                "gpu_launches": launches["plain"] * args.steps}
         if not args.no_serving:
             line["serving"] = {"plain": _serving(pt, args.serve_rate, args.serve_seconds),
                                "gated": _serving(pt, args.serve_rate, args.serve_seconds,
@@ -436,7 +510,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--batch", type=int, default=BATCH)

@@ -265,6 +265,28 @@ pt_status pt_find_doublets_noalloc(const pt_cuts* cuts, int64_t n, const float* 
                                    int32_t* inner, int32_t* outer, int64_t cap, int64_t* n_out,
                                    void* stream);
 
+/* ------------------------------------------------------------------ tracing */
+
+/* Total device time of one kernel (or of one prefix-sum helper, "scan") over the
+ * launches traced since the last pt_get_trace. */
+typedef struct {
+  char name[48];     /* kernel name, NUL terminated */
+  double total_ms;   /* sum of CUDA-event durations */
+  int64_t launches;  /* number of traced launches */
+} pt_kernel_time;
+
+/* Per-kernel timing of the stage calls (on = 1) or none (on = 0, the default): every
+ * kernel launched by pt_load_*, pt_build_doublets, pt_connect_cells, pt_find_ntuplets,
+ * pt_fit_tracks and the getters is bracketed by CUDA events on the context's stream.
+ * The whole-batch graph (pt_reconstruct_batch, pt_enqueue_batch) is never traced.
+ * Synchronises the stream; switching off discards what was not read. */
+pt_status pt_set_tracing(pt_ctx* ctx, int on);
+
+/* Synchronises the stream and returns the per-kernel totals since the last call, in
+ * the order the kernels first ran; *n receives their number.  PT_ERR_INVALID when
+ * tracing is off, PT_ERR_CAPACITY when cap < *n (the totals are kept). */
+pt_status pt_get_trace(pt_ctx* ctx, pt_kernel_time* out, int cap, int* n);
+
 /* ------------------------------------------------------------------ tuning */
 
 /* Launch sizes of the persistent grid-stride kernels, in blocks per multiprocessor

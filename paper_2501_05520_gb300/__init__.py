@@ -32,13 +32,19 @@ EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt
             "pt_find_doublets_noalloc", "pt_set_gate", "pt_get_link_features", "pt_gate_score",
             "pt_gate_loss_grad", "pt_gate_adam", "pt_server_create", "pt_server_set_gate",
             "pt_submit", "pt_poll", "pt_server_stats", "pt_server_reset_stats",
-            "pt_server_destroy", "pt_set_launch", "pt_autotune", "pt_last_error")
+            "pt_server_destroy", "pt_set_launch", "pt_autotune", "pt_set_tracing",
+            "pt_get_trace", "pt_last_error")
 
 
 class PtCuts(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_float), ("z0max", ctypes.c_float), ("cotmax", ctypes.c_float),
                 ("rz0", ctypes.c_float), ("rz1", ctypes.c_float), ("dca_b0", ctypes.c_float),
                 ("dca_other", ctypes.c_float)]
+
+
+class PtKernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("total_ms", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
 
 
 class PtGeometry(ctypes.Structure):
@@ -112,6 +118,8 @@ def lib() -> ctypes.CDLL:
             "pt_server_reset_stats": [P],
             "pt_server_destroy": [P],
             "pt_set_launch": [P, I32, I32],
+            "pt_set_tracing": [P, I32],
+            "pt_get_trace": [P, P, I32, P],
             "pt_autotune": [ctypes.POINTER(PtGeometry), ctypes.POINTER(PtCuts),
                             ctypes.POINTER(PtCapacity), I32, I32, P, P, P, P, P, P, I32, P, I32,
                             P, I32, I32, P, P],
@@ -337,6 +345,17 @@ class Context:
 
     def pt_set_launch(self, blocks_per_sm: int = 4, search_blocks_per_sm: int = 5):
         _check(lib().pt_set_launch(self.handle, int(blocks_per_sm), int(search_blocks_per_sm)))
+
+    def pt_set_tracing(self, on: bool = True):
+        _check(lib().pt_set_tracing(self.handle, 1 if on else 0))
+
+    def pt_get_trace(self) -> dict:
+        """{kernel: (total ms, launches)} since the last call (tracing must be on)."""
+        out = (PtKernelTime * 64)()
+        n = ctypes.c_int(0)
+        _check(lib().pt_get_trace(self.handle, out, 64, ctypes.byref(n)))
+        return {out[i].name.decode(): (out[i].total_ms, int(out[i].launches))
+                for i in range(n.value)}
 
     # -------------------------------------------------------------- learned gate
     def pt_set_gate(self, w, tau: float):

@@ -177,13 +177,13 @@ void launch_scan(const uint32_t* in, uint32_t* out, const unsigned long long* n_
 }
 
 void launch_clear(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s) {
-  k_clear<<<l.grid, 256, 0, s>>>(b, p.phi_bins);
+  PT_TRACE(l, s, "k_clear", k_clear<<<l.grid, 256, 0, s>>>(b, p.phi_bins));
 }
 
 void launch_bin_hits(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s) {
-  k_bin_count<<<l.grid, 256, 0, s>>>(b, p.phi_bins);
-  launch_scan(b.bin_cnt, b.bin_start, &b.cnt[CNT_SCAN_BINS], b.scan_part, s);
-  k_bin_scatter<<<l.grid, 256, 0, s>>>(b, p.cuts.kmax);
+  PT_TRACE(l, s, "k_bin_count", k_bin_count<<<l.grid, 256, 0, s>>>(b, p.phi_bins));
+  PT_TRACE(l, s, "scan", launch_scan(b.bin_cnt, b.bin_start, &b.cnt[CNT_SCAN_BINS], b.scan_part, s));
+  PT_TRACE(l, s, "k_bin_scatter", k_bin_scatter<<<l.grid, 256, 0, s>>>(b, p.cuts.kmax));
 }
 
 }  // namespace ptca

@@ -237,6 +237,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
       // counts all; if there were more, pass 1 repeats the search and writes the rest
       // straight into the reserved block.
       uint32_t nfound = 0;
+#pragma unroll 1
       for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1 && nfound <= (uint32_t)kFound) break;
         uint32_t head = 0, tail = 0, nf = 0;
@@ -326,31 +327,36 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
               w[k] = m > 0.0f ? wk * 1.01f + 1e-3f : kInf;
             }
           }
-          if (fits) {
-#pragma unroll
-            for (int k = 0; k < kMaxOuter; ++k)
-              if (W.sg[k].cnt) sweep(W.pos[k], round4(W.sg[k].cnt), ta, w[k], ix);
-          } else {
-#pragma unroll
-            for (int k = 0; k < kMaxOuter; ++k) {
-              const uint32_t cnt = W.sg[k].cnt, off = W.sg[k].off;
-              for (uint32_t j0 = 0; j0 < cnt; j0 += kOutStage) {
-                const uint32_t n = min(cnt - j0, (uint32_t)kOutStage);
+          // One sweep site: the staged segments, or (when they do not fit) each piece
+          // staged in turn.  The queue is drained before a stage changes and after the
+          // last sweep of h1.
+          const int klast = W.sg[2].cnt ? 2 : (W.sg[1].cnt ? 1 : 0);
+          const bool last_group = ib + 32 >= W.nin;
+#pragma unroll 1
+          for (int k = 0; k < kMaxOuter; ++k) {
+            const uint32_t cnt = W.sg[k].cnt;
+            const float wk = k == 0 ? w[0] : (k == 1 ? w[1] : w[2]);
+            for (uint32_t j0 = 0; j0 < cnt; j0 += kOutStage) {
+              uint32_t p = W.pos[k], n = cnt;
+              if (!fits) {
+                n = min(cnt - j0, (uint32_t)kOutStage);
+                p = 0;
                 __syncwarp();
-                stage(off + j0, n, 0, W.p1);
+                stage(W.sg[k].off + j0, n, 0, W.p1);
                 if (lane == 0) {
                   W.pos[0] = 0;
                   W.pos[1] = W.pos[2] = kOutStage;
-                  W.coff[0] = off + j0;
+                  W.coff[0] = W.sg[k].off + j0;
                 }
                 __syncwarp();
-                sweep(0, round4(n), ta, w[k], ix);
-                if (tail != head) process(tail - head);  // before the stage changes
               }
+              sweep(p, round4(n), ta, wk, ix);
+              if (!fits || (last_group && k == klast))
+                while (tail != head) process(min(32u, tail - head));
+              if (fits) break;
             }
           }
         }
-        if (tail != head) process(tail - head);
         __syncwarp();
         if (pass == 1) break;
         nfound = nf;
@@ -441,14 +447,17 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
 
 void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
                     bool gated) {
-  launch_scan(b.in_cnt, b.in_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s);
-  k_in_scatter<<<l.sms * kScatterBlocksPerSm, 256, 0, s>>>(b, p.phi_bins);
+  PT_TRACE(l, s, "scan", launch_scan(b.in_cnt, b.in_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s));
+  PT_TRACE(l, s, "k_in_scatter",
+           k_in_scatter<<<l.sms * kScatterBlocksPerSm, 256, 0, s>>>(b, p.phi_bins));
   if (gated)
-    k_connect<true><<<l.sgrid, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
-                                                          (uint64_t)p.max_links);
+    PT_TRACE(l, s, "k_connect",
+             k_connect<true><<<l.sgrid, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
+                                                                  (uint64_t)p.max_links));
   else
-    k_connect<false><<<l.sgrid, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
-                                                           (uint64_t)p.max_links);
+    PT_TRACE(l, s, "k_connect",
+             k_connect<false><<<l.sgrid, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
+                                                                   (uint64_t)p.max_links));
 }
 
 }  // namespace ptca

@@ -191,8 +191,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
 }  // namespace
 
 void launch_doublets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s) {
-  k_doublets<<<l.sgrid, kWarpsPerBlock * 32, 0, s>>>(b, p.cuts, p.phi_bins,
-                                                        (uint64_t)p.max_cells);
+  PT_TRACE(l, s, "k_doublets",
+           k_doublets<<<l.sgrid, kWarpsPerBlock * 32, 0, s>>>(b, p.cuts, p.phi_bins,
+                                                               (uint64_t)p.max_cells));
 }
 
 }  // namespace ptca

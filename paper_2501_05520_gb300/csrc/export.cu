@@ -82,7 +82,7 @@ __global__ void k_export_links(Buffers b, uint64_t cap_links, int32_t* out4, flo
 }  // namespace
 
 void launch_export_ntuplets(const Buffers& b, const Launch& l, cudaStream_t s) {
-  k_export_ntuplets<<<l.grid, 256, 0, s>>>(b);
+  PT_TRACE(l, s, "k_export_ntuplets", k_export_ntuplets<<<l.grid, 256, 0, s>>>(b));
 }
 void launch_export_candidates(const Buffers& b, const Launch& l, cudaStream_t s) {
   k_export_candidates<<<l.grid, 256, 0, s>>>(b);

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) k_fit(Buffers b, float bfield) {
 }  // namespace
 
 void launch_fit(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s) {
-  k_fit<<<l.grid, 256, 0, s>>>(b, p.bfield);
+  PT_TRACE(l, s, "k_fit", k_fit<<<l.grid, 256, 0, s>>>(b, p.bfield));
 }
 
 }  // namespace ptca

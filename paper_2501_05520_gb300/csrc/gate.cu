@@ -351,10 +351,10 @@ cudaError_t gate_prepare() {
 
 void launch_gate(const Buffers& b, const Params& p, const Launch& l, const GateWeights* w,
                  cudaStream_t s) {
-  k_gate_mlp<true><<<l.sms * 4, kTileM, kMlpSmem, s>>>(w, b, p.cuts, p.phi_bins, nullptr,
-                                                         &b.cnt[CNT_LINKS], p.max_links,
-                                                         b.gate_score, b.gate_keep,
-                                                         &b.cnt[CNT_STATUS], &b.cnt[CNT_GATE_KEPT]);
+  PT_TRACE(l, s, "k_gate_mlp",
+           k_gate_mlp<true><<<l.sms * 4, kTileM, kMlpSmem, s>>>(
+               w, b, p.cuts, p.phi_bins, nullptr, &b.cnt[CNT_LINKS], p.max_links, b.gate_score,
+               b.gate_keep, &b.cnt[CNT_STATUS], &b.cnt[CNT_GATE_KEPT]));
 }
 
 void launch_gate_score(const GateWeights* w, const float* feat, int64_t n, float* out,

@@ -221,18 +221,23 @@ __global__ void k_event_offsets(Buffers b) {
 void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
                      bool gated) {
   const uint64_t cap_nt = (uint64_t)p.max_ntuplets;
-  if (gated) k_find_ntuplets<true><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links, cap_nt);
-  else k_find_ntuplets<false><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links, cap_nt);
-  k_bucket_count<<<l.grid, 256, 0, s>>>(b, cap_nt);
-  launch_scan(b.bucket_cnt, b.bucket_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s);
-  k_bucket_scatter<<<l.grid, 256, 0, s>>>(b, cap_nt);
-  k_bucket_sort<<<l.grid, 256, 0, s>>>(b);
-  k_dedup_min<<<l.grid, 256, 0, s>>>(b);
-  k_dedup_alive<<<l.grid, 256, 0, s>>>(b);
-  k_dedup_triplets<<<l.grid, 256, 0, s>>>(b);
-  launch_scan(b.alive, b.alive_scan, &b.cnt[CNT_SCAN_NT], b.scan_part, s);
-  k_compact<<<l.grid, 256, 0, s>>>(b);
-  k_event_offsets<<<l.grid, 256, 0, s>>>(b);
+  if (gated)
+    PT_TRACE(l, s, "k_find_ntuplets",
+             k_find_ntuplets<true><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links, cap_nt));
+  else
+    PT_TRACE(l, s, "k_find_ntuplets",
+             k_find_ntuplets<false><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links, cap_nt));
+  PT_TRACE(l, s, "k_bucket_count", k_bucket_count<<<l.grid, 256, 0, s>>>(b, cap_nt));
+  PT_TRACE(l, s, "scan",
+           launch_scan(b.bucket_cnt, b.bucket_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s));
+  PT_TRACE(l, s, "k_bucket_scatter", k_bucket_scatter<<<l.grid, 256, 0, s>>>(b, cap_nt));
+  PT_TRACE(l, s, "k_bucket_sort", k_bucket_sort<<<l.grid, 256, 0, s>>>(b));
+  PT_TRACE(l, s, "k_dedup_min", k_dedup_min<<<l.grid, 256, 0, s>>>(b));
+  PT_TRACE(l, s, "k_dedup_alive", k_dedup_alive<<<l.grid, 256, 0, s>>>(b));
+  PT_TRACE(l, s, "k_dedup_triplets", k_dedup_triplets<<<l.grid, 256, 0, s>>>(b));
+  PT_TRACE(l, s, "scan", launch_scan(b.alive, b.alive_scan, &b.cnt[CNT_SCAN_NT], b.scan_part, s));
+  PT_TRACE(l, s, "k_compact", k_compact<<<l.grid, 256, 0, s>>>(b));
+  PT_TRACE(l, s, "k_event_offsets", k_event_offsets<<<l.grid, 256, 0, s>>>(b));
 }
 
 }  // namespace ptca

@@ -157,10 +157,24 @@ struct Buffers {
 
 constexpr int kScanBlocks = 256;
 
+// Optional per-kernel timing of the stage calls (pt_set_tracing): CUDA events on the
+// launching stream around every kernel; never active while the whole-batch graph is
+// captured.  Defined in runtime.cu.
+struct Tracer;
+size_t trace_begin(Tracer* t, cudaStream_t s);
+void trace_end(Tracer* t, const char* name, size_t i0, cudaStream_t s);
+#define PT_TRACE(l, s, name, ...)                                  \
+  do {                                                             \
+    const size_t pt_t0_ = (l).tr ? trace_begin((l).tr, (s)) : 0;   \
+    __VA_ARGS__;                                                   \
+    if ((l).tr) trace_end((l).tr, (name), pt_t0_, (s));            \
+  } while (0)
+
 struct Launch {
-  int sms;         // multiprocessors
-  int grid;        // generic persistent grid (blocks of 256 threads)
-  int sgrid;       // grid of the doublet and connect searches (warp per hit)
+  int sms;                // multiprocessors
+  int grid;               // generic persistent grid (blocks of 256 threads)
+  int sgrid;              // grid of the doublet and connect searches (warp per hit)
+  Tracer* tr = nullptr;   // per-kernel timing, when enabled
 };
 
 // Sets the calling thread's pt_last_error() message.

@@ -7,11 +7,74 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "ptca_internal.cuh"
 
 using namespace ptca;
+
+namespace ptca {
+
+// Per-kernel timing of stage calls: a pool of CUDA events, one (start, end) pair per
+// traced launch, reduced to per-name totals when read.
+struct Tracer {
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  struct Rec {
+    const char* name;
+    size_t e0, e1;
+  };
+  std::vector<Rec> recs;
+  std::vector<std::pair<std::string, std::pair<double, int64_t>>> totals;  // first-seen order
+  cudaStream_t last = nullptr;
+
+  size_t take(cudaStream_t s) {
+    if (used == ev.size()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) return SIZE_MAX;
+      ev.push_back(e);
+    }
+    cudaEventRecord(ev[used], s);
+    last = s;
+    return used++;
+  }
+  void add(const char* name, double ms) {
+    for (auto& t : totals)
+      if (t.first == name) {
+        t.second.first += ms;
+        t.second.second += 1;
+        return;
+      }
+    totals.push_back({name, {ms, 1}});
+  }
+  // events must have completed (the caller synchronised the stream)
+  void collect() {
+    for (const Rec& r : recs) {
+      float ms = 0.0f;
+      if (r.e0 != SIZE_MAX && r.e1 != SIZE_MAX &&
+          cudaEventElapsedTime(&ms, ev[r.e0], ev[r.e1]) == cudaSuccess)
+        add(r.name, ms);
+    }
+    recs.clear();
+    used = 0;
+  }
+  ~Tracer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
+size_t trace_begin(Tracer* t, cudaStream_t s) { return t->take(s); }
+
+void trace_end(Tracer* t, const char* name, size_t i0, cudaStream_t s) {
+  t->recs.push_back({name, i0, t->take(s)});
+  if (t->recs.size() >= 4096) {  // bound the pool: fold completed records into the totals
+    cudaStreamSynchronize(s);
+    t->collect();
+  }
+}
+
+}  // namespace ptca
 
 namespace {
 
@@ -262,14 +325,16 @@ pt_status stage_inputs(pt_ctx* c, int n_events, const int64_t* off, const float*
 }
 
 void enqueue_pipeline(pt_ctx* c, cudaStream_t s) {
-  launch_clear(c->B, c->P, c->L, s);
-  launch_bin_hits(c->B, c->P, c->L, s);
-  launch_doublets(c->B, c->P, c->L, s);
-  launch_connect(c->B, c->P, c->L, s, c->gate_on);
-  if (c->gate_on) launch_gate(c->B, c->P, c->L, c->gate, s);
-  launch_ntuplets(c->B, c->P, c->L, s, c->gate_on);
-  launch_fit(c->B, c->P, c->L, s);
-  launch_export_ntuplets(c->B, c->L, s);
+  Launch L = c->L;
+  L.tr = nullptr;  // a captured graph records no timing events
+  launch_clear(c->B, c->P, L, s);
+  launch_bin_hits(c->B, c->P, L, s);
+  launch_doublets(c->B, c->P, L, s);
+  launch_connect(c->B, c->P, L, s, c->gate_on);
+  if (c->gate_on) launch_gate(c->B, c->P, L, c->gate, s);
+  launch_ntuplets(c->B, c->P, L, s, c->gate_on);
+  launch_fit(c->B, c->P, L, s);
+  launch_export_ntuplets(c->B, L, s);
 }
 
 pt_status ensure_graph(pt_ctx* c) {
@@ -444,8 +509,43 @@ pt_status pt_destroy(pt_ctx* c) {
   if (c->h_hdr) cudaFreeHost(c->h_hdr);
   if (c->h_cnt) cudaFreeHost(c->h_cnt);
   if (c->staged) cudaEventDestroy(c->staged);
+  delete c->L.tr;
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
+  return PT_OK;
+}
+
+pt_status pt_set_tracing(pt_ctx* c, int on) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  DeviceGuard guard(c->device);
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  if (on && !c->L.tr) c->L.tr = new Tracer();
+  if (!on) {
+    delete c->L.tr;
+    c->L.tr = nullptr;
+  }
+  return PT_OK;
+}
+
+pt_status pt_get_trace(pt_ctx* c, pt_kernel_time* out, int cap, int* n) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  if (!c->L.tr) return fail(PT_ERR_INVALID, "tracing is off (pt_set_tracing)");
+  DeviceGuard guard(c->device);
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  Tracer* t = c->L.tr;
+  t->collect();
+  const int m = (int)t->totals.size();
+  if (n) *n = m;
+  if (cap < m) return fail(PT_ERR_CAPACITY, "output capacity %d < %d kernels", cap, m);
+  for (int i = 0; i < m; ++i) {
+    std::memset(out[i].name, 0, sizeof(out[i].name));
+    std::strncpy(out[i].name, t->totals[i].first.c_str(), sizeof(out[i].name) - 1);
+    out[i].total_ms = t->totals[i].second.first;
+    out[i].launches = t->totals[i].second.second;
+  }
+  t->totals.clear();
   return PT_OK;
 }
 
