@@ -44,7 +44,7 @@ static_assert(kOutStage / 4 <= 128, "queue entries hold the staged position / 4 
 __device__ __forceinline__ uint32_t round4(uint32_t n) { return (n + 3u) & ~3u; }
 
 // in_rec[in_start[h] + rank] = (cell, inner hit | inner layer is 0 << 31), grouping the
-// cells by the hit they end on.  One warp per inner hit, in sorted-hit order: the warps
+// cells by the hit they end on; every cell's two link flags are cleared on the way.  One warp per inner hit, in sorted-hit order: the warps
 // running at one time cover a narrow azimuthal range of a layer, so their records land
 // in a narrow range of in_rec and partial sectors merge in L2 before write-back.
 __global__ void k_in_scatter(Buffers b, int32_t B) {
@@ -61,7 +61,7 @@ __global__ void k_in_scatter(Buffers b, int32_t B) {
     const uint32_t o0 = sgp[0].off, o1 = sgp[1].off, o2 = sgp[2].off;
     const uint32_t tag = h0 | ((b.hbin[h0] / (uint32_t)B) % kLayers == 0 ? 0x80000000u : 0u);
     for (uint32_t i0 = 0; i0 < n; i0 += 64) {
-      uint32_t c[2], o[2], rk[2];
+      uint32_t c[2], o[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const uint32_t i = i0 + u * 32 + lane;
@@ -69,12 +69,16 @@ __global__ void k_in_scatter(Buffers b, int32_t B) {
         if (i < n) {
           c[u] = i < n0 ? o0 + i : (i < n0 + n1 ? o1 + (i - n0) : o2 + (i - n0 - n1));
           o[u] = b.cell_out[c[u]];
-          rk[u] = b.cell_inrank[c[u]];
+
         }
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u)
-        if (o[u] != kHole) b.in_rec[b.in_start[o[u]] + rk[u]] = make_uint2(c[u], tag);
+        if (o[u] != kHole) {  // the count left on the hit is the cell's slot in its list
+          b.in_rec[b.in_start[o[u]] + atomicSub(&b.in_cnt[o[u]], 1u) - 1u] = make_uint2(c[u], tag);
+          b.has_in[c[u]] = 0;
+          b.has_out[c[u]] = 0;
+        }
     }
   }
 }

@@ -13,8 +13,8 @@
 // (hit, outer layer), so the cells leaving a hit towards one layer are contiguous.
 // Each segment records the smallest dr of its cells, which bounds the link stage's
 // slope window.  Slots are reserved through a per-warp chunk allocator; unused slots
-// are marked as holes.  Each cell also takes its rank among the cells ending on its
-// outer hit, from which the link stage's per-hit lists of incoming cells are built.
+// are marked as holes.  Each cell is also counted on its outer hit, which sizes the link
+// stage's per-hit lists of incoming cells.
 #include "ptca_internal.cuh"
 
 namespace ptca {
@@ -34,15 +34,12 @@ __device__ __forceinline__ float phi_window(float asin_o, float asin_i) {
   return fminf(asin_o - asin_i + 1e-4f, kHalfPi + 1e-3f);
 }
 
-// Writes one cell and takes its rank among the cells ending on the same outer hit.
-__device__ __forceinline__ void write_cell(const Buffers& b, uint64_t c, uint32_t s, uint32_t o,
-                                          uint8_t L) {
+// Writes one cell and counts it on its outer hit (its link flags are cleared by the
+// in-list scatter, which visits every cell of every segment).
+__device__ __forceinline__ void write_cell(const Buffers& b, uint64_t c, uint32_t s, uint32_t o) {
   b.cell_in[c] = s;
   b.cell_out[c] = o;
-  b.cell_l0[c] = L;
-  b.has_in[c] = 0;
-  b.has_out[c] = 0;
-  b.cell_inrank[c] = atomicAdd(&b.in_cnt[o], 1u);
+  atomicAdd(&b.in_cnt[o], 1u);  // no return value: a fire-and-forget reduction
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
@@ -60,11 +57,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
   unsigned long long used = 0;
   auto mark_hole = [&](unsigned long long lo, unsigned long long hi) {
     hi = min(hi, (unsigned long long)cap_cells);
-    for (unsigned long long i = lo + lane; i < hi; i += 32) {
-      b.cell_out[i] = kHole;
-      b.has_in[i] = 0;
-      b.has_out[i] = 0;
-    }
+    for (unsigned long long i = lo + lane; i < hi; i += 32) b.cell_out[i] = kHole;
   };
 
   for (uint32_t s = blockIdx.x * kWarpsPerBlock + wib; s < n_sorted; s += nwarps) {
@@ -140,7 +133,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
         } else if (cnt <= (uint32_t)kStage) {
           __syncwarp();
           for (uint32_t i = lane; i < cnt; i += 32)
-            write_cell(b, base + i, s, sval[i], (uint8_t)L);
+            write_cell(b, base + i, s, sval[i]);
           seg_off = (uint32_t)base;
           seg_cnt = cnt;
         } else {
@@ -155,7 +148,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
               const unsigned bal = __ballot_sync(kFull, pass);
               if (pass) {
                 const uint64_t c = base + pos0 + __popc(bal & lt_mask);
-                write_cell(b, c, s, o, (uint8_t)L);
+                write_cell(b, c, s, o);
               }
               pos0 += __popc(bal);
             }

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kTileM, 1)
         if (src_cell != kHole) {
           const uint32_t h0 = b.cell_in[src_cell], h1 = b.cell_out[src_cell];
           const uint32_t h2 = b.cell_out[b.link_dst[row]];
-          gate_link_features(cuts, b.hit4[h0], b.hit4[h1], b.hit4[h2], b.cell_l0[src_cell],
+          gate_link_features(cuts, b.hit4[h0], b.hit4[h1], b.hit4[h2], (b.hbin[h0] / B) % kLayers,
                              (b.hbin[h1] / B) % kLayers, (b.hbin[h2] / B) % kLayers, f);
         }
       }
@@ -320,7 +320,7 @@ __global__ void k_gate_features_f32(Buffers b, pt_cuts cuts, int32_t B, uint64_t
     const uint32_t h0 = b.cell_in[a], h1 = b.cell_out[a];
     const uint32_t h2 = b.cell_out[b.link_dst[l]];
     float f[kGateFeat];
-    gate_link_features(cuts, b.hit4[h0], b.hit4[h1], b.hit4[h2], b.cell_l0[a],
+    gate_link_features(cuts, b.hit4[h0], b.hit4[h1], b.hit4[h2], (b.hbin[h0] / B) % kLayers,
                        (b.hbin[h1] / B) % kLayers, (b.hbin[h2] / B) % kLayers, f);
 #pragma unroll
     for (int k = 0; k < kGateFeat; ++k) out[l * kGateFeat + k] = f[k];

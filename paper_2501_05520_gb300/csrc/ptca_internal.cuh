@@ -111,15 +111,14 @@ struct Buffers {
   // cells
   uint32_t* cell_in;         // [max_cells] sorted hit index
   uint32_t* cell_out;        // [max_cells]
-  uint32_t* cell_inrank;     // [max_cells] rank among the cells ending on the same hit
-  uint8_t* cell_l0;          // [max_cells] layer of the inner hit
   uint8_t* has_in;           // [max_cells] an accepted link ends on the cell
   uint8_t* has_out;          // [max_cells] an accepted link starts from the cell
   uint32_t* link_off;        // [max_cells] first slot of the cell's links (valid where it
   uint32_t* link_cnt;        //   has links) and their number
   uint32_t* lk_cells;        // [max_links] cells with >= 1 outgoing link
   unsigned long long* best;  // [max_cells] duplicate-cleaning key (cells on ntuplets)
-  uint32_t* in_cnt;          // [max_hits + 1] cells ending on each sorted hit
+  uint32_t* in_cnt;          // [max_hits + 1] cells ending on each sorted hit (counted
+                             //   down to 0 again by the in-list scatter)
   uint32_t* in_start;        // [max_hits + 1] exclusive scan of in_cnt
   uint2* in_rec;             // [max_cells] cells grouped by the hit they end on:
                              //   (cell, inner sorted hit | inner layer is 0 << 31)

@@ -137,8 +137,6 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.seg = (Segment*)take(N * kMaxOuter * sizeof(Segment));
   t.cell_in = (uint32_t*)take(C * 4);
   t.cell_out = (uint32_t*)take(C * 4);
-  t.cell_inrank = (uint32_t*)take(C * 4);
-  t.cell_l0 = (uint8_t*)take(C);
   t.has_in = (uint8_t*)take(C);
   t.has_out = (uint8_t*)take(C);
   t.link_off = (uint32_t*)take(C * 4);
