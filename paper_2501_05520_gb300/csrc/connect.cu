@@ -16,16 +16,17 @@
 //                      (rz0 + rz1 |t_a|)(1/d1 + 1/m) / (1 - rz1/d1)),
 // the second term only where d1 > rz1.  It is widened by 1 % + 1e-3, far beyond the
 // float32 rounding of C1 (about 4e-7 |t_a| d1/m + 1e-6) and of the approximate
-// reciprocals used for it.  The warp sweeps the staged slopes four at a time, every lane
-// testing its own cell against them, with no divergence; a lane whose window holds any
-// of the four queues one entry (lane, 4-bit mask, position).  The queue is drained 32
-// entries at a time through the exact cuts, all lanes busy.  The links found for the 32
-// cells are collected in shared memory and written with one warp-aggregated
-// reservation: the links of one cell are contiguous (the out-link list the ntuplet
-// search walks), and cells with at least one link are appended to a compact list, the
-// only cells that can start an ntuplet.  If a group finds more links than the
-// collection holds, the sweep runs a second time and writes the remainder directly.
-// Segments larger than the stage are swept piece by piece.
+// quotients and reciprocals used for the slopes and the window (a few 1e-7 relative).
+// The warp sweeps the staged slopes eight at a time, every lane testing its own cell
+// against them, with no divergence; a lane whose window holds any of the eight queues
+// one entry (incoming index, 8-bit mask, position).  The queue is drained 32 entries
+// at a time through the exact cuts, all lanes busy.  The links of a middle hit are
+// collected in shared memory, reserved once, sorted by source cell and written as
+// per-cell lists (the out-link lists the ntuplet search walks); cells with at least one
+// link are appended to a compact list, the only cells that can start an ntuplet.  If a
+// hit has more links than the collection holds, the search runs a second time and
+// writes them all to a temporary half of a double-size reservation, which is then
+// sorted.  Segments larger than the stage are swept piece by piece.
 #include "ptca_internal.cuh"
 
 namespace ptca {
@@ -33,15 +34,15 @@ namespace ptca {
 namespace {
 
 constexpr int kConnWarps = 8;
-constexpr int kOutStage = 160;  // staged outgoing cells per warp (multiple of 4)
+constexpr int kOutStage = 160;  // staged outgoing cells per warp (multiple of 8, < 256)
 constexpr int kQueue = 128;     // candidate ring per warp (power of two, >= 31 + 32)
 constexpr int kFound = 64;      // links of one group kept in shared memory (rank < 256)
 constexpr uint32_t kNoBase = 0xffffffffu;
 constexpr uint32_t kHitChunk = 4;       // consecutive middle hits per warp chunk (<= 32)
 constexpr int kScatterBlocksPerSm = 4;  // fewer warps in flight keep the scatter local
-static_assert(kOutStage / 4 <= 128, "queue entries hold the staged position / 4 in 7 bits");
+static_assert(kOutStage % 8 == 0 && kOutStage < 256, "staged positions fit 8 bits");
 
-__device__ __forceinline__ uint32_t round4(uint32_t n) { return (n + 3u) & ~3u; }
+__device__ __forceinline__ uint32_t round8(uint32_t n) { return (n + 7u) & ~7u; }
 
 // in_rec[in_start[h] + rank] = (cell, inner hit | inner layer is 0 << 31), grouping the
 // cells by the hit they end on; every cell's two link flags are cleared on the way.  One warp per inner hit, in sorted-hit order: the warps
@@ -98,7 +99,7 @@ struct ConnWarp {
   uint32_t in0, nin;         // incoming-cell list of the middle hit
   unsigned long long lbase;  // its link block
   uint32_t lvalid;           //   (within the capacity)
-  uint2 q[kQueue];           // candidates: (incoming index, mask << 8 | staged position)
+  uint2 q[kQueue];           // candidates: (incoming index, 8-bit mask << 8 | position)
   uint32_t fs[kFound];       // found links: source cell
   uint32_t fd[kFound];       //   target cell
   float fq[kFound];          //   quality
@@ -166,14 +167,15 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
     }
   };
   // stages cells [c0, c0 + n) leaving the middle hit p1 at position p (padded to a
-  // multiple of 4 with NaN slopes)
+  // multiple of 8 with NaN slopes); the slope only places the window, so an
+  // approximate quotient is enough
   auto stage = [&](uint32_t c0, uint32_t n, uint32_t p, float4 p1) {
-    for (uint32_t i = lane; i < round4(n); i += 32) {
+    for (uint32_t i = lane; i < round8(n); i += 32) {
       float t = kNaN;
       float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
       if (i < n) {
         q = b.hit4[b.cell_out[c0 + i]];
-        t = fdiv(fsub(q.z, p1.z), fsub(q.w, p1.w));
+        t = __fdividef(q.z - p1.z, q.w - p1.w);
       }
       W.t[p + i] = t;
       W.p2[p + i] = q;
@@ -217,13 +219,13 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
       {
         const Segment* sgp = b.seg + (uint64_t)h1 * kMaxOuter;
 #pragma unroll
-        for (int k = 0; k < kMaxOuter; ++k) tot += round4(sgp[k].cnt);
+        for (int k = 0; k < kMaxOuter; ++k) tot += round8(sgp[k].cnt);
         __syncwarp();
         if (lane < kMaxOuter) {
           const Segment g = sgp[lane];
           W.sg[lane] = g;
           uint32_t p = 0;
-          for (int k = 0; k < lane; ++k) p += round4(sgp[k].cnt);
+          for (int k = 0; k < lane; ++k) p += round8(sgp[k].cnt);
           W.pos[lane] = p;
           W.coff[lane] = g.off;
         }
@@ -294,13 +296,22 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
         // sweep of staged positions [p, p + n) with the lane's window wk; ix = the
         // lane's index in the incoming list
         auto sweep = [&](uint32_t p, uint32_t n, float ta, float wk, uint32_t ix) {
-          for (uint32_t j = 0; j < n; j += 4) {
-            const float4 t4 = *reinterpret_cast<const float4*>(&W.t[p + j]);
-            const uint32_t m = (fabsf(t4.x - ta) <= wk ? 1u : 0u) | (fabsf(t4.y - ta) <= wk ? 2u : 0u) |
-                               (fabsf(t4.z - ta) <= wk ? 4u : 0u) | (fabsf(t4.w - ta) <= wk ? 8u : 0u);
-            const unsigned bal = __ballot_sync(kFull, m != 0);
+          for (uint32_t j = 0; j < n; j += 8) {
+            const float4 u = *reinterpret_cast<const float4*>(&W.t[p + j]);
+            const float4 v = *reinterpret_cast<const float4*>(&W.t[p + j + 4]);
+            const bool c0 = fabsf(u.x - ta) <= wk, c1 = fabsf(u.y - ta) <= wk;
+            const bool c2 = fabsf(u.z - ta) <= wk, c3 = fabsf(u.w - ta) <= wk;
+            const bool c4 = fabsf(v.x - ta) <= wk, c5 = fabsf(v.y - ta) <= wk;
+            const bool c6 = fabsf(v.z - ta) <= wk, c7 = fabsf(v.w - ta) <= wk;
+            const bool any = (c0 | c1 | c2 | c3) | (c4 | c5 | c6 | c7);
+            const unsigned bal = __ballot_sync(kFull, any);
             if (bal) {
-              if (m) W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2(ix, (m << 8) | (p + j));
+              if (any) {
+                const uint32_t m = (c0 ? 1u : 0u) | (c1 ? 2u : 0u) | (c2 ? 4u : 0u) | (c3 ? 8u : 0u) |
+                                   (c4 ? 16u : 0u) | (c5 ? 32u : 0u) | (c6 ? 64u : 0u) |
+                                   (c7 ? 128u : 0u);
+                W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2(ix, (m << 8) | (p + j));
+              }
               tail += __popc(bal);
               if (tail - head >= 32u) process(32);
             }
@@ -316,7 +327,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
             float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (ix < W.nin) {
               p0 = b.hit4[b.in_rec[W.in0 + ix].y & 0x7fffffffu];
-              ta = fdiv(fsub(p1.z, p0.z), fsub(p1.w, p0.w));  // the cell's slope dz/dr
+              ta = __fdividef(p1.z - p0.z, p1.w - p0.w);  // the cell's slope dz/dr
             }
             const float id1 = __fdividef(1.0f, p1.w - p0.w);
             const float wa = (cuts.rz0 + cuts.rz1 * cuts.cotmax) * id1;
@@ -354,7 +365,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
                 }
                 __syncwarp();
               }
-              sweep(p, round4(n), ta, wk, ix);
+              sweep(p, round8(n), ta, wk, ix);
               if (!fits || (last_group && k == klast))
                 while (tail != head) process(min(32u, tail - head));
               if (fits) break;
@@ -388,7 +399,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
       }
 
       // The links of h1, sorted by source cell (stable), form one list per source:
-      // link_off / link_cnt of each source, which joins the list of possible roots.
+      // link_oc (offset, count) of each source, which joins the list of possible roots.
       __syncwarp();
       if (nfound > 0 && W.lvalid) {
         const unsigned long long lbase = W.lbase;
@@ -415,10 +426,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
           __syncwarp();
           if (i < nfound) {
             write_link(lbase + rank, a, c, q);
-            if (first) {
-              b.link_off[a] = (uint32_t)(lbase + rank);
-              b.link_cnt[a] = cnt;
-            }
+            if (first) b.link_oc[a] = make_uint2((uint32_t)(lbase + rank), cnt);
           }
           const unsigned fm = __ballot_sync(kFull, first);
           if (fm) {

@@ -26,15 +26,26 @@ namespace {
 
 // Depth-first walk from root a.  EMIT == false: returns the number of ntuplets;
 // EMIT == true: writes them at slots t0, t0 + 1, ... (slots >= cap_nt are dropped).
+// A cell's links are one (offset, count) read; when emitting, the batch index of each
+// cell's outer hit is looked up once, when the cell is pushed.
 template <bool EMIT, bool GATED>
 __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, uint64_t cap_nt) {
   uint32_t path[kMaxCellsPerNt];
   uint32_t it[kMaxCellsPerNt], end[kMaxCellsPerNt];
   float qs[kMaxCellsPerNt];
+  int32_t gh[kMaxCellsPerNt];  // batch index of the outer hit of path[k] (EMIT)
   path[0] = a;
-  it[0] = b.link_off[a];
-  end[0] = it[0] + b.link_cnt[a];
+  {
+    const uint2 oc = b.link_oc[a];
+    it[0] = oc.x;
+    end[0] = oc.x + oc.y;
+  }
   qs[0] = 0.0f;
+  int32_t g0 = 0;
+  if (EMIT) {
+    g0 = (int32_t)b.perm[b.cell_in[a]];
+    gh[0] = (int32_t)b.perm[b.cell_out[a]];
+  }
   uint32_t found = 0;
   int depth = 1;
   while (depth > 0) {
@@ -56,10 +67,10 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
           const int ncell = depth + 1;
           int32_t* hp = b.nt_hits + t * kMaxHits;
           uint32_t* cp = b.nt_cells + t * kMaxCellsPerNt;
-          hp[0] = (int32_t)b.perm[b.cell_in[path[0]]];
+          hp[0] = g0;
           for (int k = 0; k < ncell; ++k) {
             const uint32_t ck = k < depth ? path[k] : c;
-            hp[k + 1] = (int32_t)b.perm[b.cell_out[ck]];
+            hp[k + 1] = k < depth ? gh[k] : (int32_t)b.perm[b.cell_out[c]];
             cp[k] = ck;
             b.best[ck] = ~0ull;  // initial duplicate-cleaning key of a cell on an ntuplet
           }
@@ -73,9 +84,11 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
       continue;
     }
     path[depth] = c;
-    it[depth] = b.link_off[c];
-    end[depth] = it[depth] + b.link_cnt[c];
+    const uint2 oc = b.link_oc[c];
+    it[depth] = oc.x;
+    end[depth] = oc.x + oc.y;
     qs[depth] = q;
+    if (EMIT) gh[depth] = (int32_t)b.perm[b.cell_out[c]];
     ++depth;
   }
   return found;

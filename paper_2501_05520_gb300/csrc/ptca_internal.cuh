@@ -113,8 +113,8 @@ struct Buffers {
   uint32_t* cell_out;        // [max_cells]
   uint8_t* has_in;           // [max_cells] an accepted link ends on the cell
   uint8_t* has_out;          // [max_cells] an accepted link starts from the cell
-  uint32_t* link_off;        // [max_cells] first slot of the cell's links (valid where it
-  uint32_t* link_cnt;        //   has links) and their number
+  uint2* link_oc;            // [max_cells] first slot and number of the cell's links
+                             //   (valid where it has links)
   uint32_t* lk_cells;        // [max_links] cells with >= 1 outgoing link
   unsigned long long* best;  // [max_cells] duplicate-cleaning key (cells on ntuplets)
   uint32_t* in_cnt;          // [max_hits + 1] cells ending on each sorted hit (counted

@@ -139,8 +139,7 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.cell_out = (uint32_t*)take(C * 4);
   t.has_in = (uint8_t*)take(C);
   t.has_out = (uint8_t*)take(C);
-  t.link_off = (uint32_t*)take(C * 4);
-  t.link_cnt = (uint32_t*)take(C * 4);
+  t.link_oc = (uint2*)take(C * 8);
   t.lk_cells = (uint32_t*)take(L * 4);
   t.best = (unsigned long long*)take(C * 8);
   t.in_cnt = (uint32_t*)take((N + 1) * 4);

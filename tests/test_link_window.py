@@ -4,9 +4,11 @@ The CUDA link kernel tests a pair of cells a = (h0, h1), b = (h1, h2) with the e
 cuts only when their r-z slopes satisfy
     |t_a - t_b| <= min((rz0 + rz1 cotmax)/d1 + (rz0 + rz1 |t_a|)/m,
                        (rz0 + rz1 |t_a|)(1/d1 + 1/m) / (1 - rz1/d1)) * 1.01 + 1e-3
-(d1 = r1 - r0, m <= r2 - r1, the second term only where d1 > rz1).  This file checks
-that inequality against C1 evaluated in float32 exactly as the oracle does, on random
-and on boundary-hugging triplets, with D4 (|t_b| <= cotmax) applied as in the chain.
+(d1 = r1 - r0, m <= r2 - r1, the second term only where d1 > rz1), with slopes from
+approximate float32 quotients (a few ulp).  This file checks that inequality against C1
+evaluated in float32 exactly as the oracle does, on random and on boundary-hugging
+triplets, with D4 (|t_b| <= cotmax) applied as in the chain, after moving both slopes
+apart by 4 ulp relative each.
 """
 
 import numpy as np
@@ -34,12 +36,13 @@ def window(ta, d1, m, rz0, rz1, cotmax):
 def _check(cuts, r0, r1, r2, z0, z1, z2):
     rz0, rz1, cotmax = f32(cuts["rz0"]), f32(cuts["rz1"]), f32(cuts["cotmax"])
     ok = c1_pass(z0, r0, z1, r1, z2, r2, rz0, rz1)
-    ta = (z1 - z0) / (r1 - r0)   # float32 slopes, as the kernel computes them
-    tb = (z2 - z1) / (r2 - r1)
+    ta = ((z1 - z0) / (r1 - r0)).astype(np.float64)   # float32 slopes
+    tb = ((z2 - z1) / (r2 - r1)).astype(np.float64)
     d4 = np.abs(z2 - z1) <= cotmax * (r2 - r1)
     sel = ok & d4
     w = window(ta, r1 - r0, r2 - r1, float(rz0), float(rz1), float(cotmax))
-    d = np.abs(ta.astype(np.float64) - tb.astype(np.float64))
+    ulp4 = 4 * 2.0 ** -23
+    d = np.abs(ta - tb) + ulp4 * (np.abs(ta) + np.abs(tb))  # approximate quotients
     assert sel.sum() > 1000
     assert np.all(d[sel] <= w[sel]), (d[sel] - w[sel]).max()
 
