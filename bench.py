@@ -49,11 +49,10 @@ CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped
 # DRAM traffic per event of the main kernels from one ncu capture (8 PU200 events per
 # launch, profiles/), valid only while the kernel's sources hash to the recorded value.
 NCU_TRAFFIC = {
-    "k_doublets": {"bytes_per_event": 41678208, "issue_active_pct": 72.1, "sha": "ef12f61da283"},
-    "k_in_scatter": {"bytes_per_event": 38948448, "issue_active_pct": 23.8, "sha": "08f4ef1d7a25"},
-    "k_connect": {"bytes_per_event": 36949760, "issue_active_pct": 64.6, "sha": "08f4ef1d7a25"},
-    "k_find_ntuplets": {"bytes_per_event": 59041664, "issue_active_pct": 11.8,
-                        "sha": "fd6594bb0d0b"},
+    "k_doublets": {"bytes_per_event": 19372416, "issue_active_pct": 73.5, "sha": "9fb817df29d2"},
+    "k_in_scatter": {"bytes_per_event": 34797408, "issue_active_pct": 19.3, "sha": "86e93db645e8"},
+    "k_connect": {"bytes_per_event": 32225568, "issue_active_pct": 57.9, "sha": "86e93db645e8"},
+    "k_find_ntuplets": {"bytes_per_event": 51738624, "issue_active_pct": 15.0, "sha": "f54dc359c651"},
 }
 
 
@@ -74,11 +73,12 @@ def capacity(batch: int = BATCH, phi_bins: int = 1024) -> dict:
 def kernel_bytes(kernel: str, c: dict) -> int | None:
     N, C, Lk, T = c["hits"], c["cells"], c["links"], c["candidates"]
     return {
-        # hit (x,y,z,r) 16 N; segments 48 N; in-degree counters 8 N (atomic read+write);
-        # cells (inner, outer, rank, layer, 2 flags) 15 C
-        "k_doublets": 16 * N + 48 * N + 8 * N + 15 * C,
-        # segments 48 N, layer tag 4 N, in_start 4 N; cell outer + rank 8 C; records 8 C
-        "k_in_scatter": 56 * N + 16 * C,
+        # hit (x,y,z,r) 16 N; segments 48 N; in-degree counters 8 N (reduction read+write);
+        # cells (inner, outer) 8 C
+        "k_doublets": 16 * N + 48 * N + 8 * N + 8 * C,
+        # segments 48 N, layer tag 4 N, in_start 4 N, counters 8 N (atomic read+write);
+        # cell outer 4 C, records 8 C, two link flags 2 C
+        "k_in_scatter": 64 * N + 14 * C,
         # in_start 4 N, segments 48 N, hits 16 N; records 8 C, outer hit of staged cells
         # 4 C; links (source, target, quality) 12 Lk, per-cell lists and flags <= 14 Lk
         "k_connect": 68 * N + 12 * C + 26 * Lk,
@@ -472,20 +472,26 @@ def run_ours(args):
         # end to end through the public call: pinned host in, host out; two host threads,
         # each with its own context and stream, so one batch's copies overlap the other's
         # kernels
-        ctx2.pt_set_gate(gw if form == "gated" else None, gtau)
-        e2e_s, S = _e2e(pt, [ctx, ctx2], host[0], B, args.steps, args.warmup)
+        e2e_s, S = 0.0, 0
+        if not args.no_e2e:
+            ctx2.pt_set_gate(gw if form == "gated" else None, gtau)
+            e2e_s, S = _e2e(pt, [ctx, ctx2], host[0], B, args.steps, args.warmup)
         e2e_s = max_over_ranks(e2e_s, dist, dev)
         forms[form] = dict(
             value=job_rate(world, B, args.steps, total_s), ms_per_step=1000.0 * total_s / args.steps,
             p99_ms_per_step=float(np.percentile(step_ms, 99)),
             stages_ms={n: round(statistics.mean(v), 4) for n, v in stage_ms.items()},
-            e2e={"value": job_rate(world, B, args.steps, e2e_s), "unit": "events/s",
+            e2e=None if args.no_e2e else {
+                 "value": job_rate(world, B, args.steps, e2e_s), "unit": "events/s",
                  "host_threads": 2,
                  "h2d_bytes_per_step": int(host[0][0][-1]) * 13 + (B + 1) * 4 + 8,
                  "d2h_bytes_per_step": S * (24 + 1 + 36) + (B + 1) * 8 + 128},
             physics=_physics(ctx, host, events) if not args.no_physics else None)
     ctx.pt_set_gate(None, 0.0)
-    config4 = _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)
+    config4 = {"plain": _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)}
+    ctx.pt_set_gate(gw, gtau)
+    config4["gated"] = _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)
+    ctx.pt_set_gate(None, 0.0)
 
     # roofline of the dominant kernel of the plain form (mean traced launch duration)
     plain = forms["plain"]
@@ -530,9 +536,11 @@ def run_ours(args):
                 "clocks": clocks,
                 "gpu_launches": launches["plain"] * args.steps}
         if not args.no_serving:
-            line["serving"] = {"plain": _serving(pt, args.serve_rate, args.serve_seconds),
-                               "gated": _serving(pt, args.serve_rate, args.serve_seconds,
-                                                 gate=(gw, gtau))}
+            line["serving"] = {
+                form: [_serving(pt, rate, args.serve_seconds,
+                                gate=(gw, gtau) if form == "gated" else None)
+                       for rate in (args.serve_rate_low, args.serve_rate)]
+                for form in ("plain", "gated")}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -555,7 +563,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-physics", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer rate (profiling)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-rate-low", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.impl == "reference":

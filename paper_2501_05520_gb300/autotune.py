@@ -23,7 +23,7 @@ import time
 
 import numpy as np
 
-PHI_BINS = (256, 512, 1024, 2048)
+PHI_BINS = (64, 128, 256, 512, 1024, 2048)
 BLOCKS_PER_SM = (2, 4, 8)
 SEARCH_BLOCKS_PER_SM = (3, 5, 8)
 

@@ -295,8 +295,10 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
         };
         // sweep of staged positions [p, p + n) with the lane's window wk; ix = the
         // lane's index in the incoming list
-        auto sweep = [&](uint32_t p, uint32_t n, float ta, float wk, uint32_t ix) {
-          for (uint32_t j = 0; j < n; j += 8) {
+        // sweeps from position j until 32 entries are queued or the end; returns where it
+        // stopped
+        auto sweep = [&](uint32_t p, uint32_t j, uint32_t n, float ta, float wk, uint32_t ix) {
+          for (; j < n; j += 8) {
             const float4 u = *reinterpret_cast<const float4*>(&W.t[p + j]);
             const float4 v = *reinterpret_cast<const float4*>(&W.t[p + j + 4]);
             const bool c0 = fabsf(u.x - ta) <= wk, c1 = fabsf(u.y - ta) <= wk;
@@ -313,9 +315,10 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
                 W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2(ix, (m << 8) | (p + j));
               }
               tail += __popc(bal);
-              if (tail - head >= 32u) process(32);
+              if (tail - head >= 32u) return j + 8;
             }
           }
+          return n;
         };
 
         for (uint32_t ib = 0; ib < W.nin; ib += 32) {
@@ -365,9 +368,16 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
                 }
                 __syncwarp();
               }
-              sweep(p, round8(n), ta, wk, ix);
-              if (!fits || (last_group && k == klast))
-                while (tail != head) process(min(32u, tail - head));
+              // one call site each for the sweep and the exact cuts (instruction cache)
+              const uint32_t n8 = round8(n);
+              const bool last = !fits || (last_group && k == klast);
+              for (uint32_t j = 0;;) {
+                j = sweep(p, j, n8, ta, wk, ix);
+                const bool done = j >= n8;
+                while (tail - head >= 32u || (done && last && tail != head))
+                  process(min(32u, tail - head));
+                if (done) break;
+              }
               if (fits) break;
             }
           }
