@@ -141,10 +141,10 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.has_out = (uint8_t*)take(C);
   t.link_oc = (uint2*)take(C * 8);
   t.lk_cells = (uint32_t*)take(L * 4);
-  t.best = (unsigned long long*)take(C * 8);
   t.in_cnt = (uint32_t*)take((N + 1) * 4);
   t.in_start = (uint32_t*)take((N + 1) * 4);
   t.in_rec = (uint2*)take(C * 8);
+  t.best = (unsigned long long*)t.in_rec;  // in_rec is dead once the links exist
   t.link_dst = (uint32_t*)take(L * 4);
   t.link_q = (float*)take(L * 4);
   t.nt_hits = (int32_t*)take(T * kMaxHits * 4);
