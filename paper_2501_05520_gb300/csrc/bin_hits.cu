@@ -32,7 +32,6 @@ __global__ void k_clear(Buffers b, int32_t phi_bins) {
     b.cnt[CNT_GATE_KEPT] = 0;
     b.cnt[CNT_SCAN_NT] = 0;
     b.cnt[CNT_SV] = 0;
-    b.cnt[CNT_LKCELLS] = 0;
     b.cnt[CNT_CELLS_USED] = 0;
     b.cnt[CNT_LINKS_USED] = 0;
     b.cnt[CNT_SCAN_BINS] = (unsigned long long)nb;

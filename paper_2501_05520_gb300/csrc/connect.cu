@@ -22,8 +22,9 @@
 // one entry (incoming index, 8-bit mask, position).  The queue is drained 32 entries
 // at a time through the exact cuts, all lanes busy.  The links of a middle hit are
 // collected in shared memory, reserved once, sorted by source cell and written as
-// per-cell lists (the out-link lists the ntuplet search walks); cells with at least one
-// link are appended to a compact list, the only cells that can start an ntuplet.  If a
+// per-cell lists (the out-link lists the ntuplet search walks): a source's links are
+// one run of equal link_src values, so the first slot of each run names a cell that
+// can start an ntuplet.  If a
 // hit has more links than the collection holds, the search runs a second time and
 // writes them all to a temporary half of a double-size reservation, which is then
 // sorted.  Segments larger than the stage are swept piece by piece.
@@ -37,7 +38,6 @@ constexpr int kConnWarps = 8;
 constexpr int kOutStage = 160;  // staged outgoing cells per warp (multiple of 8, < 256)
 constexpr int kQueue = 128;     // candidate ring per warp (power of two, >= 31 + 32)
 constexpr int kFound = 64;      // links of one group kept in shared memory (rank < 256)
-constexpr uint32_t kNoBase = 0xffffffffu;
 constexpr uint32_t kHitChunk = 4;       // consecutive middle hits per warp chunk (<= 32)
 constexpr int kScatterBlocksPerSm = 4;  // fewer warps in flight keep the scatter local
 static_assert(kOutStage % 8 == 0 && kOutStage < 256, "staged positions fit 8 bits");
@@ -93,8 +93,8 @@ struct ConnWarp {
   Segment sg[kMaxOuter];     // outgoing segments of the middle hit
   uint32_t pos[kMaxOuter];   // staged position of each segment / piece
   uint32_t coff[kMaxOuter];  // cell of each staged position pos[k]
-  unsigned long long chunk_next[2], chunk_end[2], used;  // link slots, root slots
-  uint32_t chunk_size[2];
+  unsigned long long chunk_next[1], chunk_end[1], used;  // link slots
+  uint32_t chunk_size[1];
   uint32_t hin0[kHitChunk], hnin[kHitChunk];  // incoming-cell list of each hit of the chunk
   uint32_t in0, nin;         // incoming-cell list of the middle hit
   unsigned long long lbase;  // its link block
@@ -143,16 +143,12 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
   const int E = b.hdr->n_events;
   const uint32_t n_sorted = b.bin_start[E * kLayers * B];
   const int nwarps = gridDim.x * kConnWarps;
-  if (lane < 2) {
-    W.chunk_next[lane] = W.chunk_end[lane] = 0;
-    W.chunk_size[lane] = 0;
+  if (lane == 0) {
+    W.chunk_next[0] = W.chunk_end[0] = 0;
+    W.chunk_size[0] = 0;
   }
   if (lane == 0) W.used = 0;
   __syncwarp();
-  auto mark_root_hole = [&](unsigned long long lo, unsigned long long hi) {
-    hi = min(hi, (unsigned long long)cap_links);
-    for (unsigned long long i = lo + lane; i < hi; i += 32) b.lk_cells[i] = kHole;
-  };
   auto mark_link_hole = [&](unsigned long long lo, unsigned long long hi) {
     hi = min(hi, (unsigned long long)cap_links);
     for (unsigned long long i = lo + lane; i < hi; i += 32) b.link_src[i] = kHole;
@@ -438,17 +434,6 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
             write_link(lbase + rank, a, c, q);
             if (first) b.link_oc[a] = make_uint2((uint32_t)(lbase + rank), cnt);
           }
-          const unsigned fm = __ballot_sync(kFull, first);
-          if (fm) {
-            unsigned long long rlo, rhi;
-            const unsigned long long rb = chunk_take_shared(W, 1, &b.cnt[CNT_LKCELLS], __popc(fm), &rlo, &rhi);
-            mark_root_hole(rlo, rhi);
-            const unsigned long long ri = rb + __popc(fm & lt_mask);
-            if (first) {
-              if (ri < cap_links) b.lk_cells[ri] = a;
-              else atomicOr(&b.cnt[CNT_STATUS], ST_LINKS);
-            }
-          }
         }
         if (big) {
           __syncwarp();
@@ -460,7 +445,6 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
     __syncwarp();
   }
   __syncwarp();
-  mark_root_hole(W.chunk_next[1], W.chunk_end[1]);
   mark_link_hole(W.chunk_next[0], W.chunk_end[0]);
   if (lane == 0 && W.used) atomicAdd(&b.cnt[CNT_LINKS_USED], W.used);
 }

@@ -3,8 +3,8 @@
 // picked).
 //
 // A4  every path of linked cells from a root (a cell with no incoming link) to a leaf
-//     (a cell with no outgoing link) with 3..6 hits.  Roots are taken from the compact
-//     list of cells with outgoing links (a root without one would give a 2-hit path,
+//     (a cell with no outgoing link) with 3..6 hits.  Roots are taken among the sources
+//     of the link lists (a root without an outgoing link would give a 2-hit path,
 //     which is dropped).  One thread per root walks its out-links depth first with an
 //     explicit stack (the layer graph bounds the depth at 5 cells), once to count and,
 //     after one atomic per warp reserves the slots, once to write.  The path quality q is the float32 sum of its link qualities,
@@ -94,20 +94,24 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
   return found;
 }
 
-// One thread per root; each warp counts its roots' ntuplets, reserves them with one
-// atomic and walks again to write them.
+// One thread per link slot; the slot that starts a source cell's run of links (its
+// predecessor holds another source or a hole) names a candidate root, which is a root
+// when the cell has a kept outgoing link and no incoming one.  Each warp counts its
+// roots' ntuplets, reserves them with one atomic and walks again to write them.
 template <bool GATED>
 __global__ void __launch_bounds__(256)
     k_find_ntuplets(Buffers b, uint64_t cap_links, uint64_t cap_nt) {
-  const uint64_t nl = min(b.cnt[CNT_LKCELLS], (unsigned long long)cap_links);
+  const uint64_t nl = min(b.cnt[CNT_LINKS], (unsigned long long)cap_links);
   const int lane = lane_id();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < nl;
        i0 += stride) {
     const uint64_t i = i0 + lane;
     uint32_t a = kHole;
-    if (i < nl) a = b.lk_cells[i];
-    const bool root = a != kHole && b.has_out[a] && !b.has_in[a];
+    if (i < nl) a = b.link_src[i];
+    uint32_t prev = __shfl_up_sync(kFull, a, 1);
+    if (lane == 0) prev = i0 > 0 ? b.link_src[i0 - 1] : kHole;
+    const bool root = a != kHole && a != prev && b.has_out[a] && !b.has_in[a];
     const uint32_t n = root ? walk<false, GATED>(b, a, 0, cap_nt) : 0u;
     const uint32_t inc = warp_incl_scan(n);
     const uint32_t tot = __shfl_sync(kFull, inc, 31);

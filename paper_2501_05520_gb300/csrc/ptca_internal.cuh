@@ -34,7 +34,6 @@ enum : int {
   CNT_SCAN_NT = 6,
   CNT_GATE_KEPT = 7,
   CNT_SV = 8,         // cleaned ntuplets
-  CNT_LKCELLS = 9,    // slots reserved in the list of cells with outgoing links
   CNT_CELLS_USED = 10,  // cells written (CNT_CELLS counts reserved slots incl. holes)
   CNT_LINKS_USED = 11,  // links written (CNT_LINKS counts reserved slots incl. holes)
   CNT_DBL_WORK = 12,    // doublet search: next chunk of 32 sorted hits
@@ -116,7 +115,6 @@ struct Buffers {
   uint8_t* has_out;          // [max_cells] an accepted link starts from the cell
   uint2* link_oc;            // [max_cells] first slot and number of the cell's links
                              //   (valid where it has links)
-  uint32_t* lk_cells;        // [max_links] cells with >= 1 outgoing link
   unsigned long long* best;  // [max_cells] duplicate-cleaning key (cells on ntuplets);
                              //   shares its memory with in_rec, which is dead by then
   uint32_t* in_cnt;          // [max_hits + 1] cells ending on each sorted hit (counted

@@ -140,7 +140,6 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.has_in = (uint8_t*)take(C);
   t.has_out = (uint8_t*)take(C);
   t.link_oc = (uint2*)take(C * 8);
-  t.lk_cells = (uint32_t*)take(L * 4);
   t.in_cnt = (uint32_t*)take((N + 1) * 4);
   t.in_start = (uint32_t*)take((N + 1) * 4);
   t.in_rec = (uint2*)take(C * 8);
@@ -268,9 +267,7 @@ pt_status check_status(pt_ctx* c) {
   if (st & ST_LINKS)
     return fail(PT_ERR_CAPACITY,
                 "max_links = %lld is too small: at least %llu link slots needed",
-                (long long)c->cap.max_links,
-                c->h_cnt[CNT_LINKS] > c->h_cnt[CNT_LKCELLS] ? c->h_cnt[CNT_LINKS]
-                                                            : c->h_cnt[CNT_LKCELLS]);
+                (long long)c->cap.max_links, c->h_cnt[CNT_LINKS]);
   if (st & ST_NT)
     return fail(PT_ERR_CAPACITY,
                 "max_ntuplets = %lld is too small: at least %llu ntuplets needed",
