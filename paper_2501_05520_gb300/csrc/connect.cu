@@ -289,14 +289,17 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
             nf += __popc(pm);
           }
         };
-        // sweep of staged positions [p, p + n) with the lane's window wk; ix = the
-        // lane's index in the incoming list
-        // sweeps from position j until 32 entries are queued or the end; returns where it
-        // stopped
-        auto sweep = [&](uint32_t p, uint32_t j, uint32_t n, float ta, float wk, uint32_t ix) {
+        // sweep of staged positions [j, n) (multiples of 8) with the lane's windows w0, w1,
+        // w2 for the cells of segments 0, 1, 2 (positions below pos1, below pos2, the rest;
+        // a segment's positions are padded to a multiple of 8, so eight positions share
+        // one window); ix = the lane's index in the incoming list.  Stops after the step
+        // that brings the queue to 32 entries, or at the end; returns where it stopped.
+        auto sweep = [&](uint32_t j, uint32_t n, float ta, float w0, float w1, float w2,
+                         uint32_t pos1, uint32_t pos2, uint32_t ix) {
           for (; j < n; j += 8) {
-            const float4 u = *reinterpret_cast<const float4*>(&W.t[p + j]);
-            const float4 v = *reinterpret_cast<const float4*>(&W.t[p + j + 4]);
+            const float wk = j >= pos2 ? w2 : (j >= pos1 ? w1 : w0);
+            const float4 u = *reinterpret_cast<const float4*>(&W.t[j]);
+            const float4 v = *reinterpret_cast<const float4*>(&W.t[j + 4]);
             const bool c0 = fabsf(u.x - ta) <= wk, c1 = fabsf(u.y - ta) <= wk;
             const bool c2 = fabsf(u.z - ta) <= wk, c3 = fabsf(u.w - ta) <= wk;
             const bool c4 = fabsf(v.x - ta) <= wk, c5 = fabsf(v.y - ta) <= wk;
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
                 const uint32_t m = (c0 ? 1u : 0u) | (c1 ? 2u : 0u) | (c2 ? 4u : 0u) | (c3 ? 8u : 0u) |
                                    (c4 ? 16u : 0u) | (c5 ? 32u : 0u) | (c6 ? 64u : 0u) |
                                    (c7 ? 128u : 0u);
-                W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2(ix, (m << 8) | (p + j));
+                W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2(ix, (m << 8) | j);
               }
               tail += __popc(bal);
               if (tail - head >= 32u) return j + 8;
@@ -341,20 +344,18 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
               w[k] = m > 0.0f ? wk * 1.01f + 1e-3f : kInf;
             }
           }
-          // One sweep site: the staged segments, or (when they do not fit) each piece
-          // staged in turn.  The queue is drained before a stage changes and after the
-          // last sweep of h1.
-          const int klast = W.sg[2].cnt ? 2 : (W.sg[1].cnt ? 1 : 0);
+          // One sweep site: one sweep over all staged segments, or (when they do not fit)
+          // one per piece, staged in turn at position 0.  The queue is drained before a
+          // stage changes and after the last sweep of h1.
           const bool last_group = ib + 32 >= W.nin;
 #pragma unroll 1
-          for (int k = 0; k < kMaxOuter; ++k) {
-            const uint32_t cnt = W.sg[k].cnt;
-            const float wk = k == 0 ? w[0] : (k == 1 ? w[1] : w[2]);
+          for (int k = 0; k < (fits ? 1 : kMaxOuter); ++k) {
+            const uint32_t cnt = fits ? 1u : W.sg[k].cnt;
             for (uint32_t j0 = 0; j0 < cnt; j0 += kOutStage) {
-              uint32_t p = W.pos[k], n = cnt;
+              uint32_t n8 = tot, pos1 = W.pos[1], pos2 = W.pos[2];
+              float w0 = w[0], w1 = w[1], w2 = w[2];
               if (!fits) {
-                n = min(cnt - j0, (uint32_t)kOutStage);
-                p = 0;
+                const uint32_t n = min(cnt - j0, (uint32_t)kOutStage);
                 __syncwarp();
                 stage(W.sg[k].off + j0, n, 0, W.p1);
                 if (lane == 0) {
@@ -363,18 +364,19 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
                   W.coff[0] = W.sg[k].off + j0;
                 }
                 __syncwarp();
+                n8 = round8(n);
+                pos1 = pos2 = kOutStage;
+                w0 = k == 0 ? w[0] : (k == 1 ? w[1] : w[2]);
               }
+              const bool last = !fits || last_group;
               // one call site each for the sweep and the exact cuts (instruction cache)
-              const uint32_t n8 = round8(n);
-              const bool last = !fits || (last_group && k == klast);
               for (uint32_t j = 0;;) {
-                j = sweep(p, j, n8, ta, wk, ix);
+                j = sweep(j, n8, ta, w0, w1, w2, pos1, pos2, ix);
                 const bool done = j >= n8;
                 while (tail - head >= 32u || (done && last && tail != head))
                   process(min(32u, tail - head));
                 if (done) break;
               }
-              if (fits) break;
             }
           }
         }
