@@ -230,9 +230,20 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
       }
       const bool fits = tot <= (uint32_t)kOutStage;
       if (fits) {
-#pragma unroll
-        for (int k = 0; k < kMaxOuter; ++k)
-          if (W.sg[k].cnt) stage(W.sg[k].off, W.sg[k].cnt, W.pos[k], W.p1);
+        // all segments in one pass over the staged positions (NaN slope for padding)
+        const float4 p1 = W.p1;
+        for (uint32_t P = lane; P < tot; P += 32) {
+          const int k = (P >= W.pos[1]) + (P >= W.pos[2]);
+          const uint32_t i = P - W.pos[k];
+          float t = kNaN;
+          float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (i < W.sg[k].cnt) {
+            q = b.hit4[b.cell_out[W.sg[k].off + i]];
+            t = __fdividef(q.z - p1.z, q.w - p1.w);
+          }
+          W.t[P] = t;
+          W.p2[P] = q;
+        }
       }
 
       // Pass 0 finds the links of h1, keeps up to kFound of them in shared memory and
