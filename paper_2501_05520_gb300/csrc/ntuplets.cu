@@ -6,8 +6,10 @@
 //     (a cell with no outgoing link) with 3..6 hits.  Roots are taken among the sources
 //     of the link lists (a root without an outgoing link would give a 2-hit path,
 //     which is dropped).  One thread per root walks its out-links depth first with an
-//     explicit stack (the layer graph bounds the depth at 5 cells), once to count and,
-//     after one atomic per warp reserves the slots, once to write.  The path quality q is the float32 sum of its link qualities,
+//     explicit stack (the layer graph bounds the depth at 5 cells), writing the paths to
+//     its warp's shared buffer, which one atomic per 32 roots reserves and the warp
+//     copies out (a batch of roots with more paths than the buffer holds is walked a
+//     second time and written directly).  The path quality q is the float32 sum of its link qualities,
 //     added from the innermost link outwards.
 // A6  canonical order: ntuplets sorted by their hit tuple (batch input indices, -1
 //     padded, signed).  A counting sort on the first hit puts them in per-hit buckets
@@ -24,12 +26,30 @@ namespace ptca {
 
 namespace {
 
-// Depth-first walk from root a.  EMIT == false: returns the number of ntuplets;
-// EMIT == true: writes them at slots t0, t0 + 1, ... (slots >= cap_nt are dropped).
-// A cell's links are one (offset, count) read; when emitting, the batch index of each
-// cell's outer hit is looked up once, when the cell is pushed.
-template <bool EMIT, bool GATED>
-__device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, uint64_t cap_nt) {
+// Ntuplets buffered per warp in shared memory before one global reservation.
+constexpr int kNtBuf = 64;
+constexpr int kNtWarps = 8;  // warps per block of the ntuplet search
+struct NtWarp {
+  uint32_t roots[64];                        // queued roots (< 32 + 32)
+  int32_t hits[kNtBuf][kMaxHits];            // buffered ntuplets
+  uint32_t cells[kNtBuf][kMaxCellsPerNt];
+  float q[kNtBuf];
+  uint32_t n[kNtBuf];
+  uint32_t cnt;                              // ntuplets found by the batch (may exceed kNtBuf)
+};
+
+enum WalkMode { kCount = 0, kEmit = 1, kBuffer = 2 };
+
+// Depth-first walk from root a.  kCount: returns the number of ntuplets; kEmit: also
+// writes them at slots t0, t0 + 1, ... (slots >= cap_nt are dropped); kBuffer: also
+// writes them to the warp's shared buffer (entries >= kNtBuf are dropped; the caller
+// then walks again with kEmit).  A cell's links are one (offset, count) read; when
+// writing, the batch index of each cell's outer hit is looked up once, when the cell is
+// pushed.
+template <int MODE, bool GATED>
+__device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, uint64_t cap_nt,
+                         NtWarp* W) {
+  constexpr bool EMIT = MODE != kCount;
   uint32_t path[kMaxCellsPerNt];
   uint32_t it[kMaxCellsPerNt], end[kMaxCellsPerNt];
   float qs[kMaxCellsPerNt];
@@ -62,22 +82,40 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
     if (!b.has_out[c]) {
       // leaf: path[0..d] + c, i.e. depth + 1 cells, depth + 2 hits
       if (EMIT) {
-        const unsigned long long t = t0 + found;
-        if (t < cap_nt) {
-          const int ncell = depth + 1;
-          int32_t* hp = b.nt_hits + t * kMaxHits;
-          uint32_t* cp = b.nt_cells + t * kMaxCellsPerNt;
+        const int ncell = depth + 1;
+        const int32_t gl = (int32_t)b.perm[b.cell_out[c]];
+        int32_t* hp = nullptr;
+        uint32_t* cp = nullptr;
+        bool keep = false;
+        if (MODE == kEmit) {
+          const unsigned long long t = t0 + found;
+          keep = t < cap_nt;
+          if (keep) {
+            hp = b.nt_hits + t * kMaxHits;
+            cp = b.nt_cells + t * kMaxCellsPerNt;
+            b.nt_n[t] = (uint8_t)(ncell + 1);
+            b.nt_q[t] = q;
+          }
+        } else {
+          const uint32_t e = atomicAdd(&W->cnt, 1u);
+          keep = e < (uint32_t)kNtBuf;
+          if (keep) {
+            hp = W->hits[e];
+            cp = W->cells[e];
+            W->n[e] = (uint32_t)(ncell + 1);
+            W->q[e] = q;
+          }
+        }
+        for (int k = 0; k < ncell; ++k)
+          b.best[k < depth ? path[k] : c] = ~0ull;  // initial duplicate-cleaning key
+        if (keep) {
           hp[0] = g0;
           for (int k = 0; k < ncell; ++k) {
-            const uint32_t ck = k < depth ? path[k] : c;
-            hp[k + 1] = k < depth ? gh[k] : (int32_t)b.perm[b.cell_out[c]];
-            cp[k] = ck;
-            b.best[ck] = ~0ull;  // initial duplicate-cleaning key of a cell on an ntuplet
+            hp[k + 1] = k < depth ? gh[k] : gl;
+            cp[k] = k < depth ? path[k] : c;
           }
           for (int k = ncell + 1; k < kMaxHits; ++k) hp[k] = -1;
           for (int k = ncell; k < kMaxCellsPerNt; ++k) cp[k] = 0xffffffffu;
-          b.nt_n[t] = (uint8_t)(ncell + 1);
-          b.nt_q[t] = q;
         }
       }
       ++found;
@@ -94,16 +132,22 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
   return found;
 }
 
-// One thread per link slot; the slot that starts a source cell's run of links (its
-// predecessor holds another source or a hole) names a candidate root, which is a root
-// when the cell has a kept outgoing link and no incoming one.  Each warp counts its
-// roots' ntuplets, reserves them with one atomic and walks again to write them.
+// The slot that starts a source cell's run of links (its predecessor holds another
+// source or a hole) names a candidate root, which is a root when the cell has a kept
+// outgoing link and no incoming one.  Each warp queues the roots of its link slots in
+// shared memory and walks them 32 at a time, one per lane, writing the ntuplets to its
+// shared buffer; one atomic then reserves them and the warp copies them out.  If a
+// batch finds more than the buffer holds, it is walked again and written directly.
 template <bool GATED>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kNtWarps * 32)
     k_find_ntuplets(Buffers b, uint64_t cap_links, uint64_t cap_nt) {
+  __shared__ NtWarp s_w[kNtWarps];
+  NtWarp& W = s_w[threadIdx.x >> 5];
   const uint64_t nl = min(b.cnt[CNT_LINKS], (unsigned long long)cap_links);
   const int lane = lane_id();
+  const unsigned lt_mask = (1u << lane) - 1u;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint32_t nq = 0;  // queued roots (warp-uniform)
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < nl;
        i0 += stride) {
     const uint64_t i = i0 + lane;
@@ -112,15 +156,48 @@ __global__ void __launch_bounds__(256)
     uint32_t prev = __shfl_up_sync(kFull, a, 1);
     if (lane == 0) prev = i0 > 0 ? b.link_src[i0 - 1] : kHole;
     const bool root = a != kHole && a != prev && b.has_out[a] && !b.has_in[a];
-    const uint32_t n = root ? walk<false, GATED>(b, a, 0, cap_nt) : 0u;
-    const uint32_t inc = warp_incl_scan(n);
-    const uint32_t tot = __shfl_sync(kFull, inc, 31);
-    if (tot == 0) continue;
-    unsigned long long base = 0;
-    if (lane == 31) base = atomicAdd(&b.cnt[CNT_NT], (unsigned long long)tot);
-    base = __shfl_sync(kFull, base, 31);
-    if (base + tot > cap_nt && lane == 31) atomicOr(&b.cnt[CNT_STATUS], ST_NT);
-    if (n) walk<true, GATED>(b, a, base + inc - n, cap_nt);
+    const unsigned rm = __ballot_sync(kFull, root);
+    if (root) W.roots[nq + __popc(rm & lt_mask)] = a;
+    nq += __popc(rm);
+    const bool final = i0 + stride >= nl;
+    while (nq >= 32u || (final && nq > 0u)) {
+      const uint32_t take = min(nq, 32u);
+      __syncwarp();
+      const uint32_t r = (uint32_t)lane < take ? W.roots[lane] : kHole;
+      if (lane == 0) W.cnt = 0;
+      __syncwarp();
+      const uint32_t n = r != kHole ? walk<kBuffer, GATED>(b, r, 0, cap_nt, &W) : 0u;
+      __syncwarp();
+      const uint32_t tot = W.cnt;
+      // the roots not taken move to the front of the queue
+      const uint32_t rest = nq - take;
+      const uint32_t moved = (uint32_t)lane < rest ? W.roots[take + lane] : 0u;
+      __syncwarp();
+      if ((uint32_t)lane < rest) W.roots[lane] = moved;
+      nq = rest;
+      if (tot == 0) continue;
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(&b.cnt[CNT_NT], (unsigned long long)tot);
+      base = __shfl_sync(kFull, base, 0);
+      if (base + tot > cap_nt && lane == 0) atomicOr(&b.cnt[CNT_STATUS], ST_NT);
+      if (tot <= (uint32_t)kNtBuf) {
+        for (uint32_t e = lane; e < tot; e += 32) {
+          const unsigned long long t = base + e;
+          if (t < cap_nt) {
+#pragma unroll
+            for (int k = 0; k < kMaxHits; ++k) b.nt_hits[t * kMaxHits + k] = W.hits[e][k];
+#pragma unroll
+            for (int k = 0; k < kMaxCellsPerNt; ++k)
+              b.nt_cells[t * kMaxCellsPerNt + k] = W.cells[e][k];
+            b.nt_n[t] = (uint8_t)W.n[e];
+            b.nt_q[t] = W.q[e];
+          }
+        }
+      } else {
+        const uint32_t inc = warp_incl_scan(n);
+        if (n) walk<kEmit, GATED>(b, r, base + inc - n, cap_nt, &W);
+      }
+    }
   }
 }
 
@@ -240,10 +317,10 @@ void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStr
   const uint64_t cap_nt = (uint64_t)p.max_ntuplets;
   if (gated)
     PT_TRACE(l, s, "k_find_ntuplets",
-             k_find_ntuplets<true><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links, cap_nt));
+             k_find_ntuplets<true><<<l.grid, kNtWarps * 32, 0, s>>>(b, (uint64_t)p.max_links, cap_nt));
   else
     PT_TRACE(l, s, "k_find_ntuplets",
-             k_find_ntuplets<false><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links, cap_nt));
+             k_find_ntuplets<false><<<l.grid, kNtWarps * 32, 0, s>>>(b, (uint64_t)p.max_links, cap_nt));
   PT_TRACE(l, s, "k_bucket_count", k_bucket_count<<<l.grid, 256, 0, s>>>(b, cap_nt));
   PT_TRACE(l, s, "scan",
            launch_scan(b.bucket_cnt, b.bucket_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s));
