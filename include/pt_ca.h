@@ -292,8 +292,9 @@ pt_status pt_get_trace(pt_ctx* ctx, pt_kernel_time* out, int cap, int* n);
 /* Launch sizes of the persistent grid-stride kernels, in blocks per multiprocessor
  * (each 1..32): blocks_per_sm for the 256-thread bookkeeping kernels (clear, binning,
  * scans, ntuplet walk, dedup, fit, export; default 4) and search_blocks_per_sm for the
- * warp-per-hit doublet and connect searches (default 5, their residency limit).  Any
- * value gives the same results.  Synchronises the stream; the next whole-batch call
+ * warp-per-hit doublet search (default 5, its residency limit); the link search always
+ * runs 4 blocks of 8 warps per multiprocessor, its residency limit.  Any value gives
+ * the same results.  Synchronises the stream; the next whole-batch call
  * re-captures its graph. */
 pt_status pt_set_launch(pt_ctx* ctx, int blocks_per_sm, int search_blocks_per_sm);
 

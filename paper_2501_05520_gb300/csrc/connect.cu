@@ -40,6 +40,7 @@ constexpr int kQueue = 128;     // candidate ring per warp (power of two, >= 31 
 constexpr int kFound = 64;      // links of one group kept in shared memory (rank < 256)
 constexpr uint32_t kHitChunk = 4;       // consecutive middle hits per warp chunk (<= 32)
 constexpr int kScatterBlocksPerSm = 4;  // fewer warps in flight keep the scatter local
+constexpr int kConnBlocksPerSm = 4;     // 64 registers per thread: no spills in the link search
 static_assert(kOutStage % 8 == 0 && kOutStage < 256, "staged positions fit 8 bits");
 
 __device__ __forceinline__ uint32_t round8(uint32_t n) { return (n + 7u) & ~7u; }
@@ -132,7 +133,7 @@ __device__ __forceinline__ unsigned long long chunk_take_shared(
 }
 
 template <bool GATE>
-__global__ void __launch_bounds__(kConnWarps * 32, 5)
+__global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
     k_connect(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap_links) {
   __shared__ ConnWarp s_w[kConnWarps];
   const int lane = lane_id();
@@ -229,6 +230,10 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
         __syncwarp();
       }
       const bool fits = tot <= (uint32_t)kOutStage;
+      // inner hit of the lane's incoming cell in the group to come: fetched ahead (the
+      // first group's during the stage, each later group's during the group before), so
+      // that placing a group's windows waits for one load instead of two in a row
+      uint32_t h0n = (uint32_t)lane < W.nin ? (b.in_rec[W.in0 + lane].y & 0x7fffffffu) : 0u;
       if (fits) {
         // all segments in one pass over the staged positions (NaN slope for padding)
         const float4 p1 = W.p1;
@@ -253,6 +258,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
 #pragma unroll 1
       for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1 && nfound <= (uint32_t)kFound) break;
+        if (pass == 1)
+          h0n = (uint32_t)lane < W.nin ? (b.in_rec[W.in0 + lane].y & 0x7fffffffu) : 0u;
         uint32_t head = 0, tail = 0, nf = 0;
         // exact cuts on up to 32 queued entries, all lanes busy (one round per set bit)
         auto process = [&](uint32_t nt) {
@@ -337,12 +344,11 @@ __global__ void __launch_bounds__(kConnWarps * 32, 5)
           float w[kMaxOuter];
           {
             const float4 p1 = W.p1;
-            float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (ix < W.nin) {
-              p0 = b.hit4[b.in_rec[W.in0 + ix].y & 0x7fffffffu];
-              ta = __fdividef(p1.z - p0.z, p1.w - p0.w);  // the cell's slope dz/dr
-            }
-            const float id1 = __fdividef(1.0f, p1.w - p0.w);
+            float2 zw = make_float2(0.f, 0.f);
+            if (ix < W.nin) zw = *reinterpret_cast<const float2*>(&b.hit4[h0n].z);  // z, r
+            h0n = ix + 32 < W.nin ? (b.in_rec[W.in0 + ix + 32].y & 0x7fffffffu) : 0u;
+            if (ix < W.nin) ta = __fdividef(p1.z - zw.x, p1.w - zw.y);  // the cell's slope dz/dr
+            const float id1 = __fdividef(1.0f, p1.w - zw.y);
             const float wa = (cuts.rz0 + cuts.rz1 * cuts.cotmax) * id1;
             const float ua = cuts.rz0 + cuts.rz1 * fabsf(ta);
             const float shrink = 1.0f - cuts.rz1 * id1;
@@ -471,11 +477,11 @@ void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStre
            k_in_scatter<<<l.sms * kScatterBlocksPerSm, 256, 0, s>>>(b, p.phi_bins));
   if (gated)
     PT_TRACE(l, s, "k_connect",
-             k_connect<true><<<l.sgrid, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
+             k_connect<true><<<l.sms * kConnBlocksPerSm, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
                                                                   (uint64_t)p.max_links));
   else
     PT_TRACE(l, s, "k_connect",
-             k_connect<false><<<l.sgrid, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
+             k_connect<false><<<l.sms * kConnBlocksPerSm, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
                                                                    (uint64_t)p.max_links));
 }
 

@@ -172,7 +172,7 @@ void trace_end(Tracer* t, const char* name, size_t i0, cudaStream_t s);
 struct Launch {
   int sms;                // multiprocessors
   int grid;               // generic persistent grid (blocks of 256 threads)
-  int sgrid;              // grid of the doublet and connect searches (warp per hit)
+  int sgrid;              // grid of the doublet search (warp per hit)
   Tracer* tr = nullptr;   // per-kernel timing, when enabled
 };
 
