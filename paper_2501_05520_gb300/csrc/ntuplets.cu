@@ -29,6 +29,7 @@ namespace {
 // Ntuplets buffered per warp in shared memory before one global reservation.
 constexpr int kNtBuf = 64;
 constexpr int kNtWarps = 8;  // warps per block of the ntuplet search
+constexpr int kNtBlocksPerSm = 6;  // more walks in flight hide more of their load latency
 struct NtWarp {
   uint32_t roots[64];                        // queued roots (< 32 + 32)
   int32_t hits[kNtBuf][kMaxHits];            // buffered ntuplets
@@ -79,11 +80,16 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
     if (GATED && !b.gate_keep[l]) continue;  // removed by the learned gate
     const uint32_t c = b.link_dst[l];
     const float q = fadd(qs[d], b.link_q[l]);
-    if (!b.has_out[c]) {
+    // everything c may need is loaded at once: its flag, its link list (stale and
+    // unused when c has no links) and its outer hit
+    const bool leaf = !b.has_out[c];
+    const uint2 oc = b.link_oc[c];
+    const int32_t gc = EMIT ? (int32_t)b.perm[b.cell_out[c]] : 0;
+    if (leaf) {
       // leaf: path[0..d] + c, i.e. depth + 1 cells, depth + 2 hits
       if (EMIT) {
         const int ncell = depth + 1;
-        const int32_t gl = (int32_t)b.perm[b.cell_out[c]];
+        const int32_t gl = gc;
         int32_t* hp = nullptr;
         uint32_t* cp = nullptr;
         bool keep = false;
@@ -122,11 +128,10 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
       continue;
     }
     path[depth] = c;
-    const uint2 oc = b.link_oc[c];
     it[depth] = oc.x;
     end[depth] = oc.x + oc.y;
     qs[depth] = q;
-    if (EMIT) gh[depth] = (int32_t)b.perm[b.cell_out[c]];
+    if (EMIT) gh[depth] = gc;
     ++depth;
   }
   return found;
@@ -139,7 +144,7 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
 // shared buffer; one atomic then reserves them and the warp copies them out.  If a
 // batch finds more than the buffer holds, it is walked again and written directly.
 template <bool GATED>
-__global__ void __launch_bounds__(kNtWarps * 32)
+__global__ void __launch_bounds__(kNtWarps * 32, kNtBlocksPerSm)
     k_find_ntuplets(Buffers b, uint64_t cap_links, uint64_t cap_nt) {
   __shared__ NtWarp s_w[kNtWarps];
   NtWarp& W = s_w[threadIdx.x >> 5];
@@ -317,10 +322,12 @@ void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStr
   const uint64_t cap_nt = (uint64_t)p.max_ntuplets;
   if (gated)
     PT_TRACE(l, s, "k_find_ntuplets",
-             k_find_ntuplets<true><<<l.grid, kNtWarps * 32, 0, s>>>(b, (uint64_t)p.max_links, cap_nt));
+             k_find_ntuplets<true><<<l.sms * kNtBlocksPerSm, kNtWarps * 32, 0, s>>>(
+                 b, (uint64_t)p.max_links, cap_nt));
   else
     PT_TRACE(l, s, "k_find_ntuplets",
-             k_find_ntuplets<false><<<l.grid, kNtWarps * 32, 0, s>>>(b, (uint64_t)p.max_links, cap_nt));
+             k_find_ntuplets<false><<<l.sms * kNtBlocksPerSm, kNtWarps * 32, 0, s>>>(
+                 b, (uint64_t)p.max_links, cap_nt));
   PT_TRACE(l, s, "k_bucket_count", k_bucket_count<<<l.grid, 256, 0, s>>>(b, cap_nt));
   PT_TRACE(l, s, "scan",
            launch_scan(b.bucket_cnt, b.bucket_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s));
