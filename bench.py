@@ -49,10 +49,10 @@ CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped
 # DRAM traffic per event of the main kernels from one ncu capture (8 PU200 events per
 # launch, profiles/), valid only while the kernel's sources hash to the recorded value.
 NCU_TRAFFIC = {
-    "k_doublets": {"bytes_per_event": 19372416, "issue_active_pct": 73.5, "sha": "9fb817df29d2"},
-    "k_in_scatter": {"bytes_per_event": 34797408, "issue_active_pct": 19.3, "sha": "86e93db645e8"},
-    "k_connect": {"bytes_per_event": 32225568, "issue_active_pct": 57.9, "sha": "86e93db645e8"},
-    "k_find_ntuplets": {"bytes_per_event": 51738624, "issue_active_pct": 15.0, "sha": "f54dc359c651"},
+    "k_doublets": {"bytes_per_event": 19121568, "issue_active_pct": 67.8, "sha": "09d70e1e485c"},
+    "k_in_scatter": {"bytes_per_event": 34849440, "issue_active_pct": 19.6, "sha": "5ed2457445ef"},
+    "k_connect": {"bytes_per_event": 29912160, "issue_active_pct": 71.4, "sha": "5ed2457445ef"},
+    "k_find_ntuplets": {"bytes_per_event": 48503392, "issue_active_pct": 16.7, "sha": "65d5d92c179b"},
 }
 
 
@@ -80,10 +80,11 @@ def kernel_bytes(kernel: str, c: dict) -> int | None:
         # cell outer 4 C, records 8 C, two link flags 2 C
         "k_in_scatter": 64 * N + 14 * C,
         # in_start 4 N, segments 48 N, hits 16 N; records 8 C, outer hit of staged cells
-        # 4 C; links (source, target, quality) 12 Lk, per-cell lists and flags <= 14 Lk
-        "k_connect": 68 * N + 12 * C + 26 * Lk,
-        # roots and their flags and lists <= 14 Lk, link targets and qualities 8 Lk;
-        # candidates (6 hits, 5 cells, n, q) 49 T
+        # 4 C; links (source, target, quality) 12 Lk, per-cell lists (8) and the two link
+        # flags <= 10 Lk
+        "k_connect": 68 * N + 12 * C + 22 * Lk,
+        # link sources (root search) 4 Lk, roots' flags and lists <= 10 Lk, link targets
+        # and qualities 8 Lk; candidates (6 hits, 5 cells, n, q) 49 T
         "k_find_ntuplets": 22 * Lk + 49 * T,
     }.get(kernel)
 
