@@ -50,8 +50,8 @@ CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped
 # launch, profiles/), valid only while the kernel's sources hash to the recorded value.
 NCU_TRAFFIC = {
     "k_doublets": {"bytes_per_event": 19121568, "issue_active_pct": 67.8, "sha": "09d70e1e485c"},
-    "k_in_scatter": {"bytes_per_event": 34849440, "issue_active_pct": 19.6, "sha": "5ed2457445ef"},
-    "k_connect": {"bytes_per_event": 29912160, "issue_active_pct": 71.4, "sha": "5ed2457445ef"},
+    "k_in_scatter": {"bytes_per_event": 34849440, "issue_active_pct": 19.6, "sha": "e3b22fefdd45"},
+    "k_connect": {"bytes_per_event": 29912160, "issue_active_pct": 71.4, "sha": "e3b22fefdd45"},
     "k_find_ntuplets": {"bytes_per_event": 48503392, "issue_active_pct": 16.7, "sha": "65d5d92c179b"},
 }
 

@@ -4,10 +4,11 @@
 // triplets by the cellular automaton).
 //
 // One warp per middle hit h1.  The cells leaving h1 (up to three segments, one per
-// outer layer) are staged once in shared memory: their r-z slopes and the coordinates
-// of their outer hits.  The cells ending on h1 come from a per-hit list of 8-byte
-// records (cell, inner hit | inner-layer flag) and are taken 32 at a time, one per
-// lane.  With d1 = r1-r0, d2 = r2-r1 and t_a, t_b the slopes of a and b, C1 reads
+// outer layer, each padded to a multiple of 8) are staged once, in one pass, in shared
+// memory: their r-z slopes and the coordinates of their outer hits.  The cells ending
+// on h1 come from a per-hit list of 8-byte records (cell, inner hit | inner-layer flag)
+// and are taken 32 at a time, one per lane; the inner hits of the next group are
+// fetched while a group is swept.  With d1 = r1-r0, d2 = r2-r1 and t_a, t_b the slopes of a and b, C1 reads
 //   d1 d2 |t_a - t_b| <= rz0 (d1 + d2) + rz1 |t_a d1 + t_b d2|,
 // so |t_a - t_b| <= rz0 (1/d1 + 1/d2) + rz1 (|t_a|/d2 + |t_b|/d1).  Bounding |t_b| by
 // cotmax (D4), or by |t_a| + |t_a - t_b| and solving for |t_a - t_b|, and d2 by the
@@ -17,17 +18,18 @@
 // the second term only where d1 > rz1.  It is widened by 1 % + 1e-3, far beyond the
 // float32 rounding of C1 (about 4e-7 |t_a| d1/m + 1e-6) and of the approximate
 // quotients and reciprocals used for the slopes and the window (a few 1e-7 relative).
-// The warp sweeps the staged slopes eight at a time, every lane testing its own cell
-// against them, with no divergence; a lane whose window holds any of the eight queues
-// one entry (incoming index, 8-bit mask, position).  The queue is drained 32 entries
+// The warp sweeps all staged slopes eight at a time, every lane testing its own cell
+// against them with the window of the segment the eight belong to, with no divergence;
+// a lane whose window holds any of the eight queues one entry (incoming index, 8-bit
+// mask, position).  The queue is drained 32 entries
 // at a time through the exact cuts, all lanes busy.  The links of a middle hit are
 // collected in shared memory, reserved once, sorted by source cell and written as
 // per-cell lists (the out-link lists the ntuplet search walks): a source's links are
 // one run of equal link_src values, so the first slot of each run names a cell that
-// can start an ntuplet.  If a
-// hit has more links than the collection holds, the search runs a second time and
-// writes them all to a temporary half of a double-size reservation, which is then
-// sorted.  Segments larger than the stage are swept piece by piece.
+// can start an ntuplet.  If a hit has more links than the collection holds, the search
+// runs a second time and writes them all to a temporary half of a double-size
+// reservation, which is then sorted.  Segments larger than the stage are swept piece
+// by piece.
 #include "ptca_internal.cuh"
 
 namespace ptca {
