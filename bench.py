@@ -49,10 +49,10 @@ CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped
 # DRAM traffic per event of the main kernels from one ncu capture (8 PU200 events per
 # launch, profiles/), valid only while the kernel's sources hash to the recorded value.
 NCU_TRAFFIC = {
-    "k_doublets": {"bytes_per_event": 19121568, "issue_active_pct": 67.8, "sha": "09d70e1e485c"},
-    "k_in_scatter": {"bytes_per_event": 34849440, "issue_active_pct": 19.6, "sha": "e3b22fefdd45"},
-    "k_connect": {"bytes_per_event": 29912160, "issue_active_pct": 71.4, "sha": "e3b22fefdd45"},
-    "k_find_ntuplets": {"bytes_per_event": 48503392, "issue_active_pct": 16.7, "sha": "65d5d92c179b"},
+    "k_doublets": {"bytes_per_event": 19115680, "issue_active_pct": 68.0, "sha": "36e28b7ff97f"},
+    "k_in_scatter": {"bytes_per_event": 35022240, "issue_active_pct": 19.9, "sha": "694260f6d0d8"},
+    "k_connect": {"bytes_per_event": 30141664, "issue_active_pct": 71.6, "sha": "694260f6d0d8"},
+    "k_find_ntuplets": {"bytes_per_event": 48477568, "issue_active_pct": 15.9, "sha": "855ebb585d36"},
 }
 
 
@@ -327,6 +327,32 @@ def _config4(ctx, dev, flush, stream, steps, warmup, n_events):
             "path": "whole-chain CUDA graph, device inputs"}
 
 
+def _vertexing(ctx, dbat, stream, steps: int) -> dict:
+    """Primary vertices (pt_find_vertices, quadruplets and longer, 0.02 cm steps) of the
+    fitted tracks of one bench batch, timed with CUDA events on the library's stream; the
+    chain itself runs before the events."""
+    import torch
+    off, x, y, z, layer = dbat[0]
+    ctx.pt_load_batch(off, x, y, z, layer)
+    ctx.pt_build_doublets(sync=False)
+    ctx.pt_connect_cells(sync=False)
+    ctx.pt_find_ntuplets(sync=False)
+    ctx.pt_fit_tracks(sync=False)
+    nv = ctx.pt_find_vertices()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        ctx.pt_find_vertices(sync=False)
+        e1.record(stream)
+    stream.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    E = len(off) - 1
+    return {"ms_per_step": statistics.mean(ms), "events_per_step": E,
+            "vertices_per_event": nv / E, "tracks_per_event": ctx.pt_get_tracks().shape[0] / E,
+            "workload": "the bench batch's fitted tracks (its particles have independent z0)"}
+
+
 def _physics(ctx, host, events):
     """Efficiency, fake and duplicate rates of the cleaned ntuplets (generator truth)."""
     from sim import truth
@@ -489,6 +515,8 @@ def run_ours(args):
                  "d2h_bytes_per_step": S * (24 + 1 + 36) + (B + 1) * 8 + 128},
             physics=_physics(ctx, host, events) if not args.no_physics else None)
     ctx.pt_set_gate(None, 0.0)
+    with torch.cuda.stream(stream):
+        vertexing = _vertexing(ctx, dbat, stream, min(args.steps, 20))
     config4 = {"plain": _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)}
     ctx.pt_set_gate(gw, gtau)
     config4["gated"] = _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)
@@ -533,6 +561,7 @@ def run_ours(args):
                 "physics": {"plain": plain["physics"], "gated": forms["gated"]["physics"]},
                 "counts_per_step": counts,
                 "batch_workload": config4,
+                "vertexing": vertexing,
                 "autotune": launch,
                 "clocks": clocks,
                 "gpu_launches": launches["plain"] * args.steps}

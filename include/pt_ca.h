@@ -100,6 +100,15 @@ typedef struct {
   uint8_t pad[2];
 } pt_track;
 
+/* One primary vertex (pt_find_vertices): z (cm), the sum of its tracks' pT^2 (GeV^2),
+ * its number of tracks and its event in the batch. */
+typedef struct {
+  float z;
+  float sum_pt2;
+  int32_t n_tracks;
+  int32_t event;
+} pt_vertex;
+
 /* ------------------------------------------------------------------ lifecycle */
 
 /* Device bytes needed for a context of the given capacity (the workspace that
@@ -167,6 +176,27 @@ pt_status pt_get_ntuplets(pt_ctx* ctx, int32_t* hits, uint8_t* nhits, int64_t* e
 
 /* Fitted tracks, one per cleaned ntuplet, same order.  Synchronises the stream. */
 pt_status pt_get_tracks(pt_ctx* ctx, pt_track* tracks, int64_t cap, int64_t* n, int on_device);
+
+/* Primary vertices of the fitted tracks (Sec. 2.2.1: vertex reconstruction is the last
+ * of the chain's sub-algorithms, and the reconstructed tracks and vertices are what it
+ * returns, Fig. 2; the paper gives no algorithm).  Per event: the tracks with at least
+ * min_hits hits (3..6; 4 keeps quadruplets and longer) and a finite z0 are ordered by
+ * z0 (ties: canonical track order) and the list is cut wherever the float32 step to
+ * the next z0 exceeds dz (cm, > 0; a step of exactly dz does not cut); every group of
+ * two or more tracks is a vertex with z = mean z0.  Run after pt_fit_tracks on the same
+ * batch.  n_vertices: NULL to stay asynchronous, else the call synchronises and stores
+ * the number of vertices.  Errors: PT_ERR_INVALID for bad arguments or no fitted batch;
+ * PT_ERR_CAPACITY when an event has more than 16384 such tracks. */
+pt_status pt_find_vertices(pt_ctx* ctx, int min_hits, float dz, int64_t* n_vertices);
+
+/* Vertices of the last pt_find_vertices, events in order, z ascending within an
+ * event.  vertices: [cap] (may be NULL); event_offsets: [n_events + 1] int64 (may be
+ * NULL), the vertices of event e are [event_offsets[e], event_offsets[e+1]);
+ * track_vertex: [n_tracks] int32 (may be NULL), the vertex (index into the batch's
+ * vertex list) of each fitted track in pt_get_tracks order, -1 for none.  *n = total
+ * count; PT_ERR_CAPACITY if cap < *n (nothing written).  Synchronises the stream. */
+pt_status pt_get_vertices(pt_ctx* ctx, pt_vertex* vertices, int64_t* event_offsets,
+                          int32_t* track_vertex, int64_t cap, int64_t* n, int on_device);
 
 /* Intermediate products, for validation.  Cells as (inner, outer) input-index pairs;
  * links as (h0, h1, h2) input-index triples with their quality q; ntuplets before

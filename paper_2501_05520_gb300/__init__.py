@@ -27,7 +27,8 @@ PT_OK, PT_ERR_INVALID, PT_ERR_CAPACITY, PT_ERR_CUDA, PT_ERR_TIMEOUT, PT_ERR_NOT_
 # Every symbol include/pt_ca.h declares.
 EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt_load_hits",
             "pt_load_batch", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
-            "pt_fit_tracks", "pt_get_ntuplets", "pt_get_tracks", "pt_get_cells", "pt_get_links",
+            "pt_fit_tracks", "pt_get_ntuplets", "pt_get_tracks", "pt_find_vertices",
+            "pt_get_vertices", "pt_get_cells", "pt_get_links",
             "pt_get_candidates", "pt_reconstruct_batch", "pt_enqueue_batch",
             "pt_find_doublets_noalloc", "pt_set_gate", "pt_get_link_features", "pt_gate_score",
             "pt_gate_loss_grad", "pt_gate_adam", "pt_server_create", "pt_server_set_gate",
@@ -63,6 +64,8 @@ TRACK_DTYPE = np.dtype([("kappa", "<f4"), ("phi0", "<f4"), ("d0", "<f4"), ("cot_
                         ("chi2_line", "<f4"), ("charge", "i1"), ("nhits", "u1"),
                         ("pad", "u1", (2,))])
 assert TRACK_DTYPE.itemsize == 36
+VERTEX_DTYPE = np.dtype([("z", "<f4"), ("sum_pt2", "<f4"), ("n_tracks", "<i4"), ("event", "<i4")])
+assert VERTEX_DTYPE.itemsize == 16
 
 
 class PtError(RuntimeError):
@@ -95,6 +98,8 @@ def lib() -> ctypes.CDLL:
             "pt_fit_tracks": [P, PI64],
             "pt_get_ntuplets": [P, P, P, P, I64, PI64, I32],
             "pt_get_tracks": [P, P, I64, PI64, I32],
+            "pt_find_vertices": [P, I32, ctypes.c_float, PI64],
+            "pt_get_vertices": [P, P, P, P, I64, PI64, I32],
             "pt_get_cells": [P, P, P, P, I64, PI64],
             "pt_get_links": [P, P, P, P, P, P, I64, PI64],
             "pt_get_candidates": [P, P, P, P, P, I64, PI64],
@@ -306,6 +311,31 @@ class Context:
         out = np.zeros(int(n.value), TRACK_DTYPE)
         _check(lib().pt_get_tracks(self.handle, _hptr(out), out.size, ctypes.byref(n), 0))
         return out
+
+    def pt_find_vertices(self, min_hits: int = 4, dz: float = 0.02, sync: bool = True):
+        """Primary vertices of the fitted tracks; returns their number when sync."""
+        n = ctypes.c_int64(0)
+        _check(lib().pt_find_vertices(self.handle, int(min_hits), float(dz),
+                                      ctypes.byref(n) if sync else None))
+        return int(n.value) if sync else None
+
+    def pt_get_vertices(self):
+        """(vertices VERTEX_DTYPE [V], event_offsets int64 [E+1], track_vertex int32 [S])."""
+        n = ctypes.c_int64(0)
+        st = lib().pt_get_vertices(self.handle, None, None, None, 0, ctypes.byref(n), 0)
+        if st not in (PT_OK, PT_ERR_CAPACITY):
+            _check(st)
+        V = int(n.value)
+        S = ctypes.c_int64(0)
+        st = lib().pt_get_tracks(self.handle, None, 0, ctypes.byref(S), 0)
+        if st not in (PT_OK, PT_ERR_CAPACITY):
+            _check(st)
+        out = np.zeros(V, VERTEX_DTYPE)
+        off = np.empty(self.n_events + 1, np.int64)
+        tv = np.empty(int(S.value), np.int32)
+        _check(lib().pt_get_vertices(self.handle, _hptr(out), _hptr(off), _hptr(tv), V,
+                                     ctypes.byref(n), 0))
+        return out, off, tv
 
     def pt_get_cells(self):
         n = ctypes.c_int64(0)

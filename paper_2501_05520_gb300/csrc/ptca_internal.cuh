@@ -37,6 +37,8 @@ enum : int {
   CNT_CELLS_USED = 10,  // cells written (CNT_CELLS counts reserved slots incl. holes)
   CNT_LINKS_USED = 11,  // links written (CNT_LINKS counts reserved slots incl. holes)
   CNT_DBL_WORK = 12,    // doublet search: next chunk of 32 sorted hits
+  CNT_SCAN_EV = 13,     // events (size of the scan over per-event vertex counts)
+  CNT_VTX = 14,         // vertices of the batch
   CNT_N = 16
 };
 // status bits
@@ -46,6 +48,7 @@ enum : unsigned long long {
   ST_NT = 4ull,
   ST_LAYER = 8ull,
   ST_GATE_TIMEOUT = 16ull,  // a bounded wait in the gate kernel expired
+  ST_VTX = 32ull,           // an event has more tracks for vertexing than a block sorts
 };
 
 // Gate parameters on the device: W1 and W2 as bf16 in the tensor-core operand layout,
@@ -141,6 +144,13 @@ struct Buffers {
   uint32_t* sv;              // [max_ntuplets] survivor -> sorted position
   int64_t* ev_nt_off;        // [max_events + 1]
   pt_track* tracks;          // [max_ntuplets]
+  // primary vertices (pt_find_vertices)
+  pt_vertex* vtx_stage;      // [max_ntuplets / 2 + 1] event e's vertices from floor(t0 / 2)
+  pt_vertex* vtx;            // [max_ntuplets / 2 + 1] the batch's vertices, events in order
+  int32_t* trk_vtx;          // [max_ntuplets] vertex of each track, -1 for none
+  uint32_t* ev_nv;           // [max_events + 1] vertices per event
+  uint32_t* ev_v_scan;       // [max_events + 1] exclusive scan of ev_nv
+  int64_t* ev_vtx_off;       // [max_events + 1] the same as int64
   // learned gate (valid when enabled)
   uint16_t* gate_x;          // [max_links*16] bf16 features per link slot (12 used)
   float* gate_score;         // [max_links] logit per link slot
@@ -199,6 +209,10 @@ void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStre
 void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
                      bool gated = false);
 void launch_fit(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
+// primary vertices of the fitted tracks of n_events events (tracks with >= min_hits
+// hits, groups cut at z0 steps > dz)
+cudaError_t launch_vertices(const Buffers& b, int n_events, int32_t min_hits, float dz,
+                            uint64_t cap_nt, const Launch& l, cudaStream_t s);
 // scan of n+1 entries: out[i] = sum(in[0..i)), n = *n_dev
 void launch_scan(const uint32_t* in, uint32_t* out, const unsigned long long* n_dev,
                  uint32_t* part, cudaStream_t s);

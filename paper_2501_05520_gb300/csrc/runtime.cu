@@ -160,6 +160,12 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.sv = (uint32_t*)take(T * 4);
   t.ev_nt_off = (int64_t*)take((E + 1) * 8);
   t.tracks = (pt_track*)take(T * sizeof(pt_track));
+  t.vtx_stage = (pt_vertex*)take((T / 2 + 1) * sizeof(pt_vertex));
+  t.vtx = (pt_vertex*)take((T / 2 + 1) * sizeof(pt_vertex));
+  t.trk_vtx = (int32_t*)take(T * 4);
+  t.ev_nv = (uint32_t*)take((E + 1) * 4);
+  t.ev_v_scan = (uint32_t*)take((E + 1) * 4);
+  t.ev_vtx_off = (int64_t*)take((E + 1) * 8);
   t.gate_x = (uint16_t*)take(L * 16 * 2);
   t.gate_score = (float*)take(L * 4);
   t.gate_keep = (uint8_t*)take(L);
@@ -209,6 +215,8 @@ struct pt_ctx {
   int n_events = 0;
   int64_t n_hits = 0;
   bool loaded = false;
+  bool fitted = false;     // the tracks of the loaded batch are fitted
+  bool vtx_ready = false;  // pt_find_vertices ran on the loaded batch
   std::vector<int64_t> hit_off;
   // pinned staging
   int32_t* h_off = nullptr;
@@ -257,6 +265,8 @@ pt_status sync_counters(pt_ctx* c) {
 pt_status check_status(pt_ctx* c) {
   const unsigned long long st = c->h_cnt[CNT_STATUS];
   if (st & ST_LAYER) return fail(PT_ERR_INVALID, "input contains a layer code > 9");
+  if (st & ST_VTX)
+    return fail(PT_ERR_CAPACITY, "an event has more than 16384 tracks for vertex finding");
   if (st & ST_GATE_TIMEOUT)
     return fail(PT_ERR_TIMEOUT, "a bounded wait of the gate's tensor-core kernel expired");
   if (st & ST_CELLS)
@@ -315,6 +325,8 @@ pt_status stage_inputs(pt_ctx* c, int n_events, const int64_t* off, const float*
   c->n_hits = n;
   c->hit_off.assign(off, off + n_events + 1);
   c->loaded = true;
+  c->fitted = false;
+  c->vtx_ready = false;
   return PT_OK;
 }
 
@@ -607,7 +619,7 @@ pt_status pt_find_ntuplets(pt_ctx* c, int64_t* n_ntuplets) {
 }
 
 pt_status pt_fit_tracks(pt_ctx* c, int64_t* n_tracks) {
-  STAGE_BODY(launch_fit(c->B, c->P, c->L, c->stream), CNT_SV, n_tracks)
+  STAGE_BODY((launch_fit(c->B, c->P, c->L, c->stream), c->fitted = true), CNT_SV, n_tracks)
 }
 
 pt_status pt_get_ntuplets(pt_ctx* c, int32_t* hits, uint8_t* nhits, int64_t* event_offsets,
@@ -641,6 +653,43 @@ pt_status pt_get_tracks(pt_ctx* c, pt_track* tracks, int64_t cap, int64_t* n, in
     return fail(PT_ERR_CAPACITY, "output capacity %lld is too small: %lld tracks",
                 (long long)cap, (long long)S);
   PT_TRY(copy_out(c, tracks, c->B.tracks, (size_t)S * sizeof(pt_track), on_device));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  return PT_OK;
+}
+
+pt_status pt_find_vertices(pt_ctx* c, int min_hits, float dz, int64_t* n_vertices) {
+  g_err.clear();
+  PT_TRY(need_loaded(c));
+  if (min_hits < 3 || min_hits > kMaxHits) return fail(PT_ERR_INVALID, "min_hits must be in [3, 6]");
+  if (!(dz > 0.0f) || !std::isfinite(dz)) return fail(PT_ERR_INVALID, "dz must be finite and > 0");
+  DeviceGuard guard(c->device);
+  if (!c->fitted) return fail(PT_ERR_INVALID, "pt_fit_tracks has not run on this batch");
+  PT_CUDA(launch_vertices(c->B, c->n_events, min_hits, dz, (uint64_t)c->cap.max_ntuplets, c->L,
+                          c->stream));
+  c->vtx_ready = true;
+  if (n_vertices) {
+    PT_TRY(sync_counters(c));
+    *n_vertices = (int64_t)c->h_cnt[CNT_VTX];
+  }
+  return PT_OK;
+}
+
+pt_status pt_get_vertices(pt_ctx* c, pt_vertex* vertices, int64_t* event_offsets,
+                          int32_t* track_vertex, int64_t cap, int64_t* n, int on_device) {
+  g_err.clear();
+  PT_TRY(need_loaded(c));
+  if (!c->vtx_ready) return fail(PT_ERR_INVALID, "pt_find_vertices has not run on this batch");
+  DeviceGuard guard(c->device);
+  PT_TRY(sync_counters(c));
+  const int64_t V = (int64_t)c->h_cnt[CNT_VTX];
+  const int64_t S = (int64_t)c->h_cnt[CNT_SV];
+  if (n) *n = V;
+  if (cap < V)
+    return fail(PT_ERR_CAPACITY, "output capacity %lld is too small: %lld vertices",
+                (long long)cap, (long long)V);
+  PT_TRY(copy_out(c, vertices, c->B.vtx, (size_t)V * sizeof(pt_vertex), on_device));
+  PT_TRY(copy_out(c, event_offsets, c->B.ev_vtx_off, (size_t)(c->n_events + 1) * 8, on_device));
+  PT_TRY(copy_out(c, track_vertex, c->B.trk_vtx, (size_t)S * 4, on_device));
   PT_CUDA(cudaStreamSynchronize(c->stream));
   return PT_OK;
 }
@@ -942,6 +991,7 @@ pt_status pt_enqueue_batch(pt_ctx* c, int n_events, const int64_t* hit_offsets, 
   PT_TRY(stage_inputs(c, n_events, hit_offsets, x, y, z, layer, on_device));
   PT_TRY(ensure_graph(c));
   PT_CUDA(cudaGraphLaunch(c->graph, c->stream));
+  c->fitted = true;
   return PT_OK;
 }
 
@@ -957,6 +1007,7 @@ pt_status pt_reconstruct_batch(pt_ctx* c, int n_events, const int64_t* hit_offse
   PT_TRY(stage_inputs(c, n_events, hit_offsets, x, y, z, layer, on_device));
   PT_TRY(ensure_graph(c));
   PT_CUDA(cudaGraphLaunch(c->graph, c->stream));
+  c->fitted = true;
   PT_TRY(sync_counters(c));
   const int64_t S = (int64_t)c->h_cnt[CNT_SV];
   if (n) *n = S;

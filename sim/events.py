@@ -189,11 +189,24 @@ def _noise(rng, n_noise: int, barrel_only: bool):
     return lay, x, y, z
 
 
-def generate(cfg: GenConfig, seed: int, n_particles: int | None = None) -> Event:
-    """Generate one event from a seed.  Hits are returned in a random order."""
+def generate(cfg: GenConfig, seed: int, n_particles: int | None = None,
+             n_vertices: int = 0) -> Event:
+    """Generate one event from a seed.  Hits are returned in a random order.
+
+    n_vertices > 0 groups the particles into that many interactions of equal size
+    (particle i belongs to vertex i * n_vertices // n): each vertex draws its z from
+    N(0, cfg.z0_sigma) and its particles share it; particles["vertex"] and
+    particles["vz"] record the assignment.  With n_vertices = 0 (the default) every
+    particle draws its own z0 and the event is unchanged."""
     rng = np.random.default_rng(seed)
     n = cfg.n_particles if n_particles is None else n_particles
     p = _draw_particles(rng, cfg, n)
+    if n_vertices > 0:
+        vz = rng.normal(0.0, cfg.z0_sigma, n_vertices)
+        vid = (np.arange(n) * n_vertices) // max(n, 1)
+        p["z0"] = vz[vid]
+        p["vertex"] = vid.astype(np.int32)
+        p["vz"] = vz
     pid, lay, xt, yt, zt = _crossings(p, cfg.barrel_only)
     if cfg.smear:
         xs, ys, zs = _smear(rng, lay, xt, yt, zt)
@@ -240,6 +253,13 @@ def pileup_event(seed: int, pu: int, noise_frac: float = 0.02) -> Event:
     """PU200-spectrum event with `pu` * 50 particles (batch and serving workloads)."""
     cfg = dataclasses.replace(PU200, noise_frac=noise_frac)
     return generate(cfg, seed, n_particles=pu * PARTICLES_PER_PU)
+
+
+def vertex_event(seed: int, pu: int, noise_frac: float = 0.02, smear: bool = True) -> Event:
+    """PU200-spectrum event with `pu` interactions of 50 particles each, every
+    interaction at its own z ~ N(0, 5 cm) (vertex reconstruction workload)."""
+    cfg = dataclasses.replace(PU200, noise_frac=noise_frac, smear=smear)
+    return generate(cfg, seed, n_particles=pu * PARTICLES_PER_PU, n_vertices=pu)
 
 
 def batch_pileups(seed: int, n_events: int = 64, mean: float = 140.0,
