@@ -353,6 +353,31 @@ def _vertexing(ctx, dbat, stream, steps: int) -> dict:
             "workload": "the bench batch's fitted tracks (its particles have independent z0)"}
 
 
+def _raw_input(ctx, dev, stream, steps: int, B: int) -> dict:
+    """Raw pixel data -> hits (pt_load_raw: unpack, cluster, place, bin) on B copies of
+    one PU200 event's digis in device memory, timed with CUDA events on the library's
+    stream (the call's host checks and the copy of the digis into the library's
+    scratch included)."""
+    import torch
+    from sim import pixels
+    words = pixels.digitize(make_events(1, SEED0 + 900)[0])[0]
+    off, allw = pixels.concat_raw([words] * B)
+    dw = torch.from_numpy(allw.view(np.int64)).to(dev)
+    ctx.pt_set_modules()
+    nh = ctx.pt_load_raw(off, dw)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        ctx.pt_load_raw(off, dw, sync=False)
+        e1.record(stream)
+    stream.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return {"ms_per_step": statistics.mean(ms), "events_per_step": B,
+            "digis_per_event": int(words.size), "hits_per_event": nh / B,
+            "workload": "one PU200 event's digis, repeated"}
+
+
 def _physics(ctx, host, events):
     """Efficiency, fake and duplicate rates of the cleaned ntuplets (generator truth)."""
     from sim import truth
@@ -517,6 +542,7 @@ def run_ours(args):
     ctx.pt_set_gate(None, 0.0)
     with torch.cuda.stream(stream):
         vertexing = _vertexing(ctx, dbat, stream, min(args.steps, 20))
+        raw_input = _raw_input(ctx, dev, stream, min(args.steps, 20), B)
     config4 = {"plain": _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)}
     ctx.pt_set_gate(gw, gtau)
     config4["gated"] = _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)
@@ -562,6 +588,7 @@ def run_ours(args):
                 "counts_per_step": counts,
                 "batch_workload": config4,
                 "vertexing": vertexing,
+                "raw_input": raw_input,
                 "autotune": launch,
                 "clocks": clocks,
                 "gpu_launches": launches["plain"] * args.steps}

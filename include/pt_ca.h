@@ -100,6 +100,21 @@ typedef struct {
   uint8_t pad[2];
 } pt_track;
 
+/* One detector module of the pixel readout (pt_set_modules).  A pixel (row, col) of
+ * the module covers azimuths phi0 + [col, col + 1) dphi_col and, along v (z on a barrel
+ * module, r on a disk module), v0 + [row, row + 1) dv_row. */
+typedef struct {
+  int32_t layer;     /* layer code 0..9 */
+  int32_t kind;      /* 0: barrel (at radius rz, rows along z); 1: disk (at z = rz, rows along r) */
+  float rz;          /* barrel radius or disk z (cm) */
+  float phi0;        /* azimuth of column 0's lower edge (rad) */
+  float dphi_col;    /* azimuth per column (rad) */
+  float v0;          /* z (barrel) or r (disk) of row 0's lower edge (cm) */
+  float dv_row;      /* cm per row */
+  int32_t ncol;      /* columns, 1..4096 */
+  int32_t nrow;      /* rows, 1..4096 */
+} pt_module;
+
 /* One primary vertex (pt_find_vertices): z (cm), the sum of its tracks' pT^2 (GeV^2),
  * its number of tracks and its event in the batch. */
 typedef struct {
@@ -144,6 +159,41 @@ pt_status pt_load_hits(pt_ctx* ctx, int64_t n, const float* x, const float* y, c
  * device; reported by the next call that synchronises), PT_ERR_CAPACITY. */
 pt_status pt_load_batch(pt_ctx* ctx, int n_events, const int64_t* hit_offsets, const float* x,
                         const float* y, const float* z, const uint8_t* layer, int on_device);
+
+/* Detector module table of the pixel readout, used by pt_load_raw (Sec. 2.2.1, Fig. 2:
+ * detector information such as the location of each layer and the detector indices is
+ * preloaded on the GPU).  modules[i] describes module index i; n in [1, 2^24).  The table
+ * is copied into a device buffer that the context allocates and keeps.  PT_ERR_INVALID
+ * for a layer code > 9, a kind other than 0/1, ncol or nrow outside [1, 4096] or a
+ * non-finite float. */
+pt_status pt_set_modules(pt_ctx* ctx, const pt_module* modules, int n);
+
+/* Load a batch of raw pixel events (Sec. 2.2.1, Fig. 2: the compressed raw data are
+ * unpacked on the GPU into digis, and neighbouring digis of one layer are clustered into
+ * hits; the paper fixes no format).  digis: one 64-bit word per read-out pixel,
+ * module << 40 | row << 28 | col << 16 | adc (adc <= 4095), event e owning
+ * [digi_offsets[e], digi_offsets[e+1]) (host array [n_events + 1]); within an event the
+ * digis come grouped by module and, within a module, in (row, col) order, each pixel
+ * once.  Digis of one module whose pixels touch at an edge or a corner form a cluster;
+ * each cluster gives one hit at its adc-weighted mean pixel centre on the module's
+ * surface, with the module's layer.  Hits come module run by module run in input order,
+ * and within a module in order of their cluster's first pixel.  The hits replace the
+ * context's inputs as pt_load_batch's would and are binned for the chain.  The first
+ * call allocates the raw-input scratch (8 x max_hits digis).  n_hits: NULL to stay
+ * asynchronous, else the call synchronises and stores the number of hits.  Errors:
+ * PT_ERR_INVALID (no module table, bad offsets, a module index, pixel or adc outside
+ * the table or the range, pixels out of order or repeated); PT_ERR_CAPACITY (more than
+ * 8 x max_hits digis, more hits than max_hits, more than 1024 digis on one module of an
+ * event, a cluster of more than 128 pixels). */
+pt_status pt_load_raw(pt_ctx* ctx, int n_events, const int64_t* digi_offsets,
+                      const uint64_t* digis, int on_device, int64_t* n_hits);
+
+/* The hits of the loaded batch as the chain sees them (pt_load_batch's inputs, or the
+ * hits pt_load_raw made): x, y, z [cap] float32, layer [cap] uint8 (any may be NULL),
+ * event_offsets [n_events + 1] int64 (may be NULL).  *n = number of hits;
+ * PT_ERR_CAPACITY if cap < *n (nothing written).  Host buffers; synchronises. */
+pt_status pt_get_hits(pt_ctx* ctx, float* x, float* y, float* z, uint8_t* layer,
+                      int64_t* event_offsets, int64_t cap, int64_t* n);
 
 /* Doublets of the loaded batch (Sec. 2.2.1, Fig. 2: hits in adjacent layers are
  * paired).  n_cells: NULL to stay asynchronous; else the call synchronises the stream

@@ -28,6 +28,7 @@ PT_OK, PT_ERR_INVALID, PT_ERR_CAPACITY, PT_ERR_CUDA, PT_ERR_TIMEOUT, PT_ERR_NOT_
 EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt_load_hits",
             "pt_load_batch", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
             "pt_fit_tracks", "pt_get_ntuplets", "pt_get_tracks", "pt_find_vertices",
+            "pt_set_modules", "pt_load_raw", "pt_get_hits",
             "pt_get_vertices", "pt_get_cells", "pt_get_links",
             "pt_get_candidates", "pt_reconstruct_batch", "pt_enqueue_batch",
             "pt_find_doublets_noalloc", "pt_set_gate", "pt_get_link_features", "pt_gate_score",
@@ -99,6 +100,9 @@ def lib() -> ctypes.CDLL:
             "pt_get_ntuplets": [P, P, P, P, I64, PI64, I32],
             "pt_get_tracks": [P, P, I64, PI64, I32],
             "pt_find_vertices": [P, I32, ctypes.c_float, PI64],
+            "pt_set_modules": [P, P, I32],
+            "pt_load_raw": [P, I32, P, P, I32, PI64],
+            "pt_get_hits": [P, P, P, P, P, P, I64, PI64],
             "pt_get_vertices": [P, P, P, P, I64, PI64, I32],
             "pt_get_cells": [P, P, P, P, I64, PI64],
             "pt_get_links": [P, P, P, P, P, P, I64, PI64],
@@ -188,7 +192,8 @@ def _as_input(a, dtype):
     if hasattr(a, "data_ptr"):  # torch tensor
         import torch
         t = a.contiguous()
-        want = {np.float32: torch.float32, np.uint8: torch.uint8}[dtype]
+        # 64-bit raw words travel in an int64 tensor (same bits)
+        want = {np.float32: torch.float32, np.uint8: torch.uint8, np.uint64: torch.int64}[dtype]
         if t.dtype != want:
             t = t.to(want)
         return ctypes.c_void_p(t.data_ptr()), int(t.is_cuda), t
@@ -311,6 +316,43 @@ class Context:
         out = np.zeros(int(n.value), TRACK_DTYPE)
         _check(lib().pt_get_tracks(self.handle, _hptr(out), out.size, ctypes.byref(n), 0))
         return out
+
+    def pt_set_modules(self, table=None):
+        """Preload the pixel-readout module table (default: the library's detector)."""
+        from . import pixels
+        t = np.ascontiguousarray(pixels.module_table() if table is None else table,
+                                 pixels.MODULE_DTYPE)
+        _check(lib().pt_set_modules(self.handle, _hptr(t), int(t.size)))
+
+    def pt_load_raw(self, digi_offsets, digis, sync: bool = True):
+        """Load raw digis (uint64, host array or device tensor) of a batch; returns the
+        number of hits made from them when sync."""
+        off = np.ascontiguousarray(digi_offsets, np.int64)
+        count = digis.numel() if hasattr(digis, "numel") else np.asarray(digis).size
+        if off.size < 2 or off[-1] > count:
+            raise ValueError("digi_offsets need n_events + 1 entries and at most len(digis) digis")
+        ptr, on_dev, keep = _as_input(digis, np.uint64)
+        n = ctypes.c_int64(0)
+        _check(lib().pt_load_raw(self.handle, int(off.size - 1), _hptr(off), ptr, on_dev,
+                                 ctypes.byref(n) if sync else None))
+        self.n_events = int(off.size - 1)
+        del keep
+        return int(n.value) if sync else None
+
+    def pt_get_hits(self):
+        """(x, y, z float32 [N], layer uint8 [N], event_offsets int64 [E+1]) of the
+        loaded batch."""
+        n = ctypes.c_int64(0)
+        st = lib().pt_get_hits(self.handle, None, None, None, None, None, 0, ctypes.byref(n))
+        if st not in (PT_OK, PT_ERR_CAPACITY):
+            _check(st)
+        N = int(n.value)
+        x, y, z = (np.empty(N, np.float32) for _ in range(3))
+        layer = np.empty(N, np.uint8)
+        off = np.empty(self.n_events + 1, np.int64)
+        _check(lib().pt_get_hits(self.handle, _hptr(x), _hptr(y), _hptr(z), _hptr(layer),
+                                 _hptr(off), N, ctypes.byref(n)))
+        return x, y, z, layer, off
 
     def pt_find_vertices(self, min_hits: int = 4, dz: float = 0.02, sync: bool = True):
         """Primary vertices of the fitted tracks; returns their number when sync."""

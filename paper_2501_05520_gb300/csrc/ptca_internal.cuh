@@ -39,7 +39,18 @@ enum : int {
   CNT_DBL_WORK = 12,    // doublet search: next chunk of 32 sorted hits
   CNT_SCAN_EV = 13,     // events (size of the scan over per-event vertex counts)
   CNT_VTX = 14,         // vertices of the batch
-  CNT_N = 16
+  CNT_RAW_STATUS = 15,  // raw input: status bits (RAW_*), not reset by the chain
+  CNT_RAW_DIGIS = 16,   // raw input: digis of the batch (size of the run-flag scan)
+  CNT_RAW_RUNS = 17,    // raw input: module runs (size of the hit-count scan)
+  CNT_RAW_HITS = 18,    // raw input: hits made from the digis
+  CNT_N = 24
+};
+// raw-input status bits (cnt[CNT_RAW_STATUS])
+enum : unsigned long long {
+  RAW_INVALID = 1ull,           // bad module, pixel, adc or pixel order
+  RAW_RUN_CAPACITY = 2ull,      // more than 1024 digis of one module in one event
+  RAW_CLUSTER_CAPACITY = 4ull,  // a cluster of more than 128 pixels
+  RAW_HIT_CAPACITY = 8ull,      // more hits than max_hits
 };
 // status bits
 enum : unsigned long long {
@@ -166,6 +177,22 @@ struct Buffers {
 
 constexpr int kScanBlocks = 256;
 
+// Raw-input scratch (allocated on the first pt_load_raw): the digis and the per-digi /
+// per-run arrays of the clustering; max_digis entries (+1 for the scans).
+struct RawBuffers {
+  int n_events = 0;
+  int64_t* digi_off = nullptr;   // [max_events + 1] event e owns digis [off[e], off[e+1])
+  uint64_t* words = nullptr;     // [max_digis] packed digis
+  uint32_t* flag = nullptr;      // [max_digis + 1] 1 where a module run starts
+  uint32_t* run_scan = nullptr;  // [max_digis + 1] runs starting before each digi
+  uint32_t* run_first = nullptr; // [max_digis + 1] first digi of each run (+ end)
+  uint32_t* run_nh = nullptr;    // [max_digis + 1] hits of each run
+  uint32_t* run_hoff = nullptr;  // [max_digis + 1] first hit of each run (+ total)
+  float4* stage = nullptr;       // [max_digis] hits (x, y, z, layer bits) at digi positions
+  uint32_t* scan_part = nullptr; // the context's scan partials
+  unsigned long long* cnt = nullptr;  // the context's counters
+};
+
 // Optional per-kernel timing of the stage calls (pt_set_tracing): CUDA events on the
 // launching stream around every kernel; never active while the whole-batch graph is
 // captured.  Defined in runtime.cu.
@@ -209,6 +236,9 @@ void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStre
 void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
                      bool gated = false);
 void launch_fit(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
+// raw digis -> hits in the chain's input arrays, per-event offsets and header
+cudaError_t launch_raw(const RawBuffers& r, const Buffers& b, const pt_module* mods, int n_mod,
+                       int64_t cap_hits, const Launch& l, cudaStream_t s);
 // primary vertices of the fitted tracks of n_events events (tracks with >= min_hits
 // hits, groups cut at z0 steps > dz)
 cudaError_t launch_vertices(const Buffers& b, int n_events, int32_t min_hits, float dz,

@@ -230,6 +230,11 @@ struct pt_ctx {
   // learned gate
   GateWeights* gate = nullptr;  // device, inside the workspace
   bool gate_on = false;
+  // raw input: module table and scratch (allocated on first use)
+  pt_module* modules = nullptr;
+  int n_modules = 0;
+  char* raw_mem = nullptr;
+  RawBuffers R{};
 };
 
 namespace {
@@ -265,6 +270,17 @@ pt_status sync_counters(pt_ctx* c) {
 pt_status check_status(pt_ctx* c) {
   const unsigned long long st = c->h_cnt[CNT_STATUS];
   if (st & ST_LAYER) return fail(PT_ERR_INVALID, "input contains a layer code > 9");
+  const unsigned long long raw = c->h_cnt[CNT_RAW_STATUS];
+  if (raw & RAW_INVALID)
+    return fail(PT_ERR_INVALID, "raw input: a module index, pixel or adc outside the module "
+                                "table or range, or pixels of a module out of order or repeated");
+  if (raw & RAW_RUN_CAPACITY)
+    return fail(PT_ERR_CAPACITY, "raw input: more than 1024 digis on one module of an event");
+  if (raw & RAW_CLUSTER_CAPACITY)
+    return fail(PT_ERR_CAPACITY, "raw input: a cluster of more than 128 pixels");
+  if (raw & RAW_HIT_CAPACITY)
+    return fail(PT_ERR_CAPACITY, "raw input: %llu hits, more than max_hits = %lld",
+                c->h_cnt[CNT_RAW_HITS], (long long)c->cap.max_hits);
   if (st & ST_VTX)
     return fail(PT_ERR_CAPACITY, "an event has more than 16384 tracks for vertex finding");
   if (st & ST_GATE_TIMEOUT)
@@ -306,6 +322,7 @@ pt_status stage_inputs(pt_ctx* c, int n_events, const int64_t* off, const float*
         return fail(PT_ERR_INVALID, "layer code %d > 9 at hit %lld", (int)layer[i], (long long)i);
   // the pinned staging of the previous call must have been consumed
   PT_CUDA(cudaEventSynchronize(c->staged));
+  PT_CUDA(cudaMemsetAsync(&c->B.cnt[CNT_RAW_STATUS], 0, 8, c->stream));
   for (int e = 0; e <= n_events; ++e) c->h_off[e] = (int32_t)off[e];
   c->h_hdr->n_events = n_events;
   c->h_hdr->n_hits = (int32_t)n;
@@ -510,6 +527,8 @@ pt_status pt_destroy(pt_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->val) cudaFree(c->val);
+  if (c->modules) cudaFree(c->modules);
+  if (c->raw_mem) cudaFree(c->raw_mem);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->h_off) cudaFreeHost(c->h_off);
   if (c->h_hdr) cudaFreeHost(c->h_hdr);
@@ -654,6 +673,125 @@ pt_status pt_get_tracks(pt_ctx* c, pt_track* tracks, int64_t cap, int64_t* n, in
                 (long long)cap, (long long)S);
   PT_TRY(copy_out(c, tracks, c->B.tracks, (size_t)S * sizeof(pt_track), on_device));
   PT_CUDA(cudaStreamSynchronize(c->stream));
+  return PT_OK;
+}
+
+pt_status pt_set_modules(pt_ctx* c, const pt_module* m, int n) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  if (!m || n < 1 || n >= (1 << 24)) return fail(PT_ERR_INVALID, "need 1 <= n < 2^24 modules");
+  for (int i = 0; i < n; ++i) {
+    const pt_module& d = m[i];
+    if (d.layer < 0 || d.layer >= kLayers || (d.kind != 0 && d.kind != 1) || d.ncol < 1 ||
+        d.ncol > 4096 || d.nrow < 1 || d.nrow > 4096 || !std::isfinite(d.rz) ||
+        !std::isfinite(d.phi0) || !std::isfinite(d.dphi_col) || !std::isfinite(d.v0) ||
+        !std::isfinite(d.dv_row))
+      return fail(PT_ERR_INVALID, "module %d is not valid", i);
+  }
+  DeviceGuard guard(c->device);
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->modules) cudaFree(c->modules);
+  c->modules = nullptr;
+  c->n_modules = 0;
+  PT_CUDA(cudaMalloc(&c->modules, (size_t)n * sizeof(pt_module)));
+  PT_CUDA(cudaMemcpy(c->modules, m, (size_t)n * sizeof(pt_module), cudaMemcpyHostToDevice));
+  c->n_modules = n;
+  return PT_OK;
+}
+
+pt_status pt_load_raw(pt_ctx* c, int n_events, const int64_t* off, const uint64_t* digis,
+                      int on_device, int64_t* n_hits) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  if (!c->modules) return fail(PT_ERR_INVALID, "no module table (pt_set_modules)");
+  if (n_events < 1 || n_events > c->cap.max_events)
+    return fail(PT_ERR_INVALID, "n_events must be in [1, max_events]");
+  if (!off) return fail(PT_ERR_INVALID, "digi_offsets is NULL");
+  if (off[0] != 0) return fail(PT_ERR_INVALID, "digi_offsets[0] must be 0");
+  for (int e = 0; e < n_events; ++e)
+    if (off[e + 1] < off[e]) return fail(PT_ERR_INVALID, "digi_offsets must be non-decreasing");
+  const int64_t n = off[n_events];
+  const int64_t max_digis = 8 * c->cap.max_hits;
+  if (n > max_digis)
+    return fail(PT_ERR_CAPACITY, "%lld digis, more than 8 x max_hits = %lld", (long long)n,
+                (long long)max_digis);
+  if (n > 0 && !digis) return fail(PT_ERR_INVALID, "digis is NULL");
+  DeviceGuard guard(c->device);
+  if (!c->raw_mem) {  // scratch for max_digis digis, carved like the workspace
+    const size_t D = (size_t)max_digis, E = (size_t)c->cap.max_events;
+    const size_t parts[] = {(E + 1) * 8, D * 8, (D + 1) * 4, (D + 1) * 4, (D + 1) * 4,
+                            (D + 1) * 4, (D + 1) * 4, D * 16};
+    size_t bytes = 0;
+    for (size_t p : parts) bytes += (p + kAlign - 1) / kAlign * kAlign;
+    PT_CUDA(cudaMalloc(&c->raw_mem, bytes));
+    char* q = c->raw_mem;
+    auto take = [&](size_t b) {
+      char* r = q;
+      q += (b + kAlign - 1) / kAlign * kAlign;
+      return r;
+    };
+    c->R.digi_off = (int64_t*)take(parts[0]);
+    c->R.words = (uint64_t*)take(parts[1]);
+    c->R.flag = (uint32_t*)take(parts[2]);
+    c->R.run_scan = (uint32_t*)take(parts[3]);
+    c->R.run_first = (uint32_t*)take(parts[4]);
+    c->R.run_nh = (uint32_t*)take(parts[5]);
+    c->R.run_hoff = (uint32_t*)take(parts[6]);
+    c->R.stage = (float4*)take(parts[7]);
+  }
+  c->R.n_events = n_events;
+  c->R.scan_part = c->B.scan_part;
+  c->R.cnt = c->B.cnt;
+  PT_CUDA(cudaStreamSynchronize(c->stream));  // the previous batch no longer needs its inputs
+  PT_CUDA(cudaMemcpyAsync(c->R.digi_off, off, (size_t)(n_events + 1) * 8, cudaMemcpyHostToDevice,
+                          c->stream));
+  if (n > 0)
+    PT_CUDA(cudaMemcpyAsync(c->R.words, digis, (size_t)n * 8,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            c->stream));
+  PT_CUDA(cudaMemsetAsync(&c->B.cnt[CNT_RAW_STATUS], 0, 8, c->stream));
+  PT_CUDA(launch_raw(c->R, c->B, c->modules, c->n_modules, c->cap.max_hits, c->L, c->stream));
+  launch_clear(c->B, c->P, c->L, c->stream);
+  launch_bin_hits(c->B, c->P, c->L, c->stream);
+  PT_TRY(last_launch());
+  PT_CUDA(cudaStreamSynchronize(c->stream));  // the host offsets and digis may be reused
+  c->n_events = n_events;
+  c->n_hits = -1;
+  c->hit_off.clear();
+  c->loaded = true;
+  c->fitted = false;
+  c->vtx_ready = false;
+  if (n_hits) {
+    PT_TRY(sync_counters(c));
+    *n_hits = (int64_t)c->h_cnt[CNT_RAW_HITS];
+  }
+  return PT_OK;
+}
+
+pt_status pt_get_hits(pt_ctx* c, float* x, float* y, float* z, uint8_t* layer,
+                      int64_t* event_offsets, int64_t cap, int64_t* n) {
+  g_err.clear();
+  PT_TRY(need_loaded(c));
+  DeviceGuard guard(c->device);
+  PT_TRY(sync_counters(c));
+  BatchHeader hdr{};
+  PT_CUDA(cudaMemcpyAsync(&hdr, c->B.hdr, sizeof(hdr), cudaMemcpyDeviceToHost, c->stream));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  const int64_t N = hdr.n_hits;
+  if (n) *n = N;
+  if (cap < N)
+    return fail(PT_ERR_CAPACITY, "output capacity %lld is too small: %lld hits", (long long)cap,
+                (long long)N);
+  PT_TRY(copy_out(c, x, c->B.in_x, (size_t)N * 4, 0));
+  PT_TRY(copy_out(c, y, c->B.in_y, (size_t)N * 4, 0));
+  PT_TRY(copy_out(c, z, c->B.in_z, (size_t)N * 4, 0));
+  PT_TRY(copy_out(c, layer, c->B.in_layer, (size_t)N, 0));
+  std::vector<int32_t> off32((size_t)c->n_events + 1);
+  PT_CUDA(cudaMemcpyAsync(off32.data(), c->B.hit_off, off32.size() * 4, cudaMemcpyDeviceToHost,
+                          c->stream));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  if (event_offsets)
+    for (size_t e = 0; e < off32.size(); ++e) event_offsets[e] = off32[e];
   return PT_OK;
 }
 
