@@ -43,6 +43,7 @@ enum : int {
   CNT_RAW_DIGIS = 16,   // raw input: digis of the batch (size of the run-flag scan)
   CNT_RAW_RUNS = 17,    // raw input: module runs (size of the hit-count scan)
   CNT_RAW_HITS = 18,    // raw input: hits made from the digis
+  CNT_RAW_BIG = 19,     // raw input: long module runs listed for the block-per-run launch
   CNT_N = 24
 };
 // raw-input status bits (cnt[CNT_RAW_STATUS])
@@ -189,6 +190,7 @@ struct RawBuffers {
   uint32_t* run_nh = nullptr;    // [max_digis + 1] hits of each run
   uint32_t* run_hoff = nullptr;  // [max_digis + 1] first hit of each run (+ total)
   float4* stage = nullptr;       // [max_digis] hits (x, y, z, layer bits) at digi positions
+  uint32_t* big_runs = nullptr;  // aliases flag (free once the runs are numbered): long runs
   uint32_t* scan_part = nullptr; // the context's scan partials
   unsigned long long* cnt = nullptr;  // the context's counters
 };

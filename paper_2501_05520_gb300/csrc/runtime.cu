@@ -738,6 +738,7 @@ pt_status pt_load_raw(pt_ctx* c, int n_events, const int64_t* off, const uint64_
     c->R.run_nh = (uint32_t*)take(parts[5]);
     c->R.run_hoff = (uint32_t*)take(parts[6]);
     c->R.stage = (float4*)take(parts[7]);
+    c->R.big_runs = c->R.flag;
   }
   c->R.n_events = n_events;
   c->R.scan_part = c->B.scan_part;
