@@ -111,3 +111,35 @@ def test_raw_input_errors(cuts):
             ctx.pt_load_raw([0, 3], good)  # offsets beyond the digis given
         # a valid batch after the errors works again
         assert ctx.pt_load_raw([0, 2, 2], good) == 1
+
+
+def _sparse_run(rng, module, n, nrow, ncol):
+    """n distinct pixels of one module in (row, col) order, sparse enough that clusters
+    stay small."""
+    flat = np.sort(rng.choice(nrow * ncol, size=n, replace=False))
+    adc = rng.integers(5, 4096, size=n)
+    return _words(module, [(int(f // ncol), int(f % ncol), int(a)) for f, a in zip(flat, adc)])
+
+
+@pytest.mark.parametrize("sizes", [(1, 255, 256, 257), (1024, 300, 2)])
+def test_raw_run_sizes(cuts, sizes):
+    """Runs on both sides of the warp-per-run / block-per-run split and at the largest
+    size a run may have, against the oracle."""
+    table = opix.modules(ppix.PARAMS)
+    rng = np.random.default_rng(sum(sizes))
+    mods = [3, 40, 500, 1000]
+    ev = np.concatenate([_sparse_run(rng, m, n, int(table[m, 8]), int(table[m, 7]))
+                         for m, n in zip(mods, sizes)])
+    raws = [ev, ev[: sizes[0]]]
+    off, words = simpix.concat_raw(raws)
+    with pt.Context(cuts=cuts, capacity=CAP) as ctx:
+        ctx.pt_set_modules()
+        ctx.pt_load_raw(off, words)
+        x, y, z, layer, hoff = ctx.pt_get_hits()
+    for e, w in enumerate(raws):
+        rx, ry, rz, rl, _ = opix.reconstruct(w, table)
+        sl = slice(hoff[e], hoff[e + 1])
+        assert hoff[e + 1] - hoff[e] == rx.size
+        np.testing.assert_array_equal(layer[sl], rl.astype(np.uint8))
+        for got, exp in ((x[sl], rx), (y[sl], ry), (z[sl], rz)):
+            assert np.max(np.abs(got.astype(np.float64) - exp), initial=0.0) <= TOL
