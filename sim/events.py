@@ -6,6 +6,13 @@ their helices with the detector surfaces and smears the crossings.
 
 Units: cm, GeV, tesla.  Magnetic field along +z.
 
+Multiple scattering (off unless a configuration gives material): every surface a
+particle crosses holds x0 radiation lengths at normal incidence (x0_barrel, x0_disk);
+at each crossing the direction is turned by two independent Gaussian angles of RMS
+theta0 = 13.6 MeV / p sqrt(t) (1 + 0.038 ln t), t = x0 / cos(incidence) (the Highland
+formula, beta = 1), in the two planes through the direction, and the helix continues
+from the crossing with the same momentum.
+
 Detector (layer codes are part of the library's input contract):
   0..3  barrel cylinders, r = 2.9 / 6.8 / 10.9 / 16.0 cm, |z| < 27 cm
   4..6  disks at z = +29.1 / +39.6 / +51.6 cm, 4.5 <= r <= 16 cm
@@ -85,6 +92,8 @@ class GenConfig:
     noise_frac: float
     z0_sigma: float = 5.0
     smear: bool = True
+    x0_barrel: float = 0.0  # radiation lengths per barrel layer (0: no scattering)
+    x0_disk: float = 0.0    # radiation lengths per disk
 
 
 # The five workloads.  Sizes and spectra follow the library's benchmark definitions.
@@ -148,6 +157,124 @@ def _crossings(p: dict, barrel_only: bool):
     return pid, lay, x, y, z
 
 
+def highland(p, t):
+    """RMS plane scattering angle (rad) of a momentum-p (GeV) particle with beta = 1
+    through t radiation lengths."""
+    return 0.0136 / p * np.sqrt(t) * (1.0 + 0.038 * np.log(t))
+
+
+def _crossings_ms(rng, p: dict, barrel_only: bool, x0_barrel: float, x0_disk: float):
+    """Crossings with multiple scattering, surface by surface along each helix.  Returns
+    (pid, layer, x, y, z, step) float64 arrays; step orders each particle's crossings.
+
+    State per particle: position, transverse direction psi (motion turns by -q s / R),
+    dz/ds = cot, radius R.  The next crossing is the smallest positive arc length to an
+    unused surface within its acceptance, while the total turning stays below pi (the
+    outgoing half turn, as without material)."""
+    n = p["pt"].shape[0]
+    pmag = p["pt"] * np.cosh(p["eta"])
+    px, py, pz = np.zeros(n), np.zeros(n), p["z0"].copy()
+    psi = p["phi0"].copy()
+    cot = np.sinh(p["eta"])
+    R = p["R"].copy()
+    q = p["q"]
+    turned = np.zeros(n)
+    alive = np.ones(n, bool)
+    surfaces = [("barrel", r, L) for L, r in enumerate(BARREL_R)]
+    if not barrel_only:
+        surfaces += [("disk", zd, 4 + k) for k, zd in enumerate(DISK_Z)]
+        surfaces += [("disk", -zd, 7 + k) for k, zd in enumerate(DISK_Z)]
+    used = np.zeros((n, len(surfaces)), bool)
+    out = []
+    for step in range(len(surfaces)):
+        # centre of the transverse circle and arc length to each surface
+        cx = px + q * R * np.sin(psi)
+        cy = py - q * R * np.cos(psi)
+        a0 = np.arctan2(py - cy, px - cx)
+        cand = np.full((n, len(surfaces)), np.inf)
+        for j, (kind, v, L) in enumerate(surfaces):
+            if kind == "barrel":
+                cc = np.hypot(cx, cy)
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    K = (v * v - cc * cc - R * R) / (2.0 * R * cc)
+                ok = np.abs(K) <= 1.0
+                gam = np.arctan2(cy, cx)
+                acs = np.arccos(np.clip(K, -1.0, 1.0))
+                best = np.full(n, np.inf)
+                for sgn in (1.0, -1.0):
+                    a = gam + sgn * acs
+                    turn = np.remainder(q * (a0 - a), 2.0 * np.pi)
+                    turn = np.where(turn < 1e-12, turn + 2.0 * np.pi, turn)
+                    best = np.minimum(best, np.where(ok, turn, np.inf))
+                s = R * best
+                zc = pz + cot * s
+                inside = np.abs(zc) < BARREL_ZMAX
+            else:
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    s = (v - pz) / cot
+                ok = np.isfinite(s) & (s > 1e-9)
+                aa = a0 - q * np.where(ok, s, 0.0) / R
+                s = np.where(ok, s, np.inf)
+                xc = cx + R * np.cos(aa)
+                yc = cy + R * np.sin(aa)
+                rc = np.hypot(xc, yc)
+                inside = (rc >= DISK_RMIN) & (rc <= DISK_RMAX)
+            good = np.isfinite(s) & inside & ~used[:, j] & (turned + s / R < np.pi)
+            cand[:, j] = np.where(good, s, np.inf)
+        j = np.argmin(cand, axis=1)
+        s = cand[np.arange(n), j]
+        hit = alive & np.isfinite(s)
+        alive = hit
+        g1 = rng.normal(0.0, 1.0, n)
+        g2 = rng.normal(0.0, 1.0, n)
+        if not hit.any():
+            break
+        s = np.where(hit, s, 0.0)
+        aa = a0 - q * s / R
+        nx = cx + R * np.cos(aa)
+        ny = cy + R * np.sin(aa)
+        nz = pz + cot * s
+        npsi = psi - q * s / R
+        lay = np.asarray([surfaces[k][2] for k in j])
+        idx = np.flatnonzero(hit)
+        out.append((idx, lay[idx], nx[idx], ny[idx], nz[idx], np.full(idx.size, step)))
+        used[idx, j[idx]] = True
+        # scattering at the crossing
+        sth = 1.0 / np.sqrt(1.0 + cot * cot)
+        cth = cot * sth
+        d = np.stack([sth * np.cos(npsi), sth * np.sin(npsi), cth])
+        barrel = lay < 4
+        rr = np.hypot(nx, ny)
+        cos_inc = np.where(barrel, np.abs(d[0] * nx + d[1] * ny) / np.where(rr > 0, rr, 1.0),
+                           np.abs(cth))
+        x0 = np.where(barrel, x0_barrel, x0_disk)
+        t = x0 / np.maximum(cos_inc, 1e-6)
+        th0 = np.where(x0 > 0, highland(pmag, np.where(x0 > 0, t, 1.0)), 0.0)
+        e1 = np.stack([-np.sin(npsi), np.cos(npsi), np.zeros(n)])
+        e2 = np.stack([cth * np.cos(npsi), cth * np.sin(npsi), -sth])
+        dn = d + (g1 * th0) * e1 + (g2 * th0) * e2
+        dn /= np.linalg.norm(dn, axis=0)
+        st = np.hypot(dn[0], dn[1])
+        upd = hit
+        px = np.where(upd, nx, px)
+        py = np.where(upd, ny, py)
+        pz = np.where(upd, nz, pz)
+        psi = np.where(upd, np.arctan2(dn[1], dn[0]), psi)
+        cot = np.where(upd, dn[2] / st, cot)
+        turned = np.where(upd, turned + s / R, turned)
+        R = np.where(upd, pmag * st / (C_LIGHT * BFIELD_T) * 100.0, R)
+    if not out:
+        e = np.zeros(0)
+        return e.astype(np.int32), e.astype(np.uint8), e, e, e, e.astype(np.int64)
+    pid = np.concatenate([o[0] for o in out]).astype(np.int32)
+    lay = np.concatenate([o[1] for o in out]).astype(np.uint8)
+    x = np.concatenate([o[2] for o in out])
+    y = np.concatenate([o[3] for o in out])
+    z = np.concatenate([o[4] for o in out])
+    st = np.concatenate([o[5] for o in out]).astype(np.int64)
+    return pid, lay, x, y, z, st
+
+
 def _smear(rng, lay, x, y, z):
     r = np.hypot(x, y)
     phi = np.arctan2(y, x)
@@ -207,7 +334,11 @@ def generate(cfg: GenConfig, seed: int, n_particles: int | None = None,
         p["z0"] = vz[vid]
         p["vertex"] = vid.astype(np.int32)
         p["vz"] = vz
-    pid, lay, xt, yt, zt = _crossings(p, cfg.barrel_only)
+    if cfg.x0_barrel > 0.0 or cfg.x0_disk > 0.0:
+        pid, lay, xt, yt, zt, _ = _crossings_ms(rng, p, cfg.barrel_only, cfg.x0_barrel,
+                                                cfg.x0_disk)
+    else:
+        pid, lay, xt, yt, zt = _crossings(p, cfg.barrel_only)
     if cfg.smear:
         xs, ys, zs = _smear(rng, lay, xt, yt, zt)
     else:
