@@ -353,6 +353,33 @@ def _vertexing(ctx, dbat, stream, steps: int) -> dict:
             "workload": "the bench batch's fitted tracks (its particles have independent z0)"}
 
 
+def _broken_line(ctx, dbat, stream, steps: int) -> dict:
+    """Broken-line refit (pt_refit_broken_line, 2 % X0 per layer) of the fitted tracks of
+    one bench batch, timed with CUDA events on the library's stream; the circle + line
+    fit that serves as its reference runs again before each timed call, outside the
+    events."""
+    import torch
+    off, x, y, z, layer = dbat[0]
+    ctx.pt_load_batch(off, x, y, z, layer)
+    ctx.pt_build_doublets(sync=False)
+    ctx.pt_connect_cells(sync=False)
+    ctx.pt_find_ntuplets(sync=False)
+    n = ctx.pt_fit_tracks()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for e0, e1 in ev:
+        ctx.pt_fit_tracks(sync=False)
+        e0.record(stream)
+        ctx.pt_refit_broken_line(0.02, 0.02, sync=False)
+        e1.record(stream)
+    stream.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    E = len(off) - 1
+    return {"ms_per_step": statistics.mean(ms), "events_per_step": E, "tracks_per_step": n,
+            "tracks_per_s": n / (statistics.mean(ms) / 1000.0),
+            "workload": "the bench batch's fitted tracks, refitted with 2 % X0 per layer"}
+
+
 def _raw_input(ctx, dev, stream, steps: int, B: int) -> dict:
     """Raw pixel data -> hits (pt_load_raw: unpack, cluster, place, bin) on B copies of
     one PU200 event's digis in device memory, timed with CUDA events on the library's
@@ -542,6 +569,7 @@ def run_ours(args):
     ctx.pt_set_gate(None, 0.0)
     with torch.cuda.stream(stream):
         vertexing = _vertexing(ctx, dbat, stream, min(args.steps, 20))
+        broken_line = _broken_line(ctx, dbat, stream, min(args.steps, 20))
         raw_input = _raw_input(ctx, dev, stream, min(args.steps, 20), B)
     config4 = {"plain": _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)}
     ctx.pt_set_gate(gw, gtau)
@@ -588,6 +616,7 @@ def run_ours(args):
                 "counts_per_step": counts,
                 "batch_workload": config4,
                 "vertexing": vertexing,
+                "broken_line": broken_line,
                 "raw_input": raw_input,
                 "autotune": launch,
                 "clocks": clocks,

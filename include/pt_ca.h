@@ -214,6 +214,21 @@ pt_status pt_find_ntuplets(pt_ctx* ctx, int64_t* n_ntuplets);
  * parameters).  n_tracks as above. */
 pt_status pt_fit_tracks(pt_ctx* ctx, int64_t* n_tracks);
 
+/* Broken-line refit of the fitted tracks, in place (Sec. 2.2.1: a fit determines the
+ * track parameters; broken lines after V. Blobel, NIM A566 (2006) 14).  Each track's
+ * circle + line fit is the reference; its offsets at the hits, one curvature
+ * correction and the multiple-scattering kinks at the interior hits (Highland variances
+ * for x0_barrel / x0_disk radiation lengths per layer at normal incidence, with 10 um
+ * r-phi and 20 um z / r hit errors) are solved by linear least squares in float64, and
+ * the parameters at the closest approach replace the track's; chi2_circle and
+ * chi2_line become the two planes' broken-line chi2 (measurements plus kinks).  A
+ * track whose reference is not finite, has |kappa| < 1e-7 /cm or whose hits are not
+ * strictly ordered along the reference circle keeps its fit.  Run after pt_fit_tracks
+ * (or a batch graph) on the same batch; pt_find_vertices must run again afterwards to
+ * use the refitted tracks.  n_tracks as above.  Errors: PT_ERR_INVALID for no fitted
+ * batch or material outside (0, 1]. */
+pt_status pt_refit_broken_line(pt_ctx* ctx, float x0_barrel, float x0_disk, int64_t* n_tracks);
+
 /* -------------------------------------------------------------------- results */
 
 /* Cleaned ntuplets of the batch, events in order, canonical order within an event.

@@ -50,8 +50,8 @@ kinks follow from one linear least-squares problem.  The library's reading:
        kappa = kappa0 + dkappa, phi0 + u'(0), d0 - u(0); w'_1 = (w_2 - w_1)/h'_1,
        cot = cot0 + w'_1, z0 = z00 + w_1 - s'_1 w'_1.  chi2_circle = chi2_T and
        chi2_line = chi2_L at the minimum; charge = -sign(kappa).
-  [B6] A track with fewer than 3 hits, |kappa0| < 1e-7 cm^-1 or some h_i <= 1e-6 cm
-       keeps its reference fit.
+  [B6] A track with fewer than 3 hits, a reference with a non-finite value, |kappa0| <
+       1e-7 cm^-1 or some h_i <= 1e-6 cm keeps its reference fit.
 """
 
 from __future__ import annotations
@@ -138,7 +138,7 @@ def refit(x, y, z, layer, ref, x0_barrel: float, x0_disk: float, bfield: float =
     keep = np.concatenate([ref[:5], [C_PT * bfield / (100.0 * abs(ref[0])) if ref[0] else math.inf],
                            ref[6:8] if ref.size >= 8 else [0.0, 0.0],
                            [-math.copysign(1.0, ref[0]) if ref[0] else 0.0]])
-    if n < 3 or abs(ref[0]) < 1e-7:  # [B6]
+    if n < 3 or not np.all(np.isfinite(ref[:5])) or abs(ref[0]) < 1e-7:  # [B6]
         return (keep, None) if full else keep
     s, eps, _ = reference_geometry(x, y, z, ref)
     h = np.diff(s)

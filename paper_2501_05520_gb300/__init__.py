@@ -27,7 +27,8 @@ PT_OK, PT_ERR_INVALID, PT_ERR_CAPACITY, PT_ERR_CUDA, PT_ERR_TIMEOUT, PT_ERR_NOT_
 # Every symbol include/pt_ca.h declares.
 EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt_load_hits",
             "pt_load_batch", "pt_build_doublets", "pt_connect_cells", "pt_find_ntuplets",
-            "pt_fit_tracks", "pt_get_ntuplets", "pt_get_tracks", "pt_find_vertices",
+            "pt_fit_tracks", "pt_refit_broken_line", "pt_get_ntuplets", "pt_get_tracks",
+            "pt_find_vertices",
             "pt_set_modules", "pt_load_raw", "pt_get_hits",
             "pt_get_vertices", "pt_get_cells", "pt_get_links",
             "pt_get_candidates", "pt_reconstruct_batch", "pt_enqueue_batch",
@@ -97,6 +98,7 @@ def lib() -> ctypes.CDLL:
             "pt_connect_cells": [P, PI64],
             "pt_find_ntuplets": [P, PI64],
             "pt_fit_tracks": [P, PI64],
+            "pt_refit_broken_line": [P, ctypes.c_float, ctypes.c_float, PI64],
             "pt_get_ntuplets": [P, P, P, P, I64, PI64, I32],
             "pt_get_tracks": [P, P, I64, PI64, I32],
             "pt_find_vertices": [P, I32, ctypes.c_float, PI64],
@@ -292,6 +294,15 @@ class Context:
 
     def pt_fit_tracks(self, sync: bool = True):
         return self._stage(lib().pt_fit_tracks, sync)
+
+    def pt_refit_broken_line(self, x0_barrel: float = 0.02, x0_disk: float = 0.02,
+                             sync: bool = True):
+        """Broken-line refit of the fitted tracks in place; returns their number when
+        sync."""
+        n = ctypes.c_int64(0)
+        _check(lib().pt_refit_broken_line(self.handle, float(x0_barrel), float(x0_disk),
+                                          ctypes.byref(n) if sync else None))
+        return int(n.value) if sync else None
 
     # ----------------------------------------------------------------- results
     def pt_get_ntuplets(self):

@@ -1,0 +1,308 @@
+// Broken-line refit of the fitted tracks (Sec. 2.2.1 and Fig. 2: a fit of each picked
+// group of hits determines the track parameters; the broken-line form is V. Blobel,
+// NIM A566 (2006) 14).  The track is its offsets from the circle + line fit at the n
+// hits, joined by pieces of one common curvature; the direction changes at the hits are
+// multiple-scattering kinks weighted by their expected variance.  The library's reading:
+//   [B1] reference = the track's circle + line fit; for hit i, s_i = arc length from
+//        the closest approach to the hit's radial projection on the reference circle,
+//        eps_i = signed distance from that circle (positive to the left of the motion);
+//   [B2] transverse unknowns u_1..u_n, dkappa; between hits u'' + kappa0^2 u = dkappa
+//        (first-order departure of a circle from the reference circle), so a segment of
+//        length h has end slopes a (u_b - c u_a) - a g dkappa and a (c u_b - u_a) +
+//        a g dkappa, c = cos(kappa0 h), a = kappa0 / sin(kappa0 h), g = 2 sin^2(kappa0
+//        h / 2) / kappa0^2; kink beta_i = slope after - slope before; chi2_T = sum
+//        (eps_i - u_i)^2 / (10 um)^2 + sum beta_i^2 / vartheta_i^2;
+//   [B3] z is linear in the arc length along the fitted transverse path, s'_i = s_i -
+//        kappa0 int_0^{s_i} u (per segment the parabola through its end offsets with
+//        second derivative dkappa); unknowns w_i = z offsets from z0 + cot s', kinks of
+//        the straight pieces, errors 20 um (barrel z) and |cot| 20 um (disk r);
+//   [B4] Highland theta0 = 13.6 MeV / p sqrt(t) (1 + 0.038 ln t), p and the incidence
+//        from the reference, t = x/X0 / cos(incidence) (barrel: direction . radial
+//        direction; disk: |cos theta|; floored at 1e-3); vartheta^2 = theta0^2 /
+//        sin^2 theta, tau^2 = theta0^2 / sin^4 theta;
+//   [B5] parameters at the closest approach continue the first segment backwards:
+//        kappa0 + dkappa, phi0 + u'(0), d0 - u(0), cot0 + w'_1, z0 + w(0);
+//   [B6] a reference with a non-finite value, |kappa0| < 1e-7 /cm or hits not strictly
+//        ordered along s (a step <= 1e-6 cm) keeps its circle + line fit.
+//
+// One thread per track.  Everything after the float32 loads runs in float64: the
+// residuals are micrometres on coordinates of tens of centimetres, and the normal
+// equations mix weights of 1e6 (hits) and 1e4..1e8 (kinks).  The at most 7 (transverse)
+// and 6 (longitudinal) unknowns are solved by an LDL^T factorisation held in registers:
+// every loop is unrolled over the largest ntuplet, and the unknowns of absent hits are
+// padded with unit diagonal entries so they decouple and solve to zero.
+#include "brokenline.cuh"
+
+namespace ptca {
+
+namespace {
+
+constexpr int kN = kMaxHits;
+constexpr double kSigmaT = 10e-4;  // cm
+constexpr double kSigmaL = 20e-4;  // cm
+constexpr double kCpt = 0.299792458;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+__device__ __forceinline__ double sinc(double x) {
+  return fabs(x) > 1e-4 ? sin(x) / x : 1.0 - x * x * (1.0 / 6.0);
+}
+
+// Solves A v = r for symmetric positive definite A (lower triangle read) by LDL^T;
+// r is replaced by v.
+template <int M>
+__device__ __forceinline__ void ldl_solve(double (&A)[M][M], double (&r)[M]) {
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    double d = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k] * A[k][k];
+    A[j][j] = d;
+#pragma unroll
+    for (int i = j + 1; i < M; ++i) {
+      double v = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v -= A[i][k] * A[j][k] * A[k][k];
+      A[i][j] = v / d;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+#pragma unroll
+    for (int k = 0; k < i; ++k) r[i] -= A[i][k] * r[k];
+  }
+#pragma unroll
+  for (int i = 0; i < M; ++i) r[i] /= A[i][i];
+#pragma unroll
+  for (int i = M - 1; i >= 0; --i) {
+#pragma unroll
+    for (int k = i + 1; k < M; ++k) r[i] -= A[k][i] * r[k];
+  }
+}
+
+__global__ void __launch_bounds__(128) k_refit_bl(Buffers b, double bfield, double x0b,
+                                                   double x0d) {
+  const uint64_t S = b.cnt[CNT_SV];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < S; j += stride) {
+    const uint32_t t = b.ord[b.sv[j]];
+    const int n = b.nt_n[t];
+    pt_track tr = b.tracks[j];
+    const double k0 = tr.kappa, phi0 = tr.phi0, d0 = tr.d0, cot0 = tr.cot_theta, z00 = tr.z0;
+    // [B6]
+    if (n < 3 || n > kN || !isfinite(k0) || !isfinite(phi0) || !isfinite(d0) ||
+        !isfinite(cot0) || !isfinite(z00) || fabs(k0) < 1e-7)
+      continue;
+    double x[kN], y[kN], z[kN];
+    bool barrel[kN];
+#pragma unroll
+    for (int i = 0; i < kN; ++i) {
+      x[i] = y[i] = z[i] = 0.0;
+      barrel[i] = true;
+      if (i < n) {
+        const int32_t g = b.nt_hits[(uint64_t)t * kMaxHits + i];
+        x[i] = b.in_x[g];
+        y[i] = b.in_y[g];
+        z[i] = b.in_z[g];
+        barrel[i] = b.in_layer[g] < 4;
+      }
+    }
+    // [B1] arc lengths and transverse residuals
+    double sp0, cp0;
+    sincos(phi0, &sp0, &cp0);
+    const double ccen = d0 - 1.0 / k0;
+    const double cx = ccen * sp0, cy = -ccen * cp0;
+    const double ax = sp0 / k0, ay = -cp0 / k0;
+    const double sgn = k0 > 0.0 ? 1.0 : -1.0, rad = 1.0 / fabs(k0);
+    double s[kN], eps[kN];
+#pragma unroll
+    for (int i = 0; i < kN; ++i) {
+      s[i] = eps[i] = 0.0;
+      if (i < n) {
+        const double bx = x[i] - cx, by = y[i] - cy;
+        s[i] = atan2(ax * by - ay * bx, ax * bx + ay * by) / k0;
+        eps[i] = sgn * (rad - hypot(bx, by));
+      }
+    }
+    double h[kN - 1];
+    bool ordered = true;
+#pragma unroll
+    for (int i = 0; i < kN - 1; ++i) {
+      h[i] = 1.0;
+      if (i + 1 < n) {
+        h[i] = s[i + 1] - s[i];
+        ordered = ordered && h[i] > 1e-6;
+      }
+    }
+    if (!ordered) continue;
+    // [B4] kink variances at the interior hits
+    const double sth = 1.0 / sqrt(1.0 + cot0 * cot0), cth = cot0 * sth;
+    const double p = kCpt * bfield / (100.0 * fabs(k0)) / sth;
+    double wt[kN], wl[kN];  // inverse variances
+#pragma unroll
+    for (int i = 0; i < kN; ++i) {
+      wt[i] = wl[i] = 0.0;
+      if (i >= 1 && i + 1 < n) {
+        double tx;
+        if (barrel[i]) {
+          double sps, cps;
+          sincos(phi0 + k0 * s[i], &sps, &cps);
+          const double cos_inc = fabs(sth * (cps * x[i] + sps * y[i])) / hypot(x[i], y[i]);
+          tx = x0b / fmax(cos_inc, 1e-3);
+        } else {
+          tx = x0d / fmax(fabs(cth), 1e-3);
+        }
+        const double th0 = 0.0136 / p * sqrt(tx) * (1.0 + 0.038 * log(tx));
+        const double v = th0 * th0 / (sth * sth);
+        wt[i] = 1.0 / v;
+        wl[i] = sth * sth / v;
+      }
+    }
+    // [B2] segment coefficients
+    double sc[kN - 1], sa[kN - 1], sg[kN - 1];
+#pragma unroll
+    for (int i = 0; i < kN - 1; ++i) {
+      sc[i] = cos(k0 * h[i]);
+      sa[i] = 1.0 / (h[i] * sinc(k0 * h[i]));
+      const double sh = sinc(0.5 * k0 * h[i]);
+      sg[i] = 0.5 * h[i] * h[i] * sh * sh;
+    }
+    // transverse normal equations: unknowns u_0..u_5, dkappa (index kN)
+    double A[kN + 1][kN + 1];
+    double r[kN + 1];
+#pragma unroll
+    for (int i = 0; i <= kN; ++i) {
+      r[i] = 0.0;
+#pragma unroll
+      for (int k = 0; k <= i; ++k) A[i][k] = 0.0;
+    }
+    const double wm = 1.0 / (kSigmaT * kSigmaT);
+#pragma unroll
+    for (int i = 0; i < kN; ++i) {
+      A[i][i] = i < n ? wm : 1.0;
+      r[i] = i < n ? eps[i] * wm : 0.0;
+    }
+#pragma unroll
+    for (int i = 1; i < kN - 1; ++i) {
+      if (i + 1 < n) {
+        const double q0 = sa[i - 1], q1 = -(sa[i] * sc[i] + sa[i - 1] * sc[i - 1]);
+        const double q2 = sa[i], q3 = -(sa[i] * sg[i] + sa[i - 1] * sg[i - 1]);
+        const double w = wt[i];
+        A[i - 1][i - 1] += w * q0 * q0;
+        A[i][i - 1] += w * q1 * q0;
+        A[i + 1][i - 1] += w * q2 * q0;
+        A[kN][i - 1] += w * q3 * q0;
+        A[i][i] += w * q1 * q1;
+        A[i + 1][i] += w * q2 * q1;
+        A[kN][i] += w * q3 * q1;
+        A[i + 1][i + 1] += w * q2 * q2;
+        A[kN][i + 1] += w * q3 * q2;
+        A[kN][kN] += w * q3 * q3;
+      }
+    }
+    ldl_solve(A, r);
+    double u[kN];
+#pragma unroll
+    for (int i = 0; i < kN; ++i) u[i] = r[i];
+    const double dk = r[kN];
+    double chi2t = 0.0;
+#pragma unroll
+    for (int i = 0; i < kN; ++i) {
+      if (i < n) chi2t += (eps[i] - u[i]) * (eps[i] - u[i]) * wm;
+      if (i >= 1 && i + 1 < n) {
+        const double beta = sa[i] * (u[i + 1] - sc[i] * u[i]) - sa[i] * sg[i] * dk -
+                            (sa[i - 1] * (sc[i - 1] * u[i] - u[i - 1]) + sa[i - 1] * sg[i - 1] * dk);
+        chi2t += beta * beta * wt[i];
+      }
+    }
+    // [B5] transverse parameters at the closest approach
+    const double du1 = sa[0] * (u[1] - sc[0] * u[0]) - sa[0] * sg[0] * dk;
+    const double cs = cos(k0 * s[0]), snk = s[0] * sinc(k0 * s[0]);
+    const double gsh = sinc(0.5 * k0 * s[0]);
+    const double gs = 0.5 * s[0] * s[0] * gsh * gsh;
+    const double u0 = u[0] * cs + gs * dk - du1 * snk;
+    const double du0 = du1 * cs + k0 * k0 * u[0] * snk - dk * snk;
+    // [B3] arc lengths along the fitted transverse path, z residuals
+    double sp[kN];
+    double acc = s[0] * (u0 + u[0]) * 0.5 - dk * s[0] * s[0] * s[0] * (1.0 / 12.0);
+    sp[0] = s[0] - k0 * acc;
+#pragma unroll
+    for (int i = 1; i < kN; ++i) {
+      sp[i] = 0.0;
+      if (i < n) {
+        const double hh = h[i - 1];
+        acc += hh * (u[i - 1] + u[i]) * 0.5 - dk * hh * hh * hh * (1.0 / 12.0);
+        sp[i] = s[i] - k0 * acc;
+      }
+    }
+    double hp[kN - 1];
+#pragma unroll
+    for (int i = 0; i < kN - 1; ++i) hp[i] = i + 1 < n ? sp[i + 1] - sp[i] : 1.0;
+    double B[kN][kN];
+    double c[kN];
+#pragma unroll
+    for (int i = 0; i < kN; ++i) {
+#pragma unroll
+      for (int k = 0; k <= i; ++k) B[i][k] = 0.0;
+      c[i] = 0.0;
+    }
+    double dl[kN], wz[kN];
+#pragma unroll
+    for (int i = 0; i < kN; ++i) {
+      dl[i] = 0.0;
+      wz[i] = 0.0;
+      if (i < n) {
+        const double sl = fmax(barrel[i] ? kSigmaL : fabs(cot0) * kSigmaL, 1e-12);
+        wz[i] = 1.0 / (sl * sl);
+        dl[i] = z[i] - (z00 + cot0 * sp[i]);
+      }
+      B[i][i] = i < n ? wz[i] : 1.0;
+      c[i] = dl[i] * wz[i];
+    }
+#pragma unroll
+    for (int i = 1; i < kN - 1; ++i) {
+      if (i + 1 < n) {
+        const double q0 = 1.0 / hp[i - 1], q2 = 1.0 / hp[i], q1 = -(q0 + q2);
+        const double w = wl[i];
+        B[i - 1][i - 1] += w * q0 * q0;
+        B[i][i - 1] += w * q1 * q0;
+        B[i + 1][i - 1] += w * q2 * q0;
+        B[i][i] += w * q1 * q1;
+        B[i + 1][i] += w * q2 * q1;
+        B[i + 1][i + 1] += w * q2 * q2;
+      }
+    }
+    ldl_solve(B, c);
+    double chi2l = 0.0;
+#pragma unroll
+    for (int i = 0; i < kN; ++i) {
+      if (i < n) chi2l += (dl[i] - c[i]) * (dl[i] - c[i]) * wz[i];
+      if (i >= 1 && i + 1 < n) {
+        const double g = (c[i + 1] - c[i]) / hp[i] - (c[i] - c[i - 1]) / hp[i - 1];
+        chi2l += g * g * wl[i];
+      }
+    }
+    const double dw1 = (c[1] - c[0]) / hp[0];
+    const double kappa = k0 + dk;
+    tr.kappa = (float)kappa;
+    tr.phi0 = (float)remainder(phi0 + du0, kTwoPi);
+    tr.d0 = (float)(d0 - u0);
+    tr.cot_theta = (float)(cot0 + dw1);
+    tr.z0 = (float)(z00 + c[0] - sp[0] * dw1);
+    tr.pt = (float)(kCpt * bfield / (100.0 * fabs(kappa)));
+    tr.chi2_circle = (float)chi2t;
+    tr.chi2_line = (float)chi2l;
+    tr.charge = kappa > 0.0 ? -1 : (kappa < 0.0 ? 1 : 0);
+    b.tracks[j] = tr;
+  }
+}
+
+}  // namespace
+
+void launch_refit_broken_line(const Buffers& b, const Params& p, float x0_barrel, float x0_disk,
+                              const Launch& l, cudaStream_t s) {
+  PT_TRACE(l, s, "k_refit_bl",
+           k_refit_bl<<<l.sms * 8, 128, 0, s>>>(b, (double)p.bfield, (double)x0_barrel,
+                                                 (double)x0_disk));
+}
+
+}  // namespace ptca

@@ -10,6 +10,7 @@
 #include <utility>
 #include <vector>
 
+#include "brokenline.cuh"
 #include "ptca_internal.cuh"
 
 using namespace ptca;
@@ -639,6 +640,23 @@ pt_status pt_find_ntuplets(pt_ctx* c, int64_t* n_ntuplets) {
 
 pt_status pt_fit_tracks(pt_ctx* c, int64_t* n_tracks) {
   STAGE_BODY((launch_fit(c->B, c->P, c->L, c->stream), c->fitted = true), CNT_SV, n_tracks)
+}
+
+pt_status pt_refit_broken_line(pt_ctx* c, float x0_barrel, float x0_disk, int64_t* n_tracks) {
+  g_err.clear();
+  PT_TRY(need_loaded(c));
+  if (!(x0_barrel > 0.0f && x0_barrel <= 1.0f) || !(x0_disk > 0.0f && x0_disk <= 1.0f))
+    return fail(PT_ERR_INVALID, "material must be in (0, 1] radiation lengths");
+  if (!c->fitted) return fail(PT_ERR_INVALID, "pt_fit_tracks has not run on this batch");
+  DeviceGuard guard(c->device);
+  launch_refit_broken_line(c->B, c->P, x0_barrel, x0_disk, c->L, c->stream);
+  PT_TRY(last_launch());
+  c->vtx_ready = false;
+  if (n_tracks) {
+    PT_TRY(sync_counters(c));
+    *n_tracks = (int64_t)c->h_cnt[CNT_SV];
+  }
+  return PT_OK;
 }
 
 pt_status pt_get_ntuplets(pt_ctx* c, int32_t* hits, uint8_t* nhits, int64_t* event_offsets,
