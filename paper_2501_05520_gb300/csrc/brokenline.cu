@@ -23,14 +23,23 @@
 //   [B5] parameters at the closest approach continue the first segment backwards:
 //        kappa0 + dkappa, phi0 + u'(0), d0 - u(0), cot0 + w'_1, z0 + w(0);
 //   [B6] a reference with a non-finite value, |kappa0| < 1e-7 /cm or hits not strictly
-//        ordered along s (a step <= 1e-6 cm) keeps its circle + line fit.
+//        ordered along s (a step <= 1e-6 cm) keeps its circle + line fit;
+//   [B7] passes repeat with the previous result as the reference while a pass changes
+//        the curvature by more than 1e-3 relative, at most four (one pass is linear in
+//        the departures from its reference, and the first moves low-momentum forward
+//        tracks by up to 13 % from the circle fit).
 //
-// One thread per track.  Everything after the float32 loads runs in float64: the
-// residuals are micrometres on coordinates of tens of centimetres, and the normal
-// equations mix weights of 1e6 (hits) and 1e4..1e8 (kinks).  The at most 7 (transverse)
-// and 6 (longitudinal) unknowns are solved by an LDL^T factorisation held in registers:
-// every loop is unrolled over the largest ntuplet, and the unknowns of absent hits are
-// padded with unit diagonal entries so they decouple and solve to zero.
+// One thread per track.  The geometry, the normal equations and their solution run in
+// float64: the residuals are micrometres on coordinates of tens of centimetres, and the
+// normal equations mix weights of 1e6 (hits) and 1e4..1e8 (kinks).  The kink variances
+// only need a few significant digits and are formed in float32.  GB300 issues few
+// float64 operations per cycle, so the segment trigonometry (|kappa0 h| <= 0.5 on
+// nearly every track) uses the Taylor series of cos x, sin x / x and (1 - cos x) / x^2
+// (truncation below 1e-15) instead of library calls, and distances use sqrt.  The at
+// most 7 (transverse) and 6 (longitudinal) unknowns are solved by an LDL^T
+// factorisation held in registers: every loop is unrolled over the largest ntuplet, and
+// the unknowns of absent hits are padded with unit diagonal entries so they decouple
+// and solve to zero.
 #include "brokenline.cuh"
 
 namespace ptca {
@@ -43,8 +52,26 @@ constexpr double kSigmaL = 20e-4;  // cm
 constexpr double kCpt = 0.299792458;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
-__device__ __forceinline__ double sinc(double x) {
-  return fabs(x) > 1e-4 ? sin(x) / x : 1.0 - x * x * (1.0 / 6.0);
+constexpr double kPassTol = 1e-3;
+constexpr int kMaxPasses = 4;
+
+// cos x, sin x / x and (1 - cos x) / x^2: Taylor series in x^2 for |x| <= 0.5 (the next
+// terms are below 1e-15), the library beyond.
+__device__ __forceinline__ void trig3(double x, double& c, double& sc, double& vc) {
+  if (fabs(x) <= 0.5) {
+    const double t = x * x;
+    c = 1.0 + t * (-1.0 / 2 + t * (1.0 / 24 + t * (-1.0 / 720 + t * (1.0 / 40320 +
+        t * (-1.0 / 3628800 + t * (1.0 / 479001600))))));
+    sc = 1.0 + t * (-1.0 / 6 + t * (1.0 / 120 + t * (-1.0 / 5040 + t * (1.0 / 362880 +
+         t * (-1.0 / 39916800 + t * (1.0 / 6227020800.0))))));
+    vc = 1.0 / 2 + t * (-1.0 / 24 + t * (1.0 / 720 + t * (-1.0 / 40320 + t * (1.0 / 3628800 +
+         t * (-1.0 / 479001600 + t * (1.0 / 87178291200.0))))));
+  } else {
+    double sn;
+    sincos(x, &sn, &c);
+    sc = sn / x;
+    vc = (1.0 - c) / (x * x);
+  }
 }
 
 // Solves A v = r for symmetric positive definite A (lower triangle read) by LDL^T;
@@ -87,211 +114,240 @@ __global__ void __launch_bounds__(128) k_refit_bl(Buffers b, double bfield, doub
     const uint32_t t = b.ord[b.sv[j]];
     const int n = b.nt_n[t];
     pt_track tr = b.tracks[j];
-    const double k0 = tr.kappa, phi0 = tr.phi0, d0 = tr.d0, cot0 = tr.cot_theta, z00 = tr.z0;
-    // [B6]
-    if (n < 3 || n > kN || !isfinite(k0) || !isfinite(phi0) || !isfinite(d0) ||
-        !isfinite(cot0) || !isfinite(z00) || fabs(k0) < 1e-7)
-      continue;
+    if (n < 3 || n > kN) continue;
+    float xf[kN], yf[kN];
     double x[kN], y[kN], z[kN];
     bool barrel[kN];
 #pragma unroll
     for (int i = 0; i < kN; ++i) {
-      x[i] = y[i] = z[i] = 0.0;
+      xf[i] = yf[i] = 0.0f;
+      z[i] = 0.0;
       barrel[i] = true;
       if (i < n) {
         const int32_t g = b.nt_hits[(uint64_t)t * kMaxHits + i];
-        x[i] = b.in_x[g];
-        y[i] = b.in_y[g];
+        xf[i] = b.in_x[g];
+        yf[i] = b.in_y[g];
         z[i] = b.in_z[g];
         barrel[i] = b.in_layer[g] < 4;
       }
+      x[i] = xf[i];
+      y[i] = yf[i];
     }
-    // [B1] arc lengths and transverse residuals
-    double sp0, cp0;
-    sincos(phi0, &sp0, &cp0);
-    const double ccen = d0 - 1.0 / k0;
-    const double cx = ccen * sp0, cy = -ccen * cp0;
-    const double ax = sp0 / k0, ay = -cp0 / k0;
-    const double sgn = k0 > 0.0 ? 1.0 : -1.0, rad = 1.0 / fabs(k0);
-    double s[kN], eps[kN];
+    // reference of the current pass
+    double k0 = tr.kappa, phi0 = tr.phi0, d0 = tr.d0, cot0 = tr.cot_theta, z00 = tr.z0;
+    double chi2t = 0.0, chi2l = 0.0;
+    bool refitted = false;
+    for (int pass = 0; pass < kMaxPasses; ++pass) {
+      // [B6]
+      if (!isfinite(k0) || !isfinite(phi0) || !isfinite(d0) || !isfinite(cot0) ||
+          !isfinite(z00) || fabs(k0) < 1e-7)
+        break;
+      // [B1] arc lengths and transverse residuals
+      double sp0, cp0;
+      sincos(phi0, &sp0, &cp0);
+      const double ccen = d0 - 1.0 / k0;
+      const double cx = ccen * sp0, cy = -ccen * cp0;
+      const double ax = sp0 / k0, ay = -cp0 / k0;
+      const double sgn = k0 > 0.0 ? 1.0 : -1.0, rad = 1.0 / fabs(k0);
+      double s[kN], eps[kN];
 #pragma unroll
-    for (int i = 0; i < kN; ++i) {
-      s[i] = eps[i] = 0.0;
-      if (i < n) {
-        const double bx = x[i] - cx, by = y[i] - cy;
-        s[i] = atan2(ax * by - ay * bx, ax * bx + ay * by) / k0;
-        eps[i] = sgn * (rad - hypot(bx, by));
-      }
-    }
-    double h[kN - 1];
-    bool ordered = true;
-#pragma unroll
-    for (int i = 0; i < kN - 1; ++i) {
-      h[i] = 1.0;
-      if (i + 1 < n) {
-        h[i] = s[i + 1] - s[i];
-        ordered = ordered && h[i] > 1e-6;
-      }
-    }
-    if (!ordered) continue;
-    // [B4] kink variances at the interior hits
-    const double sth = 1.0 / sqrt(1.0 + cot0 * cot0), cth = cot0 * sth;
-    const double p = kCpt * bfield / (100.0 * fabs(k0)) / sth;
-    double wt[kN], wl[kN];  // inverse variances
-#pragma unroll
-    for (int i = 0; i < kN; ++i) {
-      wt[i] = wl[i] = 0.0;
-      if (i >= 1 && i + 1 < n) {
-        double tx;
-        if (barrel[i]) {
-          double sps, cps;
-          sincos(phi0 + k0 * s[i], &sps, &cps);
-          const double cos_inc = fabs(sth * (cps * x[i] + sps * y[i])) / hypot(x[i], y[i]);
-          tx = x0b / fmax(cos_inc, 1e-3);
-        } else {
-          tx = x0d / fmax(fabs(cth), 1e-3);
+      for (int i = 0; i < kN; ++i) {
+        s[i] = eps[i] = 0.0;
+        if (i < n) {
+          const double bx = x[i] - cx, by = y[i] - cy;
+          s[i] = atan2(ax * by - ay * bx, ax * bx + ay * by) / k0;
+          eps[i] = sgn * (rad - sqrt(bx * bx + by * by));
         }
-        const double th0 = 0.0136 / p * sqrt(tx) * (1.0 + 0.038 * log(tx));
-        const double v = th0 * th0 / (sth * sth);
-        wt[i] = 1.0 / v;
-        wl[i] = sth * sth / v;
       }
-    }
-    // [B2] segment coefficients
-    double sc[kN - 1], sa[kN - 1], sg[kN - 1];
+      double h[kN - 1];
+      bool ordered = true;
 #pragma unroll
-    for (int i = 0; i < kN - 1; ++i) {
-      sc[i] = cos(k0 * h[i]);
-      sa[i] = 1.0 / (h[i] * sinc(k0 * h[i]));
-      const double sh = sinc(0.5 * k0 * h[i]);
-      sg[i] = 0.5 * h[i] * h[i] * sh * sh;
-    }
-    // transverse normal equations: unknowns u_0..u_5, dkappa (index kN)
-    double A[kN + 1][kN + 1];
-    double r[kN + 1];
-#pragma unroll
-    for (int i = 0; i <= kN; ++i) {
-      r[i] = 0.0;
-#pragma unroll
-      for (int k = 0; k <= i; ++k) A[i][k] = 0.0;
-    }
-    const double wm = 1.0 / (kSigmaT * kSigmaT);
-#pragma unroll
-    for (int i = 0; i < kN; ++i) {
-      A[i][i] = i < n ? wm : 1.0;
-      r[i] = i < n ? eps[i] * wm : 0.0;
-    }
-#pragma unroll
-    for (int i = 1; i < kN - 1; ++i) {
-      if (i + 1 < n) {
-        const double q0 = sa[i - 1], q1 = -(sa[i] * sc[i] + sa[i - 1] * sc[i - 1]);
-        const double q2 = sa[i], q3 = -(sa[i] * sg[i] + sa[i - 1] * sg[i - 1]);
-        const double w = wt[i];
-        A[i - 1][i - 1] += w * q0 * q0;
-        A[i][i - 1] += w * q1 * q0;
-        A[i + 1][i - 1] += w * q2 * q0;
-        A[kN][i - 1] += w * q3 * q0;
-        A[i][i] += w * q1 * q1;
-        A[i + 1][i] += w * q2 * q1;
-        A[kN][i] += w * q3 * q1;
-        A[i + 1][i + 1] += w * q2 * q2;
-        A[kN][i + 1] += w * q3 * q2;
-        A[kN][kN] += w * q3 * q3;
+      for (int i = 0; i < kN - 1; ++i) {
+        h[i] = 1.0;
+        if (i + 1 < n) {
+          h[i] = s[i + 1] - s[i];
+          ordered = ordered && h[i] > 1e-6;
+        }
       }
-    }
-    ldl_solve(A, r);
-    double u[kN];
+      if (!ordered) break;
+      // [B4] kink variances at the interior hits (float32)
+      const double sth = 1.0 / sqrt(1.0 + cot0 * cot0);
+      const float sthf = (float)sth, cthf = (float)(cot0 * sth);
+      const float pf = (float)(kCpt * bfield / (100.0 * fabs(k0)) / sth);
+      double wt[kN], wl[kN];  // inverse variances
 #pragma unroll
-    for (int i = 0; i < kN; ++i) u[i] = r[i];
-    const double dk = r[kN];
-    double chi2t = 0.0;
-#pragma unroll
-    for (int i = 0; i < kN; ++i) {
-      if (i < n) chi2t += (eps[i] - u[i]) * (eps[i] - u[i]) * wm;
-      if (i >= 1 && i + 1 < n) {
-        const double beta = sa[i] * (u[i + 1] - sc[i] * u[i]) - sa[i] * sg[i] * dk -
-                            (sa[i - 1] * (sc[i - 1] * u[i] - u[i - 1]) + sa[i - 1] * sg[i - 1] * dk);
-        chi2t += beta * beta * wt[i];
+      for (int i = 0; i < kN; ++i) {
+        wt[i] = wl[i] = 0.0;
+        if (i >= 1 && i + 1 < n) {
+          float tx;
+          if (barrel[i]) {
+            float sps, cps;
+            sincosf((float)(phi0 + k0 * s[i]), &sps, &cps);
+            const float cos_inc = fabsf(sthf * (cps * xf[i] + sps * yf[i])) /
+                                  sqrtf(xf[i] * xf[i] + yf[i] * yf[i]);
+            tx = (float)x0b / fmaxf(cos_inc, 1e-3f);
+          } else {
+            tx = (float)x0d / fmaxf(fabsf(cthf), 1e-3f);
+          }
+          const float th0 = 0.0136f / pf * sqrtf(tx) * (1.0f + 0.038f * logf(tx));
+          const float inv = (sthf * sthf) / (th0 * th0);
+          wt[i] = inv;
+          wl[i] = (double)inv * (double)(sthf * sthf);
+        }
       }
-    }
-    // [B5] transverse parameters at the closest approach
-    const double du1 = sa[0] * (u[1] - sc[0] * u[0]) - sa[0] * sg[0] * dk;
-    const double cs = cos(k0 * s[0]), snk = s[0] * sinc(k0 * s[0]);
-    const double gsh = sinc(0.5 * k0 * s[0]);
-    const double gs = 0.5 * s[0] * s[0] * gsh * gsh;
-    const double u0 = u[0] * cs + gs * dk - du1 * snk;
-    const double du0 = du1 * cs + k0 * k0 * u[0] * snk - dk * snk;
-    // [B3] arc lengths along the fitted transverse path, z residuals
-    double sp[kN];
-    double acc = s[0] * (u0 + u[0]) * 0.5 - dk * s[0] * s[0] * s[0] * (1.0 / 12.0);
-    sp[0] = s[0] - k0 * acc;
+      // [B2] segment coefficients c, a and g
+      double sc[kN - 1], sa[kN - 1], sg[kN - 1];
 #pragma unroll
-    for (int i = 1; i < kN; ++i) {
-      sp[i] = 0.0;
-      if (i < n) {
-        const double hh = h[i - 1];
-        acc += hh * (u[i - 1] + u[i]) * 0.5 - dk * hh * hh * hh * (1.0 / 12.0);
-        sp[i] = s[i] - k0 * acc;
+      for (int i = 0; i < kN - 1; ++i) {
+        double snc, vc;
+        trig3(k0 * h[i], sc[i], snc, vc);
+        sa[i] = 1.0 / (h[i] * snc);
+        sg[i] = h[i] * h[i] * vc;
       }
-    }
-    double hp[kN - 1];
+      // transverse normal equations: unknowns u_0..u_5, dkappa (index kN)
+      double A[kN + 1][kN + 1];
+      double r[kN + 1];
 #pragma unroll
-    for (int i = 0; i < kN - 1; ++i) hp[i] = i + 1 < n ? sp[i + 1] - sp[i] : 1.0;
-    double B[kN][kN];
-    double c[kN];
+      for (int i = 0; i <= kN; ++i) {
+        r[i] = 0.0;
 #pragma unroll
-    for (int i = 0; i < kN; ++i) {
-#pragma unroll
-      for (int k = 0; k <= i; ++k) B[i][k] = 0.0;
-      c[i] = 0.0;
-    }
-    double dl[kN], wz[kN];
-#pragma unroll
-    for (int i = 0; i < kN; ++i) {
-      dl[i] = 0.0;
-      wz[i] = 0.0;
-      if (i < n) {
-        const double sl = fmax(barrel[i] ? kSigmaL : fabs(cot0) * kSigmaL, 1e-12);
-        wz[i] = 1.0 / (sl * sl);
-        dl[i] = z[i] - (z00 + cot0 * sp[i]);
+        for (int k = 0; k <= i; ++k) A[i][k] = 0.0;
       }
-      B[i][i] = i < n ? wz[i] : 1.0;
-      c[i] = dl[i] * wz[i];
-    }
+      const double wm = 1.0 / (kSigmaT * kSigmaT);
 #pragma unroll
-    for (int i = 1; i < kN - 1; ++i) {
-      if (i + 1 < n) {
-        const double q0 = 1.0 / hp[i - 1], q2 = 1.0 / hp[i], q1 = -(q0 + q2);
-        const double w = wl[i];
-        B[i - 1][i - 1] += w * q0 * q0;
-        B[i][i - 1] += w * q1 * q0;
-        B[i + 1][i - 1] += w * q2 * q0;
-        B[i][i] += w * q1 * q1;
-        B[i + 1][i] += w * q2 * q1;
-        B[i + 1][i + 1] += w * q2 * q2;
+      for (int i = 0; i < kN; ++i) {
+        A[i][i] = i < n ? wm : 1.0;
+        r[i] = i < n ? eps[i] * wm : 0.0;
       }
-    }
-    ldl_solve(B, c);
-    double chi2l = 0.0;
 #pragma unroll
-    for (int i = 0; i < kN; ++i) {
-      if (i < n) chi2l += (dl[i] - c[i]) * (dl[i] - c[i]) * wz[i];
-      if (i >= 1 && i + 1 < n) {
-        const double g = (c[i + 1] - c[i]) / hp[i] - (c[i] - c[i - 1]) / hp[i - 1];
-        chi2l += g * g * wl[i];
+      for (int i = 1; i < kN - 1; ++i) {
+        if (i + 1 < n) {
+          const double q0 = sa[i - 1], q1 = -(sa[i] * sc[i] + sa[i - 1] * sc[i - 1]);
+          const double q2 = sa[i], q3 = -(sa[i] * sg[i] + sa[i - 1] * sg[i - 1]);
+          const double w = wt[i];
+          A[i - 1][i - 1] += w * q0 * q0;
+          A[i][i - 1] += w * q1 * q0;
+          A[i + 1][i - 1] += w * q2 * q0;
+          A[kN][i - 1] += w * q3 * q0;
+          A[i][i] += w * q1 * q1;
+          A[i + 1][i] += w * q2 * q1;
+          A[kN][i] += w * q3 * q1;
+          A[i + 1][i + 1] += w * q2 * q2;
+          A[kN][i + 1] += w * q3 * q2;
+          A[kN][kN] += w * q3 * q3;
+        }
       }
+      ldl_solve(A, r);
+      double u[kN];
+#pragma unroll
+      for (int i = 0; i < kN; ++i) u[i] = r[i];
+      const double dk = r[kN];
+      double c2t = 0.0;
+#pragma unroll
+      for (int i = 0; i < kN; ++i) {
+        if (i < n) c2t += (eps[i] - u[i]) * (eps[i] - u[i]) * wm;
+        if (i >= 1 && i + 1 < n) {
+          const double beta = sa[i] * (u[i + 1] - sc[i] * u[i]) - sa[i] * sg[i] * dk -
+                              (sa[i - 1] * (sc[i - 1] * u[i] - u[i - 1]) +
+                               sa[i - 1] * sg[i - 1] * dk);
+          c2t += beta * beta * wt[i];
+        }
+      }
+      // [B5] transverse parameters at the closest approach
+      const double du1 = sa[0] * (u[1] - sc[0] * u[0]) - sa[0] * sg[0] * dk;
+      double cs, snc0, vc0;
+      trig3(k0 * s[0], cs, snc0, vc0);
+      const double snk = s[0] * snc0;
+      const double gs = s[0] * s[0] * vc0;
+      const double u0 = u[0] * cs + gs * dk - du1 * snk;
+      const double du0 = du1 * cs + k0 * k0 * u[0] * snk - dk * snk;
+      // [B3] arc lengths along the fitted transverse path, z residuals
+      double sp[kN];
+      double acc = s[0] * (u0 + u[0]) * 0.5 - dk * s[0] * s[0] * s[0] * (1.0 / 12.0);
+      sp[0] = s[0] - k0 * acc;
+#pragma unroll
+      for (int i = 1; i < kN; ++i) {
+        sp[i] = 0.0;
+        if (i < n) {
+          const double hh = h[i - 1];
+          acc += hh * (u[i - 1] + u[i]) * 0.5 - dk * hh * hh * hh * (1.0 / 12.0);
+          sp[i] = s[i] - k0 * acc;
+        }
+      }
+      double hp[kN - 1], ih[kN - 1];
+#pragma unroll
+      for (int i = 0; i < kN - 1; ++i) {
+        hp[i] = i + 1 < n ? sp[i + 1] - sp[i] : 1.0;
+        ih[i] = 1.0 / hp[i];
+      }
+      double B[kN][kN];
+      double c[kN];
+#pragma unroll
+      for (int i = 0; i < kN; ++i) {
+#pragma unroll
+        for (int k = 0; k <= i; ++k) B[i][k] = 0.0;
+      }
+      double dl[kN], wz[kN];
+      const double wzb = 1.0 / (kSigmaL * kSigmaL);
+      const double sld = fmax(fabs(cot0) * kSigmaL, 1e-12);
+      const double wzd = 1.0 / (sld * sld);
+#pragma unroll
+      for (int i = 0; i < kN; ++i) {
+        dl[i] = 0.0;
+        wz[i] = 0.0;
+        if (i < n) {
+          wz[i] = barrel[i] ? wzb : wzd;
+          dl[i] = z[i] - (z00 + cot0 * sp[i]);
+        }
+        B[i][i] = i < n ? wz[i] : 1.0;
+        c[i] = dl[i] * wz[i];
+      }
+#pragma unroll
+      for (int i = 1; i < kN - 1; ++i) {
+        if (i + 1 < n) {
+          const double q0 = ih[i - 1], q2 = ih[i], q1 = -(q0 + q2);
+          const double w = wl[i];
+          B[i - 1][i - 1] += w * q0 * q0;
+          B[i][i - 1] += w * q1 * q0;
+          B[i + 1][i - 1] += w * q2 * q0;
+          B[i][i] += w * q1 * q1;
+          B[i + 1][i] += w * q2 * q1;
+          B[i + 1][i + 1] += w * q2 * q2;
+        }
+      }
+      ldl_solve(B, c);
+      double c2l = 0.0;
+#pragma unroll
+      for (int i = 0; i < kN; ++i) {
+        if (i < n) c2l += (dl[i] - c[i]) * (dl[i] - c[i]) * wz[i];
+        if (i >= 1 && i + 1 < n) {
+          const double g = (c[i + 1] - c[i]) * ih[i] - (c[i] - c[i - 1]) * ih[i - 1];
+          c2l += g * g * wl[i];
+        }
+      }
+      const double dw1 = (c[1] - c[0]) * ih[0];
+      const double kappa = k0 + dk;
+      const double change = fabs(dk) / fabs(k0);
+      k0 = kappa;
+      phi0 = remainder(phi0 + du0, kTwoPi);
+      d0 = d0 - u0;
+      z00 = z00 + c[0] - sp[0] * dw1;
+      cot0 = cot0 + dw1;
+      chi2t = c2t;
+      chi2l = c2l;
+      refitted = true;
+      if (!(change > kPassTol)) break;
     }
-    const double dw1 = (c[1] - c[0]) / hp[0];
-    const double kappa = k0 + dk;
-    tr.kappa = (float)kappa;
-    tr.phi0 = (float)remainder(phi0 + du0, kTwoPi);
-    tr.d0 = (float)(d0 - u0);
-    tr.cot_theta = (float)(cot0 + dw1);
-    tr.z0 = (float)(z00 + c[0] - sp[0] * dw1);
-    tr.pt = (float)(kCpt * bfield / (100.0 * fabs(kappa)));
+    if (!refitted) continue;
+    tr.kappa = (float)k0;
+    tr.phi0 = (float)phi0;
+    tr.d0 = (float)d0;
+    tr.cot_theta = (float)cot0;
+    tr.z0 = (float)z00;
+    tr.pt = (float)(kCpt * bfield / (100.0 * fabs(k0)));
     tr.chi2_circle = (float)chi2t;
     tr.chi2_line = (float)chi2l;
-    tr.charge = kappa > 0.0 ? -1 : (kappa < 0.0 ? 1 : 0);
+    tr.charge = k0 > 0.0 ? -1 : (k0 < 0.0 ? 1 : 0);
     b.tracks[j] = tr;
   }
 }

@@ -165,3 +165,25 @@ def test_material_off_leaves_events_unchanged():
     assert np.array_equal(a.x64, b.x64) and np.array_equal(a.pid, b.pid)
     c = E.generate(dataclasses.replace(E.PU50, x0_barrel=0.02, x0_disk=0.02), 2000)
     assert c.n_hits > 0.95 * a.n_hits and not np.array_equal(a.x64[:100], c.x64[:100])
+
+
+def test_iterated_refit_is_a_fixed_point():
+    """[B7] After the passes stop, one more pass from the result changes the curvature
+    by far less than the stopping threshold (on a forward sample where the first pass
+    moves it by per cents)."""
+    x0 = 0.02
+    p, pid, lay, xs, ys, zs, step = _scattered_tracks(12, 600, 0.5, 0.9, 2.4, x0)
+    worst_first, worst_after = 0.0, 0.0
+    for i in range(p["pt"].size):
+        m = np.flatnonzero(pid == i)
+        if m.size < 3:
+            continue
+        m = m[np.argsort(step[m])]
+        ref = oracle.fit_hits(xs[m], ys[m], zs[m])
+        one = bl.refit(xs[m], ys[m], zs[m], lay[m], ref, x0, x0)
+        it = bl.refit_iterated(xs[m], ys[m], zs[m], lay[m], ref, x0, x0)
+        again = bl.refit(xs[m], ys[m], zs[m], lay[m], it, x0, x0)
+        worst_first = max(worst_first, abs(one[0] - ref[0]) / abs(ref[0]))
+        worst_after = max(worst_after, abs(again[0] - it[0]) / abs(it[0]))
+    assert worst_first > 0.02
+    assert worst_after < 1e-4
