@@ -39,7 +39,12 @@
 // most 7 (transverse) and 6 (longitudinal) unknowns are solved by an LDL^T
 // factorisation held in registers: every loop is unrolled over the largest ntuplet, and
 // the unknowns of absent hits are padded with unit diagonal entries so they decouple
-// and solve to zero.
+// and solve to zero.  Each pass is its own launch over the tracks the previous pass
+// listed as still moving (a warp-aggregated append), so a warp never waits for the
+// slowest of its tracks; the reference of a later pass is the float32 track the previous
+// pass wrote (the result depends on its reference only at second order).
+#include <cooperative_groups.h>
+
 #include "brokenline.cuh"
 
 namespace ptca {
@@ -54,6 +59,7 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 constexpr double kPassTol = 1e-3;
 constexpr int kMaxPasses = 4;
+static_assert(kMaxPasses <= kRefitCounters, "one counter per pass");
 
 // cos x, sin x / x and (1 - cos x) / x^2: Taylor series in x^2 for |x| <= 0.5 (the next
 // terms are below 1e-15), the library beyond.
@@ -106,15 +112,16 @@ __device__ __forceinline__ void ldl_solve(double (&A)[M][M], double (&r)[M]) {
   }
 }
 
-__global__ void __launch_bounds__(128) k_refit_bl(Buffers b, double bfield, double x0b,
-                                                   double x0d) {
-  const uint64_t S = b.cnt[CNT_SV];
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < S; j += stride) {
-    const uint32_t t = b.ord[b.sv[j]];
-    const int n = b.nt_n[t];
-    pt_track tr = b.tracks[j];
-    if (n < 3 || n > kN) continue;
+// One refit pass of track j from its current fit; writes the result and returns true
+// when the pass ran, with *more set when the curvature moved by more than kPassTol.
+__device__ __forceinline__ bool refit_pass(const Buffers& b, uint64_t j, double bfield,
+                                           double x0b, double x0d, bool* more) {
+  *more = false;
+  const uint32_t t = b.ord[b.sv[j]];
+  const int n = b.nt_n[t];
+  pt_track tr = b.tracks[j];
+  if (n < 3 || n > kN) return false;
+  {
     float xf[kN], yf[kN];
     double x[kN], y[kN], z[kN];
     bool barrel[kN];
@@ -133,15 +140,14 @@ __global__ void __launch_bounds__(128) k_refit_bl(Buffers b, double bfield, doub
       x[i] = xf[i];
       y[i] = yf[i];
     }
-    // reference of the current pass
+    // reference of this pass
     double k0 = tr.kappa, phi0 = tr.phi0, d0 = tr.d0, cot0 = tr.cot_theta, z00 = tr.z0;
     double chi2t = 0.0, chi2l = 0.0;
-    bool refitted = false;
-    for (int pass = 0; pass < kMaxPasses; ++pass) {
+    {
       // [B6]
       if (!isfinite(k0) || !isfinite(phi0) || !isfinite(d0) || !isfinite(cot0) ||
           !isfinite(z00) || fabs(k0) < 1e-7)
-        break;
+        return false;
       // [B1] arc lengths and transverse residuals
       double sp0, cp0;
       sincos(phi0, &sp0, &cp0);
@@ -169,7 +175,7 @@ __global__ void __launch_bounds__(128) k_refit_bl(Buffers b, double bfield, doub
           ordered = ordered && h[i] > 1e-6;
         }
       }
-      if (!ordered) break;
+      if (!ordered) return false;
       // [B4] kink variances at the interior hits (float32)
       const double sth = 1.0 / sqrt(1.0 + cot0 * cot0);
       const float sthf = (float)sth, cthf = (float)(cot0 * sth);
@@ -335,10 +341,8 @@ __global__ void __launch_bounds__(128) k_refit_bl(Buffers b, double bfield, doub
       cot0 = cot0 + dw1;
       chi2t = c2t;
       chi2l = c2l;
-      refitted = true;
-      if (!(change > kPassTol)) break;
+      *more = change > kPassTol;
     }
-    if (!refitted) continue;
     tr.kappa = (float)k0;
     tr.phi0 = (float)phi0;
     tr.d0 = (float)d0;
@@ -350,15 +354,50 @@ __global__ void __launch_bounds__(128) k_refit_bl(Buffers b, double bfield, doub
     tr.charge = k0 > 0.0 ? -1 : (k0 < 0.0 ? 1 : 0);
     b.tracks[j] = tr;
   }
+  return true;
+}
+
+// One pass over every cleaned track (in_list null) or over the in_n[0] tracks of
+// in_list; tracks that keep moving are appended to out_list (when given).
+__global__ void __launch_bounds__(128) k_refit_bl(Buffers b, double bfield, double x0b,
+                                                   double x0d, const uint32_t* in_list,
+                                                   const unsigned long long* in_n,
+                                                   uint32_t* out_list,
+                                                   unsigned long long* out_n, uint64_t cap) {
+  namespace cg = cooperative_groups;
+  const uint64_t N = min(in_list ? *in_n : b.cnt[CNT_SV], (unsigned long long)cap);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    const uint64_t j = in_list ? in_list[i] : i;
+    bool more;
+    refit_pass(b, j, bfield, x0b, x0d, &more);
+    if (more && out_list) {
+      cg::coalesced_group g = cg::coalesced_threads();
+      unsigned long long base = 0;
+      if (g.thread_rank() == 0) base = atomicAdd(out_n, (unsigned long long)g.size());
+      base = g.shfl(base, 0);
+      out_list[base + g.thread_rank()] = (uint32_t)j;
+    }
+  }
 }
 
 }  // namespace
 
 void launch_refit_broken_line(const Buffers& b, const Params& p, float x0_barrel, float x0_disk,
-                              const Launch& l, cudaStream_t s) {
-  PT_TRACE(l, s, "k_refit_bl",
-           k_refit_bl<<<l.sms * 8, 128, 0, s>>>(b, (double)p.bfield, (double)x0_barrel,
-                                                 (double)x0_disk));
+                              uint32_t* list, unsigned long long* counters, const Launch& l,
+                              cudaStream_t s) {
+  const uint64_t cap = (uint64_t)p.max_ntuplets;
+  uint32_t* lists[2] = {list, list + cap};
+  cudaMemsetAsync(counters, 0, kMaxPasses * sizeof(unsigned long long), s);
+  for (int pass = 0; pass < kMaxPasses; ++pass) {
+    const uint32_t* in = pass == 0 ? nullptr : lists[(pass - 1) & 1];
+    const unsigned long long* in_n = pass == 0 ? nullptr : &counters[pass - 1];
+    uint32_t* out = pass + 1 < kMaxPasses ? lists[pass & 1] : nullptr;
+    unsigned long long* out_n = pass + 1 < kMaxPasses ? &counters[pass] : nullptr;
+    PT_TRACE(l, s, "k_refit_bl",
+             k_refit_bl<<<l.sms * 8, 128, 0, s>>>(b, (double)p.bfield, (double)x0_barrel,
+                                                   (double)x0_disk, in, in_n, out, out_n, cap));
+  }
 }
 
 }  // namespace ptca

@@ -6,9 +6,13 @@
 
 namespace ptca {
 
-// Replaces b.tracks[0, cnt[CNT_SV]) by their broken-line refits; x0_barrel and
-// x0_disk are the layers' material in radiation lengths at normal incidence (> 0).
+// Passes of the broken-line refit over the cleaned tracks (b.tracks[0, cnt[CNT_SV]),
+// replaced in place); x0_barrel and x0_disk are the layers' material in radiation
+// lengths at normal incidence (> 0).  Scratch: list holds 2 x max_ntuplets track
+// indices and counters kRefitCounters values.
+constexpr int kRefitCounters = 4;
 void launch_refit_broken_line(const Buffers& b, const Params& p, float x0_barrel, float x0_disk,
-                              const Launch& l, cudaStream_t s);
+                              uint32_t* list, unsigned long long* counters, const Launch& l,
+                              cudaStream_t s);
 
 }  // namespace ptca

@@ -236,6 +236,8 @@ struct pt_ctx {
   int n_modules = 0;
   char* raw_mem = nullptr;
   RawBuffers R{};
+  // broken-line refit scratch: two track lists and the pass counters (first use)
+  char* bl_mem = nullptr;
 };
 
 namespace {
@@ -530,6 +532,7 @@ pt_status pt_destroy(pt_ctx* c) {
   if (c->val) cudaFree(c->val);
   if (c->modules) cudaFree(c->modules);
   if (c->raw_mem) cudaFree(c->raw_mem);
+  if (c->bl_mem) cudaFree(c->bl_mem);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->h_off) cudaFreeHost(c->h_off);
   if (c->h_hdr) cudaFreeHost(c->h_hdr);
@@ -649,7 +652,11 @@ pt_status pt_refit_broken_line(pt_ctx* c, float x0_barrel, float x0_disk, int64_
     return fail(PT_ERR_INVALID, "material must be in (0, 1] radiation lengths");
   if (!c->fitted) return fail(PT_ERR_INVALID, "pt_fit_tracks has not run on this batch");
   DeviceGuard guard(c->device);
-  launch_refit_broken_line(c->B, c->P, x0_barrel, x0_disk, c->L, c->stream);
+  const size_t list_bytes = (size_t)c->cap.max_ntuplets * 2 * sizeof(uint32_t);
+  if (!c->bl_mem)
+    PT_CUDA(cudaMalloc(&c->bl_mem, list_bytes + kRefitCounters * sizeof(unsigned long long)));
+  launch_refit_broken_line(c->B, c->P, x0_barrel, x0_disk, (uint32_t*)c->bl_mem,
+                           (unsigned long long*)(c->bl_mem + list_bytes), c->L, c->stream);
   PT_TRY(last_launch());
   c->vtx_ready = false;
   if (n_tracks) {

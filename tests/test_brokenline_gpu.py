@@ -17,7 +17,7 @@ import pytest
 import oracle
 import sim
 from oracle import brokenline as bl
-from parity import CHI2_REL, assert_fits_close
+from parity import CHI2_REL, FIT_FLOORS, assert_fits_close
 
 pytestmark = pytest.mark.gpu
 
@@ -99,7 +99,9 @@ def test_refit_matches_oracle(cuts, x0b, x0d):
 
 def test_refit_of_a_refit_is_stable(cuts):
     """A second refit takes the first as its reference and lands on the same tracks
-    (the linearisation error is second order)."""
+    within the passes' stopping precision (a pass that moves the curvature by at most
+    1e-3 relative ends them; the slope weights follow the reference, so z0 and
+    cot(theta) settle to the same order): 1e-3 relative with the circle fit's floors."""
     events = _events()[:1]
     with pt.Context(cuts=cuts, capacity=CAP) as ctx:
         _chain(ctx, events)
@@ -107,10 +109,13 @@ def test_refit_of_a_refit_is_stable(cuts):
         a = ctx.pt_get_tracks()
         ctx.pt_refit_broken_line(**MAT)
         b = ctx.pt_get_tracks()
-    ref = np.stack([a[f].astype(np.float64) for f in
-                    ("kappa", "phi0", "d0", "cot_theta", "z0", "pt", "chi2_circle", "chi2_line")]
-                   + [a["charge"].astype(np.float64)], axis=1)
-    assert_fits_close(b, ref)
+    assert np.array_equal(a["charge"], b["charge"])
+    for name, floor in FIT_FLOORS.items():
+        r = a[name].astype(np.float64)
+        d = np.abs(b[name].astype(np.float64) - r)
+        if name == "phi0":
+            d = np.abs(np.remainder(d + np.pi, 2 * np.pi) - np.pi)
+        assert np.all(d <= 1e-3 * np.maximum(np.abs(r), floor)), name
 
 
 def test_refit_errors(cuts):
