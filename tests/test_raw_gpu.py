@@ -107,6 +107,18 @@ def test_raw_input_errors(cuts):
         with pytest.raises(pt.PtError) as err:
             ctx.pt_load_raw([0, big.size], big)
         assert err.value.status == pt.PT_ERR_CAPACITY
+        # the same errors inside runs long enough for the block-per-run launch
+        grid = [(r, c, 9) for r in range(0, 60, 3) for c in range(0, 45, 3)]  # 300 isolated
+        long_bad = _words(5, grid[:150] + [(200, 1, 9), (199, 1, 9)] + grid[152:])
+        assert long_bad.size == 300
+        with pytest.raises(pt.PtError) as err:
+            ctx.pt_load_raw([0, long_bad.size], long_bad)
+        assert err.value.status == pt.PT_ERR_INVALID
+        blob = [(r, c, 9) for r in range(100, 112) for c in range(0, 12)]  # 144 pixels
+        long_big = _words(5, sorted(grid[:200] + blob))
+        with pytest.raises(pt.PtError) as err:
+            ctx.pt_load_raw([0, long_big.size], long_big)
+        assert err.value.status == pt.PT_ERR_CAPACITY
         with pytest.raises(ValueError):
             ctx.pt_load_raw([0, 3], good)  # offsets beyond the digis given
         # a valid batch after the errors works again
