@@ -78,9 +78,9 @@ static int near_thr(float lhs, float rhs) {
 
 /* Outcome bookkeeping for one candidate: pass/fail of the AND of its cuts, plus
  * whether a cut close to its threshold could decide the outcome. */
-typedef struct { int fail_far; int fail_near; int pass_near; } verdict;
+typedef struct { int fail_far; int fail_near; int pass_near; } cut_tally;
 
-static void judge(verdict* v, int pass, float lhs, float rhs) {
+static void classify(cut_tally* v, int pass, float lhs, float rhs) {
   int nr = near_thr(lhs, rhs);
   if (pass) { if (nr) v->pass_near = 1; }
   else if (nr) v->fail_near = 1;
@@ -94,24 +94,24 @@ static void judge(verdict* v, int pass, float lhs, float rhs) {
  * flip under a 1e-6 relative change of a cut variable. */
 static int doublet_ok(const orc_cuts* c, float xi, float yi, float zi, float ri, float xo,
                       float yo, float zo, float ro, int* near) {
-  verdict v = {0, 0, 0};
+  cut_tally v = {0, 0, 0};
   float dx = xo - xi, dy = yo - yi, dr = ro - ri, dz = zo - zi;
-  judge(&v, dr > 0.0f, dr, 0.0f);
+  classify(&v, dr > 0.0f, dr, 0.0f);
   if (v.fail_far) { *near = 0; return 0; }
   float dot = (xi * xo) + (yi * yo);
-  judge(&v, dot > 0.0f, dot, 0.0f);
+  classify(&v, dot > 0.0f, dot, 0.0f);
   if (v.fail_far) { *near = 0; return 0; }
   float l3 = fabsf((zi * dr) - (ri * dz));
   float r3 = c->z0max * dr;
-  judge(&v, l3 <= r3, l3, r3);
+  classify(&v, l3 <= r3, l3, r3);
   if (v.fail_far) { *near = 0; return 0; }
   float l4 = fabsf(dz);
   float r4 = c->cotmax * dr;
-  judge(&v, l4 <= r4, l4, r4);
+  classify(&v, l4 <= r4, l4, r4);
   if (v.fail_far) { *near = 0; return 0; }
   float l2 = fabsf((xi * yo) - (yi * xo)) * 2.0f;
   float r2 = c->kmax * ((ri * ro) * sqrtf((dx * dx) + (dy * dy)));
-  judge(&v, l2 <= r2, l2, r2);
+  classify(&v, l2 <= r2, l2, r2);
   if (v.fail_far) { *near = 0; return 0; }
   *near = v.fail_near || v.pass_near;
   return !v.fail_near;
@@ -125,10 +125,10 @@ static int doublet_ok(const orc_cuts* c, float xi, float yi, float zi, float ri,
 static int link_ok(const orc_cuts* c, float x0, float y0, float z0, float r0, int layer0,
                    float x1, float y1, float z1, float r1, float x2, float y2, float z2,
                    float r2, int* near, float* quality) {
-  verdict v = {0, 0, 0};
+  cut_tally v = {0, 0, 0};
   float lc1 = fabsf(((z1 - z0) * (r2 - r0)) - ((z2 - z0) * (r1 - r0)));
   float rc1 = (c->rz0 * (r2 - r0)) + (c->rz1 * fabsf(z2 - z0));
-  judge(&v, lc1 <= rc1, lc1, rc1);
+  classify(&v, lc1 <= rc1, lc1, rc1);
   if (v.fail_far) { *near = 0; return 0; }
   float ax = x1 - x0, ay = y1 - y0;
   float bx = x2 - x0, by = y2 - y0;
@@ -138,7 +138,7 @@ static int link_ok(const orc_cuts* c, float x0, float y0, float z0, float r0, in
   float cr = (ax * by) - (ay * bx);
   float lc2 = fabsf(cr) * 2.0f;
   float rc2 = c->kmax * ((sqrtf(a2) * sqrtf(b2)) * sqrtf((cx * cx) + (cy * cy)));
-  judge(&v, lc2 <= rc2, lc2, rc2);
+  classify(&v, lc2 <= rc2, lc2, rc2);
   if (v.fail_far) { *near = 0; return 0; }
   float D = cr * 2.0f;
   float ux = (by * a2) - (ay * b2);
@@ -150,7 +150,7 @@ static int link_ok(const orc_cuts* c, float x0, float y0, float z0, float r0, in
   float dcamax = layer0 == 0 ? c->dca_b0 : c->dca_other;
   float lc3 = fabsf(num);
   float rc3 = dcamax * den;
-  judge(&v, lc3 <= rc3, lc3, rc3);
+  classify(&v, lc3 <= rc3, lc3, rc3);
   if (v.fail_far) { *near = 0; return 0; }
   *near = v.fail_near || v.pass_near;
   *quality = lc3 / den;
