@@ -383,12 +383,13 @@ __global__ void __launch_bounds__(128) k_refit_bl(Buffers b, double bfield, doub
 
 }  // namespace
 
-void launch_refit_broken_line(const Buffers& b, const Params& p, float x0_barrel, float x0_disk,
-                              uint32_t* list, unsigned long long* counters, const Launch& l,
-                              cudaStream_t s) {
+cudaError_t launch_refit_broken_line(const Buffers& b, const Params& p, float x0_barrel,
+                                     float x0_disk, uint32_t* list, unsigned long long* counters,
+                                     const Launch& l, cudaStream_t s) {
   const uint64_t cap = (uint64_t)p.max_ntuplets;
   uint32_t* lists[2] = {list, list + cap};
-  cudaMemsetAsync(counters, 0, kMaxPasses * sizeof(unsigned long long), s);
+  const cudaError_t e = cudaMemsetAsync(counters, 0, kMaxPasses * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
   for (int pass = 0; pass < kMaxPasses; ++pass) {
     const uint32_t* in = pass == 0 ? nullptr : lists[(pass - 1) & 1];
     const unsigned long long* in_n = pass == 0 ? nullptr : &counters[pass - 1];
@@ -398,6 +399,7 @@ void launch_refit_broken_line(const Buffers& b, const Params& p, float x0_barrel
              k_refit_bl<<<l.sms * 8, 128, 0, s>>>(b, (double)p.bfield, (double)x0_barrel,
                                                    (double)x0_disk, in, in_n, out, out_n, cap));
   }
+  return cudaGetLastError();
 }
 
 }  // namespace ptca

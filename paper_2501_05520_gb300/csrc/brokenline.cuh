@@ -11,8 +11,8 @@ namespace ptca {
 // lengths at normal incidence (> 0).  Scratch: list holds 2 x max_ntuplets track
 // indices and counters kRefitCounters values.
 constexpr int kRefitCounters = 4;
-void launch_refit_broken_line(const Buffers& b, const Params& p, float x0_barrel, float x0_disk,
-                              uint32_t* list, unsigned long long* counters, const Launch& l,
-                              cudaStream_t s);
+cudaError_t launch_refit_broken_line(const Buffers& b, const Params& p, float x0_barrel,
+                                     float x0_disk, uint32_t* list, unsigned long long* counters,
+                                     const Launch& l, cudaStream_t s);
 
 }  // namespace ptca

@@ -655,8 +655,9 @@ pt_status pt_refit_broken_line(pt_ctx* c, float x0_barrel, float x0_disk, int64_
   const size_t list_bytes = (size_t)c->cap.max_ntuplets * 2 * sizeof(uint32_t);
   if (!c->bl_mem)
     PT_CUDA(cudaMalloc(&c->bl_mem, list_bytes + kRefitCounters * sizeof(unsigned long long)));
-  launch_refit_broken_line(c->B, c->P, x0_barrel, x0_disk, (uint32_t*)c->bl_mem,
-                           (unsigned long long*)(c->bl_mem + list_bytes), c->L, c->stream);
+  PT_CUDA(launch_refit_broken_line(c->B, c->P, x0_barrel, x0_disk, (uint32_t*)c->bl_mem,
+                                   (unsigned long long*)(c->bl_mem + list_bytes), c->L,
+                                   c->stream));
   PT_TRY(last_launch());
   c->vtx_ready = false;
   if (n_tracks) {
