@@ -41,7 +41,8 @@ constexpr int kBigBlocksPerSm = 4;
 constexpr int kLoadBatch = 8;           // digis per lane loaded before use
 constexpr uint32_t kAdcMax = 4095;
 
-// Per-warp working set of one run of at most CAP pixels (22 bytes a pixel).
+// Working set of one run of at most CAP pixels (22 bytes a pixel): one per warp in the
+// warp-per-run launch, one per block in the block-per-run launch.
 template <int CAP>
 struct RawWarp {
   uint32_t key[CAP];   // row << 12 | col
