@@ -159,8 +159,10 @@ def _peaks() -> dict:
     return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-def cpu_baseline(n_events: int | None = None, seed0: int = SEED0 + 500) -> dict:
-    """The oracle as it stands, one PU200 event per host thread."""
+def cpu_baseline(n_events: int | None = None, seed0: int = SEED0 + 500,
+                 one_thread: bool = True) -> dict:
+    """The oracle as it stands, one PU200 event per host thread (and, with one_thread,
+    the first event alone on one thread before that)."""
     import oracle
     import paper_2501_05520_gb300 as pt
     cuts = pt.default_cuts()
@@ -168,13 +170,22 @@ def cpu_baseline(n_events: int | None = None, seed0: int = SEED0 + 500) -> dict:
     n = n_events or max(1, min(cores, 16))
     evs = make_events(n, seed0)
     oracle.build()
+    dt1 = None
+    if one_thread:
+        t1 = time.perf_counter()
+        oracle.reconstruct(evs[0].x, evs[0].y, evs[0].z, evs[0].layer, cuts)
+        dt1 = time.perf_counter() - t1
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=min(cores, n)) as ex:
         list(ex.map(lambda e: oracle.reconstruct(e.x, e.y, e.z, e.layer, cuts), evs))
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "events/s", "cores": min(cores, n), "kind": "oracle",
-            "sample": f"{n} PU200 events (seeds {seed0}..{seed0 + n - 1}), one per thread, "
-                      f"{platform.machine()} host, {dt:.1f} s"}
+    out = {"value": n / dt, "unit": "events/s", "cores": min(cores, n), "kind": "oracle",
+           "sample": f"{n} PU200 events (seeds {seed0}..{seed0 + n - 1}), one per thread, "
+                     f"{platform.machine()} host, {dt:.1f} s", "host_cores": cores}
+    if dt1 is not None:
+        out["one_thread"] = {"value": 1.0 / dt1, "unit": "events/s",
+                             "sample": f"event {seed0} alone, {dt1:.1f} s"}
+    return out
 
 
 def _dist_env():
@@ -212,11 +223,11 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     per_step = max(1, min(cores, 16))
     for w in range(args.warmup):
-        cpu_baseline(per_step, seed0=SEED0 + 700 + w * per_step)
+        cpu_baseline(per_step, seed0=SEED0 + 700 + w * per_step, one_thread=False)
     vals = []
     t_all = 0.0
     for s in range(args.steps):
-        r = cpu_baseline(per_step, seed0=SEED0 + s * per_step)
+        r = cpu_baseline(per_step, seed0=SEED0 + s * per_step, one_thread=False)
         vals.append(r)
         t_all += per_step / r["value"]
     value = args.steps * per_step / t_all
