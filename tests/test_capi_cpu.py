@@ -51,3 +51,30 @@ def test_workspace_size_and_capacity_validation():
 
 def test_build_is_incremental():
     assert pkg_build.up_to_date()
+
+
+def test_null_handles_are_rejected_before_any_cuda_call():
+    """Every call that takes a context or server answers a NULL handle with
+    PT_ERR_INVALID and a message (destroy accepts NULL), without touching CUDA."""
+    L = pt.lib()
+    calls = {
+        "pt_build_doublets": (None, None), "pt_connect_cells": (None, None),
+        "pt_find_ntuplets": (None, None), "pt_fit_tracks": (None, None),
+        "pt_refit_broken_line": (None, 0.02, 0.02, None),
+        "pt_find_vertices": (None, 4, 0.02, None),
+        "pt_get_vertices": (None, None, None, None, 0, None, 0),
+        "pt_set_modules": (None, None, 0),
+        "pt_load_raw": (None, 1, None, None, 0, None),
+        "pt_get_hits": (None, None, None, None, None, None, 0, None),
+        "pt_get_ntuplets": (None, None, None, None, 0, None, 0),
+        "pt_get_tracks": (None, None, 0, None, 0),
+        "pt_set_tracing": (None, 1), "pt_get_trace": (None, None, 0, None),
+        "pt_submit": (None, 0, None, None, None, None, None),
+        "pt_poll": (None, 0, 0, None, None, None, 0, None),
+        "pt_server_stats": (None, None, None, None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == pt.PT_ERR_INVALID, name
+        assert L.pt_last_error().decode(), name
+    assert L.pt_destroy(None) == pt.PT_OK
+    assert L.pt_server_destroy(None) == pt.PT_OK
