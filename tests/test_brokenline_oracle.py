@@ -187,3 +187,53 @@ def test_iterated_refit_is_a_fixed_point():
         worst_after = max(worst_after, abs(again[0] - it[0]) / abs(it[0]))
     assert worst_first > 0.02
     assert worst_after < 1e-4
+
+
+def _arc_tangents(p0, p1, R, q):
+    """Unit tangents at p0 and p1 of the minor arc of radius R from p0 to p1, turning
+    clockwise for q > 0 and counter-clockwise for q < 0."""
+    u = p1 - p0
+    lu = np.hypot(u[0], u[1])
+    m = 0.5 * (p0 + p1)
+    b = math.sqrt(max(R * R - 0.25 * lu * lu, 0.0))
+    right = np.array([u[1], -u[0]]) / lu
+    c = m + (b if q > 0 else -b) * right
+
+    def tangent(pt):
+        r = pt - c
+        t = np.array([r[1], -r[0]]) if q > 0 else np.array([-r[1], r[0]])
+        return t / np.hypot(t[0], t[1])
+
+    return tangent(p0), tangent(p1)
+
+
+def test_generator_scattering_follows_highland():
+    """Noiseless barrel tracks at eta = 0 (all scattering in the transverse direction
+    shows as a turn of the arc): the turn at each interior layer, measured from the arcs
+    of known radius through consecutive hits, divided by the Highland width for that
+    crossing (13.6 MeV / p sqrt(t)(1 + 0.038 ln t), t = x0 / cos(incidence)) has mean 0
+    and width 1 (2 x 2000 turns: 3 sigma is 0.05 on the width)."""
+    x0, n = 0.03, 2000
+    rng = np.random.default_rng(21)
+    pt_ = np.full(n, 0.8)
+    p = dict(pt=pt_, eta=np.zeros(n), phi0=rng.uniform(0, 2 * np.pi, n),
+             q=np.where(rng.random(n) < 0.5, -1.0, 1.0), z0=np.zeros(n),
+             R=pt_ / (E.C_LIGHT * E.BFIELD_T) * 100.0)
+    pid, lay, x, y, z, step = E._crossings_ms(rng, p, True, x0, x0)
+    pulls = []
+    for i in range(n):
+        m = np.flatnonzero(pid == i)
+        m = m[np.argsort(step[m])]
+        assert lay[m].tolist() == [0, 1, 2, 3]
+        pts = [np.array([x[k], y[k]]) for k in m]
+        R, q = p["R"][i], p["q"][i]
+        for j in (1, 2):
+            _, t_in = _arc_tangents(pts[j - 1], pts[j], R, q)
+            t_out, _ = _arc_tangents(pts[j], pts[j + 1], R, q)
+            turn = math.atan2(t_in[0] * t_out[1] - t_in[1] * t_out[0], t_in @ t_out)
+            cos_inc = abs(t_in @ pts[j]) / np.hypot(*pts[j])
+            t = x0 / cos_inc
+            th0 = 0.0136 / 0.8 * math.sqrt(t) * (1.0 + 0.038 * math.log(t))
+            pulls.append(math.tan(turn) / th0)
+    pulls = np.asarray(pulls)
+    assert abs(pulls.mean()) < 0.07 and 0.95 < pulls.std() < 1.05
