@@ -161,8 +161,8 @@ pt_status pt_load_batch(pt_ctx* ctx, int n_events, const int64_t* hit_offsets, c
                         const float* y, const float* z, const uint8_t* layer, int on_device);
 
 /* Detector module table of the pixel readout, used by pt_load_raw (Sec. 2.2.1, Fig. 2:
- * detector information such as the location of each layer and the detector indices is
- * preloaded on the GPU).  modules[i] describes module index i; n in [1, 2^24).  The table
+ * the fixed description of the detector's layers and module numbering sits on the GPU
+ * before any event arrives).  modules[i] describes module index i; n in [1, 2^24).  The table
  * is copied into a device buffer that the context allocates and keeps.  PT_ERR_INVALID
  * for a layer code > 9, a kind other than 0/1, ncol or nrow outside [1, 4096] or a
  * non-finite float. */
