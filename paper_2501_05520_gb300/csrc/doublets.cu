@@ -1,6 +1,6 @@
 // Stage A2: doublets ("cells").  Every hit is paired with the hits of each adjacent
-// outer layer that pass the cuts D0..D4 (Sec. 2.2.1, Fig. 2: hits in adjacent layers
-// are paired to form doublets).
+// outer layer that pass the cuts D0..D4 (Sec. 2.2.1, Fig. 2: the chain's first
+// combinatorial step joins hits of neighbouring layers two by two).
 //
 // A warp searches the doublets of one inner hit at a time.  For each outer layer the
 // candidates are the hits of the

@@ -1,5 +1,5 @@
-// Stage A7: per-candidate helix fit (Sec. 2.2.1, Fig. 2: a fit is applied to determine
-// the track parameters).  Circle in the transverse plane by the closed-form fit of
+// Stage A7: per-candidate helix fit (Sec. 2.2.1, Fig. 2: each picked group of hits is
+// fitted, which yields its track parameters).  Circle in the transverse plane by the closed-form fit of
 // V. Karimaki (NIM A305 (1991) 187) with equal weights, then z = z0 + cot(theta) s by
 // least squares in the transverse arc length s from the point of closest approach.
 //
