@@ -52,7 +52,7 @@ NCU_TRAFFIC = {
     "k_doublets": {"bytes_per_event": 19105312, "issue_active_pct": 68.1, "sha": "30d941786a35"},
     "k_in_scatter": {"bytes_per_event": 35091680, "issue_active_pct": 19.6, "sha": "efe768eb76c3"},
     "k_connect": {"bytes_per_event": 29828608, "issue_active_pct": 71.5, "sha": "efe768eb76c3"},
-    "k_find_ntuplets": {"bytes_per_event": 47944064, "issue_active_pct": 16.0, "sha": "d586515131b3"},
+    "k_find_ntuplets": {"bytes_per_event": 47944064, "issue_active_pct": 16.0, "sha": "bea2a2a22db7"},
 }
 
 

@@ -205,8 +205,8 @@ pt_status pt_build_doublets(pt_ctx* ctx, int64_t* n_cells);
 pt_status pt_connect_cells(pt_ctx* ctx, int64_t* n_links);
 
 /* Ntuplets: every path of linked cells from a cell without an incoming link to a cell
- * without an outgoing link, 3..6 hits (Sec. 2.2.1: a group of hits that may form a
- * track is picked), then duplicate cleaning and canonical ordering.  n_ntuplets
+ * without an outgoing link, 3..6 hits (Sec. 2.2.1: the chain selects candidate sets of
+ * hits), then duplicate cleaning and canonical ordering.  n_ntuplets
  * receives the number of cleaned ntuplets. */
 pt_status pt_find_ntuplets(pt_ctx* ctx, int64_t* n_ntuplets);
 
@@ -243,8 +243,8 @@ pt_status pt_get_ntuplets(pt_ctx* ctx, int32_t* hits, uint8_t* nhits, int64_t* e
 pt_status pt_get_tracks(pt_ctx* ctx, pt_track* tracks, int64_t cap, int64_t* n, int on_device);
 
 /* Primary vertices of the fitted tracks (Sec. 2.2.1: vertex reconstruction is the last
- * of the chain's sub-algorithms, and the reconstructed tracks and vertices are what it
- * returns, Fig. 2; the paper gives no algorithm).  Per event: the tracks with at least
+ * of the chain's sub-algorithms, and Fig. 2 has the chain hand back both tracks and
+ * vertices; the paper gives no algorithm).  Per event: the tracks with at least
  * min_hits hits (3..6; 4 keeps quadruplets and longer) and a finite z0 are ordered by
  * z0 (ties: canonical track order) and the list is cut wherever the float32 step to
  * the next z0 exceeds dz (cm, > 0; a step of exactly dz does not cut); every group of

@@ -5,10 +5,10 @@
  * library.  It shares no code with the CUDA path.  It is deliberately plain: every
  * stage is the definition written out, with no binning, blocking or reordering.
  *
- * What it computes (the paper's Patatrack chain, Sec. 2.2.1 and Fig. 2: hits on
- * adjacent layers are paired into doublets, doublets sharing a hit are paired into
- * triplets by a cellular automaton, hit groups that may form a track are picked,
- * and a fit gives the track parameters).  The paper prints no cut formula, constant
+ * What it computes (the paper's Patatrack chain, Sec. 2.2.1 and Fig. 2: hits of
+ * neighbouring layers are joined two by two, a cellular automaton chains those pairs
+ * when they share a hit, chains long enough to be track candidates are selected, and
+ * each candidate is fitted for its parameters).  The paper prints no cut formula, constant
  * or fit equation, so the concrete predicates below are this library's readings:
  *
  *   r = sqrt(x*x + y*y)                                   (per hit, float32)

@@ -4,8 +4,8 @@ TEST INFRASTRUCTURE ONLY: the tests and the benchmark's CPU-baseline leg are the
 callers; the product never loads it.  It shares no code with the CUDA path.
 
 The paper lists vertex reconstruction as the last of Patatrack's sub-algorithms and
-says that the reconstructed tracks and vertices are what the chain returns (Sec.
-2.2.1 and the caption of Fig. 2); it gives no algorithm.  This library's reading (the
+has the chain hand back vertices along with the tracks (Sec. 2.2.1 and the caption
+of Fig. 2); it gives no algorithm.  This library's reading (the
 plain definition the GPU must reproduce):
 
   [V1] The input of an event is its cleaned, fitted tracks with at least `min_hits`

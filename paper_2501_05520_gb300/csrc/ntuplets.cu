@@ -1,6 +1,6 @@
 // Stages A4-A6: ntuplet extraction, canonical order and duplicate cleaning (Sec.
-// 2.2.1, Fig. 2: from the seeds, a group of hits that potentially forms a track is
-// picked).
+// 2.2.1, Fig. 2: starting from the seeds, the chain selects the sets of hits that are
+// candidate tracks).
 //
 // A4  every path of linked cells from a root (a cell with no incoming link) to a leaf
 //     (a cell with no outgoing link) with 3..6 hits.  Roots are taken among the sources
