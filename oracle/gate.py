@@ -1,7 +1,7 @@
 """CPU oracle of the learned link gate (TEST INFRASTRUCTURE ONLY).
 
-Callers: the tests and the training driver's checks.  Shares no code with the CUDA
-path.  Float64 throughout unless stated.
+Callers: the tests only (the training script runs the library's own kernels).  Shares
+no code with the CUDA path.  Float64 throughout unless stated.
 
 The gate is a small MLP that scores each accepted cell link (h0 -> h1 -> h2) and drops
 links whose score is below a threshold before the ntuplet search.  It is the library's

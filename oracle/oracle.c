@@ -372,7 +372,7 @@ int64_t orc_dedup(int64_t T, const int32_t* hits, const int32_t* cells, const in
   return S;
 }
 
-/* ----------------------------------------------------------------------- driver */
+/* ------------------------------------------------------------------ whole chain */
 /* link_keep (optional, may be NULL): one flag per link accepted by the cuts, in the
  * order the plain run lists them (cell a major); links with flag 0 are removed before
  * the ntuplet search (the learned gate's decision, computed by the caller). */

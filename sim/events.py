@@ -1,7 +1,7 @@
 """Seeded synthetic pixel events: charged helices in a solenoid, plus uniform noise.
 
-This module is the input recipe shared by the tests, the benchmark and the training
-driver.  It contains no reconstruction arithmetic: it draws particles, intersects
+This module is the input recipe shared by the tests, the benchmark and the gate
+training script.  It contains no reconstruction arithmetic: it draws particles, intersects
 their helices with the detector surfaces and smears the crossings.
 
 Units: cm, GeV, tesla.  Magnetic field along +z.
