@@ -25,6 +25,19 @@ _lib = None
 FIT_FIELDS = ("kappa", "phi0", "d0", "cot_theta", "z0", "pt", "chi2_circle", "chi2_line",
               "charge")
 
+# The chain's (inner, outer) layer pairs: consecutive surfaces a primary track can cross.
+DEFAULT_PAIRS = ((0, 1), (1, 2), (2, 3), (0, 4), (1, 4), (2, 4), (4, 5), (5, 6),
+                 (0, 7), (1, 7), (2, 7), (7, 8), (8, 9))
+
+
+def gap_pairs(pairs=DEFAULT_PAIRS) -> tuple:
+    """[G1] Skip-layer pairs: (a, c) for every two-step path a -> b -> c of the pair graph
+    that is not itself a pair (a track that misses the surface b still joins a and c),
+    in (a, c) order."""
+    allowed = set(pairs)
+    out = {(a, c) for a, b in pairs for b2, c in pairs if b2 == b and (a, c) not in allowed}
+    return tuple(sorted(out))
+
 
 class Cuts(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_float), ("z0max", ctypes.c_float), ("cotmax", ctypes.c_float),
@@ -55,6 +68,9 @@ def _load():
         lib.orc_reconstruct_masked.restype = P
         lib.orc_reconstruct_masked.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.POINTER(Cuts),
                                                ctypes.c_double, P, ctypes.c_int64]
+        lib.orc_reconstruct_pairs.restype = P
+        lib.orc_reconstruct_pairs.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.POINTER(Cuts),
+                                              ctypes.c_double, ctypes.c_int, P, P]
         for name in ("orc_sizes", "orc_get_radius", "orc_get_near"):
             getattr(lib, name).argtypes = [P, P]
         lib.orc_get_cells.argtypes = [P, P, P]
@@ -79,11 +95,14 @@ def make_cuts(d: dict) -> Cuts:
     return Cuts(*(float(np.float32(d[f])) for f, _ in Cuts._fields_))
 
 
-def reconstruct(x, y, z, layer, cuts: dict, bfield: float = 3.8, link_keep=None) -> dict:
+def reconstruct(x, y, z, layer, cuts: dict, bfield: float = 3.8, link_keep=None,
+                pairs=None) -> dict:
     """Run the whole chain on one event.  Hit arrays are float32 / uint8, input order.
 
     link_keep: optional bool array, one entry per link of the plain run (its link order);
     links with False are removed before the ntuplet search (a gate decision).
+    pairs: optional (inner, outer) layer-pair table replacing DEFAULT_PAIRS (e.g.
+    DEFAULT_PAIRS + gap_pairs()); not combined with link_keep.
 
     Returns a dict of numpy arrays:
       r                      float32 [N]
@@ -102,7 +121,17 @@ def reconstruct(x, y, z, layer, cuts: dict, bfield: float = 3.8, link_keep=None)
     layer = np.ascontiguousarray(layer, np.uint8)
     n = x.shape[0]
     c = make_cuts(cuts)
-    if link_keep is None:
+    if pairs is not None:
+        if link_keep is not None:
+            raise ValueError("pairs and link_keep are not combined")
+        pt = np.ascontiguousarray(np.asarray(pairs, np.int32).reshape(-1, 2).T)
+        pin, pout = np.ascontiguousarray(pt[0]), np.ascontiguousarray(pt[1])
+        h = lib.orc_reconstruct_pairs(n, _ptr(x), _ptr(y), _ptr(z), _ptr(layer),
+                                      ctypes.byref(c), float(bfield), int(pin.size), _ptr(pin),
+                                      _ptr(pout))
+        if not h:
+            raise ValueError("invalid layer-pair table")
+    elif link_keep is None:
         h = lib.orc_reconstruct(n, _ptr(x), _ptr(y), _ptr(z), _ptr(layer), ctypes.byref(c),
                                 float(bfield))
     else:

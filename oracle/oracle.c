@@ -31,6 +31,7 @@
 #define ORC_MAX_CELLS (ORC_MAX_HITS - 1)
 #define ORC_N_LAYERS 10
 #define ORC_N_PAIRS 13
+#define ORC_MAX_PAIRS 64
 #define ORC_PI 3.14159265358979323846
 
 typedef struct {
@@ -376,18 +377,46 @@ int64_t orc_dedup(int64_t T, const int32_t* hits, const int32_t* cells, const in
 /* link_keep (optional, may be NULL): one flag per link accepted by the cuts, in the
  * order the plain run lists them (cell a major); links with flag 0 are removed before
  * the ntuplet search (the learned gate's decision, computed by the caller). */
-orc_result* orc_reconstruct_masked(int64_t n, const float* x, const float* y, const float* z,
-                                   const uint8_t* layer, const orc_cuts* cuts, double bfield,
-                                   const uint8_t* link_keep, int64_t n_keep);
+/* The chain over the layer pairs pin[p] -> pout[p], p < n_pairs. */
+static orc_result* reconstruct_pairs(int64_t n, const float* x, const float* y, const float* z,
+                                     const uint8_t* layer, const orc_cuts* cuts, double bfield,
+                                     int n_pairs, const int* pin, const int* pout,
+                                     const uint8_t* link_keep, int64_t n_keep);
 
 orc_result* orc_reconstruct(int64_t n, const float* x, const float* y, const float* z,
                             const uint8_t* layer, const orc_cuts* cuts, double bfield) {
-  return orc_reconstruct_masked(n, x, y, z, layer, cuts, bfield, NULL, 0);
+  return reconstruct_pairs(n, x, y, z, layer, cuts, bfield, ORC_N_PAIRS, PAIR_IN, PAIR_OUT,
+                           NULL, 0);
 }
 
 orc_result* orc_reconstruct_masked(int64_t n, const float* x, const float* y, const float* z,
                                    const uint8_t* layer, const orc_cuts* cuts, double bfield,
                                    const uint8_t* link_keep, int64_t n_keep) {
+  return reconstruct_pairs(n, x, y, z, layer, cuts, bfield, ORC_N_PAIRS, PAIR_IN, PAIR_OUT,
+                           link_keep, n_keep);
+}
+
+/* The chain over a caller's layer-pair table (at most ORC_MAX_PAIRS pairs of layer
+ * codes < ORC_N_LAYERS, inner != outer); NULL for an invalid table. */
+orc_result* orc_reconstruct_pairs(int64_t n, const float* x, const float* y, const float* z,
+                                  const uint8_t* layer, const orc_cuts* cuts, double bfield,
+                                  int n_pairs, const int32_t* pin, const int32_t* pout) {
+  int ti[ORC_MAX_PAIRS], to[ORC_MAX_PAIRS];
+  if (n_pairs < 1 || n_pairs > ORC_MAX_PAIRS) return NULL;
+  for (int p = 0; p < n_pairs; ++p) {
+    if (pin[p] < 0 || pin[p] >= ORC_N_LAYERS || pout[p] < 0 || pout[p] >= ORC_N_LAYERS ||
+        pin[p] == pout[p])
+      return NULL;
+    ti[p] = pin[p];
+    to[p] = pout[p];
+  }
+  return reconstruct_pairs(n, x, y, z, layer, cuts, bfield, n_pairs, ti, to, NULL, 0);
+}
+
+static orc_result* reconstruct_pairs(int64_t n, const float* x, const float* y, const float* z,
+                                     const uint8_t* layer, const orc_cuts* cuts, double bfield,
+                                     int n_pairs, const int* pin, const int* pout,
+                                     const uint8_t* link_keep, int64_t n_keep) {
   int64_t lidx = 0; /* index among all links accepted by the cuts */
   orc_result* R = (orc_result*)calloc(1, sizeof(orc_result));
   R->n_hits = n;
@@ -402,9 +431,9 @@ orc_result* orc_reconstruct_masked(int64_t n, const float* x, const float* y, co
     if (layer[i] < ORC_N_LAYERS) iv_push(&by_layer[layer[i]], (int32_t)i);
 
   /* doublets: every (inner, outer) hit pair of every allowed layer pair */
-  for (int p = 0; p < ORC_N_PAIRS; ++p) {
-    const ivec* LI = &by_layer[PAIR_IN[p]];
-    const ivec* LO = &by_layer[PAIR_OUT[p]];
+  for (int p = 0; p < n_pairs; ++p) {
+    const ivec* LI = &by_layer[pin[p]];
+    const ivec* LO = &by_layer[pout[p]];
     for (int64_t a = 0; a < LI->n; ++a) {
       int32_t i = LI->v[a];
       for (int64_t b = 0; b < LO->n; ++b) {

@@ -94,6 +94,7 @@ class GenConfig:
     smear: bool = True
     x0_barrel: float = 0.0  # radiation lengths per barrel layer (0: no scattering)
     x0_disk: float = 0.0    # radiation lengths per disk
+    hit_eff: float = 1.0    # probability that a crossing gives a hit (1: every crossing)
 
 
 # The five workloads.  Sizes and spectra follow the library's benchmark definitions.
@@ -339,6 +340,9 @@ def generate(cfg: GenConfig, seed: int, n_particles: int | None = None,
                                                 cfg.x0_disk)
     else:
         pid, lay, xt, yt, zt = _crossings(p, cfg.barrel_only)
+    if cfg.hit_eff < 1.0:  # inefficient sensors: each crossing kept independently
+        keep = rng.random(pid.shape[0]) < cfg.hit_eff
+        pid, lay, xt, yt, zt = pid[keep], lay[keep], xt[keep], yt[keep], zt[keep]
     if cfg.smear:
         xs, ys, zs = _smear(rng, lay, xt, yt, zt)
     else:

@@ -21,8 +21,10 @@ _ALLOWED = set(LAYER_PAIRS)
 _DEPTH = np.array([0, 1, 2, 3, 4, 5, 6, 4, 5, 6])
 
 
-def particle_chains(pid: np.ndarray, layer: np.ndarray) -> dict:
-    """Per particle: its hits ordered along the track, and the longest allowed chain."""
+def particle_chains(pid: np.ndarray, layer: np.ndarray, pairs=LAYER_PAIRS) -> dict:
+    """Per particle: its hits ordered along the track, and the longest chain of hits whose
+    consecutive layers are pairs of `pairs`."""
+    allowed = _ALLOWED if pairs is LAYER_PAIRS else set(map(tuple, pairs))
     out = {}
     order = np.argsort(pid, kind="stable")
     ps = pid[order]
@@ -33,7 +35,7 @@ def particle_chains(pid: np.ndarray, layer: np.ndarray) -> dict:
         hits = grp[np.argsort(_DEPTH[layer[grp]], kind="stable")]
         best, cur = [hits[0]], [hits[0]]
         for h in hits[1:]:
-            if (int(layer[cur[-1]]), int(layer[h])) in _ALLOWED:
+            if (int(layer[cur[-1]]), int(layer[h])) in allowed:
                 cur.append(h)
             else:
                 cur = [h]
@@ -113,9 +115,11 @@ def match_fast(ntuplets: np.ndarray, pid: np.ndarray) -> np.ndarray:
     return np.where(same, first, -1).astype(np.int64)
 
 
-def rates_fast(ntuplets: np.ndarray, pid: np.ndarray, layer: np.ndarray) -> dict:
-    """`rates` with frac = 1, vectorised over ntuplets."""
-    chains = particle_chains(pid, layer)
+def rates_fast(ntuplets: np.ndarray, pid: np.ndarray, layer: np.ndarray,
+               pairs=LAYER_PAIRS) -> dict:
+    """`rates` with frac = 1, vectorised over ntuplets; reconstructable particles are
+    those with a chain of >= 3 hits on `pairs`."""
+    chains = particle_chains(pid, layer, pairs)
     reco = np.array([p for p, c in chains.items() if c["chain"].size >= 3], np.int64)
     m = match_fast(ntuplets, pid)
     matched, counts = np.unique(m[m >= 0], return_counts=True)
