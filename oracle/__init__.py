@@ -31,7 +31,7 @@ DEFAULT_PAIRS = ((0, 1), (1, 2), (2, 3), (0, 4), (1, 4), (2, 4), (4, 5), (5, 6),
 
 
 def gap_pairs(pairs=DEFAULT_PAIRS) -> tuple:
-    """[G1] Skip-layer pairs: (a, c) for every two-step path a -> b -> c of the pair graph
+    """[L1] Skip-layer pairs: (a, c) for every two-step path a -> b -> c of the pair graph
     that is not itself a pair (a track that misses the surface b still joins a and c),
     in (a, c) order."""
     allowed = set(pairs)
