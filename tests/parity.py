@@ -10,7 +10,8 @@ import numpy as np
 # cm, 1, cm) cover parameters near zero, where float32 cannot give 1e-4 relative.
 FIT_REL = 1e-4
 FIT_FLOORS = dict(kappa=1e-3, phi0=1.0, d0=1.0, cot_theta=1.0, z0=1.0)
-# chi2 values are quality figures from micrometre residuals; compared loosely.
+# chi2: float32 residuals carry ~1e-6 cm of rounding (1e-3 of the 10 um resolution), so a
+# term (eps/sigma)^2 moves by ~2e-3 |eps/sigma|; 1e-2 * max(chi2, 1) covers six hits.
 CHI2_REL = 1e-2
 
 

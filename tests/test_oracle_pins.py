@@ -228,6 +228,91 @@ def test_fit_triplet_equals_circumcircle():
     assert n > 500
 
 
+def _helix_at_pca(rng, b, sign, kappa, cot, z0, arcs):
+    """Float64 points of a helix built from its point of closest approach P to the beam
+    line: P at distance b in a random direction, the transverse direction t at P
+    perpendicular to P (turned left of P for sign = +1, right for -1), the circle of
+    signed curvature kappa tangent to t at P (centre on the left of t for kappa > 0), and
+    the points at the given transverse arc lengths from P with z = z0 + cot * s.
+    Returns the points with the signed impact parameter P x t and the direction of t,
+    both computed from the construction rather than from any fit convention."""
+    beta = rng.uniform(-math.pi, math.pi)
+    P = b * np.array([math.cos(beta), math.sin(beta)])
+    t = sign * np.array([-math.sin(beta), math.cos(beta)])
+    left = np.array([-t[1], t[0]])
+    C = P + left / kappa
+    v = P - C
+    ang = kappa * np.asarray(arcs)
+    x = C[0] + np.cos(ang) * v[0] - np.sin(ang) * v[1]
+    y = C[1] + np.sin(ang) * v[0] + np.cos(ang) * v[1]
+    z = z0 + cot * np.asarray(arcs)
+    d0 = float(P[0] * t[1] - P[1] * t[0])
+    return x, y, z, d0, math.atan2(t[1], t[0]), C
+
+
+def test_fit_signed_impact_parameter_displaced_helices():
+    """Noiseless helices whose closest approach to the beam line lies 0.01-0.5 cm from it,
+    on either side, for both charges: the fit returns the construction's signed d0 = P x t
+    (the z component of the closest-approach point crossed with the unit direction of
+    travel there), its direction phi0, curvature, cot(theta) and z0 at that point, to
+    1e-6 relative.  A flipped d0 sign or a closest-approach point taken on the wrong side
+    of the circle fails on half of the cases."""
+    rng = np.random.default_rng(23)
+    signs = set()
+    for k in range(2000):
+        b = rng.uniform(0.01, 0.5)
+        side = float(rng.choice([-1.0, 1.0]))
+        q = float(rng.choice([-1.0, 1.0]))
+        R = 100.0 / rng.uniform(0.1, 2.0) / (0.299792458 * 3.8)
+        kappa = -q / R
+        cot = math.sinh(rng.uniform(-2.5, 2.5))
+        z0 = rng.normal(0.0, 5.0)
+        n = int(rng.integers(3, 7))
+        arcs = np.sort(rng.uniform(2.5, 18.0, n))
+        x, y, z, d0, phi0, C = _helix_at_pca(rng, b, side, kappa, cot, z0, arcs)
+        assert abs(abs(d0) - b) <= 1e-12 and abs(float(np.hypot(*C)) - (R - d0 * np.sign(kappa))) < 1e-9 * R
+        f = oracle.fit_hits(x, y, z)
+        assert f[0] == pytest.approx(kappa, rel=1e-6), k
+        assert f[2] == pytest.approx(d0, rel=1e-6), k
+        assert abs(math.remainder(f[1] - phi0, 2 * math.pi)) <= 1e-6, k
+        assert f[3] == pytest.approx(cot, rel=1e-6, abs=1e-6), k
+        assert abs(f[4] - z0) <= 1e-6 * max(abs(z0), 1.0), k
+        assert f[8] == q
+        signs.add((np.sign(d0), q))
+    assert len(signs) == 4
+
+
+def test_fit_chi2_per_degree_of_freedom_is_one():
+    """Hits moved off an exact helix along the circle's normal by N(0, 10 um) and in z by
+    N(0, 20 um), the resolutions the fit divides by: summed over 3000 tracks of 4-6 hits,
+    chi2_circle / (n - 3) and chi2_line / (n - 2) are 1 within five standard deviations
+    of a chi-square mean, sqrt(2 / total ndf).  A wrong resolution, a missing factor in
+    the residual or a wrong degree-of-freedom count fails."""
+    rng = np.random.default_rng(31)
+    sig_rphi, sig_z = 10e-4, 20e-4
+    c2c = c2l = ndf_c = ndf_l = 0.0
+    for k in range(3000):
+        q = float(rng.choice([-1.0, 1.0]))
+        R = 100.0 / rng.uniform(0.1, 2.0) / (0.299792458 * 3.8)
+        cot = math.sinh(rng.uniform(-2.0, 2.0))
+        n = int(rng.integers(4, 7))
+        arcs = np.sort(rng.uniform(2.5, 18.0, n))
+        x, y, z, _, _, C = _helix_at_pca(rng, rng.uniform(0.0, 0.1), float(rng.choice([-1.0, 1.0])),
+                                         -q / R, cot, rng.normal(0.0, 5.0), arcs)
+        rad = np.hypot(x - C[0], y - C[1])
+        move = rng.normal(0.0, sig_rphi, n)
+        x = x + move * (x - C[0]) / rad
+        y = y + move * (y - C[1]) / rad
+        z = z + rng.normal(0.0, sig_z, n)
+        f = oracle.fit_hits(x, y, z)
+        c2c += f[6]
+        c2l += f[7]
+        ndf_c += n - 3
+        ndf_l += n - 2
+    assert abs(c2c / ndf_c - 1.0) <= 5.0 * math.sqrt(2.0 / ndf_c), c2c / ndf_c
+    assert abs(c2l / ndf_l - 1.0) <= 5.0 * math.sqrt(2.0 / ndf_l), c2l / ndf_l
+
+
 def test_ntuplets_are_all_maximal_chains(cuts):
     """Ntuplets are exactly the root-to-leaf paths (>= 2 cells) of the link graph, as
     enumerated by networkx; consecutive cells share a hit; the layer sequence follows
