@@ -396,8 +396,9 @@ orc_result* orc_reconstruct_masked(int64_t n, const float* x, const float* y, co
                            link_keep, n_keep);
 }
 
-/* The chain over a caller's layer-pair table (at most ORC_MAX_PAIRS pairs of layer
- * codes < ORC_N_LAYERS, inner != outer); NULL for an invalid table. */
+/* The chain over a caller's layer-pair table (at most ORC_MAX_PAIRS distinct pairs of
+ * layer codes < ORC_N_LAYERS, inner != outer); NULL for an invalid table.  A pair named
+ * twice would make every cell on it twice, so a repeated pair is invalid. */
 orc_result* orc_reconstruct_pairs(int64_t n, const float* x, const float* y, const float* z,
                                   const uint8_t* layer, const orc_cuts* cuts, double bfield,
                                   int n_pairs, const int32_t* pin, const int32_t* pout) {
@@ -407,6 +408,8 @@ orc_result* orc_reconstruct_pairs(int64_t n, const float* x, const float* y, con
     if (pin[p] < 0 || pin[p] >= ORC_N_LAYERS || pout[p] < 0 || pout[p] >= ORC_N_LAYERS ||
         pin[p] == pout[p])
       return NULL;
+    for (int q = 0; q < p; ++q)
+      if (ti[q] == pin[p] && to[q] == pout[p]) return NULL;
     ti[p] = pin[p];
     to[p] = pout[p];
   }

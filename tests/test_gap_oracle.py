@@ -38,7 +38,8 @@ def test_default_table_gives_the_default_chain(cuts):
 
 def test_invalid_tables_are_refused(cuts):
     e = sim.generate(sim.SINGLE_MUON_LIKE, 1000)
-    for bad in ([(0, 0)], [(0, 10)], [(-1, 2)], [], [(0, 1)] * 65):
+    for bad in ([(0, 0)], [(0, 10)], [(-1, 2)], [], [(0, 1)] * 65, [(0, 1), (0, 1)],
+                [(0, 1), (1, 2), (0, 1)]):
         with pytest.raises(ValueError):
             oracle.reconstruct(e.x, e.y, e.z, e.layer, cuts, pairs=bad)
 
