@@ -67,10 +67,37 @@ def capacity(batch: int = BATCH, phi_bins: int = 1024) -> dict:
                                ntuplets_per_event=196_608, phi_bins=phi_bins)
 
 
-# Algorithmic bytes of one launch of each main kernel (every array the kernel must touch,
-# read once or written once, in this library's layout): N hits, C cells, Lk links,
-# T ntuplet candidates.
-def kernel_bytes(kernel: str, c: dict) -> int | None:
+# Algorithmic bytes of each step of the chain per batch (SURVEY-level accounting, the
+# least each step must read or write whatever the layout): N hits, C cells, Lk links,
+# T ntuplet candidates, I (cell, candidate) incidences, S cleaned ntuplets holding H hits.
+#   A1 load + bin: 13 B/hit read (x, y, z, layer) + 20 B/hit written (x, y, z, r, index)
+#   A2 doublets: 20 B/hit read (each hit staged once) + 10 B/cell written
+#   A3 links: 8 B/cell read + 1 B/cell flag + 8 B/hit (per-hit lists) + 4 B/link written
+#   A4 ntuplets: 4 B/link + 4 B/cell read + 29 B/candidate written
+#   A5/A6 cleaning and order: 2 x 29 B/candidate + 4 B per incidence
+#   A7 fit: 12 B per hit read + 36 B per track written
+def stage_bytes(stage: str, c: dict) -> int:
+    N, C, Lk, T = c["hits"], c["cells"], c["links"], c["candidates"]
+    return {
+        "A1": 13 * N + 20 * N,
+        "A2": 20 * N + 10 * C,
+        "A3": 9 * C + 8 * N + 4 * Lk,
+        "A4": 4 * Lk + 4 * C + 29 * T,
+        "A5A6": 58 * T + 4 * c["incidences"],
+        "A7": 12 * c["survivor_hits"] + 36 * c["survivors"],
+    }[stage]
+
+
+# The step each traced kernel belongs to, and the steps each timed stage call covers.
+KERNEL_STAGE = {"k_doublets": "A2", "k_in_scatter": "A3", "k_connect": "A3",
+                "k_find_ntuplets": "A4", "k_fit": "A7"}
+CALL_STAGES = {"load": ("A1",), "doublets": ("A2",), "connect": ("A3",),
+               "ntuplets": ("A4", "A5A6"), "fit": ("A7",)}
+
+
+# Bytes of one launch of each main kernel in this library's own layout (every array the
+# kernel touches, read or written once): reported beside the step accounting above.
+def kernel_layout_bytes(kernel: str, c: dict) -> int | None:
     N, C, Lk, T = c["hits"], c["cells"], c["links"], c["candidates"]
     return {
         # hit (x,y,z,r) 16 N; segments 48 N; in-degree counters 8 N (reduction read+write);
@@ -535,7 +562,10 @@ def run_ours(args):
                 ctx.pt_load_batch(off, x, y, z, layer)
                 counts = dict(hits=int(off[-1]), cells=ctx.pt_build_doublets(),
                               links=ctx.pt_connect_cells(), survivors=ctx.pt_find_ntuplets())
-                counts["candidates"] = int(ctx.pt_get_candidates()[0].shape[0])
+                _, cnh, _, _ = ctx.pt_get_candidates()
+                counts["candidates"] = int(cnh.size)
+                counts["incidences"] = int(cnh.astype(np.int64).sum() - cnh.size)
+                counts["survivor_hits"] = int(ctx.pt_get_ntuplets()[1].astype(np.int64).sum())
                 ctx.pt_fit_tracks()
             if dist:
                 dist.barrier()
@@ -587,20 +617,45 @@ def run_ours(args):
     config4["gated"] = _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)
     ctx.pt_set_gate(None, 0.0)
 
-    # roofline of the dominant kernel of the plain form (mean traced launch duration)
+    # roofline of the dominant kernel of the plain form: its step's algorithmic bytes over
+    # the kernel's mean traced launch time; the same bytes over the whole step call's time,
+    # and every step of the chain, beside it
     plain = forms["plain"]
     km = kernels["plain"]
-    dom = max((k for k in km if kernel_bytes(k, counts) is not None), key=lambda k: km[k])
-    ab = kernel_bytes(dom, counts)
     peaks = _peaks()
+    pk = peaks["hbm_gbs"]
+    dom = max((k for k in km if k in KERNEL_STAGE), key=lambda k: km[k])
+    dstage = KERNEL_STAGE[dom]
+    ab = stage_bytes(dstage, counts)
     achieved = ab / (km[dom] / 1000.0) / 1e9
     rec = NCU_TRAFFIC.get(dom)
     fresh = rec is not None and rec["sha"] == kernel_sources_sha(dom)
+    traffic = int(rec["bytes_per_event"] * B) if fresh else None
+    steps_frac = {}
+    for call, st in CALL_STAGES.items():
+        by = sum(stage_bytes(x, counts) for x in st)
+        ms = plain["stages_ms"][call]
+        steps_frac["+".join(st)] = {"bytes": by, "ms": ms,
+                                    "achieved_gbs": round(by / (ms / 1000.0) / 1e9, 1),
+                                    "frac": round(by / (ms / 1000.0) / 1e9 / pk, 4)}
+    graph = [c for c in CALL_STAGES if c != "fit"]
+    gby = sum(steps_frac["+".join(CALL_STAGES[c])]["bytes"] for c in graph)
+    gms = sum(plain["stages_ms"][c] for c in graph)
+    call_of = {st[0]: c for c, st in CALL_STAGES.items()}
+    sms_ = plain["stages_ms"][call_of[dstage]] if dstage in call_of else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": int(rec["bytes_per_event"] * B) if fresh else None,
-                "peak_src": peaks["src"], "algorithmic_bytes": ab, "launch_ms": km[dom],
-                "issue_active_pct": rec["issue_active_pct"] if fresh else None}
+                "peak": pk, "unit": "GB/s", "frac": achieved / pk,
+                "traffic": traffic, "peak_src": peaks["src"],
+                "algorithmic_bytes": ab, "bytes_source": f"step {dstage} accounting",
+                "launch_ms": km[dom],
+                "traffic_over_algorithmic": round(traffic / ab, 3) if traffic else None,
+                "layout_bytes": kernel_layout_bytes(dom, counts),
+                "issue_active_pct": rec["issue_active_pct"] if fresh else None,
+                "stage": {"name": dstage, "ms": sms_,
+                          "frac": round(ab / (sms_ / 1000.0) / 1e9 / pk, 4) if sms_ else None},
+                "graph_stages_A1_A6": {"bytes": gby, "ms": round(gms, 4),
+                                       "frac": round(gby / (gms / 1000.0) / 1e9 / pk, 4)},
+                "steps": steps_frac}
 
     if rank == 0:
         line = {"metric": METRIC, "value": plain["value"], "unit": "events/s", "n_gpus": world,
