@@ -49,9 +49,7 @@ CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped
 # DRAM traffic per event of the main kernels from one ncu capture (8 PU200 events per
 # launch, profiles/), valid only while the kernel's sources hash to the recorded value.
 NCU_TRAFFIC = {
-    "k_doublets": {"bytes_per_event": 19105312, "issue_active_pct": 68.1, "sha": "30d941786a35"},
-    "k_in_scatter": {"bytes_per_event": 35091680, "issue_active_pct": 19.6, "sha": "efe768eb76c3"},
-    "k_connect": {"bytes_per_event": 29828608, "issue_active_pct": 71.5, "sha": "efe768eb76c3"},
+    "k_doublets": {"bytes_per_event": 24389312, "issue_active_pct": 56.7, "sha": "ce03c03e8c77"},
     "k_find_ntuplets": {"bytes_per_event": 47944064, "issue_active_pct": 16.0, "sha": "bea2a2a22db7"},
 }
 
@@ -89,7 +87,7 @@ def stage_bytes(stage: str, c: dict) -> int:
 
 
 # The step each traced kernel belongs to, and the steps each timed stage call covers.
-KERNEL_STAGE = {"k_doublets": "A2", "k_in_scatter": "A3", "k_connect": "A3",
+KERNEL_STAGE = {"k_doublets": "A2", "k_connect": "A3", "k_link_targets": "A3",
                 "k_find_ntuplets": "A4", "k_fit": "A7"}
 CALL_STAGES = {"load": ("A1",), "doublets": ("A2",), "connect": ("A3",),
                "ntuplets": ("A4", "A5A6"), "fit": ("A7",)}
@@ -100,16 +98,15 @@ CALL_STAGES = {"load": ("A1",), "doublets": ("A2",), "connect": ("A3",),
 def kernel_layout_bytes(kernel: str, c: dict) -> int | None:
     N, C, Lk, T = c["hits"], c["cells"], c["links"], c["candidates"]
     return {
-        # hit (x,y,z,r) 16 N; segments 48 N; in-degree counters 8 N (reduction read+write);
-        # cells (inner, outer) 8 C
-        "k_doublets": 16 * N + 48 * N + 8 * N + 8 * C,
-        # segments 48 N, layer tag 4 N, in_start 4 N, counters 8 N (atomic read+write);
-        # cell outer 4 C, records 8 C, two link flags 2 C
-        "k_in_scatter": 64 * N + 14 * C,
-        # in_start 4 N, segments 48 N, hits 16 N; records 8 C, outer hit of staged cells
-        # 4 C; links (source, target, quality) 12 Lk, per-cell lists (8) and the two link
-        # flags <= 10 Lk
-        "k_connect": 68 * N + 12 * C + 22 * Lk,
+        # hit (x,y,z,r) and bin 20 N; incoming segments 24 N; cells (inner, outer) 8 C and
+        # their two link flags 2 C
+        "k_doublets": 20 * N + 24 * N + 10 * C,
+        # hit and bin 20 N, incoming segments 24 N; inner hit of each incoming cell 4 C;
+        # links (source, target, quality) 12 Lk, per-cell lists (8) and out flag <= 9 Lk
+        "k_connect": 44 * N + 4 * C + 21 * Lk,
+        # link source and target 8 Lk (read), the source's outer hit and the target's
+        # segment 12 Lk, target (write) and in flag 5 Lk
+        "k_link_targets": 25 * Lk,
         # link sources (root search) 4 Lk, roots' flags and lists <= 10 Lk, link targets
         # and qualities 8 Lk; candidates (6 hits, 5 cells, n, q) 49 T
         "k_find_ntuplets": 22 * Lk + 49 * T,
@@ -118,7 +115,7 @@ def kernel_layout_bytes(kernel: str, c: dict) -> int | None:
 
 def kernel_sources_sha(kernel: str) -> str:
     import hashlib
-    src = {"k_doublets": "doublets.cu", "k_in_scatter": "connect.cu", "k_connect": "connect.cu",
+    src = {"k_doublets": "doublets.cu", "k_connect": "connect.cu", "k_link_targets": "connect.cu",
            "k_find_ntuplets": "ntuplets.cu"}[kernel]
     d = os.path.join(ROOT, "paper_2501_05520_gb300", "csrc")
     h = hashlib.sha1()

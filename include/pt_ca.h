@@ -132,6 +132,9 @@ typedef struct {
 pt_status pt_workspace_size(const pt_capacity* cap, size_t* bytes);
 
 /* Create a context on `device` (Sec. 3: detector constants are loaded once at start).
+ * Capacity limits: max_hits < 2^30, max_cells and max_links < 2^32 - 1, max_ntuplets
+ * < 2^29, phi_bins in [16, 4096], max_events * 10 * phi_bins < 2^31 - 1, reserved 0;
+ * anything else is PT_ERR_INVALID.
  * workspace: device memory of >= pt_workspace_size bytes, 256-byte aligned, owned by
  *            the caller and borrowed until pt_destroy; NULL lets the library allocate.
  * stream:    a cudaStream_t owned by the caller, or NULL to create a private stream.
@@ -348,11 +351,13 @@ pt_status pt_enqueue_batch(pt_ctx* ctx, int n_events, const int64_t* hit_offsets
  *   of cap int32 entries receiving each accepted doublet as input hit indices (inner,
  *   outer), in no particular order; the set equals the cells of pt_build_doublets with
  *   the same cuts.  *n_out (host) receives the number of doublets; if it exceeds cap the
- *   call returns PT_ERR_CAPACITY and only cap of them were written.
+ *   call returns PT_ERR_CAPACITY and only cap of them were written (which ones is
+ *   unspecified).  A layer code > 9 gives PT_ERR_INVALID.
  *   stream: cudaStream_t or NULL; the call synchronises it before returning.
- * The first call on a device looks up the scratch array's device address (set-up done
- * once per device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and each call clears what it reads as zero:
+ * Every call looks up the scratch array's device address on the current device (the
+ * first lookup on a device loads the library's device code there; later ones allocate
+ * nothing), so the address stays right if the device's context is reset and made
+ * again; make the first call on a device before any stream capture.  All calls share the one array and each call clears what it reads as zero:
  * calls whose GPU work overlaps (other threads, other streams) race and must not be
  * issued concurrently.  No cudaMalloc, cudaFree or other allocating call is made. */
 pt_status pt_find_doublets_noalloc(const pt_cuts* cuts, int64_t n, const float* x,

@@ -18,11 +18,11 @@ __global__ void k_clear(Buffers b, int32_t phi_bins) {
   const int stride = gridDim.x * blockDim.x;
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
   for (int i = t0; i <= nb; i += stride) b.bin_cnt[i] = 0;
-  for (int i = t0; i < E * kLayers; i += stride) b.layer_rmax[i] = 0u;
-  for (int i = t0; i <= N; i += stride) {
-    b.bucket_cnt[i] = 0;
-    b.in_cnt[i] = 0;
+  for (int i = t0; i < E * kLayers; i += stride) {
+    b.layer_rmax[i] = 0u;
+    b.layer_rmin[i] = 0x7f800000u;  // +inf
   }
+  for (int i = t0; i <= N; i += stride) b.bucket_cnt[i] = 0;
   for (int i = t0; i < N; i += stride) b.used[i] = 0;
   if (t0 == 0) {
     b.cnt[CNT_CELLS] = 0;
@@ -43,8 +43,8 @@ __device__ __forceinline__ float hit_radius(float x, float y) {
   return fsqrt(fadd(fmul(x, x), fmul(y, y)));
 }
 
-// Histogram: global bin of every input hit and its rank inside the bin; max r per
-// (event, layer), reduced within the warp before the atomic.
+// Histogram: global bin of every input hit and its rank inside the bin; max and min r
+// per (event, layer), reduced within the warp before the atomics.
 __global__ void k_bin_count(Buffers b, int32_t B) {
   const int E = b.hdr->n_events, N = b.hdr->n_hits;
   const float scale = (float)B / (2.0f * kPi);
@@ -71,21 +71,28 @@ __global__ void k_bin_count(Buffers b, int32_t B) {
         b.in_rank[g] = atomicAdd(&b.bin_cnt[gb], 1u);
       }
     }
-    // per (event, layer) maximum radius: one atomic per distinct key in the warp
+    // per (event, layer) radius range: one atomic each per distinct key in the warp
     const unsigned peers = __match_any_sync(kFull, key);
     // r >= 0, so the integer order of the bit patterns is the float order
     const unsigned m = __reduce_max_sync(peers, __float_as_uint(r));
-    if (key != 0xffffffffu && (__ffs(peers) - 1) == lane_id()) atomicMax(&b.layer_rmax[key], m);
+    const unsigned mn = __reduce_min_sync(peers, __float_as_uint(r));
+    if (key != 0xffffffffu && (__ffs(peers) - 1) == lane_id()) {
+      atomicMax(&b.layer_rmax[key], m);
+      atomicMin(&b.layer_rmin[key], mn);
+    }
   }
 }
 
 __global__ void k_bin_scatter(Buffers b, float kmax) {
   const int N = b.hdr->n_hits;
   const int stride = gridDim.x * blockDim.x;
-  // per event layer: the outer-radius term of the doublet stage's azimuthal window
+  // per event layer: the outer- and inner-radius terms of the azimuthal windows of the
+  // doublet search (inner term 0, the widest window, where the bound does not apply)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.hdr->n_events * kLayers; i += stride) {
     const float a = 0.5f * kmax * __uint_as_float(b.layer_rmax[i]);
     b.layer_asin[i] = a >= 0.7f ? __int_as_float(0x7f800000) : asinf(a);
+    const float c = 0.5f * kmax * __uint_as_float(b.layer_rmin[i]);
+    b.layer_asin_lo[i] = c < 0.7f ? asinf(c) : 0.0f;
   }
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += stride) {
     const uint32_t gb = b.in_bin[g];

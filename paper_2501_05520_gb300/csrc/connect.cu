@@ -3,130 +3,163 @@
 // and the beam-spot distance cut C3 (Sec. 2.2.1, Fig. 2: doublets are paired into
 // triplets by the cellular automaton).
 //
-// One warp per middle hit h1.  The cells leaving h1 (up to three segments, one per
-// outer layer, each padded to a multiple of 8) are staged once, in one pass, in shared
-// memory: their r-z slopes and the coordinates of their outer hits.  The cells ending
-// on h1 come from a per-hit list of 8-byte records (cell, inner hit | inner-layer flag)
-// and are taken 32 at a time, one per lane; the inner hits of the next group are
-// fetched while a group is swept.  With d1 = r1-r0, d2 = r2-r1 and t_a, t_b the slopes of a and b, C1 reads
+// One warp per middle hit h1.  The cells arriving at h1 are its incoming segments
+// (written contiguously by the doublet stage).  The cells leaving h1 are found again
+// here by the doublet search towards its outer layers (the same window and exact cuts,
+// so exactly the cells the doublet stage made), staged in shared memory with their
+// outer hit and r-z slope, and ordered by slope with a counting sort into 64 buckets
+// spanning the staged slopes.  With d1 = r1-r0, d2 = r2-r1 and t_a, t_b the slopes of
+// a and b, C1 reads
 //   d1 d2 |t_a - t_b| <= rz0 (d1 + d2) + rz1 |t_a d1 + t_b d2|,
 // so |t_a - t_b| <= rz0 (1/d1 + 1/d2) + rz1 (|t_a|/d2 + |t_b|/d1).  Bounding |t_b| by
 // cotmax (D4), or by |t_a| + |t_a - t_b| and solving for |t_a - t_b|, and d2 by the
-// smallest r2-r1 of the segment, m, gives the window
+// smallest r2-r1 of the staged cells, m, gives the window
 //   |t_a - t_b| <= min((rz0 + rz1 cotmax)/d1 + (rz0 + rz1 |t_a|)/m,
 //                      (rz0 + rz1 |t_a|)(1/d1 + 1/m) / (1 - rz1/d1)),
 // the second term only where d1 > rz1.  It is widened by 1 % + 1e-3, far beyond the
 // float32 rounding of C1 (about 4e-7 |t_a| d1/m + 1e-6) and of the approximate
-// quotients and reciprocals used for the slopes and the window (a few 1e-7 relative).
-// The warp sweeps all staged slopes eight at a time, every lane testing its own cell
-// against them with the window of the segment the eight belong to, with no divergence;
-// a lane whose window holds any of the eight queues one entry (incoming index, 8-bit
-// mask, position).  The queue is drained 32 entries
-// at a time through the exact cuts, all lanes busy.  The links of a middle hit are
-// collected in shared memory, reserved once, sorted by source cell and written as
-// per-cell lists (the out-link lists the ntuplet search walks): a source's links are
-// one run of equal link_src values, so the first slot of each run names a cell that
-// can start an ntuplet.  If a hit has more links than the collection holds, the search
-// runs a second time and writes them all to a temporary half of a double-size
-// reservation, which is then sorted.  Segments larger than the stage are swept piece
-// by piece.
+// quotients used for the slopes and the window (a few 1e-7 relative).  Each lane takes
+// one incoming cell and visits only the buckets its window overlaps (the bucket of a
+// slope is a monotone function of it, evaluated the same way for the staged slopes and
+// for the window's ends, which are moved out by a further 0.1 % + 1e-5 so that rounding
+// of t_a -+ w cannot exclude a bucket); the staged cells there that fall inside the
+// window are tested with C1, and the pairs that pass are queued and tested with C2 and
+// C3 32 at a time, all lanes busy.
+//
+// The target cell (h1, h2) of a link is found afterwards, one thread per link, in h2's
+// incoming segment from h1's layer (ordered by inner hit) by binary search: in the
+// warp's own path those dependent loads would hold up the search.  Every link of a
+// source cell is found by the
+// lane that holds the cell, so a group of 32 incoming cells is finalised at once: each
+// cell's links take consecutive slots of one reservation (the out-link list the
+// ntuplet search walks, one run of equal link_src values per source).  If a group finds
+// more links than the shared buffer holds, its search runs again and writes them
+// straight to their slots.  A middle hit with more outgoing cells than the stage holds
+// is handled piece by piece, every incoming group visiting every piece.
 #include "ptca_internal.cuh"
 
 namespace ptca {
 
 namespace {
 
+constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr float kHalfPi = 1.57079632679489661923f;
 constexpr int kConnWarps = 8;
-constexpr int kOutStage = 160;  // staged outgoing cells per warp (multiple of 8, < 256)
-constexpr int kQueue = 128;     // candidate ring per warp (power of two, >= 31 + 32)
-constexpr int kFound = 64;      // links of one group kept in shared memory (rank < 256)
-constexpr uint32_t kHitChunk = 4;       // consecutive middle hits per warp chunk (<= 32)
-constexpr int kScatterBlocksPerSm = 4;  // fewer warps in flight keep the scatter local
-constexpr int kConnBlocksPerSm = 4;     // 64 registers per thread: no spills in the link search
-static_assert(kOutStage % 8 == 0 && kOutStage < 256, "staged positions fit 8 bits");
+constexpr int kConnBlocksPerSm = 4;  // 64 registers per thread
+constexpr int kOut = 128;            // staged outgoing cells of one piece (<= 256)
+constexpr int kNb = 64;              // slope buckets of a piece (two per lane)
+constexpr int kQueue = 64;           // pairs that passed C1, waiting for C2/C3 (power of two)
+constexpr int kFound = 64;           // links of one incoming group kept before writing
+static_assert(kOut <= 256 && kOut % 32 == 0, "staged index fits 8 bits");
+static_assert(kQueue >= 63 && (kQueue & (kQueue - 1)) == 0, "queue holds 31 + 32 entries");
 
-__device__ __forceinline__ uint32_t round8(uint32_t n) { return (n + 7u) & ~7u; }
-
-// in_rec[in_start[h] + rank] = (cell, inner hit | inner layer is 0 << 31), grouping the
-// cells by the hit they end on; every cell's two link flags are cleared on the way.  One warp per inner hit, in sorted-hit order: the warps
-// running at one time cover a narrow azimuthal range of a layer, so their records land
-// in a narrow range of in_rec and partial sectors merge in L2 before write-back.
-__global__ void k_in_scatter(Buffers b, int32_t B) {
-  const int lane = lane_id();
-  const int E = b.hdr->n_events;
-  const uint32_t n_sorted = b.bin_start[E * kLayers * B];
-  const int wpb = blockDim.x >> 5;
-  const int nwarps = gridDim.x * wpb;
-  for (uint32_t h0 = blockIdx.x * wpb + (threadIdx.x >> 5); h0 < n_sorted; h0 += nwarps) {
-    const Segment* sgp = b.seg + (uint64_t)h0 * kMaxOuter;
-    const uint32_t n0 = sgp[0].cnt, n1 = sgp[1].cnt, n2 = sgp[2].cnt;
-    const uint32_t n = n0 + n1 + n2;
-    if (n == 0) continue;
-    const uint32_t o0 = sgp[0].off, o1 = sgp[1].off, o2 = sgp[2].off;
-    const uint32_t tag = h0 | ((b.hbin[h0] / (uint32_t)B) % kLayers == 0 ? 0x80000000u : 0u);
-    for (uint32_t i0 = 0; i0 < n; i0 += 64) {
-      uint32_t c[2], o[2];
+// Slot of inner layer Li among the inner layers of layer L (-1 where (Li, L) is no pair).
+__device__ __forceinline__ int inner_slot(int L, int Li) {
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const uint32_t i = i0 + u * 32 + lane;
-        o[u] = kHole;
-        if (i < n) {
-          c[u] = i < n0 ? o0 + i : (i < n0 + n1 ? o1 + (i - n0) : o2 + (i - n0 - n1));
-          o[u] = b.cell_out[c[u]];
-
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-        if (o[u] != kHole) {  // the count left on the hit is the cell's slot in its list
-          b.in_rec[b.in_start[o[u]] + atomicSub(&b.in_cnt[o[u]], 1u) - 1u] = make_uint2(c[u], tag);
-          b.has_in[c[u]] = 0;
-          b.has_out[c[u]] = 0;
-        }
-    }
-  }
+  for (int k = 0; k < kMaxInner; ++k)
+    if (kInner[L][k] == Li) return k;
+  return -1;
 }
 
-// Per-warp shared state.  Warp-uniform values live here rather than in registers, so
-// that the sweep keeps only a lane's slope and window live.
+// Azimuthal window of inner hit `hi` (global bin gb, asin_i = asin(kmax*ri/2)) towards
+// outer slot k, the doublet search's window from the inner side: the outer layer's
+// asin(kmax*ro_max/2) - asin_i (+1e-4 rad, +1 bin); up to two ranges [r.x, r.y) and
+// [r.z, r.w) of the sorted hits; empty where the slot is unused or the outer layer ends
+// inside the inner hit's radius.
+__device__ __forceinline__ uint4 forward_window(const Buffers& b, int32_t B, float bins_per_rad,
+                                                uint32_t gb, float4 hi, float asin_i, int k) {
+  const int el = gb / B;  // event*10 + layer
+  const int e = el / kLayers, L = el - e * kLayers;
+  const int bin = gb - el * B;
+  uint4 r = make_uint4(0u, 0u, 0u, 0u);
+  if (k >= kNOuter[L]) return r;
+  const int Lo = kOuter[L][k];
+  const float ro_max = __uint_as_float(b.layer_rmax[e * kLayers + Lo]);
+  if (!(ro_max > hi.w)) return r;
+  const float asin_o = b.layer_asin[e * kLayers + Lo];
+  float win = kHalfPi + 1e-3f;
+  if (asin_o != __int_as_float(0x7f800000)) win = fminf(asin_o - asin_i + 1e-4f, win);
+  const int w = (int)ceilf(win * bins_per_rad) + 1;
+  const uint32_t base = (uint32_t)(e * kLayers + Lo) * (uint32_t)B;
+  if (2 * w + 1 >= B) {
+    r.x = b.bin_start[base];
+    r.y = b.bin_start[base + B];
+  } else {
+    const int lo = bin - w, hb = bin + w;
+    if (lo < 0) {
+      r.x = b.bin_start[base + B + lo];
+      r.y = b.bin_start[base + B];
+      r.z = b.bin_start[base];
+      r.w = b.bin_start[base + hb + 1];
+    } else if (hb >= B) {
+      r.x = b.bin_start[base + lo];
+      r.y = b.bin_start[base + B];
+      r.z = b.bin_start[base];
+      r.w = b.bin_start[base + hb - B + 1];
+    } else {
+      r.x = b.bin_start[base + lo];
+      r.y = b.bin_start[base + hb + 1];
+    }
+  }
+  return r;
+}
+
+// Per-warp shared state.
 struct ConnWarp {
-  float4 p2[kOutStage];      // staged outgoing cells: outer hit
-  float t[kOutStage];        //   slope (NaN padding)
-  float4 p1;                 // middle hit
-  Segment sg[kMaxOuter];     // outgoing segments of the middle hit
-  uint32_t pos[kMaxOuter];   // staged position of each segment / piece
-  uint32_t coff[kMaxOuter];  // cell of each staged position pos[k]
-  unsigned long long chunk_next[1], chunk_end[1], used;  // link slots
-  uint32_t chunk_size[1];
-  uint32_t hin0[kHitChunk], hnin[kHitChunk];  // incoming-cell list of each hit of the chunk
-  uint32_t in0, nin;         // incoming-cell list of the middle hit
-  unsigned long long lbase;  // its link block
-  uint32_t lvalid;           //   (within the capacity)
-  uint2 q[kQueue];           // candidates: (incoming index, 8-bit mask << 8 | position)
-  uint32_t fs[kFound];       // found links: source cell
-  uint32_t fd[kFound];       //   target cell
+  float4 p2[kOut];           // staged outgoing cells: outer hit (x, y, z, r)
+  float t[kOut];             //   r-z slope
+  uint32_t h2[kOut];         //   outer hit (sorted index)
+  uint8_t j2[kOut];          //   slot of the middle hit's layer among the outer hit's
+                             //   inner layers
+  uint8_t perm[kOut];        // bucket order -> staged index
+  uint32_t bstart[kNb + 1];  // first bucket-ordered position of each slope bucket
+  uint32_t lcnt[32];         // links found per incoming cell of the group
+  uint32_t loff[32];         // first slot of each incoming cell's links
+  uint2 q[kQueue];           // C1 passes: (incoming lane, staged index)
+  uint32_t fa[kFound];       // found links: incoming lane | rank << 5
+  uint32_t fb[kFound];       //   target: outer hit | slot << 30
   float fq[kFound];          //   quality
+  float4 p1;                 // middle hit
+  uint4 rg[kMaxOuter];       //   its forward windows, one per outer slot
+  uint32_t so[kMaxInner];    //   its incoming segments: first cell
+  uint32_t sc[kMaxInner];    //   and number of cells
+  float tmin, scale, m;      // the staged piece: slope origin and scale of the buckets,
+                             //   smallest r2 - r1
+  int piece;                 // the staged piece (-1: none)
+  unsigned long long chunk_next, chunk_end, used;  // link slots
+  uint32_t chunk_size;
 };
+
+// Bucket of a slope (monotone non-decreasing in x): the same correctly rounded
+// operations for the staged slopes and the window ends.
+__device__ __forceinline__ int slope_bucket(float x, float tmin, float scale) {
+  const int k = __float2int_rz(__fmul_rn(__fsub_rn(x, tmin), scale));
+  return min(kNb - 1, max(0, k));
+}
+
+// Largest chunk of link slots a warp takes at once: a warp's last chunk is mostly
+// unused (a hole), and link slots are scanned by the later stages.
+constexpr uint32_t kLinkChunkMax = 256;
 
 // Warp chunk reservation with the chunk state in shared memory, lane 0 acting.
 __device__ __forceinline__ unsigned long long chunk_take_shared(
-    ConnWarp& W, int which, unsigned long long* counter, uint32_t n, unsigned long long* hlo,
+    ConnWarp& W, unsigned long long* counter, uint32_t n, unsigned long long* hlo,
     unsigned long long* hhi) {
   unsigned long long r = 0, lo = 0, hi = 0;
   if ((threadIdx.x & 31) == 0) {
-    unsigned long long next = W.chunk_next[which], end = W.chunk_end[which];
+    unsigned long long next = W.chunk_next, end = W.chunk_end;
     if (next + n > end) {
       lo = next;
       hi = end;
-      uint32_t size = W.chunk_size[which];
+      const uint32_t size = W.chunk_size;
       const uint32_t want = size == 0 ? n : (n > size ? n : size);
-      W.chunk_size[which] = size == 0 ? (n > kChunkMin ? n : kChunkMin) : min(2 * size, kChunkMax);
+      W.chunk_size = size == 0 ? (n > kChunkMin ? n : kChunkMin) : min(2 * size, kLinkChunkMax);
       next = atomicAdd(counter, (unsigned long long)want);
       end = next + want;
     }
     r = next;
-    W.chunk_next[which] = next + n;
-    W.chunk_end[which] = end;
+    W.chunk_next = next + n;
+    W.chunk_end = end;
   }
   r = __shfl_sync(kFull, r, 0);
   *hlo = __shfl_sync(kFull, lo, 0);
@@ -141,350 +174,350 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
   const int lane = lane_id();
   ConnWarp& W = s_w[threadIdx.x >> 5];
   const unsigned lt_mask = (1u << lane) - 1u;
-  const float kNaN = __int_as_float(0x7fc00000);
-  const float kInf = __int_as_float(0x7f800000);
   const int E = b.hdr->n_events;
   const uint32_t n_sorted = b.bin_start[E * kLayers * B];
-  const int nwarps = gridDim.x * kConnWarps;
+  const float bins_per_rad = (float)B / kTwoPi;
   if (lane == 0) {
-    W.chunk_next[0] = W.chunk_end[0] = 0;
-    W.chunk_size[0] = 0;
+    W.chunk_next = W.chunk_end = 0;
+    W.chunk_size = 0;
+    W.used = 0;
   }
-  if (lane == 0) W.used = 0;
   __syncwarp();
   auto mark_link_hole = [&](unsigned long long lo, unsigned long long hi) {
     hi = min(hi, (unsigned long long)cap_links);
     for (unsigned long long i = lo + lane; i < hi; i += 32) b.link_src[i] = kHole;
   };
-  auto write_link = [&](uint64_t slot, uint32_t a, uint32_t c, float q) {
+  auto write_link = [&](uint64_t slot, uint32_t a, uint32_t t, float q) {
     b.link_src[slot] = a;
-    b.link_dst[slot] = c;
+    b.link_dst[slot] = t;  // outer hit | slot << 30, made a cell id by k_link_targets
     b.link_q[slot] = q;
-    if (!GATE) {  // gated form: the gate sets the flags of the links it keeps
-      b.has_out[a] = 1;
-      b.has_in[c] = 1;
-    }
-  };
-  // stages cells [c0, c0 + n) leaving the middle hit p1 at position p (padded to a
-  // multiple of 8 with NaN slopes); the slope only places the window, so an
-  // approximate quotient is enough
-  auto stage = [&](uint32_t c0, uint32_t n, uint32_t p, float4 p1) {
-    for (uint32_t i = lane; i < round8(n); i += 32) {
-      float t = kNaN;
-      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (i < n) {
-        q = b.hit4[b.cell_out[c0 + i]];
-        t = __fdividef(q.z - p1.z, q.w - p1.w);
-      }
-      W.t[p + i] = t;
-      W.p2[p + i] = q;
-    }
+    if (!GATE) b.has_out[a] = 1;  // gated form: the gate sets the flags of the links it keeps
   };
 
-  // chunks of kHitChunk consecutive middle hits per warp; one round of loads finds the
-  // hits with both incoming and outgoing cells
-  for (uint32_t hc = (blockIdx.x * kConnWarps + (threadIdx.x >> 5)) * kHitChunk; hc < n_sorted;
-       hc += (uint32_t)nwarps * kHitChunk) {
+  for (;;) {
+    unsigned long long chunk = 0;
+    if (lane == 0) chunk = atomicAdd(&b.cnt[CNT_LNK_WORK], 1ull);
+    const uint64_t s0 = __shfl_sync(kFull, chunk, 0) * 32ull;
+    if (s0 >= n_sorted) break;
+    // one round of loads finds the hits with incoming cells and outer layers
+    uint32_t my_gb = 0;
+    uint2 my_sg[kMaxInner];
     bool work = false;
     {
-      const uint32_t hl = hc + lane;
-      uint32_t in0 = 0, nin = 0;
-      if ((uint32_t)lane < kHitChunk && hl < n_sorted) {
-        in0 = b.in_start[hl];
-        nin = b.in_start[hl + 1] - in0;
-        if (nin) {
-          const Segment* sgp = b.seg + (uint64_t)hl * kMaxOuter;
-          work = (sgp[0].cnt | sgp[1].cnt | sgp[2].cnt) != 0;
+      const uint64_t s = s0 + lane;
+#pragma unroll
+      for (int k = 0; k < kMaxInner; ++k) my_sg[k] = make_uint2(0u, 0u);
+      if (s < n_sorted) {
+        my_gb = b.hbin[s];
+        const int L = (my_gb / (uint32_t)B) % kLayers;
+        if (kNOuter[L] > 0) {
+#pragma unroll
+          for (int k = 0; k < kMaxInner; ++k) my_sg[k] = b.seg[s * kMaxInner + k];
+          work = (my_sg[0].y | my_sg[1].y | my_sg[2].y) != 0;
         }
-      }
-      __syncwarp();
-      if ((uint32_t)lane < kHitChunk) {
-        W.hin0[lane] = in0;
-        W.hnin[lane] = nin;
       }
     }
     unsigned todo = __ballot_sync(kFull, work);
     while (todo) {
       const int src = __ffs(todo) - 1;
       todo &= todo - 1;
-      const uint32_t h1 = hc + src;
+      const uint32_t h1 = (uint32_t)s0 + src;
+      const uint32_t gb = __shfl_sync(kFull, my_gb, src);
+      const int L1 = (gb / (uint32_t)B) % kLayers;
+      const float4 p1 = b.hit4[h1];
       __syncwarp();
+      if (lane == src) {
+#pragma unroll
+        for (int k = 0; k < kMaxInner; ++k) {
+          W.so[k] = my_sg[k].x;
+          W.sc[k] = my_sg[k].y;
+        }
+      }
+      // forward windows, one outer slot per lane
+      if (lane < kMaxOuter)
+        W.rg[lane] = forward_window(b, B, bins_per_rad, gb, p1,
+                                    asinf(0.5f * cuts.kmax * p1.w), lane);
       if (lane == 0) {
-        W.in0 = W.hin0[src];
-        W.nin = W.hnin[src];
-        W.lvalid = 0;
+        W.p1 = p1;
+        W.piece = -1;
       }
-      uint32_t tot = 0;
-      {
-        const Segment* sgp = b.seg + (uint64_t)h1 * kMaxOuter;
-#pragma unroll
-        for (int k = 0; k < kMaxOuter; ++k) tot += round8(sgp[k].cnt);
-        __syncwarp();
-        if (lane < kMaxOuter) {
-          const Segment g = sgp[lane];
-          W.sg[lane] = g;
-          uint32_t p = 0;
-          for (int k = 0; k < lane; ++k) p += round8(sgp[k].cnt);
-          W.pos[lane] = p;
-          W.coff[lane] = g.off;
-        }
-        if (lane == 0) W.p1 = b.hit4[h1];
-        __syncwarp();
-      }
-      const bool fits = tot <= (uint32_t)kOutStage;
-      // inner hit of the lane's incoming cell in the group to come: fetched ahead (the
-      // first group's during the stage, each later group's during the group before), so
-      // that placing a group's windows waits for one load instead of two in a row
-      uint32_t h0n = (uint32_t)lane < W.nin ? (b.in_rec[W.in0 + lane].y & 0x7fffffffu) : 0u;
-      if (fits) {
-        // all segments in one pass over the staged positions (NaN slope for padding)
-        const float4 p1 = W.p1;
-        for (uint32_t P = lane; P < tot; P += 32) {
-          const int k = (P >= W.pos[1]) + (P >= W.pos[2]);
-          const uint32_t i = P - W.pos[k];
-          float t = kNaN;
-          float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (i < W.sg[k].cnt) {
-            q = b.hit4[b.cell_out[W.sg[k].off + i]];
-            t = __fdividef(q.z - p1.z, q.w - p1.w);
-          }
-          W.t[P] = t;
-          W.p2[P] = q;
-        }
-      }
+      __syncwarp();
+      const uint32_t nin = W.sc[0] + W.sc[1] + W.sc[2];
 
-      // Pass 0 finds the links of h1, keeps up to kFound of them in shared memory and
-      // counts all; if there were more, pass 1 repeats the search and writes the rest
-      // straight into the reserved block.
-      uint32_t nfound = 0;
-#pragma unroll 1
-      for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1 && nfound <= (uint32_t)kFound) break;
-        if (pass == 1)
-          h0n = (uint32_t)lane < W.nin ? (b.in_rec[W.in0 + lane].y & 0x7fffffffu) : 0u;
-        uint32_t head = 0, tail = 0, nf = 0;
-        // exact cuts on up to 32 queued entries, all lanes busy (one round per set bit)
-        auto process = [&](uint32_t nt) {
-          __syncwarp();
-          const bool v = (uint32_t)lane < nt;
-          const uint2 e = v ? W.q[(head + lane) & (kQueue - 1)] : make_uint2(0u, 0u);
-          head += nt;
-          const uint32_t jb = e.y & 0xffu;
-          uint32_t mask = e.y >> 8;
-          uint32_t a = 0;
-          float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f);
-          bool qb0 = false;
-          if (v) {
-            const uint2 r = b.in_rec[W.in0 + e.x];
-            a = r.x;
-            qb0 = (r.y >> 31) != 0;
-            p0 = b.hit4[r.y & 0x7fffffffu];
-          }
-          const float4 p1 = W.p1;
-          while (__any_sync(kFull, mask != 0)) {
-            bool ok = false;
-            float q = 0.0f;
-            uint32_t jj = 0;
-            if (mask) {
-              jj = jb + (__ffs(mask) - 1);
-              mask &= mask - 1;
-              const float4 p2 = W.p2[jj];
-              ok = link_c1(cuts, p0, p1, p2) && link_c23(cuts, p0, qb0, p1, p2, q);
-            }
-            const unsigned pm = __ballot_sync(kFull, ok);
-            if (ok) {
-              const uint32_t seq = nf + __popc(pm & lt_mask);
-              const int k = (jj >= W.pos[1]) + (jj >= W.pos[2]);
-              const uint32_t c = W.coff[k] + (jj - W.pos[k]);
-              if (pass == 0) {
-                if (seq < (uint32_t)kFound) {
-                  W.fs[seq] = a;
-                  W.fd[seq] = c;
-                  W.fq[seq] = q;
+      // Stages piece `piece` (the passing outgoing cells of ordinal [piece*kOut,
+      // (piece+1)*kOut) in search order) and orders it by slope; returns the number of
+      // outgoing cells of h1.
+      auto stage_piece = [&](int piece) -> uint32_t {
+        const uint32_t lo_ord = (uint32_t)piece * kOut;
+        uint32_t cnt = 0;
+        float m = __int_as_float(0x7f800000), tlo = m, thi = -m;
+        for (int k = 0; k < kNOuter[L1]; ++k) {
+          const uint8_t j2 = (uint8_t)inner_slot(kOuter[L1][k], L1);
+          for (int part = 0; part < 2; ++part) {
+            const uint4 rk = W.rg[k];
+            const uint32_t beg = part ? rk.z : rk.x, end = part ? rk.w : rk.y;
+            for (uint32_t o0 = beg; o0 < end; o0 += 32) {
+              const uint32_t o = o0 + lane;
+              bool pass = false;
+              float4 ho = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (o < end) {
+                ho = b.hit4[o];
+                pass = doublet_pass(cuts, p1, ho);
+              }
+              const unsigned bal = __ballot_sync(kFull, pass);
+              if (pass) {
+                const uint32_t pos = cnt + __popc(bal & lt_mask);
+                if (pos >= lo_ord && pos < lo_ord + kOut) {
+                  const uint32_t st = pos - lo_ord;
+                  const float t = __fdividef(ho.z - p1.z, ho.w - p1.w);
+                  W.p2[st] = ho;
+                  W.t[st] = t;
+                  W.h2[st] = o;
+                  W.j2[st] = j2;
+                  m = fminf(m, fsub(ho.w, p1.w));
+                  tlo = fminf(tlo, t);
+                  thi = fmaxf(thi, t);
                 }
-              } else if (seq >= (uint32_t)kFound && W.lvalid) {
-                write_link(W.lbase + nfound + seq, a, c, q);
               }
-            }
-            nf += __popc(pm);
-          }
-        };
-        // sweep of staged positions [j, n) (multiples of 8) with the lane's windows w0, w1,
-        // w2 for the cells of segments 0, 1, 2 (positions below pos1, below pos2, the rest;
-        // a segment's positions are padded to a multiple of 8, so eight positions share
-        // one window); ix = the lane's index in the incoming list.  Stops after the step
-        // that brings the queue to 32 entries, or at the end; returns where it stopped.
-        auto sweep = [&](uint32_t j, uint32_t n, float ta, float w0, float w1, float w2,
-                         uint32_t pos1, uint32_t pos2, uint32_t ix) {
-          for (; j < n; j += 8) {
-            const float wk = j >= pos2 ? w2 : (j >= pos1 ? w1 : w0);
-            const float4 u = *reinterpret_cast<const float4*>(&W.t[j]);
-            const float4 v = *reinterpret_cast<const float4*>(&W.t[j + 4]);
-            const bool c0 = fabsf(u.x - ta) <= wk, c1 = fabsf(u.y - ta) <= wk;
-            const bool c2 = fabsf(u.z - ta) <= wk, c3 = fabsf(u.w - ta) <= wk;
-            const bool c4 = fabsf(v.x - ta) <= wk, c5 = fabsf(v.y - ta) <= wk;
-            const bool c6 = fabsf(v.z - ta) <= wk, c7 = fabsf(v.w - ta) <= wk;
-            const bool any = (c0 | c1 | c2 | c3) | (c4 | c5 | c6 | c7);
-            const unsigned bal = __ballot_sync(kFull, any);
-            if (bal) {
-              if (any) {
-                const uint32_t m = (c0 ? 1u : 0u) | (c1 ? 2u : 0u) | (c2 ? 4u : 0u) | (c3 ? 8u : 0u) |
-                                   (c4 ? 16u : 0u) | (c5 ? 32u : 0u) | (c6 ? 64u : 0u) |
-                                   (c7 ? 128u : 0u);
-                W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2(ix, (m << 8) | j);
-              }
-              tail += __popc(bal);
-              if (tail - head >= 32u) return j + 8;
+              cnt += __popc(bal);
             }
           }
-          return n;
-        };
-
-        for (uint32_t ib = 0; ib < W.nin; ib += 32) {
-          const uint32_t ix = ib + lane;
-          float ta = kNaN;
-          float w[kMaxOuter];
-          {
-            const float4 p1 = W.p1;
-            float2 zw = make_float2(0.f, 0.f);
-            if (ix < W.nin) zw = *reinterpret_cast<const float2*>(&b.hit4[h0n].z);  // z, r
-            h0n = ix + 32 < W.nin ? (b.in_rec[W.in0 + ix + 32].y & 0x7fffffffu) : 0u;
-            if (ix < W.nin) ta = __fdividef(p1.z - zw.x, p1.w - zw.y);  // the cell's slope dz/dr
-            const float id1 = __fdividef(1.0f, p1.w - zw.y);
-            const float wa = (cuts.rz0 + cuts.rz1 * cuts.cotmax) * id1;
-            const float ua = cuts.rz0 + cuts.rz1 * fabsf(ta);
-            const float shrink = 1.0f - cuts.rz1 * id1;
+        }
 #pragma unroll
-            for (int k = 0; k < kMaxOuter; ++k) {
-              const float m = W.sg[k].mdr;
+        for (int off = 16; off > 0; off >>= 1) {
+          m = fminf(m, __shfl_xor_sync(kFull, m, off));
+          tlo = fminf(tlo, __shfl_xor_sync(kFull, tlo, off));
+          thi = fmaxf(thi, __shfl_xor_sync(kFull, thi, off));
+        }
+        const uint32_t n = cnt > lo_ord ? min(cnt - lo_ord, (uint32_t)kOut) : 0u;
+        const float scale = thi - tlo > 1e-6f ? __fdiv_rn((float)kNb, thi - tlo) : 0.0f;
+        // counting sort of the staged cells by slope bucket
+        __syncwarp();
+        for (int i = lane; i <= kNb; i += 32) W.bstart[i] = 0;
+        __syncwarp();
+        int key[kOut / 32];
+        uint32_t rank[kOut / 32];
+#pragma unroll
+        for (int u = 0; u < kOut / 32; ++u) {
+          const uint32_t st = lane + 32 * u;
+          key[u] = 0;
+          rank[u] = 0;
+          if (st < n) {
+            key[u] = slope_bucket(W.t[st], tlo, scale);
+            rank[u] = atomicAdd(&W.bstart[key[u] + 1], 1u);
+          }
+        }
+        __syncwarp();
+        {
+          const uint32_t c0 = W.bstart[2 * lane + 1], c1 = W.bstart[2 * lane + 2];
+          const uint32_t inc = warp_incl_scan(c0 + c1);
+          __syncwarp();
+          W.bstart[2 * lane + 1] = inc - c1;
+          W.bstart[2 * lane + 2] = inc;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kOut / 32; ++u) {
+          const uint32_t st = lane + 32 * u;
+          if (st < n) W.perm[W.bstart[key[u]] + rank[u]] = (uint8_t)st;
+        }
+        if (lane == 0) {
+          W.tmin = tlo;
+          W.scale = scale;
+          W.m = m;
+          W.piece = piece;
+        }
+        __syncwarp();
+        return cnt;
+      };
+
+      const uint32_t nout = stage_piece(0);
+      if (nout == 0) continue;
+
+      const int npieces = (int)((nout + kOut - 1) / kOut);
+
+      for (uint32_t g0 = 0; g0 < nin; g0 += 32) {
+        // the lane's incoming cell
+        const uint32_t i = g0 + lane;
+        const bool valid = i < nin;
+        uint32_t c = 0;
+        int kin = 0;
+        if (valid) {
+          const uint32_t n0 = W.sc[0], n1 = W.sc[1];
+          kin = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);
+          const uint32_t before = kin == 0 ? 0u : (kin == 1 ? n0 : n0 + n1);
+          c = W.so[kin] + (i - before);
+        }
+        float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) p0 = b.hit4[b.cell_in[c]];
+        const bool first_b0 = valid && kInner[L1][kin] == 0;
+        const float ta = __fdividef(p1.z - p0.z, p1.w - p0.w);  // the cell's slope dz/dr
+        const float id1 = __fdividef(1.0f, p1.w - p0.w);
+        const float wa = (cuts.rz0 + cuts.rz1 * cuts.cotmax) * id1;
+        const float ua = cuts.rz0 + cuts.rz1 * fabsf(ta);
+        const float shrink = 1.0f - cuts.rz1 * id1;
+
+        // mode 0: links buffered in shared memory; mode 1: written straight to their
+        // slots (the group found more than the buffer holds)
+        unsigned long long lbase = 0;
+#pragma unroll 1
+        for (int mode = 0; mode < 2; ++mode) {
+          __syncwarp();
+          W.lcnt[lane] = 0;
+          uint32_t nf = 0;  // links found by the group (mode 0)
+          __syncwarp();
+#pragma unroll 1
+          for (int piece = 0; piece < npieces; ++piece) {
+            if (W.piece != piece) stage_piece(piece);
+            const float m = W.m, tmin = W.tmin, scale = W.scale;
+            float w = 0.0f;
+            uint32_t pos = 0, pend = 0;
+            if (valid) {
               const float im = __fdividef(1.0f, m);
               float wk = fmaf(ua, im, wa);
               if (shrink > 0.0f) wk = fminf(wk, __fdividef(ua * (id1 + im), shrink));
-              w[k] = m > 0.0f ? wk * 1.01f + 1e-3f : kInf;
+              w = wk * 1.01f + 1e-3f;
+              const float w2 = w * 1.001f + 1e-5f;
+              pos = W.bstart[slope_bucket(__fsub_rn(ta, w2), tmin, scale)];
+              pend = W.bstart[slope_bucket(__fadd_rn(ta, w2), tmin, scale) + 1];
             }
-          }
-          // One sweep site: one sweep over all staged segments, or (when they do not fit)
-          // one per piece, staged in turn at position 0.  The queue is drained before a
-          // stage changes and after the last sweep of h1.
-          const bool last_group = ib + 32 >= W.nin;
-#pragma unroll 1
-          for (int k = 0; k < (fits ? 1 : kMaxOuter); ++k) {
-            const uint32_t cnt = fits ? 1u : W.sg[k].cnt;
-            for (uint32_t j0 = 0; j0 < cnt; j0 += kOutStage) {
-              uint32_t n8 = tot, pos1 = W.pos[1], pos2 = W.pos[2];
-              float w0 = w[0], w1 = w[1], w2 = w[2];
-              if (!fits) {
-                const uint32_t n = min(cnt - j0, (uint32_t)kOutStage);
-                __syncwarp();
-                stage(W.sg[k].off + j0, n, 0, W.p1);
-                if (lane == 0) {
-                  W.pos[0] = 0;
-                  W.pos[1] = W.pos[2] = kOutStage;
-                  W.coff[0] = W.sg[k].off + j0;
+            uint32_t head = 0, tail = 0;
+            // C2 and C3 on up to 32 queued pairs, all lanes busy
+            auto process = [&](uint32_t nt) {
+              __syncwarp();
+              const bool v = (uint32_t)lane < nt;
+              const uint2 e = v ? W.q[(head + lane) & (kQueue - 1)] : make_uint2(0u, 0u);
+              head += nt;
+              const int il = (int)e.x;
+              const float4 q0 = make_float4(__shfl_sync(kFull, p0.x, il), __shfl_sync(kFull, p0.y, il),
+                                            __shfl_sync(kFull, p0.z, il), __shfl_sync(kFull, p0.w, il));
+              const bool qb0 = __shfl_sync(kFull, first_b0, il);
+              const uint32_t ca = __shfl_sync(kFull, c, il);
+              bool ok = false;
+              float q = 0.0f;
+              uint32_t cb = 0;
+              if (v) {
+                ok = link_c23(cuts, q0, qb0, p1, W.p2[e.y], q);
+                // the target cell, named by its outer hit and the slot of h1's layer
+                // among that hit's inner layers until k_link_targets finds it
+                cb = W.h2[e.y] | ((uint32_t)W.j2[e.y] << 30);
+              }
+              uint32_t rk = 0;
+              if (ok) rk = atomicAdd(&W.lcnt[il], 1u);
+              const unsigned pm = __ballot_sync(kFull, ok);
+              if (ok) {
+                if (mode == 0) {
+                  const uint32_t seq = nf + __popc(pm & lt_mask);
+                  if (seq < (uint32_t)kFound) {
+                    W.fa[seq] = (uint32_t)il | (rk << 5);
+                    W.fb[seq] = cb;
+                    W.fq[seq] = q;
+                  }
+                } else {
+                  write_link(lbase + W.loff[il] + rk, ca, cb, q);
                 }
-                __syncwarp();
-                n8 = round8(n);
-                pos1 = pos2 = kOutStage;
-                w0 = k == 0 ? w[0] : (k == 1 ? w[1] : w[2]);
               }
-              const bool last = !fits || last_group;
-              // one call site each for the sweep and the exact cuts (instruction cache)
-              for (uint32_t j = 0;;) {
-                j = sweep(j, n8, ta, w0, w1, w2, pos1, pos2, ix);
-                const bool done = j >= n8;
-                while (tail - head >= 32u || (done && last && tail != head))
-                  process(min(32u, tail - head));
-                if (done) break;
+              nf += __popc(pm);
+            };
+            // each lane walks its own bucket range; C1 passes are queued
+            while (__any_sync(kFull, pos < pend)) {
+              bool pass = false;
+              uint32_t e = 0;
+              if (pos < pend) {
+                e = W.perm[pos++];
+                const float tb = W.t[e];
+                if (fabsf(tb - ta) <= w) pass = link_c1(cuts, p0, p1, W.p2[e]);
               }
+              const unsigned bal = __ballot_sync(kFull, pass);
+              if (pass) W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2((uint32_t)lane, e);
+              tail += __popc(bal);
+              if (tail - head >= 32u) process(32u);
             }
-          }
-        }
-        __syncwarp();
-        if (pass == 1) break;
-        nfound = nf;
-        if (nf == 0) break;
-
-        // One reservation for the links of h1; with more than kFound of them, twice as
-        // many slots, the second half holding them in search order until they are sorted.
-        const uint32_t nres = nf <= (uint32_t)kFound ? nf : 2 * nf;
-        unsigned long long hlo, hhi;
-        const unsigned long long lbase = chunk_take_shared(W, 0, &b.cnt[CNT_LINKS], nres, &hlo, &hhi);
-        mark_link_hole(hlo, hhi);
-        const bool lvalid = lbase + nres <= cap_links;
-        if (lane == 0) {
-          W.used += nf;
-          W.lbase = lbase;
-          W.lvalid = lvalid;
-        }
-        if (!lvalid) {
-          if (lane == 0) atomicOr(&b.cnt[CNT_STATUS], ST_LINKS);
-          mark_link_hole(lbase, lbase + nres);  // slots below the capacity stay readable
-        } else if (nf > (uint32_t)kFound) {
-          for (uint32_t i = lane; i < (uint32_t)kFound; i += 32)
-            write_link(lbase + nf + i, W.fs[i], W.fd[i], W.fq[i]);
-        }
-      }
-
-      // The links of h1, sorted by source cell (stable), form one list per source:
-      // link_oc (offset, count) of each source, which joins the list of possible roots.
-      __syncwarp();
-      if (nfound > 0 && W.lvalid) {
-        const unsigned long long lbase = W.lbase;
-        const bool big = nfound > (uint32_t)kFound;
-        const unsigned long long tmp = lbase + nfound;  // search-order copy when big
-        auto src_of = [&](uint32_t j) { return big ? b.link_src[tmp + j] : W.fs[j]; };
-        for (uint32_t i0 = 0; i0 < nfound; i0 += 32) {
-          const uint32_t i = i0 + lane;
-          uint32_t a = kHole, rank = 0, cnt = 0, c = 0;
-          float q = 0.0f;
-          bool first = false;
-          if (i < nfound) {
-            a = src_of(i);
-            first = true;
-            for (uint32_t j = 0; j < nfound; ++j) {
-              const uint32_t aj = src_of(j);
-              rank += (aj < a) || (aj == a && j < i);
-              cnt += aj == a;
-              first = first && !(aj == a && j < i);
-            }
-            c = big ? b.link_dst[tmp + i] : W.fd[i];
-            q = big ? b.link_q[tmp + i] : W.fq[i];
+            while (tail != head) process(min(32u, tail - head));
           }
           __syncwarp();
-          if (i < nfound) {
-            write_link(lbase + rank, a, c, q);
-            if (first) b.link_oc[a] = make_uint2((uint32_t)(lbase + rank), cnt);
+          if (mode == 1) break;
+          // finalise the group: one reservation, each cell's links consecutive
+          const uint32_t nl = valid ? W.lcnt[lane] : 0u;
+          const uint32_t inc = warp_incl_scan(nl);
+          const uint32_t tot = __shfl_sync(kFull, inc, 31);
+          if (tot == 0) break;
+          unsigned long long hlo, hhi;
+          lbase = chunk_take_shared(W, &b.cnt[CNT_LINKS], tot, &hlo, &hhi);
+          mark_link_hole(hlo, hhi);
+          if (lane == 0) W.used += tot;
+          if (lbase + tot > cap_links) {
+            if (lane == 0) atomicOr(&b.cnt[CNT_STATUS], ST_LINKS);
+            mark_link_hole(lbase, lbase + tot);  // slots below the capacity stay readable
+            break;
           }
-        }
-        if (big) {
+          W.loff[lane] = inc - nl;
+          if (nl) b.link_oc[c] = make_uint2((uint32_t)(lbase + inc - nl), nl);
           __syncwarp();
-          mark_link_hole(tmp, tmp + nfound);
+          if (tot > (uint32_t)kFound) continue;  // search again, writing directly
+          for (uint32_t f0 = 0; f0 < tot; f0 += 32) {
+            const uint32_t f = f0 + lane;
+            const uint32_t fa = f < tot ? W.fa[f] : 0u;
+            const int il = (int)(fa & 31u);
+            const uint32_t ca = __shfl_sync(kFull, c, il);
+            if (f < tot) write_link(lbase + W.loff[il] + (fa >> 5), ca, W.fb[f], W.fq[f]);
+          }
+          break;
         }
       }
-      __syncwarp();
     }
-    __syncwarp();
   }
   __syncwarp();
-  mark_link_hole(W.chunk_next[0], W.chunk_end[0]);
+  mark_link_hole(W.chunk_next, W.chunk_end);
   if (lane == 0 && W.used) atomicAdd(&b.cnt[CNT_LINKS_USED], W.used);
+}
+
+// The target cell (h1, h2) of every link: h1 (the outer hit of the source cell) in h2's
+// incoming segment from h1's layer, which is ordered by inner hit, by binary search;
+// one thread per link slot.  Plain form: the target's incoming-link flag is set.  A
+// target can be missing only when the doublet stage ran out of cell slots (its status
+// bit is set then); the link then points back to its source, a valid cell, so that the
+// later stages stay within their arrays.
+template <bool GATE>
+__global__ void k_link_targets(Buffers b, uint64_t cap_links) {
+  const uint64_t nl = min(b.cnt[CNT_LINKS], (unsigned long long)cap_links);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += stride) {
+    const uint32_t a = b.link_src[l];
+    if (a == kHole) continue;
+    const uint32_t t = b.link_dst[l];
+    const uint32_t h1 = b.cell_out[a];
+    const uint2 sg = b.seg[(uint64_t)(t & 0x3fffffffu) * kMaxInner + (t >> 30)];
+    uint32_t lo = sg.x, hi = sg.x + sg.y;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (b.cell_in[mid] < h1) lo = mid + 1; else hi = mid;
+    }
+    const bool found = lo < sg.x + sg.y && b.cell_in[lo] == h1;
+    const uint32_t c = found ? lo : a;
+    b.link_dst[l] = c;
+    if (!GATE && found) b.has_in[c] = 1;
+  }
 }
 
 }  // namespace
 
 void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
                     bool gated) {
-  PT_TRACE(l, s, "scan", launch_scan(b.in_cnt, b.in_start, &b.cnt[CNT_SCAN_HITS], b.scan_part, s));
-  PT_TRACE(l, s, "k_in_scatter",
-           k_in_scatter<<<l.sms * kScatterBlocksPerSm, 256, 0, s>>>(b, p.phi_bins));
-  if (gated)
+  cudaMemsetAsync(&b.cnt[CNT_LNK_WORK], 0, sizeof(unsigned long long), s);  // work counter
+  if (gated) {
     PT_TRACE(l, s, "k_connect",
-             k_connect<true><<<l.sms * kConnBlocksPerSm, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
-                                                                  (uint64_t)p.max_links));
-  else
+             k_connect<true><<<l.sms * kConnBlocksPerSm, kConnWarps * 32, 0, s>>>(
+                 b, p.cuts, p.phi_bins, (uint64_t)p.max_links));
+    PT_TRACE(l, s, "k_link_targets",
+             k_link_targets<true><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links));
+  } else {
     PT_TRACE(l, s, "k_connect",
-             k_connect<false><<<l.sms * kConnBlocksPerSm, kConnWarps * 32, 0, s>>>(b, p.cuts, p.phi_bins,
-                                                                   (uint64_t)p.max_links));
+             k_connect<false><<<l.sms * kConnBlocksPerSm, kConnWarps * 32, 0, s>>>(
+                 b, p.cuts, p.phi_bins, (uint64_t)p.max_links));
+    PT_TRACE(l, s, "k_link_targets",
+             k_link_targets<false><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links));
+  }
 }
 
 }  // namespace ptca

@@ -1,21 +1,24 @@
 // Stage A2: doublets ("cells").  Every hit is paired with the hits of each adjacent
-// outer layer that pass the cuts D0..D4 (Sec. 2.2.1, Fig. 2: the chain's first
-// combinatorial step joins hits of neighbouring layers two by two).
+// layer that pass the cuts D0..D4 (Sec. 2.2.1, Fig. 2: the chain's first combinatorial
+// step joins hits of neighbouring layers two by two).
 //
-// A warp searches the doublets of one inner hit at a time.  For each outer layer the
-// candidates are the hits of the
-// azimuthal window that can pass D1 and D2: a circle through the beam spot with
-// curvature <= kmax turns by at most asin(kmax*ro/2) - asin(kmax*ri/2) between radii
-// ri < ro, so the window is that angle (ro = the largest radius seen on the outer
-// layer in this event) plus a safety margin and one bin each side.  The window is one
-// contiguous range of the sorted hits (two when it wraps).  Lanes stride over it,
-// test the exact float32 cuts, and stage the passing outer hits in shared memory; the
-// segment is then appended with one reservation per
-// (hit, outer layer), so the cells leaving a hit towards one layer are contiguous.
-// Each segment records the smallest dr of its cells, which bounds the link stage's
-// slope window.  Slots are reserved through a per-warp chunk allocator; unused slots
-// are marked as holes.  Each cell is also counted on its outer hit, which sizes the link
-// stage's per-hit lists of incoming cells.
+// The search runs from the outer hit of each pair towards its inner layers, so that
+// the cells ending on one hit come out contiguous: for each outer hit and inner-layer
+// slot, one segment of cells ordered by inner hit.  The link stage then finds the cells
+// arriving at a middle hit in its own segments, with no scatter by outer hit and no
+// returning atomic per cell.
+//
+// Candidates are the inner-layer hits of an azimuthal window that can pass D1 and D2:
+// a circle through the beam spot with curvature <= kmax turns by at most
+// asin(kmax*ro/2) - asin(kmax*ri/2) between radii ri < ro (and every radius of this
+// detector lies on the first half of such a circle, which D1 keeps), so with ri bounded
+// below by the smallest radius seen on the inner layer in this event the window is
+// asin(kmax*ro/2) - asin(kmax*ri_min/2), plus a safety margin and one bin each side.
+// It is one contiguous range of the sorted hits, or two when it wraps, taken in
+// increasing index order.  Lanes stride over it, test the exact float32 cuts and stage
+// the passing inner hits in shared memory; the segment is then appended with one
+// reservation per (hit, inner slot).  Slots are reserved through a per-warp chunk
+// allocator; unused slots are marked as holes.
 #include "ptca_internal.cuh"
 
 namespace ptca {
@@ -26,54 +29,48 @@ constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kHalfPi = 1.57079632679489661923f;
 constexpr int kWarpsPerBlock = 8;
 
-// Largest azimuth difference (radians) between an inner hit at ri and any outer hit
-// at radius <= ro_max that can pass D1 (same hemisphere) and D2 (curvature <= kmax):
-// asin(kmax*ro_max/2) - asin(kmax*ri/2), given the first term (asin_o, +inf when
-// kmax*ro_max/2 >= 0.7, where only D1 bounds the angle) and the second (asin_i).
-__device__ __forceinline__ float phi_window(float asin_o, float asin_i) {
-  if (asin_o == __int_as_float(0x7f800000)) return kHalfPi + 1e-3f;
-  return fminf(asin_o - asin_i + 1e-4f, kHalfPi + 1e-3f);
+// Writes one cell; its two link flags start cleared.
+__device__ __forceinline__ void write_cell(const Buffers& b, uint64_t c, uint32_t in, uint32_t out) {
+  b.cell_in[c] = in;
+  b.cell_out[c] = out;
+  b.has_in[c] = 0;
+  b.has_out[c] = 0;
 }
 
-// Writes one cell and counts it on its outer hit (its link flags are cleared by the
-// in-list scatter, which visits every cell slot).
-__device__ __forceinline__ void write_cell(const Buffers& b, uint64_t c, uint32_t s, uint32_t o) {
-  b.cell_in[c] = s;
-  b.cell_out[c] = o;
-  atomicAdd(&b.in_cnt[o], 1u);  // no return value: a fire-and-forget reduction
-}
-
-// Azimuthal window of inner hit `hi` (global bin gb) towards outer slot k: up to two
-// ranges [r.x, r.y) and [r.z, r.w) of the sorted hits; all empty where the slot is
-// unused or the outer layer ends inside the inner hit's radius.
-__device__ __forceinline__ uint4 doublet_window(const Buffers& b, const pt_cuts& cuts, int32_t B,
-                                                float bins_per_rad, uint32_t gb, float4 hi,
-                                                float asin_i, int k) {
+// Azimuthal window of outer hit `ho` (global bin gb, asin_o = asin(kmax*ro/2), +inf where
+// kmax*ro/2 >= 0.7) towards inner slot k: up to two ranges [r.x, r.y) and [r.z, r.w) of
+// the sorted hits, the first below the second; empty where the slot is unused or the
+// inner layer has no hit inside the outer hit's radius.
+__device__ __forceinline__ uint4 reverse_window(const Buffers& b, int32_t B, float bins_per_rad,
+                                                uint32_t gb, float4 ho, float asin_o, int k) {
   const int el = gb / B;  // event*10 + layer
   const int e = el / kLayers, L = el - e * kLayers;
   const int bin = gb - el * B;
   uint4 r = make_uint4(0u, 0u, 0u, 0u);
-  if (k >= kNOuter[L]) return r;
-  const int Lo = kOuter[L][k];
-  const float ro_max = __uint_as_float(b.layer_rmax[e * kLayers + Lo]);
-  if (!(ro_max > hi.w)) return r;
-  const int w = (int)ceilf(phi_window(b.layer_asin[e * kLayers + Lo], asin_i) * bins_per_rad) + 1;
-  const uint32_t base = (uint32_t)(e * kLayers + Lo) * (uint32_t)B;
+  if (k >= kNInner[L]) return r;
+  const int Li = kInner[L][k];
+  const float ri_min = __uint_as_float(b.layer_rmin[e * kLayers + Li]);
+  if (!(ho.w > ri_min)) return r;  // D0 fails for every hit of the inner layer
+  float win = kHalfPi + 1e-3f;     // where the curvature bound is void, D1's
+  if (asin_o != __int_as_float(0x7f800000))
+    win = fminf(asin_o - b.layer_asin_lo[e * kLayers + Li] + 1e-4f, win);
+  const int w = (int)ceilf(win * bins_per_rad) + 1;
+  const uint32_t base = (uint32_t)(e * kLayers + Li) * (uint32_t)B;
   if (2 * w + 1 >= B) {
     r.x = b.bin_start[base];
     r.y = b.bin_start[base + B];
   } else {
     const int lo = bin - w, hb = bin + w;
     if (lo < 0) {
-      r.x = b.bin_start[base + B + lo];
-      r.y = b.bin_start[base + B];
-      r.z = b.bin_start[base];
-      r.w = b.bin_start[base + hb + 1];
+      r.x = b.bin_start[base];
+      r.y = b.bin_start[base + hb + 1];
+      r.z = b.bin_start[base + B + lo];
+      r.w = b.bin_start[base + B];
     } else if (hb >= B) {
-      r.x = b.bin_start[base + lo];
-      r.y = b.bin_start[base + B];
-      r.z = b.bin_start[base];
-      r.w = b.bin_start[base + hb - B + 1];
+      r.x = b.bin_start[base];
+      r.y = b.bin_start[base + hb - B + 1];
+      r.z = b.bin_start[base + lo];
+      r.w = b.bin_start[base + B];
     } else {
       r.x = b.bin_start[base + lo];
       r.y = b.bin_start[base + hb + 1];
@@ -82,13 +79,13 @@ __device__ __forceinline__ uint4 doublet_window(const Buffers& b, const pt_cuts&
   return r;
 }
 
-// Warps take chunks of 32 consecutive sorted hits from a work counter.  The chunk's
-// windows are found lane-parallel (one hit per lane, all of its loads in flight at
-// once) and kept in shared memory; the warp then searches them hit by hit.
+// Warps take chunks of 32 consecutive sorted (outer) hits from a work counter.  The
+// chunk's windows are found lane-parallel (one hit per lane, all of its loads in flight
+// at once) and kept in shared memory; the warp then searches them hit by hit.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
     k_doublets(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap_cells) {
   __shared__ uint32_t st_val[kWarpsPerBlock][kStage];
-  __shared__ uint4 st_rng[kWarpsPerBlock][32][kMaxOuter];
+  __shared__ uint4 st_rng[kWarpsPerBlock][32][kMaxInner];
   __shared__ float4 st_hit[kWarpsPerBlock][32];
   const int lane = lane_id(), wib = threadIdx.x >> 5;
   uint32_t* sval = st_val[wib];
@@ -114,37 +111,32 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
     if ((uint32_t)lane < nh) {
       const uint32_t s = (uint32_t)s0 + lane;
       const uint32_t gb = b.hbin[s];
-      const float4 hi = b.hit4[s];
-      const float asin_i = asinf(0.5f * cuts.kmax * hi.w);  // unused where the outer term is +inf
-      st_hit[wib][lane] = hi;
+      const float4 ho = b.hit4[s];
+      const float a = 0.5f * cuts.kmax * ho.w;
+      const float asin_o = a >= 0.7f ? __int_as_float(0x7f800000) : asinf(a);
+      st_hit[wib][lane] = ho;
 #pragma unroll
-      for (int k = 0; k < kMaxOuter; ++k)
-        st_rng[wib][lane][k] = doublet_window(b, cuts, B, bins_per_rad, gb, hi, asin_i, k);
+      for (int k = 0; k < kMaxInner; ++k)
+        st_rng[wib][lane][k] = reverse_window(b, B, bins_per_rad, gb, ho, asin_o, k);
     }
     __syncwarp();
 
     for (uint32_t j = 0; j < nh; ++j) {
       const uint32_t s = (uint32_t)s0 + j;
-      const float4 hi = st_hit[wib][j];
-      for (int k = 0; k < kMaxOuter; ++k) {
+      const float4 ho = st_hit[wib][j];
+      for (int k = 0; k < kMaxInner; ++k) {
         const uint4 rg = st_rng[wib][j][k];
         uint32_t cnt = 0;
-        float mdr = __int_as_float(0x7f800000);
         // pass 1: test, stage up to kStage passing hits, count all
         for (int part = 0; part < 2; ++part) {
           const uint32_t beg = part ? rg.z : rg.x, end = part ? rg.w : rg.y;
-          for (uint32_t o0 = beg; o0 < end; o0 += 32) {
-            const uint32_t o = o0 + lane;
-            bool pass = false;
-            if (o < end) {
-              const float4 ho = b.hit4[o];
-              pass = doublet_pass(cuts, hi, ho);
-              if (pass) mdr = fminf(mdr, fsub(ho.w, hi.w));
-            }
+          for (uint32_t i0 = beg; i0 < end; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            const bool pass = i < end && doublet_pass(cuts, b.hit4[i], ho);
             const unsigned bal = __ballot_sync(kFull, pass);
             if (pass) {
               const uint32_t pos = cnt + __popc(bal & lt_mask);
-              if (pos < kStage) sval[pos] = o;
+              if (pos < kStage) sval[pos] = i;
             }
             cnt += __popc(bal);
           }
@@ -152,8 +144,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
 
         uint32_t seg_off = 0, seg_cnt = 0;
         if (cnt > 0) {
-          // warp minimum of dr over the passing hits
-          for (int off = 16; off > 0; off >>= 1) mdr = fminf(mdr, __shfl_xor_sync(kFull, mdr, off));
           unsigned long long hlo, hhi;
           const unsigned long long base = chunk_take(ch, &b.cnt[CNT_CELLS], cnt, &hlo, &hhi);
           mark_hole(hlo, hhi);
@@ -163,8 +153,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
             mark_hole(base, base + cnt);  // slots below the capacity stay readable
           } else if (cnt <= (uint32_t)kStage) {
             __syncwarp();
-            for (uint32_t i = lane; i < cnt; i += 32)
-              write_cell(b, base + i, s, sval[i]);
+            for (uint32_t i = lane; i < cnt; i += 32) write_cell(b, base + i, sval[i], s);
             seg_off = (uint32_t)base;
             seg_cnt = cnt;
           } else {
@@ -172,15 +161,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
             uint32_t pos0 = 0;
             for (int part = 0; part < 2; ++part) {
               const uint32_t beg = part ? rg.z : rg.x, end = part ? rg.w : rg.y;
-              for (uint32_t o0 = beg; o0 < end; o0 += 32) {
-                const uint32_t o = o0 + lane;
-                bool pass = false;
-                if (o < end) pass = doublet_pass(cuts, hi, b.hit4[o]);
+              for (uint32_t i0 = beg; i0 < end; i0 += 32) {
+                const uint32_t i = i0 + lane;
+                const bool pass = i < end && doublet_pass(cuts, b.hit4[i], ho);
                 const unsigned bal = __ballot_sync(kFull, pass);
-                if (pass) {
-                  const uint64_t c = base + pos0 + __popc(bal & lt_mask);
-                  write_cell(b, c, s, o);
-                }
+                if (pass) write_cell(b, base + pos0 + __popc(bal & lt_mask), i, s);
                 pos0 += __popc(bal);
               }
             }
@@ -188,16 +173,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
             seg_cnt = cnt;
           }
         }
-        // every slot is written (empty where the layer has fewer outer layers), so
+        // every slot is written (empty where the layer has fewer inner layers), so
         // readers need not know the hit's layer
-        if (lane == 0) {
-          Segment sg;
-          sg.off = seg_off;
-          sg.cnt = seg_cnt;
-          sg.mdr = seg_cnt ? mdr : -1.0f;
-          sg.pad = 0;
-          b.seg[(uint64_t)s * kMaxOuter + k] = sg;
-        }
+        if (lane == 0) b.seg[(uint64_t)s * kMaxInner + k] = make_uint2(seg_off, seg_cnt);
         __syncwarp();
       }
     }

@@ -3,7 +3,6 @@
 // memory (see pt_ca.h).  It reuses the library's binning kernels on a view of that
 // array and runs its own doublet kernel, which writes the pairs straight into the
 // caller's output arrays instead of the context's cell arrays.
-#include <mutex>
 #include <string>
 
 #include "ptca_internal.cuh"
@@ -21,7 +20,7 @@ constexpr size_t kNaNb = (size_t)kLayers * kNaBins + 1;
 // Bytes of each scratch buffer, in the order na_layout carves them.
 enum NaPart {
   NA_HDR, NA_CNT, NA_OFF, NA_IN_BIN, NA_IN_RANK, NA_HIT4, NA_PERM, NA_HBIN, NA_BIN_CNT,
-  NA_BIN_START, NA_RMAX, NA_ASIN, NA_BUCKET_CNT, NA_IN_CNT, NA_USED, NA_SCAN,
+  NA_BIN_START, NA_RMAX, NA_ASIN, NA_RMIN, NA_ASIN_LO, NA_BUCKET_CNT, NA_USED, NA_SCAN,
   NA_PARTS
 };
 constexpr size_t kNaPart[NA_PARTS] = {
@@ -29,7 +28,8 @@ constexpr size_t kNaPart[NA_PARTS] = {
     kNaMaxHits * 4, kNaMaxHits * 4,                          // in_bin, in_rank
     kNaMaxHits * 16, kNaMaxHits * 4, kNaMaxHits * 4,         // hit4, perm, hbin
     kNaNb * 4, kNaNb * 4, kLayers * 4, kLayers * 4,          // bins, layer r max, layer asin
-    (kNaMaxHits + 1) * 4, (kNaMaxHits + 1) * 4, kNaMaxHits,  // cleared: bucket, in, used
+    kLayers * 4, kLayers * 4,                                // layer r min, its asin
+    (kNaMaxHits + 1) * 4, kNaMaxHits,                        // cleared: bucket, used
     (kScanBlocks + 1) * 4};                                  // scan partials
 constexpr size_t na_offset(int part) {
   size_t off = 0;
@@ -58,8 +58,9 @@ Buffers na_layout(char* base, const float* x, const float* y, const float* z,
   b.bin_start = (uint32_t*)at(NA_BIN_START);
   b.layer_rmax = (uint32_t*)at(NA_RMAX);
   b.layer_asin = (float*)at(NA_ASIN);
+  b.layer_rmin = (uint32_t*)at(NA_RMIN);
+  b.layer_asin_lo = (float*)at(NA_ASIN_LO);
   b.bucket_cnt = (uint32_t*)at(NA_BUCKET_CNT);
-  b.in_cnt = (uint32_t*)at(NA_IN_CNT);
   b.used = (uint8_t*)at(NA_USED);
   b.scan_part = (uint32_t*)at(NA_SCAN);
   b.in_x = (float*)x;
@@ -142,9 +143,6 @@ __global__ void k_na_doublets(Buffers b, pt_cuts cuts, int32_t* inner, int32_t* 
   }
 }
 
-std::mutex g_na_mutex;
-void* g_na_ptr[64];  // device address of g_scratch, per device ordinal
-
 pt_status na_fail(pt_status st, const char* msg, cudaError_t e = cudaSuccess) {
   std::string m = msg;
   if (e != cudaSuccess) {
@@ -178,20 +176,12 @@ extern "C" pt_status pt_find_doublets_noalloc(const pt_cuts* cuts, int64_t n, co
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_fail(PT_ERR_CUDA, "cudaGetDevice failed", e);
-  if (dev < 0 || dev >= 64) return na_fail(PT_ERR_INVALID, "device ordinal >= 64");
+  // The scratch array's device address on the current device, looked up on every call
+  // (with the device current) so that a context made again after a reset is followed.
   void* base = nullptr;
-  {
-    // set-up, once per device, with that device current
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-      e = cudaGetSymbolAddress(&g_na_ptr[dev], g_scratch);
-      if (e != cudaSuccess) {
-        g_na_ptr[dev] = nullptr;
-        return na_fail(PT_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed", e);
-      }
-    }
-    base = g_na_ptr[dev];
-  }
+  e = cudaGetSymbolAddress(&base, g_scratch);
+  if (e != cudaSuccess || !base)
+    return na_fail(PT_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed", e);
   cudaStream_t s = (cudaStream_t)stream;
   Buffers b = na_layout((char*)base, x, y, z, layer);
   Params p{};

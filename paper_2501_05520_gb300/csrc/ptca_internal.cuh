@@ -19,6 +19,7 @@ constexpr int kLayers = 10;
 constexpr int kMaxHits = 6;                // longest chain of the layer graph
 constexpr int kMaxCellsPerNt = kMaxHits - 1;
 constexpr int kMaxOuter = 3;               // outer layers paired with one inner layer
+constexpr int kMaxInner = 3;               // inner layers paired with one outer layer
 constexpr int kStage = 256;                // staged doublets per (hit, outer layer)
 constexpr int kLocalLinks = 8;             // links of one cell kept in registers
 constexpr int kRankBits = 29;              // duplicate-cleaning key: rank field width
@@ -44,6 +45,7 @@ enum : int {
   CNT_RAW_RUNS = 17,    // raw input: module runs (size of the hit-count scan)
   CNT_RAW_HITS = 18,    // raw input: hits made from the digis
   CNT_RAW_BIG = 19,     // raw input: long module runs listed for the block-per-run launch
+  CNT_LNK_WORK = 20,    // link search: next chunk of 32 sorted middle hits
   CNT_N = 24
 };
 // raw-input status bits (cnt[CNT_RAW_STATUS])
@@ -79,15 +81,6 @@ struct GateWeights {
   float tau;
 };
 
-// Cells leaving one hit towards one outer layer: [off, off + cnt) of the cell arrays;
-// mdr = the smallest dr (r_outer - r_inner) among them, -1 when the segment is empty.
-struct __align__(16) Segment {
-  uint32_t off;
-  uint32_t cnt;
-  float mdr;
-  uint32_t pad;
-};
-
 struct BatchHeader {
   int32_t n_events;
   int32_t n_hits;
@@ -121,8 +114,13 @@ struct Buffers {
   uint32_t* layer_rmax;      // [max_events*10] float bits of max r per event layer
   float* layer_asin;         // [max_events*10] asin(kmax r_max / 2) per event layer,
                              //   +inf when kmax r_max / 2 >= 0.7
-  // doublet segments: per sorted hit and outer-layer slot (all 3 slots written)
-  Segment* seg;              // [max_hits*3]
+  uint32_t* layer_rmin;      // [max_events*10] float bits of min r per event layer (+inf
+                             //   for an empty layer)
+  float* layer_asin_lo;      // [max_events*10] asin(kmax r_min / 2) (0 where that is >= 0.7
+                             //   or the layer is empty)
+  // incoming segments: per sorted (outer) hit and inner-layer slot, the cells ending on
+  // the hit from that layer, cells [x, x + y), ordered by inner hit (all 3 slots written)
+  uint2* seg;                // [max_hits*3]
   // cells
   uint32_t* cell_in;         // [max_cells] sorted hit index
   uint32_t* cell_out;        // [max_cells]
@@ -130,13 +128,7 @@ struct Buffers {
   uint8_t* has_out;          // [max_cells] an accepted link starts from the cell
   uint2* link_oc;            // [max_cells] first slot and number of the cell's links
                              //   (valid where it has links)
-  unsigned long long* best;  // [max_cells] duplicate-cleaning key (cells on ntuplets);
-                             //   shares its memory with in_rec, which is dead by then
-  uint32_t* in_cnt;          // [max_hits + 1] cells ending on each sorted hit (counted
-                             //   down to 0 again by the in-list scatter)
-  uint32_t* in_start;        // [max_hits + 1] exclusive scan of in_cnt
-  uint2* in_rec;             // [max_cells] cells grouped by the hit they end on:
-                             //   (cell, inner sorted hit | inner layer is 0 << 31)
+  unsigned long long* best;  // [max_cells] duplicate-cleaning key (cells on ntuplets)
   // links
   uint32_t* link_dst;        // [max_links]
   float* link_q;             // [max_links]
@@ -455,6 +447,12 @@ static __constant__ int8_t kOuter[kLayers][kMaxOuter] = {
     {1, 4, 7}, {2, 4, 7}, {3, 4, 7}, {-1, -1, -1}, {5, -1, -1},
     {6, -1, -1}, {-1, -1, -1}, {8, -1, -1}, {9, -1, -1}, {-1, -1, -1}};
 static __constant__ int8_t kNOuter[kLayers] = {3, 3, 3, 0, 1, 1, 0, 1, 1, 0};
+// Inner layers of each outer layer (the same pairs seen from the outer side), -1 padded;
+// a hit's incoming segments are numbered by these slots.
+static __constant__ int8_t kInner[kLayers][kMaxInner] = {
+    {-1, -1, -1}, {0, -1, -1}, {1, -1, -1}, {2, -1, -1}, {0, 1, 2},
+    {4, -1, -1}, {5, -1, -1}, {0, 1, 2}, {7, -1, -1}, {8, -1, -1}};
+static __constant__ int8_t kNInner[kLayers] = {0, 1, 1, 1, 3, 1, 1, 3, 1, 1};
 #endif
 
 }  // namespace ptca

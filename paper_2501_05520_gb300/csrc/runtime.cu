@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <initializer_list>
 #include <utility>
 #include <vector>
 
@@ -135,16 +136,15 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.bin_start = (uint32_t*)take(NB * 4);
   t.layer_rmax = (uint32_t*)take(E * kLayers * 4);
   t.layer_asin = (float*)take(E * kLayers * 4);
-  t.seg = (Segment*)take(N * kMaxOuter * sizeof(Segment));
+  t.layer_rmin = (uint32_t*)take(E * kLayers * 4);
+  t.layer_asin_lo = (float*)take(E * kLayers * 4);
+  t.seg = (uint2*)take(N * kMaxInner * sizeof(uint2));
   t.cell_in = (uint32_t*)take(C * 4);
   t.cell_out = (uint32_t*)take(C * 4);
   t.has_in = (uint8_t*)take(C);
   t.has_out = (uint8_t*)take(C);
   t.link_oc = (uint2*)take(C * 8);
-  t.in_cnt = (uint32_t*)take((N + 1) * 4);
-  t.in_start = (uint32_t*)take((N + 1) * 4);
-  t.in_rec = (uint2*)take(C * 8);
-  t.best = (unsigned long long*)t.in_rec;  // in_rec is dead once the links exist
+  t.best = (unsigned long long*)take(C * 8);
   t.link_dst = (uint32_t*)take(L * 4);
   t.link_q = (float*)take(L * 4);
   t.nt_hits = (int32_t*)take(T * kMaxHits * 4);
@@ -187,7 +187,7 @@ pt_status check_capacity(const pt_capacity* c) {
   if (c->max_events < 1 || c->max_hits < 1 || c->max_cells < 1 || c->max_links < 1 ||
       c->max_ntuplets < 1)
     return fail(PT_ERR_INVALID, "capacities must be >= 1");
-  if (c->max_hits >= (1ll << 31) - 1) return fail(PT_ERR_INVALID, "max_hits must be < 2^31 - 1");
+  if (c->max_hits >= (1ll << 30)) return fail(PT_ERR_INVALID, "max_hits must be < 2^30");
   if (c->max_cells >= (1ll << 32) - 1 || c->max_links >= (1ll << 32) - 1)
     return fail(PT_ERR_INVALID, "max_cells and max_links must be < 2^32 - 1");
   if (c->max_ntuplets >= (1ll << kRankBits))
@@ -624,21 +624,39 @@ pt_status pt_load_hits(pt_ctx* c, int64_t n, const float* x, const float* y, con
   }                                                      \
   return PT_OK;
 
+// A stage call may run again on the same loaded batch: the counters it accumulates (and
+// the ntuplet stage's per-hit tallies) start from zero each time.  The whole-batch graph
+// has these cleared once by launch_clear.
+int64_t loaded_hits(const pt_ctx* c) { return c->n_hits >= 0 ? c->n_hits : c->cap.max_hits; }
+
+void reset_counters(pt_ctx* c, std::initializer_list<int> which) {
+  for (int k : which) cudaMemsetAsync(&c->B.cnt[k], 0, sizeof(unsigned long long), c->stream);
+}
+
 pt_status pt_build_doublets(pt_ctx* c, int64_t* n_cells) {
-  STAGE_BODY(launch_doublets(c->B, c->P, c->L, c->stream), CNT_CELLS_USED, n_cells)
+  STAGE_BODY((reset_counters(c, {CNT_CELLS, CNT_CELLS_USED}),
+              launch_doublets(c->B, c->P, c->L, c->stream)),
+             CNT_CELLS_USED, n_cells)
 }
 
 pt_status pt_connect_cells(pt_ctx* c, int64_t* n_links) {
   if (c && c->gate_on) {
-    STAGE_BODY((launch_connect(c->B, c->P, c->L, c->stream, true),
+    STAGE_BODY((reset_counters(c, {CNT_LINKS, CNT_LINKS_USED, CNT_GATE_KEPT}),
+                launch_connect(c->B, c->P, c->L, c->stream, true),
                 launch_gate(c->B, c->P, c->L, c->gate, c->stream)),
                CNT_GATE_KEPT, n_links)
   }
-  STAGE_BODY(launch_connect(c->B, c->P, c->L, c->stream), CNT_LINKS_USED, n_links)
+  STAGE_BODY((reset_counters(c, {CNT_LINKS, CNT_LINKS_USED, CNT_GATE_KEPT}),
+              launch_connect(c->B, c->P, c->L, c->stream)),
+             CNT_LINKS_USED, n_links)
 }
 
 pt_status pt_find_ntuplets(pt_ctx* c, int64_t* n_ntuplets) {
-  STAGE_BODY(launch_ntuplets(c->B, c->P, c->L, c->stream, c->gate_on), CNT_SV, n_ntuplets)
+  STAGE_BODY((reset_counters(c, {CNT_NT, CNT_SCAN_NT, CNT_SV}),
+              cudaMemsetAsync(c->B.bucket_cnt, 0, (size_t)(loaded_hits(c) + 1) * 4, c->stream),
+              cudaMemsetAsync(c->B.used, 0, (size_t)loaded_hits(c), c->stream),
+              launch_ntuplets(c->B, c->P, c->L, c->stream, c->gate_on)),
+             CNT_SV, n_ntuplets)
 }
 
 pt_status pt_fit_tracks(pt_ctx* c, int64_t* n_tracks) {

@@ -42,6 +42,7 @@ def test_workspace_size_and_capacity_validation():
     for bad in (dict(pt.default_capacity(), phi_bins=8),
                 dict(pt.default_capacity(), max_ntuplets=1 << 29),
                 dict(pt.default_capacity(), max_cells=0),
+                dict(pt.default_capacity(), max_hits=1 << 30),
                 dict(pt.default_capacity(), reserved=1)):
         with pytest.raises(pt.PtError) as ei:
             pt.pt_workspace_size(bad)

@@ -17,8 +17,8 @@ import paper_2501_05520_gb300 as pt  # noqa: E402
 
 CAP = pt.default_capacity(max_events=2, hits_per_event=16384, cells_per_event=1 << 20,
                           links_per_event=1 << 17, ntuplets_per_event=1 << 16)
-STAGE_KERNELS = {"k_clear": 1, "k_bin_count": 1, "scan": 4, "k_bin_scatter": 1,
-                 "k_doublets": 1, "k_in_scatter": 1, "k_connect": 1, "k_find_ntuplets": 1,
+STAGE_KERNELS = {"k_clear": 1, "k_bin_count": 1, "scan": 3, "k_bin_scatter": 1,
+                 "k_doublets": 1, "k_connect": 1, "k_link_targets": 1, "k_find_ntuplets": 1,
                  "k_bucket_count": 1, "k_bucket_scatter": 1, "k_bucket_sort": 1,
                  "k_dedup_min": 1, "k_dedup_alive": 1, "k_dedup_triplets": 1, "k_compact": 1,
                  "k_event_offsets": 1, "k_fit": 1}

@@ -26,6 +26,14 @@ CAP = pt.default_capacity(max_events=1, hits_per_event=65536, cells_per_event=4 
                           links_per_event=1 << 20, ntuplets_per_event=1 << 19)
 
 
+class _Hits:
+    """Bare hit arrays with the attributes _noalloc reads."""
+
+    def __init__(self, x, y, z, layer):
+        self.x, self.y, self.z, self.layer = x, y, z, layer
+        self.n_hits = int(x.shape[0])
+
+
 def _noalloc(ev, cuts, cap):
     dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (ev.x, ev.y, ev.z, ev.layer)]
     inner = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
@@ -67,3 +75,24 @@ def test_noalloc_limits(cuts):
     st, _, _, _ = _noalloc(big, cuts, 16)
     assert st == pt.PT_ERR_CAPACITY
     assert "65536" in pt.lib().pt_last_error().decode()
+
+
+def test_noalloc_edge_cases(cuts):
+    """An empty event gives no doublets; a layer code of 10 is refused; a second call
+    leaves the device's free memory unchanged (the call allocates nothing)."""
+    ev = sim.generate(sim.PU50, 2062)
+    empty = _Hits(ev.x[:0], ev.y[:0], ev.z[:0], ev.layer[:0])
+    st, n, _, _ = _noalloc(empty, cuts, 16)
+    assert st == pt.PT_OK and n == 0
+    layer = ev.layer.copy()
+    layer[17] = 10
+    st, _, _, _ = _noalloc(_Hits(ev.x, ev.y, ev.z, layer), cuts, 4 << 20)
+    assert st == pt.PT_ERR_INVALID
+    st, n1, _, _ = _noalloc(ev, cuts, 4 << 20)
+    assert st == pt.PT_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    st, n2, _, _ = _noalloc(ev, cuts, 4 << 20)
+    torch.cuda.synchronize()
+    assert st == pt.PT_OK and n2 == n1
+    assert torch.cuda.mem_get_info()[0] == free0
