@@ -112,6 +112,7 @@ struct ConnWarp {
   uint8_t j2[kOut];          //   slot of the middle hit's layer among the outer hit's
                              //   inner layers
   uint8_t perm[kOut];        // bucket order -> staged index
+  float ts[kOut];            // slopes in bucket order
   uint32_t bstart[kNb + 1];  // first bucket-ordered position of each slope bucket
   uint32_t lcnt[32];         // links found per incoming cell of the group
   uint32_t loff[32];         // first slot of each incoming cell's links
@@ -256,30 +257,36 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
           for (int part = 0; part < 2; ++part) {
             const uint4 rk = W.rg[k];
             const uint32_t beg = part ? rk.z : rk.x, end = part ? rk.w : rk.y;
-            for (uint32_t o0 = beg; o0 < end; o0 += 32) {
-              const uint32_t o = o0 + lane;
-              bool pass = false;
-              float4 ho = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (o < end) {
-                ho = b.hit4[o];
-                pass = doublet_pass(cuts, p1, ho);
+            // two candidates per lane in flight: both loads are issued before either test
+            for (uint32_t o0 = beg; o0 < end; o0 += 64) {
+              float4 hv[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const uint32_t o = o0 + 32 * u + lane;
+                hv[u] = o < end ? b.hit4[o] : make_float4(0.f, 0.f, 0.f, 0.f);
               }
-              const unsigned bal = __ballot_sync(kFull, pass);
-              if (pass) {
-                const uint32_t pos = cnt + __popc(bal & lt_mask);
-                if (pos >= lo_ord && pos < lo_ord + kOut) {
-                  const uint32_t st = pos - lo_ord;
-                  const float t = __fdividef(ho.z - p1.z, ho.w - p1.w);
-                  W.p2[st] = ho;
-                  W.t[st] = t;
-                  W.h2[st] = o;
-                  W.j2[st] = j2;
-                  m = fminf(m, fsub(ho.w, p1.w));
-                  tlo = fminf(tlo, t);
-                  thi = fmaxf(thi, t);
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const uint32_t o = o0 + 32 * u + lane;
+                const float4 ho = hv[u];
+                const bool pass = o < end && doublet_pass(cuts, p1, ho);
+                const unsigned bal = __ballot_sync(kFull, pass);
+                if (pass) {
+                  const uint32_t pos = cnt + __popc(bal & lt_mask);
+                  if (pos >= lo_ord && pos < lo_ord + kOut) {
+                    const uint32_t st = pos - lo_ord;
+                    const float t = __fdividef(ho.z - p1.z, ho.w - p1.w);
+                    W.p2[st] = ho;
+                    W.t[st] = t;
+                    W.h2[st] = o;
+                    W.j2[st] = j2;
+                    m = fminf(m, fsub(ho.w, p1.w));
+                    tlo = fminf(tlo, t);
+                    thi = fmaxf(thi, t);
+                  }
                 }
+                cnt += __popc(bal);
               }
-              cnt += __popc(bal);
             }
           }
         }
@@ -319,7 +326,11 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
 #pragma unroll
         for (int u = 0; u < kOut / 32; ++u) {
           const uint32_t st = lane + 32 * u;
-          if (st < n) W.perm[W.bstart[key[u]] + rank[u]] = (uint8_t)st;
+          if (st < n) {
+            const uint32_t sp = W.bstart[key[u]] + rank[u];
+            W.perm[sp] = (uint8_t)st;
+            W.ts[sp] = W.t[st];
+          }
         }
         if (lane == 0) {
           W.tmin = tlo;
@@ -331,6 +342,20 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
         return cnt;
       };
 
+      // incoming cell i of h1: its cell id and inner-layer slot
+      auto incoming = [&](uint32_t i, int& kin) -> uint32_t {
+        const uint32_t n0 = W.sc[0], n1 = W.sc[1];
+        kin = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);
+        const uint32_t before = kin == 0 ? 0u : (kin == 1 ? n0 : n0 + n1);
+        return W.so[kin] + (i - before);
+      };
+      // the first incoming group's inner hits are fetched while the outgoing cells are
+      // searched, each later group's while the group before it is processed
+      float4 p0_next = make_float4(0.f, 0.f, 0.f, 0.f);
+      if ((uint32_t)lane < nin) {
+        int kin;
+        p0_next = b.hit4[b.cell_in[incoming(lane, kin)]];
+      }
       const uint32_t nout = stage_piece(0);
       if (nout == 0) continue;
 
@@ -342,14 +367,14 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
         const bool valid = i < nin;
         uint32_t c = 0;
         int kin = 0;
-        if (valid) {
-          const uint32_t n0 = W.sc[0], n1 = W.sc[1];
-          kin = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);
-          const uint32_t before = kin == 0 ? 0u : (kin == 1 ? n0 : n0 + n1);
-          c = W.so[kin] + (i - before);
+        if (valid) c = incoming(i, kin);
+        const float4 p0 = p0_next;
+        uint32_t h0_next = 0;
+        const bool valid_next = i + 32 < nin;
+        if (valid_next) {
+          int kn;
+          h0_next = b.cell_in[incoming(i + 32, kn)];
         }
-        float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (valid) p0 = b.hit4[b.cell_in[c]];
         const bool first_b0 = valid && kInner[L1][kin] == 0;
         const float ta = __fdividef(p1.z - p0.z, p1.w - p0.w);  // the cell's slope dz/dr
         const float id1 = __fdividef(1.0f, p1.w - p0.w);
@@ -424,9 +449,12 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
               bool pass = false;
               uint32_t e = 0;
               if (pos < pend) {
-                e = W.perm[pos++];
-                const float tb = W.t[e];
-                if (fabsf(tb - ta) <= w) pass = link_c1(cuts, p0, p1, W.p2[e]);
+                const float tb = W.ts[pos];
+                if (fabsf(tb - ta) <= w) {
+                  e = W.perm[pos];
+                  pass = link_c1(cuts, p0, p1, W.p2[e]);
+                }
+                ++pos;
               }
               const unsigned bal = __ballot_sync(kFull, pass);
               if (pass) W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2((uint32_t)lane, e);
@@ -464,6 +492,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
           }
           break;
         }
+        if (valid_next) p0_next = b.hit4[h0_next];
       }
     }
   }

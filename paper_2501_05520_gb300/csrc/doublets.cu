@@ -127,18 +127,28 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
       for (int k = 0; k < kMaxInner; ++k) {
         const uint4 rg = st_rng[wib][j][k];
         uint32_t cnt = 0;
-        // pass 1: test, stage up to kStage passing hits, count all
+        // pass 1: test, stage up to kStage passing hits, count all; two candidates per
+        // lane in flight (both loads issued before either test)
         for (int part = 0; part < 2; ++part) {
           const uint32_t beg = part ? rg.z : rg.x, end = part ? rg.w : rg.y;
-          for (uint32_t i0 = beg; i0 < end; i0 += 32) {
-            const uint32_t i = i0 + lane;
-            const bool pass = i < end && doublet_pass(cuts, b.hit4[i], ho);
-            const unsigned bal = __ballot_sync(kFull, pass);
-            if (pass) {
-              const uint32_t pos = cnt + __popc(bal & lt_mask);
-              if (pos < kStage) sval[pos] = i;
+          for (uint32_t i0 = beg; i0 < end; i0 += 64) {
+            float4 hv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const uint32_t i = i0 + 32 * u + lane;
+              hv[u] = i < end ? b.hit4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            cnt += __popc(bal);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const uint32_t i = i0 + 32 * u + lane;
+              const bool pass = i < end && doublet_pass(cuts, hv[u], ho);
+              const unsigned bal = __ballot_sync(kFull, pass);
+              if (pass) {
+                const uint32_t pos = cnt + __popc(bal & lt_mask);
+                if (pos < kStage) sval[pos] = i;
+              }
+              cnt += __popc(bal);
+            }
           }
         }
 
