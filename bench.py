@@ -49,8 +49,10 @@ CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped
 # DRAM traffic per event of the main kernels from one ncu capture (8 PU200 events per
 # launch, profiles/), valid only while the kernel's sources hash to the recorded value.
 NCU_TRAFFIC = {
-    "k_doublets": {"bytes_per_event": 24389312, "issue_active_pct": 56.7, "sha": "ce03c03e8c77"},
-    "k_find_ntuplets": {"bytes_per_event": 47944064, "issue_active_pct": 16.0, "sha": "bea2a2a22db7"},
+    "k_doublets": {"bytes_per_event": 24326944, "issue_active_pct": 61.7, "sha": "475ef52e4346"},
+    "k_connect": {"bytes_per_event": 16760064, "issue_active_pct": 61.1, "sha": "d380666c7d1c"},
+    "k_link_targets": {"bytes_per_event": 10689760, "issue_active_pct": 11.9, "sha": "d380666c7d1c"},
+    "k_find_ntuplets": {"bytes_per_event": 43214880, "issue_active_pct": 18.3, "sha": "03ddbdc91d19"},
 }
 
 
@@ -362,6 +364,63 @@ def _config4(ctx, dev, flush, stream, steps, warmup, n_events):
             "path": "whole-chain CUDA graph, device inputs"}
 
 
+def _latency(pt, dev, n_timed: int = 40, warmup: int = 10) -> dict:
+    """Per-event latency of single events through the public whole-chain call
+    (pt_reconstruct_batch, host buffers in and out, one event per call): the
+    50-particle barrel event, one PU50 event and one PU200 event; and PU50 events/s in
+    batches of 64 through the captured graph with device inputs.  A single event's working
+    set fits in L2, so these latencies are not HBM-bound."""
+    import torch
+    out = {}
+    for name, cfg, seed0, hits in (("config1_barrel50", sim.SINGLE_MUON_LIKE, 1000, 4096),
+                                   ("pu50_single", sim.PU50, 2000, 32768),
+                                   ("pu200_single", sim.PU200, 3000, 65536)):
+        evs = [sim.generate(cfg, seed0 + i) for i in range(warmup + n_timed)]
+        cap = pt.default_capacity(max_events=1, hits_per_event=hits,
+                                  cells_per_event=max(1 << 16, hits * 80),
+                                  links_per_event=max(1 << 14, hits * 8),
+                                  ntuplets_per_event=max(1 << 13, hits * 6), phi_bins=1024)
+        with pt.Context(capacity=cap, device=dev.index or 0) as c:
+            ms = []
+            for i, e in enumerate(evs):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                c.pt_reconstruct_batch([0, e.n_hits], e.x, e.y, e.z, e.layer)
+                t1 = time.perf_counter()
+                if i >= warmup:
+                    ms.append(1000.0 * (t1 - t0))
+        out[name] = {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                     "mean_ms": float(np.mean(ms)), "events": len(ms),
+                     "hits_per_event": float(np.mean([e.n_hits for e in evs])),
+                     "path": "pt_reconstruct_batch, one event per call, host buffers"}
+    # PU50 throughput in 64-event batches (graph, device inputs, L2 flushed per step)
+    evs = [sim.generate(sim.PU50, 2000 + i) for i in range(64)]
+    off, *arrs = sim.concat(evs)
+    d = [torch.from_numpy(a).to(dev) for a in arrs]
+    cap = pt.default_capacity(max_events=64, hits_per_event=16384, cells_per_event=400_000,
+                              links_per_event=65536, ntuplets_per_event=65536, phi_bins=1024)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    with pt.Context(capacity=cap, device=dev.index or 0) as c:
+        s_ = c.stream
+        with torch.cuda.stream(s_):
+            for _ in range(3):
+                c.pt_enqueue_batch(off, *d)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(20)]
+            for e0, e1 in ev:
+                flush.zero_()
+                e0.record(s_)
+                c.pt_enqueue_batch(off, *d)
+                e1.record(s_)
+        s_.synchronize()
+        c.pt_get_ntuplets()
+        ms = [a.elapsed_time(b) for a, b in ev]
+    out["pu50_batch64"] = {"value": 64 * len(ms) / (sum(ms) / 1000.0), "unit": "events/s",
+                           "ms_per_step": float(np.mean(ms)), "hits_per_step": int(off[-1]),
+                           "path": "whole-chain CUDA graph, device inputs, L2 flushed per step"}
+    return out
+
+
 def _vertexing(ctx, dbat, stream, steps: int) -> dict:
     """Primary vertices (pt_find_vertices, quadruplets and longer, 0.02 cm steps) of the
     fitted tracks of one bench batch, timed with CUDA events on the library's stream; the
@@ -609,6 +668,7 @@ def run_ours(args):
         vertexing = _vertexing(ctx, dbat, stream, min(args.steps, 20))
         broken_line = _broken_line(ctx, dbat, stream, min(args.steps, 20))
         raw_input = _raw_input(ctx, dev, stream, min(args.steps, 20), B)
+    latency = _latency(pt, dev) if not args.no_latency else None
     config4 = {"plain": _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)}
     ctx.pt_set_gate(gw, gtau)
     config4["gated"] = _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)
@@ -678,6 +738,7 @@ def run_ours(args):
                 "physics": {"plain": plain["physics"], "gated": forms["gated"]["physics"]},
                 "counts_per_step": counts,
                 "batch_workload": config4,
+                "latency": latency,
                 "vertexing": vertexing,
                 "broken_line": broken_line,
                 "raw_input": raw_input,
@@ -713,6 +774,7 @@ def main():
     ap.add_argument("--no-physics", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer rate (profiling)")
+    ap.add_argument("--no-latency", action="store_true", help="skip the single-event latencies")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-rate-low", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)

@@ -285,3 +285,35 @@ def test_dense_middle_hits_many_links(cuts):
             [ev, sim.generate(sim.SINGLE_MUON_LIKE, 1100)]))
     assert n_links == ref["link_a"].size + out["links"][0][out["links"][4] == 1].size
     assert_ntuplets_equal(hits[eoff[0]:eoff[1]], oracle.survivors_hits(ref), ref)
+
+
+def test_poisson_batch_sampled(cuts):
+    """The batch workload (64 events, pileup ~ Poisson(140) clipped to [20, 250], seeds
+    5000+i) through the whole-chain graph at the benchmark's capacity: four events of
+    different sizes (the smallest, the largest and two others) bit-exact against the
+    oracle, every event in canonical order with allowed layer chains."""
+    import bench
+    pus = sim.batch_pileups(bench.CONFIG4_SEED0, bench.BATCH)
+    events = [sim.pileup_event(bench.CONFIG4_SEED0 + i, int(p)) for i, p in enumerate(pus)]
+    off, x, y, z, layer = sim.concat(events)
+    with pt.Context(cuts=cuts, capacity=bench.capacity(bench.BATCH, 2048)) as ctx:
+        dev = [torch.from_numpy(a).cuda() for a in (x, y, z, layer)]
+        ctx.pt_enqueue_batch(off, *dev)
+        hits, nh, evoff = (np.copy(v) for v in ctx.pt_get_ntuplets())
+        tracks = ctx.pt_get_tracks()
+    from sim import truth
+    allowed = set(truth.LAYER_PAIRS)
+    for e, ev in enumerate(events):
+        h = hits[evoff[e]:evoff[e + 1]]
+        keys = [tuple(r) for r in h.tolist()]
+        assert keys == sorted(keys) and len(set(keys)) == len(keys)
+        for r, n in zip(h, nh[evoff[e]:evoff[e + 1]]):
+            lay = ev.layer[r[:n]].tolist()
+            assert all((u, v) in allowed for u, v in zip(lay[:-1], lay[1:]))
+    sizes = np.array([ev.n_hits for ev in events])
+    for e in sorted({int(sizes.argmin()), int(sizes.argmax()), 7, 40}):
+        ev = events[e]
+        ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts)
+        sl = slice(evoff[e], evoff[e + 1])
+        assert_ntuplets_equal(hits[sl], oracle.survivors_hits(ref), ref)
+        assert_fits_close(tracks[sl], ref["fit"])
