@@ -421,6 +421,57 @@ def _latency(pt, dev, n_timed: int = 40, warmup: int = 10) -> dict:
     return out
 
 
+def _gap_form(pt, dev, flush, steps: int, n_events: int = 64) -> dict:
+    """Skip-layer pairs: PU200 events whose sensors miss 10 % of the crossings (seeds
+    3500+i), through the whole-chain graph with device inputs, with the default 13 pairs
+    and with the 10 two-step pairs added; events/s and efficiency / fake rate against
+    generator truth, a particle counting as reconstructable when it has a chain of >= 3
+    hits on the extended table (the same denominator for both tables)."""
+    import dataclasses
+    import torch
+    from sim import truth
+    full = pt.DEFAULT_PAIRS + pt.gap_pairs()
+    cfg = dataclasses.replace(sim.PU200, hit_eff=0.9)
+    evs = [sim.generate(cfg, 3500 + i) for i in range(n_events)]
+    off, *arrs = sim.concat(evs)
+    d = [torch.from_numpy(a).to(dev) for a in arrs]
+    cap = pt.default_capacity(max_events=n_events, hits_per_event=49152,
+                              cells_per_event=8_500_000, links_per_event=524_288,
+                              ntuplets_per_event=393_216, phi_bins=2048)
+    out = {"workload": f"{n_events} PU200 events, 10 % of crossings lost, seeds 3500+i",
+           "path": "whole-chain CUDA graph, device inputs, L2 flushed per step"}
+    with pt.Context(capacity=cap, device=dev.index or 0) as c:
+        c.pt_set_launch(8, 8)
+        for name, pairs in (("default_pairs", None), ("gap_pairs", full)):
+            c.pt_set_layer_pairs(pairs)
+            s_ = c.stream
+            with torch.cuda.stream(s_):
+                for _ in range(2):
+                    c.pt_enqueue_batch(off, *d)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(steps)]
+                for e0, e1 in ev:
+                    flush.zero_()
+                    e0.record(s_)
+                    c.pt_enqueue_batch(off, *d)
+                    e1.record(s_)
+            s_.synchronize()
+            hits, nh, eoff = c.pt_get_ntuplets()
+            ms = [a.elapsed_time(b) for a, b in ev]
+            tot = dict(reco=0, matched=0.0, fake=0, nt=0)
+            for e, evt in enumerate(evs):
+                r = truth.rates_fast(hits[eoff[e]:eoff[e + 1]], evt.pid, evt.layer, pairs=full)
+                tot["reco"] += r["n_reconstructable"]
+                tot["matched"] += r["efficiency"] * r["n_reconstructable"]
+                tot["fake"] += r["n_fake"]
+                tot["nt"] += r["n_ntuplets"]
+            out[name] = {"value": n_events * len(ms) / (sum(ms) / 1000.0), "unit": "events/s",
+                         "ms_per_step": float(np.mean(ms)),
+                         "efficiency": tot["matched"] / max(tot["reco"], 1),
+                         "fake_rate": tot["fake"] / max(tot["nt"], 1), "n_ntuplets": tot["nt"]}
+    return out
+
+
 def _vertexing(ctx, dbat, stream, steps: int) -> dict:
     """Primary vertices (pt_find_vertices, quadruplets and longer, 0.02 cm steps) of the
     fitted tracks of one bench batch, timed with CUDA events on the library's stream; the
@@ -669,6 +720,7 @@ def run_ours(args):
         broken_line = _broken_line(ctx, dbat, stream, min(args.steps, 20))
         raw_input = _raw_input(ctx, dev, stream, min(args.steps, 20), B)
     latency = _latency(pt, dev) if not args.no_latency else None
+    gap = _gap_form(pt, dev, flush, min(args.steps, 10)) if not args.no_physics else None
     config4 = {"plain": _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)}
     ctx.pt_set_gate(gw, gtau)
     config4["gated"] = _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)
@@ -739,6 +791,7 @@ def run_ours(args):
                 "counts_per_step": counts,
                 "batch_workload": config4,
                 "latency": latency,
+                "gap_pairs": gap,
                 "vertexing": vertexing,
                 "broken_line": broken_line,
                 "raw_input": raw_input,

@@ -132,7 +132,7 @@ typedef struct {
 pt_status pt_workspace_size(const pt_capacity* cap, size_t* bytes);
 
 /* Create a context on `device` (Sec. 3: detector constants are loaded once at start).
- * Capacity limits: max_hits < 2^30, max_cells and max_links < 2^32 - 1, max_ntuplets
+ * Capacity limits: max_hits < 2^29, max_cells and max_links < 2^32 - 1, max_ntuplets
  * < 2^29, phi_bins in [16, 4096], max_events * 10 * phi_bins < 2^31 - 1, reserved 0;
  * anything else is PT_ERR_INVALID.
  * workspace: device memory of >= pt_workspace_size bytes, 256-byte aligned, owned by
@@ -397,6 +397,19 @@ pt_status pt_get_trace(pt_ctx* ctx, pt_kernel_time* out, int cap, int* n);
  * the same results.  Synchronises the stream; the next whole-batch call
  * re-captures its graph. */
 pt_status pt_set_launch(pt_ctx* ctx, int blocks_per_sm, int search_blocks_per_sm);
+
+/* Layer pairs on which doublets are made (Sec. 2.2.1 and Fig. 2: hits of adjacent layers
+ * are paired; the paper lists no pairs).  A context starts with the chain's 13 pairs:
+ * barrel 0-1, 1-2, 2-3 and, per side, 0/1/2-4, 4-5, 5-6 and 0/1/2-7, 7-8, 8-9 (layer
+ * codes as in pt_load_hits).  inner[i], outer[i] (host arrays of n_pairs int32) replace
+ * them, e.g. with skip-layer pairs added so that a track that missed a layer still gives
+ * a chain; n_pairs = 0 restores the default.  Every other step of the chain is unchanged
+ * (the same cuts on every pair, maximal chains of 3..6 hits, the same cleaning).
+ * PT_ERR_INVALID unless 1 <= n_pairs <= 64, every code is 0..9, inner != outer, no pair
+ * repeats, no layer has more than 6 outer or 6 inner layers, and the pairs form no cycle
+ * and no chain of more than 5 pairs (an ntuplet holds 6 hits).  Synchronises the stream;
+ * the next whole-batch call re-captures its graph. */
+pt_status pt_set_layer_pairs(pt_ctx* ctx, int n_pairs, const int32_t* inner, const int32_t* outer);
 
 /* Autotuner for the batched chain.  For every candidate azimuthal bin count
  * phi_bins[i] (context capacity otherwise as `cap`) it creates a context on `device`,

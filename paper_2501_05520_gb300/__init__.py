@@ -36,7 +36,20 @@ EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt
             "pt_gate_loss_grad", "pt_gate_adam", "pt_server_create", "pt_server_set_gate",
             "pt_submit", "pt_poll", "pt_server_stats", "pt_server_reset_stats",
             "pt_server_destroy", "pt_set_launch", "pt_autotune", "pt_set_tracing",
-            "pt_get_trace", "pt_last_error")
+            "pt_get_trace", "pt_set_layer_pairs", "pt_last_error")
+
+
+# The chain's 13 (inner, outer) layer pairs, the library's default table (pt_set_layer_pairs).
+DEFAULT_PAIRS = ((0, 1), (1, 2), (2, 3), (0, 4), (1, 4), (2, 4), (4, 5), (5, 6),
+                 (0, 7), (1, 7), (2, 7), (7, 8), (8, 9))
+
+
+def gap_pairs(pairs=DEFAULT_PAIRS) -> tuple:
+    """Skip-layer pairs of a table: (a, c) for each a -> b -> c of its pair graph that is
+    not itself a pair, so a track that misses layer b still joins a and c."""
+    have = set(pairs)
+    return tuple(sorted({(a, c) for a, b in pairs for b2, c in pairs
+                         if b2 == b and (a, c) not in have}))
 
 
 class PtCuts(ctypes.Structure):
@@ -129,6 +142,7 @@ def lib() -> ctypes.CDLL:
             "pt_server_reset_stats": [P],
             "pt_server_destroy": [P],
             "pt_set_launch": [P, I32, I32],
+            "pt_set_layer_pairs": [P, I32, P, P],
             "pt_set_tracing": [P, I32],
             "pt_get_trace": [P, P, I32, P],
             "pt_autotune": [ctypes.POINTER(PtGeometry), ctypes.POINTER(PtCuts),
@@ -428,6 +442,15 @@ class Context:
 
     def pt_set_launch(self, blocks_per_sm: int = 4, search_blocks_per_sm: int = 5):
         _check(lib().pt_set_launch(self.handle, int(blocks_per_sm), int(search_blocks_per_sm)))
+
+    def pt_set_layer_pairs(self, pairs=None):
+        """Layer pairs [(inner, outer), ...] for the doublets; None restores the default 13."""
+        if not pairs:
+            _check(lib().pt_set_layer_pairs(self.handle, 0, None, None))
+            return
+        a = np.ascontiguousarray([p[0] for p in pairs], np.int32)
+        b = np.ascontiguousarray([p[1] for p in pairs], np.int32)
+        _check(lib().pt_set_layer_pairs(self.handle, int(a.size), _hptr(a), _hptr(b)))
 
     def pt_set_tracing(self, on: bool = True):
         _check(lib().pt_set_tracing(self.handle, 1 if on else 0))

@@ -53,27 +53,20 @@ constexpr int kFound = 64;           // links of one incoming group kept before 
 static_assert(kOut <= 256 && kOut % 32 == 0, "staged index fits 8 bits");
 static_assert(kQueue >= 63 && (kQueue & (kQueue - 1)) == 0, "queue holds 31 + 32 entries");
 
-// Slot of inner layer Li among the inner layers of layer L (-1 where (Li, L) is no pair).
-__device__ __forceinline__ int inner_slot(int L, int Li) {
-#pragma unroll
-  for (int k = 0; k < kMaxInner; ++k)
-    if (kInner[L][k] == Li) return k;
-  return -1;
-}
-
 // Azimuthal window of inner hit `hi` (global bin gb, asin_i = asin(kmax*ri/2)) towards
 // outer slot k, the doublet search's window from the inner side: the outer layer's
 // asin(kmax*ro_max/2) - asin_i (+1e-4 rad, +1 bin); up to two ranges [r.x, r.y) and
 // [r.z, r.w) of the sorted hits; empty where the slot is unused or the outer layer ends
 // inside the inner hit's radius.
-__device__ __forceinline__ uint4 forward_window(const Buffers& b, int32_t B, float bins_per_rad,
-                                                uint32_t gb, float4 hi, float asin_i, int k) {
+__device__ __forceinline__ uint4 forward_window(const Buffers& b, const PairTable& pt, int32_t B,
+                                                float bins_per_rad, uint32_t gb, float4 hi,
+                                                float asin_i, int k) {
   const int el = gb / B;  // event*10 + layer
   const int e = el / kLayers, L = el - e * kLayers;
   const int bin = gb - el * B;
   uint4 r = make_uint4(0u, 0u, 0u, 0u);
-  if (k >= kNOuter[L]) return r;
-  const int Lo = kOuter[L][k];
+  if (k >= pt.n_outer[L]) return r;
+  const int Lo = pt.outer[L][k];
   const float ro_max = __uint_as_float(b.layer_rmax[e * kLayers + Lo]);
   if (!(ro_max > hi.w)) return r;
   const float asin_o = b.layer_asin[e * kLayers + Lo];
@@ -118,12 +111,13 @@ struct ConnWarp {
   uint32_t loff[32];         // first slot of each incoming cell's links
   uint2 q[kQueue];           // C1 passes: (incoming lane, staged index)
   uint32_t fa[kFound];       // found links: incoming lane | rank << 5
-  uint32_t fb[kFound];       //   target: outer hit | slot << 30
+  uint32_t fb[kFound];       //   target: outer hit | slot << 29
   float fq[kFound];          //   quality
   float4 p1;                 // middle hit
   uint4 rg[kMaxOuter];       //   its forward windows, one per outer slot
   uint32_t so[kMaxInner];    //   its incoming segments: first cell
   uint32_t sc[kMaxInner];    //   and number of cells
+  uint32_t sb[kMaxInner + 1];  //   incoming cells before each segment (the last: all)
   float tmin, scale, m;      // the staged piece: slope origin and scale of the buckets,
                              //   smallest r2 - r1
   int piece;                 // the staged piece (-1: none)
@@ -170,7 +164,7 @@ __device__ __forceinline__ unsigned long long chunk_take_shared(
 
 template <bool GATE>
 __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
-    k_connect(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap_links) {
+    k_connect(Buffers b, pt_cuts cuts, PairTable pt, int32_t B, uint64_t cap_links) {
   __shared__ ConnWarp s_w[kConnWarps];
   const int lane = lane_id();
   ConnWarp& W = s_w[threadIdx.x >> 5];
@@ -190,7 +184,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
   };
   auto write_link = [&](uint64_t slot, uint32_t a, uint32_t t, float q) {
     b.link_src[slot] = a;
-    b.link_dst[slot] = t;  // outer hit | slot << 30, made a cell id by k_link_targets
+    b.link_dst[slot] = t;  // outer hit | slot << 29, made a cell id by k_link_targets
     b.link_q[slot] = q;
     if (!GATE) b.has_out[a] = 1;  // gated form: the gate sets the flags of the links it keeps
   };
@@ -202,19 +196,16 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
     if (s0 >= n_sorted) break;
     // one round of loads finds the hits with incoming cells and outer layers
     uint32_t my_gb = 0;
-    uint2 my_sg[kMaxInner];
     bool work = false;
     {
       const uint64_t s = s0 + lane;
-#pragma unroll
-      for (int k = 0; k < kMaxInner; ++k) my_sg[k] = make_uint2(0u, 0u);
       if (s < n_sorted) {
         my_gb = b.hbin[s];
         const int L = (my_gb / (uint32_t)B) % kLayers;
-        if (kNOuter[L] > 0) {
-#pragma unroll
-          for (int k = 0; k < kMaxInner; ++k) my_sg[k] = b.seg[s * kMaxInner + k];
-          work = (my_sg[0].y | my_sg[1].y | my_sg[2].y) != 0;
+        if (pt.n_outer[L] > 0) {
+          uint32_t any = 0;
+          for (int k = 0; k < pt.max_inner; ++k) any |= b.seg[s * pt.max_inner + k].y;
+          work = any != 0;
         }
       }
     }
@@ -227,23 +218,28 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
       const int L1 = (gb / (uint32_t)B) % kLayers;
       const float4 p1 = b.hit4[h1];
       __syncwarp();
-      if (lane == src) {
-#pragma unroll
-        for (int k = 0; k < kMaxInner; ++k) {
-          W.so[k] = my_sg[k].x;
-          W.sc[k] = my_sg[k].y;
+      {
+        // h1's incoming segments, one slot per lane, and the cells before each
+        const uint2 sgl = lane < pt.max_inner ? b.seg[(uint64_t)h1 * pt.max_inner + lane]
+                                              : make_uint2(0u, 0u);
+        const uint32_t inc = warp_incl_scan(sgl.y);
+        if (lane < kMaxInner) {
+          W.so[lane] = sgl.x;
+          W.sc[lane] = sgl.y;
+          W.sb[lane] = inc - sgl.y;
         }
+        if (lane == kMaxInner) W.sb[kMaxInner] = inc;
       }
       // forward windows, one outer slot per lane
       if (lane < kMaxOuter)
-        W.rg[lane] = forward_window(b, B, bins_per_rad, gb, p1,
+        W.rg[lane] = forward_window(b, pt, B, bins_per_rad, gb, p1,
                                     asinf(0.5f * cuts.kmax * p1.w), lane);
       if (lane == 0) {
         W.p1 = p1;
         W.piece = -1;
       }
       __syncwarp();
-      const uint32_t nin = W.sc[0] + W.sc[1] + W.sc[2];
+      const uint32_t nin = W.sb[kMaxInner];
 
       // Stages piece `piece` (the passing outgoing cells of ordinal [piece*kOut,
       // (piece+1)*kOut) in search order) and orders it by slope; returns the number of
@@ -252,8 +248,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
         const uint32_t lo_ord = (uint32_t)piece * kOut;
         uint32_t cnt = 0;
         float m = __int_as_float(0x7f800000), tlo = m, thi = -m;
-        for (int k = 0; k < kNOuter[L1]; ++k) {
-          const uint8_t j2 = (uint8_t)inner_slot(kOuter[L1][k], L1);
+        for (int k = 0; k < pt.n_outer[L1]; ++k) {
+          const uint8_t j2 = (uint8_t)pt.slot[pt.outer[L1][k]][L1];
           for (int part = 0; part < 2; ++part) {
             const uint4 rk = W.rg[k];
             const uint32_t beg = part ? rk.z : rk.x, end = part ? rk.w : rk.y;
@@ -344,10 +340,9 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
 
       // incoming cell i of h1: its cell id and inner-layer slot
       auto incoming = [&](uint32_t i, int& kin) -> uint32_t {
-        const uint32_t n0 = W.sc[0], n1 = W.sc[1];
-        kin = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);
-        const uint32_t before = kin == 0 ? 0u : (kin == 1 ? n0 : n0 + n1);
-        return W.so[kin] + (i - before);
+        kin = 0;
+        while (i >= W.sb[kin + 1]) ++kin;  // i < W.sb[max_inner] bounds the walk
+        return W.so[kin] + (i - W.sb[kin]);
       };
       // the first incoming group's inner hits are fetched while the outgoing cells are
       // searched, each later group's while the group before it is processed
@@ -375,7 +370,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
           int kn;
           h0_next = b.cell_in[incoming(i + 32, kn)];
         }
-        const bool first_b0 = valid && kInner[L1][kin] == 0;
+        const bool first_b0 = valid && pt.inner[L1][kin] == 0;
         const float ta = __fdividef(p1.z - p0.z, p1.w - p0.w);  // the cell's slope dz/dr
         const float id1 = __fdividef(1.0f, p1.w - p0.w);
         const float wa = (cuts.rz0 + cuts.rz1 * cuts.cotmax) * id1;
@@ -425,7 +420,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
                 ok = link_c23(cuts, q0, qb0, p1, W.p2[e.y], q);
                 // the target cell, named by its outer hit and the slot of h1's layer
                 // among that hit's inner layers until k_link_targets finds it
-                cb = W.h2[e.y] | ((uint32_t)W.j2[e.y] << 30);
+                cb = W.h2[e.y] | ((uint32_t)W.j2[e.y] << 29);
               }
               uint32_t rk = 0;
               if (ok) rk = atomicAdd(&W.lcnt[il], 1u);
@@ -508,7 +503,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
 // bit is set then); the link then points back to its source, a valid cell, so that the
 // later stages stay within their arrays.
 template <bool GATE>
-__global__ void k_link_targets(Buffers b, uint64_t cap_links) {
+__global__ void k_link_targets(Buffers b, int max_inner, uint64_t cap_links) {
   const uint64_t nl = min(b.cnt[CNT_LINKS], (unsigned long long)cap_links);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += stride) {
@@ -516,7 +511,7 @@ __global__ void k_link_targets(Buffers b, uint64_t cap_links) {
     if (a == kHole) continue;
     const uint32_t t = b.link_dst[l];
     const uint32_t h1 = b.cell_out[a];
-    const uint2 sg = b.seg[(uint64_t)(t & 0x3fffffffu) * kMaxInner + (t >> 30)];
+    const uint2 sg = b.seg[(uint64_t)(t & 0x1fffffffu) * max_inner + (t >> 29)];
     uint32_t lo = sg.x, hi = sg.x + sg.y;
     while (lo < hi) {
       const uint32_t mid = (lo + hi) >> 1;
@@ -537,15 +532,15 @@ void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStre
   if (gated) {
     PT_TRACE(l, s, "k_connect",
              k_connect<true><<<l.sms * kConnBlocksPerSm, kConnWarps * 32, 0, s>>>(
-                 b, p.cuts, p.phi_bins, (uint64_t)p.max_links));
+                 b, p.cuts, p.pairs, p.phi_bins, (uint64_t)p.max_links));
     PT_TRACE(l, s, "k_link_targets",
-             k_link_targets<true><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links));
+             k_link_targets<true><<<l.grid, 256, 0, s>>>(b, p.pairs.max_inner, (uint64_t)p.max_links));
   } else {
     PT_TRACE(l, s, "k_connect",
              k_connect<false><<<l.sms * kConnBlocksPerSm, kConnWarps * 32, 0, s>>>(
-                 b, p.cuts, p.phi_bins, (uint64_t)p.max_links));
+                 b, p.cuts, p.pairs, p.phi_bins, (uint64_t)p.max_links));
     PT_TRACE(l, s, "k_link_targets",
-             k_link_targets<false><<<l.grid, 256, 0, s>>>(b, (uint64_t)p.max_links));
+             k_link_targets<false><<<l.grid, 256, 0, s>>>(b, p.pairs.max_inner, (uint64_t)p.max_links));
   }
 }
 

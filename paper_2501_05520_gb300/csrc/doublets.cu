@@ -41,14 +41,15 @@ __device__ __forceinline__ void write_cell(const Buffers& b, uint64_t c, uint32_
 // kmax*ro/2 >= 0.7) towards inner slot k: up to two ranges [r.x, r.y) and [r.z, r.w) of
 // the sorted hits, the first below the second; empty where the slot is unused or the
 // inner layer has no hit inside the outer hit's radius.
-__device__ __forceinline__ uint4 reverse_window(const Buffers& b, int32_t B, float bins_per_rad,
-                                                uint32_t gb, float4 ho, float asin_o, int k) {
+__device__ __forceinline__ uint4 reverse_window(const Buffers& b, const PairTable& pt, int32_t B,
+                                                float bins_per_rad, uint32_t gb, float4 ho,
+                                                float asin_o, int k) {
   const int el = gb / B;  // event*10 + layer
   const int e = el / kLayers, L = el - e * kLayers;
   const int bin = gb - el * B;
   uint4 r = make_uint4(0u, 0u, 0u, 0u);
-  if (k >= kNInner[L]) return r;
-  const int Li = kInner[L][k];
+  if (k >= pt.n_inner[L]) return r;
+  const int Li = pt.inner[L][k];
   const float ri_min = __uint_as_float(b.layer_rmin[e * kLayers + Li]);
   if (!(ho.w > ri_min)) return r;  // D0 fails for every hit of the inner layer
   float win = kHalfPi + 1e-3f;     // where the curvature bound is void, D1's
@@ -83,7 +84,7 @@ __device__ __forceinline__ uint4 reverse_window(const Buffers& b, int32_t B, flo
 // chunk's windows are found lane-parallel (one hit per lane, all of its loads in flight
 // at once) and kept in shared memory; the warp then searches them hit by hit.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
-    k_doublets(Buffers b, pt_cuts cuts, int32_t B, uint64_t cap_cells) {
+    k_doublets(Buffers b, pt_cuts cuts, PairTable pt, int32_t B, uint64_t cap_cells) {
   __shared__ uint32_t st_val[kWarpsPerBlock][kStage];
   __shared__ uint4 st_rng[kWarpsPerBlock][32][kMaxInner];
   __shared__ float4 st_hit[kWarpsPerBlock][32];
@@ -115,16 +116,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
       const float a = 0.5f * cuts.kmax * ho.w;
       const float asin_o = a >= 0.7f ? __int_as_float(0x7f800000) : asinf(a);
       st_hit[wib][lane] = ho;
-#pragma unroll
-      for (int k = 0; k < kMaxInner; ++k)
-        st_rng[wib][lane][k] = reverse_window(b, B, bins_per_rad, gb, ho, asin_o, k);
+      for (int k = 0; k < pt.max_inner; ++k)
+        st_rng[wib][lane][k] = reverse_window(b, pt, B, bins_per_rad, gb, ho, asin_o, k);
     }
     __syncwarp();
 
     for (uint32_t j = 0; j < nh; ++j) {
       const uint32_t s = (uint32_t)s0 + j;
       const float4 ho = st_hit[wib][j];
-      for (int k = 0; k < kMaxInner; ++k) {
+      for (int k = 0; k < pt.max_inner; ++k) {
         const uint4 rg = st_rng[wib][j][k];
         uint32_t cnt = 0;
         // pass 1: test, stage up to kStage passing hits, count all; two candidates per
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
         }
         // every slot is written (empty where the layer has fewer inner layers), so
         // readers need not know the hit's layer
-        if (lane == 0) b.seg[(uint64_t)s * kMaxInner + k] = make_uint2(seg_off, seg_cnt);
+        if (lane == 0) b.seg[(uint64_t)s * pt.max_inner + k] = make_uint2(seg_off, seg_cnt);
         __syncwarp();
       }
     }
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
 void launch_doublets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s) {
   cudaMemsetAsync(&b.cnt[CNT_DBL_WORK], 0, sizeof(unsigned long long), s);  // work counter
   PT_TRACE(l, s, "k_doublets",
-           k_doublets<<<l.sgrid, kWarpsPerBlock * 32, 0, s>>>(b, p.cuts, p.phi_bins,
+           k_doublets<<<l.sgrid, kWarpsPerBlock * 32, 0, s>>>(b, p.cuts, p.pairs, p.phi_bins,
                                                                (uint64_t)p.max_cells));
 }
 

@@ -82,8 +82,8 @@ __global__ void k_na_header(Buffers b, int32_t n) {
 // Doublet search of the binned event: one warp per inner hit, the same azimuthal
 // window and exact cuts as the batched doublet stage; each accepted pair is written as
 // (inner, outer) input indices at a slot taken with one atomic per warp iteration.
-__global__ void k_na_doublets(Buffers b, pt_cuts cuts, int32_t* inner, int32_t* outer,
-                              int64_t cap) {
+__global__ void k_na_doublets(Buffers b, pt_cuts cuts, PairTable pt, int32_t* inner,
+                              int32_t* outer, int64_t cap) {
   constexpr float kTwoPi = 6.28318530717958647692f;
   constexpr float kHalfPi = 1.57079632679489661923f;
   const int lane = lane_id();
@@ -96,8 +96,8 @@ __global__ void k_na_doublets(Buffers b, pt_cuts cuts, int32_t* inner, int32_t* 
     const uint32_t gb = b.hbin[s];
     const int L = gb / kNaBins, bin = gb - L * kNaBins;
     const float4 hi = b.hit4[s];
-    for (int k = 0; k < kNOuter[L]; ++k) {
-      const int Lo = kOuter[L][k];
+    for (int k = 0; k < pt.n_outer[L]; ++k) {
+      const int Lo = pt.outer[L][k];
       const float ro_max = __uint_as_float(b.layer_rmax[Lo]);
       if (!(ro_max > hi.w)) continue;
       const float a = 0.5f * cuts.kmax * ro_max;
@@ -194,7 +194,7 @@ extern "C" pt_status pt_find_doublets_noalloc(const pt_cuts* cuts, int64_t n, co
   k_na_header<<<1, 32, 0, s>>>(b, (int32_t)n);
   launch_clear(b, p, l, s);  // zeroes the counters and histograms the last call left
   launch_bin_hits(b, p, l, s);
-  k_na_doublets<<<sms * 4, 256, 0, s>>>(b, *cuts, inner, outer, cap);
+  k_na_doublets<<<sms * 4, 256, 0, s>>>(b, *cuts, default_pair_table(), inner, outer, cap);
   e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(PT_ERR_CUDA, "kernel launch failed", e);
   unsigned long long cnt[CNT_N];

@@ -18,8 +18,9 @@ namespace ptca {
 constexpr int kLayers = 10;
 constexpr int kMaxHits = 6;                // longest chain of the layer graph
 constexpr int kMaxCellsPerNt = kMaxHits - 1;
-constexpr int kMaxOuter = 3;               // outer layers paired with one inner layer
-constexpr int kMaxInner = 3;               // inner layers paired with one outer layer
+constexpr int kMaxOuter = 6;               // outer layers paired with one inner layer
+constexpr int kMaxInner = 6;               // inner layers paired with one outer layer
+constexpr int kMaxPairs = 64;              // layer pairs of one table
 constexpr int kStage = 256;                // staged doublets per (hit, outer layer)
 constexpr int kLocalLinks = 8;             // links of one cell kept in registers
 constexpr int kRankBits = 29;              // duplicate-cleaning key: rank field width
@@ -86,8 +87,32 @@ struct BatchHeader {
   int32_t n_hits;
 };
 
+// The layer-pair table of a context, as the kernels read it (a kernel argument):
+// outer[L][k], k < n_outer[L], are the outer layers paired with inner layer L, inner[L][k],
+// k < n_inner[L], the inner layers paired with outer layer L (a hit's incoming segments
+// are numbered by these slots), slot[L][Li] = k with inner[L][k] == Li (-1 if none), and
+// max_inner = the largest n_inner (the number of incoming segments stored per hit).
+struct PairTable {
+  int8_t outer[kLayers][kMaxOuter];
+  int8_t n_outer[kLayers];
+  int8_t inner[kLayers][kMaxInner];
+  int8_t n_inner[kLayers];
+  int8_t slot[kLayers][kLayers];
+  int8_t max_inner;
+};
+
+// Builds the table of n (inner, outer) pairs, in the given order; false if a pair is out
+// of range, repeated or pairs a layer with itself, if a layer gets more than kMaxOuter
+// outer or kMaxInner inner layers, or if the layer graph has a cycle or a path of more
+// than kMaxHits - 1 pairs.
+bool make_pair_table(int n, const int32_t* inner, const int32_t* outer, PairTable* t);
+// The chain's 13 pairs: barrel 0-1, 1-2, 2-3, and per side the three inner barrel
+// layers and the disk chain into the first disk (0/1/2-4, 4-5, 5-6; 0/1/2-7, 7-8, 8-9).
+PairTable default_pair_table();
+
 struct Params {
   pt_cuts cuts;
+  PairTable pairs;
   float bfield;
   int32_t phi_bins;
   int64_t max_events, max_hits, max_cells, max_links, max_ntuplets;
@@ -119,8 +144,9 @@ struct Buffers {
   float* layer_asin_lo;      // [max_events*10] asin(kmax r_min / 2) (0 where that is >= 0.7
                              //   or the layer is empty)
   // incoming segments: per sorted (outer) hit and inner-layer slot, the cells ending on
-  // the hit from that layer, cells [x, x + y), ordered by inner hit (all 3 slots written)
-  uint2* seg;                // [max_hits*3]
+  // the hit from that layer, cells [x, x + y), ordered by inner hit; the table's
+  // max_inner slots per hit, all written
+  uint2* seg;                // [max_hits*kMaxInner]
   // cells
   uint32_t* cell_in;         // [max_cells] sorted hit index
   uint32_t* cell_out;        // [max_cells]
@@ -442,17 +468,6 @@ __device__ __forceinline__ int find_event(const int32_t* off, int n_events, int 
   return lo;
 }
 
-// Outer layers of each inner layer (allowed layer pairs), -1 padded.
-static __constant__ int8_t kOuter[kLayers][kMaxOuter] = {
-    {1, 4, 7}, {2, 4, 7}, {3, 4, 7}, {-1, -1, -1}, {5, -1, -1},
-    {6, -1, -1}, {-1, -1, -1}, {8, -1, -1}, {9, -1, -1}, {-1, -1, -1}};
-static __constant__ int8_t kNOuter[kLayers] = {3, 3, 3, 0, 1, 1, 0, 1, 1, 0};
-// Inner layers of each outer layer (the same pairs seen from the outer side), -1 padded;
-// a hit's incoming segments are numbered by these slots.
-static __constant__ int8_t kInner[kLayers][kMaxInner] = {
-    {-1, -1, -1}, {0, -1, -1}, {1, -1, -1}, {2, -1, -1}, {0, 1, 2},
-    {4, -1, -1}, {5, -1, -1}, {0, 1, 2}, {7, -1, -1}, {8, -1, -1}};
-static __constant__ int8_t kNInner[kLayers] = {0, 1, 1, 1, 3, 1, 1, 3, 1, 1};
 #endif
 
 }  // namespace ptca

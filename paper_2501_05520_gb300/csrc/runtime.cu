@@ -68,6 +68,46 @@ struct Tracer {
 
 size_t trace_begin(Tracer* t, cudaStream_t s) { return t->take(s); }
 
+bool make_pair_table(int n, const int32_t* in, const int32_t* out, PairTable* t) {
+  if (n < 1 || n > kMaxPairs || !in || !out) return false;
+  PairTable p;
+  std::memset(&p, -1, sizeof(p));
+  for (int L = 0; L < kLayers; ++L) p.n_outer[L] = p.n_inner[L] = 0;
+  bool adj[kLayers][kLayers] = {};
+  for (int i = 0; i < n; ++i) {
+    const int a = in[i], c = out[i];
+    if (a < 0 || a >= kLayers || c < 0 || c >= kLayers || a == c || adj[a][c]) return false;
+    if (p.n_outer[a] >= kMaxOuter || p.n_inner[c] >= kMaxInner) return false;
+    adj[a][c] = true;
+    p.outer[a][p.n_outer[a]++] = (int8_t)c;
+    p.slot[c][a] = p.n_inner[c];
+    p.inner[c][p.n_inner[c]++] = (int8_t)a;
+  }
+  // longest path (in pairs) ending at each layer, by repeated relaxation: a cycle keeps
+  // growing it past kLayers, a chain longer than an ntuplet can hold passes kMaxHits - 1
+  int depth[kLayers] = {};
+  for (int it = 0; it <= kLayers; ++it)
+    for (int a = 0; a < kLayers; ++a)
+      for (int c = 0; c < kLayers; ++c)
+        if (adj[a][c] && depth[c] < depth[a] + 1) depth[c] = depth[a] + 1;
+  int8_t mi = 1;
+  for (int L = 0; L < kLayers; ++L) {
+    if (depth[L] > kMaxHits - 1) return false;
+    if (p.n_inner[L] > mi) mi = p.n_inner[L];
+  }
+  p.max_inner = mi;
+  *t = p;
+  return true;
+}
+
+PairTable default_pair_table() {
+  static const int32_t in[13] = {0, 1, 2, 0, 1, 2, 4, 5, 0, 1, 2, 7, 8};
+  static const int32_t out[13] = {1, 2, 3, 4, 4, 4, 5, 6, 7, 7, 7, 8, 9};
+  PairTable t;
+  make_pair_table(13, in, out, &t);
+  return t;
+}
+
 void trace_end(Tracer* t, const char* name, size_t i0, cudaStream_t s) {
   t->recs.push_back({name, i0, t->take(s)});
   if (t->recs.size() >= 4096) {  // bound the pool: fold completed records into the totals
@@ -138,7 +178,7 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.layer_asin = (float*)take(E * kLayers * 4);
   t.layer_rmin = (uint32_t*)take(E * kLayers * 4);
   t.layer_asin_lo = (float*)take(E * kLayers * 4);
-  t.seg = (uint2*)take(N * kMaxInner * sizeof(uint2));
+  t.seg = (uint2*)take(N * kMaxInner * sizeof(uint2));  // the table's max_inner slots used
   t.cell_in = (uint32_t*)take(C * 4);
   t.cell_out = (uint32_t*)take(C * 4);
   t.has_in = (uint8_t*)take(C);
@@ -187,7 +227,7 @@ pt_status check_capacity(const pt_capacity* c) {
   if (c->max_events < 1 || c->max_hits < 1 || c->max_cells < 1 || c->max_links < 1 ||
       c->max_ntuplets < 1)
     return fail(PT_ERR_INVALID, "capacities must be >= 1");
-  if (c->max_hits >= (1ll << 30)) return fail(PT_ERR_INVALID, "max_hits must be < 2^30");
+  if (c->max_hits >= (1ll << 29)) return fail(PT_ERR_INVALID, "max_hits must be < 2^29");
   if (c->max_cells >= (1ll << 32) - 1 || c->max_links >= (1ll << 32) - 1)
     return fail(PT_ERR_INVALID, "max_cells and max_links must be < 2^32 - 1");
   if (c->max_ntuplets >= (1ll << kRankBits))
@@ -475,6 +515,7 @@ pt_status pt_create(const pt_geometry* geom, const pt_cuts* cuts, const pt_capac
   c->device = device;
   c->cap = *cap;
   c->P.cuts = *cuts;
+  c->P.pairs = default_pair_table();
   c->P.bfield = geom->bfield_T;
   c->P.phi_bins = cap->phi_bins;
   c->P.max_events = cap->max_events;
@@ -1106,6 +1147,29 @@ pt_status pt_set_launch(pt_ctx* c, int blocks_per_sm, int search_blocks_per_sm) 
   }
   c->L.grid = c->L.sms * blocks_per_sm;
   c->L.sgrid = c->L.sms * search_blocks_per_sm;
+  return PT_OK;
+}
+
+pt_status pt_set_layer_pairs(pt_ctx* c, int n_pairs, const int32_t* inner, const int32_t* outer) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  PairTable t;
+  if (n_pairs == 0) {
+    t = default_pair_table();
+  } else if (!make_pair_table(n_pairs, inner, outer, &t)) {
+    return fail(PT_ERR_INVALID,
+                "invalid layer-pair table: need 1..%d distinct pairs of layer codes 0..9 with "
+                "inner != outer, at most %d outer and %d inner layers per layer, no cycle and "
+                "no chain of more than %d pairs",
+                kMaxPairs, kMaxOuter, kMaxInner, kMaxHits - 1);
+  }
+  DeviceGuard guard(c->device);
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->P.pairs = t;
   return PT_OK;
 }
 
