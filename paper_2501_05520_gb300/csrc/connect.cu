@@ -104,6 +104,7 @@ struct ConnWarp {
   uint32_t h2[kOut];         //   outer hit (sorted index)
   uint8_t j2[kOut];          //   slot of the middle hit's layer among the outer hit's
                              //   inner layers
+  uint8_t l2[kOut];          //   outer layer (gate features)
   uint8_t perm[kOut];        // bucket order -> staged index
   float ts[kOut];            // slopes in bucket order
   uint32_t bstart[kNb + 1];  // first bucket-ordered position of each slope bucket
@@ -113,6 +114,7 @@ struct ConnWarp {
   uint32_t fa[kFound];       // found links: incoming lane | rank << 5
   uint32_t fb[kFound];       //   target: outer hit | slot << 29
   float fq[kFound];          //   quality
+  uint8_t fe[kFound];        //   staged index of the outgoing cell (gate features)
   float4 p1;                 // middle hit
   uint4 rg[kMaxOuter];       //   its forward windows, one per outer slot
   uint32_t so[kMaxInner];    //   its incoming segments: first cell
@@ -182,11 +184,20 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
     hi = min(hi, (unsigned long long)cap_links);
     for (unsigned long long i = lo + lane; i < hi; i += 32) b.link_src[i] = kHole;
   };
-  auto write_link = [&](uint64_t slot, uint32_t a, uint32_t t, float q) {
+  // The link's three hits and layers feed the gated form's feature row, written here
+  // while they are at hand so that the gate's MLP reads one row per link.
+  auto write_link = [&](uint64_t slot, uint32_t a, uint32_t t, float q, float4 f0, int l0,
+                        float4 f1, int l1, float4 f2, int l2) {
     b.link_src[slot] = a;
     b.link_dst[slot] = t;  // outer hit | slot << 29, made a cell id by k_link_targets
     b.link_q[slot] = q;
-    if (!GATE) b.has_out[a] = 1;  // gated form: the gate sets the flags of the links it keeps
+    if (!GATE) {
+      b.has_out[a] = 1;  // gated form: the gate sets the flags of the links it keeps
+    } else {
+      float f[kGateFeat];
+      gate_link_features(cuts, f0, f1, f2, l0, l1, l2, f);
+      store_gate_row(b.gate_x + slot * kGateK1, f);
+    }
   };
 
   for (;;) {
@@ -276,6 +287,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
                     W.t[st] = t;
                     W.h2[st] = o;
                     W.j2[st] = j2;
+                    W.l2[st] = (uint8_t)pt.outer[L1][k];
                     m = fminf(m, fsub(ho.w, p1.w));
                     tlo = fminf(tlo, t);
                     thi = fmaxf(thi, t);
@@ -413,6 +425,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
                                             __shfl_sync(kFull, p0.z, il), __shfl_sync(kFull, p0.w, il));
               const bool qb0 = __shfl_sync(kFull, first_b0, il);
               const uint32_t ca = __shfl_sync(kFull, c, il);
+              const int ql0 = GATE ? pt.inner[L1][__shfl_sync(kFull, kin, il)] : 0;
               bool ok = false;
               float q = 0.0f;
               uint32_t cb = 0;
@@ -432,9 +445,11 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
                     W.fa[seq] = (uint32_t)il | (rk << 5);
                     W.fb[seq] = cb;
                     W.fq[seq] = q;
+                    W.fe[seq] = (uint8_t)e.y;
                   }
                 } else {
-                  write_link(lbase + W.loff[il] + rk, ca, cb, q);
+                  write_link(lbase + W.loff[il] + rk, ca, cb, q, q0, ql0, p1, L1, W.p2[e.y],
+                             W.l2[e.y]);
                 }
               }
               nf += __popc(pm);
@@ -483,7 +498,26 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
             const uint32_t fa = f < tot ? W.fa[f] : 0u;
             const int il = (int)(fa & 31u);
             const uint32_t ca = __shfl_sync(kFull, c, il);
-            if (f < tot) write_link(lbase + W.loff[il] + (fa >> 5), ca, W.fb[f], W.fq[f]);
+            float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g2 = g0;
+            int gl0 = 0, gl2 = 0;
+            if (GATE) {
+              g0 = make_float4(__shfl_sync(kFull, p0.x, il), __shfl_sync(kFull, p0.y, il),
+                               __shfl_sync(kFull, p0.z, il), __shfl_sync(kFull, p0.w, il));
+              gl0 = pt.inner[L1][__shfl_sync(kFull, kin, il)];
+              if (f < tot) {
+                if (npieces == 1) {  // the outgoing cell is still staged
+                  g2 = W.p2[W.fe[f]];
+                  gl2 = W.l2[W.fe[f]];
+                } else {
+                  const uint32_t h2 = W.fb[f] & 0x1fffffffu;
+                  g2 = b.hit4[h2];
+                  gl2 = (int)((b.hbin[h2] / (uint32_t)B) % kLayers);
+                }
+              }
+            }
+            if (f < tot)
+              write_link(lbase + W.loff[il] + (fa >> 5), ca, W.fb[f], W.fq[f], g0, gl0, p1, L1,
+                         g2, gl2);
           }
           break;
         }

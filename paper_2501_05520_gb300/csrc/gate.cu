@@ -1,7 +1,7 @@
 // Learned link gate (optional stage after the cellular-automaton links): every accepted
-// link (h0 -> h1 -> h2) gets 12 geometric features (computed by the MLP kernel from the
-// link's three hits while it fills its operand tile), a 12 -> 64 -> 64 -> 1 MLP scores
-// it on the tensor cores, and
+// link (h0 -> h1 -> h2) gets 12 geometric features (computed by the link search from the
+// three hits it holds when it writes the link, one bf16 row per link slot), a
+// 12 -> 64 -> 64 -> 1 MLP scores it on the tensor cores, and
 // links scoring below the threshold are skipped by the ntuplet search: the MLP's
 // epilogue sets the in/out flags of the cells of kept links only.  It plays the role of the edge-filtering MLP of the paper's ML
 // pipeline (Sec. 2.2.2: an MLP scores graph edges, a fixed threshold removes clearly
@@ -116,8 +116,8 @@ constexpr int kOffTmem = 31752;       // TMEM base address
 constexpr int kOffFlag = 31756;       // wait status
 constexpr int kMlpSmem = 48 * 1024;   // requested: at most 4 CTAs per SM (TMEM 4 x 128 cols)
 
-// PIPE = true: rows are link slots of the batch; each thread gathers its link's three
-// hits and computes the features; kept links set the flags the ntuplet search reads.
+// PIPE = true: rows are link slots of the batch, whose bf16 feature rows the link search
+// wrote to gate_x; kept links set the flags the ntuplet search reads.
 // PIPE = false: rows are given bf16 feature rows X (standalone scoring).
 template <bool PIPE>
 __global__ void __launch_bounds__(kTileM, 1)
@@ -180,27 +180,15 @@ __global__ void __launch_bounds__(kTileM, 1)
     unsigned char* xr = sm + kOffX + (tid >> 3) * 256 + (tid & 7) * 16;
     uint32_t src_cell = kHole;
     if (PIPE) {
-      float f[kGateFeat];
-#pragma unroll
-      for (int k = 0; k < kGateFeat; ++k) f[k] = 0.0f;
+      uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
       if (row < n) {
         src_cell = b.link_src[row];
         if (src_cell != kHole) {
-          const uint32_t h0 = b.cell_in[src_cell], h1 = b.cell_out[src_cell];
-          const uint32_t h2 = b.cell_out[b.link_dst[row]];
-          gate_link_features(cuts, b.hit4[h0], b.hit4[h1], b.hit4[h2], (b.hbin[h0] / B) % kLayers,
-                             (b.hbin[h1] / B) % kLayers, (b.hbin[h2] / B) % kLayers, f);
+          const uint4* srcp = (const uint4*)(b.gate_x + row * kGateK1);
+          lo = srcp[0];
+          hi = srcp[1];
         }
       }
-      uint4 lo, hi;
-      lo.x = pack_bf16x2(f[0], f[1]);
-      lo.y = pack_bf16x2(f[2], f[3]);
-      lo.z = pack_bf16x2(f[4], f[5]);
-      lo.w = pack_bf16x2(f[6], f[7]);
-      hi.x = pack_bf16x2(f[8], f[9]);
-      hi.y = pack_bf16x2(f[10], f[11]);
-      hi.z = 0;
-      hi.w = 0;
       *(uint4*)xr = lo;
       *(uint4*)(xr + 128) = hi;
     } else {
