@@ -411,6 +411,18 @@ pt_status pt_set_launch(pt_ctx* ctx, int blocks_per_sm, int search_blocks_per_sm
  * the next whole-batch call re-captures its graph. */
 pt_status pt_set_layer_pairs(pt_ctx* ctx, int n_pairs, const int32_t* inner, const int32_t* outer);
 
+/* Limit, in SM clock cycles (>= 1; default 2^31, about 1 s at 2 GHz), of the context's
+ * bounded device-side waits: the learned gate's waits for its tensor-core results
+ * (pt_connect_cells in the gated form, pt_gate_score, the whole-batch graph).  A wait that
+ * runs out ends the kernel's work with a status bit, which the next synchronising call
+ * reports as PT_ERR_TIMEOUT; the context stays usable.  The paper has no counterpart:
+ * this bounds how long a kernel of the library can hold a GPU (a small limit is also how
+ * the timeout path is tested).  When a wait gives up, the kernel still lets the matrix
+ * multiplication in flight finish (waiting up to the default limit) before it frees
+ * its tensor memory.  Synchronises the stream; the next whole-batch call re-captures
+ * its graph. */
+pt_status pt_set_wait_limit(pt_ctx* ctx, int64_t cycles);
+
 /* Autotuner for the batched chain.  For every candidate azimuthal bin count
  * phi_bins[i] (context capacity otherwise as `cap`) it creates a context on `device`,
  * copies the caller's sample batch (HOST arrays, pt_load_batch layout) to it once, and

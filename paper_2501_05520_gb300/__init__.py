@@ -36,7 +36,7 @@ EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt
             "pt_gate_loss_grad", "pt_gate_adam", "pt_server_create", "pt_server_set_gate",
             "pt_submit", "pt_poll", "pt_server_stats", "pt_server_reset_stats",
             "pt_server_destroy", "pt_set_launch", "pt_autotune", "pt_set_tracing",
-            "pt_get_trace", "pt_set_layer_pairs", "pt_last_error")
+            "pt_get_trace", "pt_set_layer_pairs", "pt_set_wait_limit", "pt_last_error")
 
 
 # The chain's 13 (inner, outer) layer pairs, the library's default table (pt_set_layer_pairs).
@@ -143,6 +143,7 @@ def lib() -> ctypes.CDLL:
             "pt_server_destroy": [P],
             "pt_set_launch": [P, I32, I32],
             "pt_set_layer_pairs": [P, I32, P, P],
+            "pt_set_wait_limit": [P, I64],
             "pt_set_tracing": [P, I32],
             "pt_get_trace": [P, P, I32, P],
             "pt_autotune": [ctypes.POINTER(PtGeometry), ctypes.POINTER(PtCuts),
@@ -451,6 +452,10 @@ class Context:
         a = np.ascontiguousarray([p[0] for p in pairs], np.int32)
         b = np.ascontiguousarray([p[1] for p in pairs], np.int32)
         _check(lib().pt_set_layer_pairs(self.handle, int(a.size), _hptr(a), _hptr(b)))
+
+    def pt_set_wait_limit(self, cycles: int = 1 << 31):
+        """Limit (SM cycles) of the context's bounded device-side waits."""
+        _check(lib().pt_set_wait_limit(self.handle, int(cycles)))
 
     def pt_set_tracing(self, on: bool = True):
         _check(lib().pt_set_tracing(self.handle, 1 if on else 0))

@@ -104,7 +104,6 @@ struct ConnWarp {
   uint32_t h2[kOut];         //   outer hit (sorted index)
   uint8_t j2[kOut];          //   slot of the middle hit's layer among the outer hit's
                              //   inner layers
-  uint8_t l2[kOut];          //   outer layer (gate features)
   uint8_t perm[kOut];        // bucket order -> staged index
   float ts[kOut];            // slopes in bucket order
   uint32_t bstart[kNb + 1];  // first bucket-ordered position of each slope bucket
@@ -114,7 +113,6 @@ struct ConnWarp {
   uint32_t fa[kFound];       // found links: incoming lane | rank << 5
   uint32_t fb[kFound];       //   target: outer hit | slot << 29
   float fq[kFound];          //   quality
-  uint8_t fe[kFound];        //   staged index of the outgoing cell (gate features)
   float4 p1;                 // middle hit
   uint4 rg[kMaxOuter];       //   its forward windows, one per outer slot
   uint32_t so[kMaxInner];    //   its incoming segments: first cell
@@ -184,20 +182,11 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
     hi = min(hi, (unsigned long long)cap_links);
     for (unsigned long long i = lo + lane; i < hi; i += 32) b.link_src[i] = kHole;
   };
-  // The link's three hits and layers feed the gated form's feature row, written here
-  // while they are at hand so that the gate's MLP reads one row per link.
-  auto write_link = [&](uint64_t slot, uint32_t a, uint32_t t, float q, float4 f0, int l0,
-                        float4 f1, int l1, float4 f2, int l2) {
+  auto write_link = [&](uint64_t slot, uint32_t a, uint32_t t, float q) {
     b.link_src[slot] = a;
     b.link_dst[slot] = t;  // outer hit | slot << 29, made a cell id by k_link_targets
     b.link_q[slot] = q;
-    if (!GATE) {
-      b.has_out[a] = 1;  // gated form: the gate sets the flags of the links it keeps
-    } else {
-      float f[kGateFeat];
-      gate_link_features(cuts, f0, f1, f2, l0, l1, l2, f);
-      store_gate_row(b.gate_x + slot * kGateK1, f);
-    }
+    if (!GATE) b.has_out[a] = 1;  // gated form: the gate sets the flags of the links it keeps
   };
 
   for (;;) {
@@ -287,7 +276,6 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
                     W.t[st] = t;
                     W.h2[st] = o;
                     W.j2[st] = j2;
-                    W.l2[st] = (uint8_t)pt.outer[L1][k];
                     m = fminf(m, fsub(ho.w, p1.w));
                     tlo = fminf(tlo, t);
                     thi = fmaxf(thi, t);
@@ -425,7 +413,6 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
                                             __shfl_sync(kFull, p0.z, il), __shfl_sync(kFull, p0.w, il));
               const bool qb0 = __shfl_sync(kFull, first_b0, il);
               const uint32_t ca = __shfl_sync(kFull, c, il);
-              const int ql0 = GATE ? pt.inner[L1][__shfl_sync(kFull, kin, il)] : 0;
               bool ok = false;
               float q = 0.0f;
               uint32_t cb = 0;
@@ -445,11 +432,9 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
                     W.fa[seq] = (uint32_t)il | (rk << 5);
                     W.fb[seq] = cb;
                     W.fq[seq] = q;
-                    W.fe[seq] = (uint8_t)e.y;
                   }
                 } else {
-                  write_link(lbase + W.loff[il] + rk, ca, cb, q, q0, ql0, p1, L1, W.p2[e.y],
-                             W.l2[e.y]);
+                  write_link(lbase + W.loff[il] + rk, ca, cb, q);
                 }
               }
               nf += __popc(pm);
@@ -498,26 +483,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
             const uint32_t fa = f < tot ? W.fa[f] : 0u;
             const int il = (int)(fa & 31u);
             const uint32_t ca = __shfl_sync(kFull, c, il);
-            float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g2 = g0;
-            int gl0 = 0, gl2 = 0;
-            if (GATE) {
-              g0 = make_float4(__shfl_sync(kFull, p0.x, il), __shfl_sync(kFull, p0.y, il),
-                               __shfl_sync(kFull, p0.z, il), __shfl_sync(kFull, p0.w, il));
-              gl0 = pt.inner[L1][__shfl_sync(kFull, kin, il)];
-              if (f < tot) {
-                if (npieces == 1) {  // the outgoing cell is still staged
-                  g2 = W.p2[W.fe[f]];
-                  gl2 = W.l2[W.fe[f]];
-                } else {
-                  const uint32_t h2 = W.fb[f] & 0x1fffffffu;
-                  g2 = b.hit4[h2];
-                  gl2 = (int)((b.hbin[h2] / (uint32_t)B) % kLayers);
-                }
-              }
-            }
-            if (f < tot)
-              write_link(lbase + W.loff[il] + (fa >> 5), ca, W.fb[f], W.fq[f], g0, gl0, p1, L1,
-                         g2, gl2);
+            if (f < tot) write_link(lbase + W.loff[il] + (fa >> 5), ca, W.fb[f], W.fq[f]);
           }
           break;
         }
@@ -532,12 +498,15 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
 
 // The target cell (h1, h2) of every link: h1 (the outer hit of the source cell) in h2's
 // incoming segment from h1's layer, which is ordered by inner hit, by binary search;
-// one thread per link slot.  Plain form: the target's incoming-link flag is set.  A
+// one thread per link slot.  Plain form: the target's incoming-link flag is set.  Gated
+// form: the link's bf16 feature row for the gate's MLP is computed here, one thread per
+// link with every lane busy, from the three hits (mostly still in L2).  A
 // target can be missing only when the doublet stage ran out of cell slots (its status
 // bit is set then); the link then points back to its source, a valid cell, so that the
 // later stages stay within their arrays.
 template <bool GATE>
-__global__ void k_link_targets(Buffers b, int max_inner, uint64_t cap_links) {
+__global__ void k_link_targets(Buffers b, pt_cuts cuts, int32_t B, int max_inner,
+                               uint64_t cap_links) {
   const uint64_t nl = min(b.cnt[CNT_LINKS], (unsigned long long)cap_links);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += stride) {
@@ -555,6 +524,13 @@ __global__ void k_link_targets(Buffers b, int max_inner, uint64_t cap_links) {
     const uint32_t c = found ? lo : a;
     b.link_dst[l] = c;
     if (!GATE && found) b.has_in[c] = 1;
+    if (GATE) {
+      const uint32_t h0 = b.cell_in[a], h2 = t & 0x1fffffffu;
+      float f[kGateFeat];
+      gate_link_features(cuts, b.hit4[h0], b.hit4[h1], b.hit4[h2], (b.hbin[h0] / B) % kLayers,
+                         (b.hbin[h1] / B) % kLayers, (b.hbin[h2] / B) % kLayers, f);
+      store_gate_row(b.gate_x + l * kGateK1, f);
+    }
   }
 }
 
@@ -568,13 +544,15 @@ void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStre
              k_connect<true><<<l.sms * kConnBlocksPerSm, kConnWarps * 32, 0, s>>>(
                  b, p.cuts, p.pairs, p.phi_bins, (uint64_t)p.max_links));
     PT_TRACE(l, s, "k_link_targets",
-             k_link_targets<true><<<l.grid, 256, 0, s>>>(b, p.pairs.max_inner, (uint64_t)p.max_links));
+             k_link_targets<true><<<l.grid, 256, 0, s>>>(b, p.cuts, p.phi_bins, p.pairs.max_inner,
+                                                         (uint64_t)p.max_links));
   } else {
     PT_TRACE(l, s, "k_connect",
              k_connect<false><<<l.sms * kConnBlocksPerSm, kConnWarps * 32, 0, s>>>(
                  b, p.cuts, p.pairs, p.phi_bins, (uint64_t)p.max_links));
     PT_TRACE(l, s, "k_link_targets",
-             k_link_targets<false><<<l.grid, 256, 0, s>>>(b, p.pairs.max_inner, (uint64_t)p.max_links));
+             k_link_targets<false><<<l.grid, 256, 0, s>>>(b, p.cuts, p.phi_bins, p.pairs.max_inner,
+                                                          (uint64_t)p.max_links));
   }
 }
 

@@ -1,7 +1,7 @@
 // Learned link gate (optional stage after the cellular-automaton links): every accepted
-// link (h0 -> h1 -> h2) gets 12 geometric features (computed by the link search from the
-// three hits it holds when it writes the link, one bf16 row per link slot), a
-// 12 -> 64 -> 64 -> 1 MLP scores it on the tensor cores, and
+// link (h0 -> h1 -> h2) gets 12 geometric features (computed from its three hits by the
+// link stage's target pass, one bf16 row per link slot), a 12 -> 64 -> 64 -> 1 MLP scores
+// it on the tensor cores, and
 // links scoring below the threshold are skipped by the ntuplet search: the MLP's
 // epilogue sets the in/out flags of the cells of kept links only.  It plays the role of the edge-filtering MLP of the paper's ML
 // pipeline (Sec. 2.2.2: an MLP scores graph edges, a fixed threshold removes clearly
@@ -34,7 +34,7 @@ constexpr uint32_t kIdesc = (1u << 4)                          // D: float32
                             | (1u << 7) | (1u << 10)            // A, B: bf16
                             | ((uint32_t)(kGateHidden >> 3) << 17)  // N = 64
                             | ((uint32_t)(kTileM >> 4) << 24);     // M = 128
-constexpr long long kWaitCycles = 1ll << 31;  // ~1 s at 2 GHz
+constexpr long long kWaitCycles = 1ll << 31;  // ~1 s at 2 GHz: the teardown's limit
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -70,8 +70,8 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
                : "memory");
 }
 
-// Bounded wait for the mbarrier phase `parity` to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// Bounded wait for the mbarrier phase `parity` to complete; false after `limit` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (true) {
     uint32_t ok;
@@ -82,7 +82,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
         : "r"(smem_u32(mbar)), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -116,14 +116,14 @@ constexpr int kOffTmem = 31752;       // TMEM base address
 constexpr int kOffFlag = 31756;       // wait status
 constexpr int kMlpSmem = 48 * 1024;   // requested: at most 4 CTAs per SM (TMEM 4 x 128 cols)
 
-// PIPE = true: rows are link slots of the batch, whose bf16 feature rows the link search
+// PIPE = true: rows are link slots of the batch, whose bf16 feature rows the link stage
 // wrote to gate_x; kept links set the flags the ntuplet search reads.
 // PIPE = false: rows are given bf16 feature rows X (standalone scoring).
 template <bool PIPE>
 __global__ void __launch_bounds__(kTileM, 1)
     k_gate_mlp(const GateWeights* gw, Buffers b, pt_cuts cuts, int32_t B, const uint16_t* X,
                const unsigned long long* n_dev, int64_t n_max, float* score, uint8_t* keep,
-               unsigned long long* status, unsigned long long* kept) {
+               unsigned long long* status, unsigned long long* kept, long long wait_limit) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5;
   float* sb1 = (float*)(sm + kOffF);
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kTileM, 1)
       mma_bf16(tmem, smem_desc(ax, 128, 256), smem_desc(aw1, 128, 256), 0u);
       mma_commit(mbar);
       pending = true;
-      if (!mbar_wait(mbar, phase)) *flag = 1;
+      if (!mbar_wait(mbar, phase, wait_limit)) *flag = 1;
       else pending = false;
     }
     __syncthreads();
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kTileM, 1)
                  j > 0 ? 1u : 0u);
       mma_commit(mbar);
       pending = true;
-      if (!mbar_wait(mbar, phase)) *flag = 1;
+      if (!mbar_wait(mbar, phase, wait_limit)) *flag = 1;
       else pending = false;
     }
     __syncthreads();
@@ -285,10 +285,11 @@ __global__ void __launch_bounds__(kTileM, 1)
     __syncthreads();
     tc_after_sync();
   }
-  // teardown: report a timeout, let an MMA still in flight finish (bounded), free TMEM
+  // teardown: report a timeout, let an MMA still in flight finish (bounded by the full
+  // limit whatever the step waits used), and only then free TMEM
   if (tid == 0 && *flag) {
     atomicOr(status, ST_GATE_TIMEOUT);
-    if (pending) mbar_wait(mbar, phase);
+    if (pending) mbar_wait(mbar, phase, kWaitCycles);
   }
   tc_before_sync();
   __syncthreads();
@@ -342,14 +343,15 @@ void launch_gate(const Buffers& b, const Params& p, const Launch& l, const GateW
   PT_TRACE(l, s, "k_gate_mlp",
            k_gate_mlp<true><<<l.sms * 4, kTileM, kMlpSmem, s>>>(
                w, b, p.cuts, p.phi_bins, nullptr, &b.cnt[CNT_LINKS], p.max_links, b.gate_score,
-               b.gate_keep, &b.cnt[CNT_STATUS], &b.cnt[CNT_GATE_KEPT]));
+               b.gate_keep, &b.cnt[CNT_STATUS], &b.cnt[CNT_GATE_KEPT], p.wait_cycles));
 }
 
 void launch_gate_score(const GateWeights* w, const float* feat, int64_t n, float* out,
-                       uint16_t* xbuf, unsigned long long* status, int sms, cudaStream_t s) {
+                       uint16_t* xbuf, unsigned long long* status, int sms, long long wait_cycles,
+                       cudaStream_t s) {
   k_gate_pack<<<sms * 4, 256, 0, s>>>(feat, n, xbuf);
   k_gate_mlp<false><<<sms * 4, kTileM, kMlpSmem, s>>>(w, Buffers{}, pt_cuts{}, 1, xbuf, nullptr, n,
-                                                        out, nullptr, status, nullptr);
+                                                        out, nullptr, status, nullptr, wait_cycles);
 }
 
 void launch_export_link_features(const Buffers& b, const Params& p, const Launch& l, bool gated,

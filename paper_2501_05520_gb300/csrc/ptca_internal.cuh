@@ -113,6 +113,7 @@ PairTable default_pair_table();
 struct Params {
   pt_cuts cuts;
   PairTable pairs;
+  long long wait_cycles;  // limit of the bounded device-side waits (SM clock cycles)
   float bfield;
   int32_t phi_bins;
   int64_t max_events, max_hits, max_cells, max_links, max_ntuplets;
@@ -273,7 +274,8 @@ void launch_gate(const Buffers& b, const Params& p, const Launch& l, const GateW
                  cudaStream_t s);
 // scores of n feature rows (float32 [n][12], device) with the gate's MLP -> out [n]
 void launch_gate_score(const GateWeights* w, const float* feat, int64_t n, float* out,
-                       uint16_t* xbuf, unsigned long long* status, int sms, cudaStream_t s);
+                       uint16_t* xbuf, unsigned long long* status, int sms, long long wait_cycles,
+                       cudaStream_t s);
 // float32 features of the current links (gated: kept only) -> out [slots][12]
 void launch_export_link_features(const Buffers& b, const Params& p, const Launch& l, bool gated,
                                  float* out, cudaStream_t s);

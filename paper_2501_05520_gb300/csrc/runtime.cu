@@ -516,6 +516,7 @@ pt_status pt_create(const pt_geometry* geom, const pt_cuts* cuts, const pt_capac
   c->cap = *cap;
   c->P.cuts = *cuts;
   c->P.pairs = default_pair_table();
+  c->P.wait_cycles = 1ll << 31;
   c->P.bfield = geom->bfield_T;
   c->P.phi_bins = cap->phi_bins;
   c->P.max_events = cap->max_events;
@@ -1107,7 +1108,8 @@ pt_status pt_gate_score(pt_ctx* c, const float* feat, int64_t n, float* out) {
   if (n == 0) return PT_OK;
   if (!feat || !out) return fail(PT_ERR_INVALID, "feat and out must not be NULL");
   DeviceGuard guard(c->device);
-  launch_gate_score(c->gate, feat, n, out, c->B.gate_x, &c->B.cnt[CNT_STATUS], c->L.sms, c->stream);
+  launch_gate_score(c->gate, feat, n, out, c->B.gate_x, &c->B.cnt[CNT_STATUS], c->L.sms,
+                    c->P.wait_cycles, c->stream);
   PT_TRY(last_launch());
   PT_TRY(sync_counters(c));
   return PT_OK;
@@ -1147,6 +1149,20 @@ pt_status pt_set_launch(pt_ctx* c, int blocks_per_sm, int search_blocks_per_sm) 
   }
   c->L.grid = c->L.sms * blocks_per_sm;
   c->L.sgrid = c->L.sms * search_blocks_per_sm;
+  return PT_OK;
+}
+
+pt_status pt_set_wait_limit(pt_ctx* c, int64_t cycles) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  if (cycles < 1) return fail(PT_ERR_INVALID, "the wait limit must be >= 1 cycle");
+  DeviceGuard guard(c->device);
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->P.wait_cycles = (long long)cycles;
   return PT_OK;
 }
 
