@@ -570,55 +570,46 @@ def _physics(ctx, host, events):
             "n_fake": tot["fake"], "n_ntuplets": tot["nt"], "events": len(events)}
 
 
-def _serving(pt, rate: float, seconds: float, gate=None, threads: int = 16,
-             budget: int = 2 << 30, slots: int = 4) -> dict:
-    """Poisson arrivals of PU 50-200 events at `rate` events/s from `threads` clients into
-    a pt_server with a `budget`-byte device budget: latency percentiles and sustained
-    events/s (server clock, submit to result ready)."""
-    import threading
+def _serving(pt, rates, seconds: float, gate=None, threads: int = 16,
+             budget: int = 2 << 30, slots: int = 4) -> list:
+    """Open-loop Poisson arrivals of PU 50-200 events from `threads` native client threads
+    (lib/serve_load: each client submits at its arrival times and never waits for its
+    results; a collector thread per client polls them) into a pt_server with a
+    `budget`-byte device budget, at each offered rate in `rates`.  Per rate: completions
+    over the offered window (sustained events/s), the server's latency percentiles
+    (submit to result ready) and the clients' (submit to poll returning)."""
+    from paper_2501_05520_gb300 import build as pbuild
     pus = sim.serving_pileups(6000, 96, 50, 200)
     pool = [sim.pileup_event(6000 + i, int(pu)) for i, pu in enumerate(pus)]
-    with pt.Server(budget_bytes=budget, slots=slots) as srv:
+    with tempfile.TemporaryDirectory() as td:
+        evf = os.path.join(td, "events.bin")
+        with open(evf, "wb") as f:
+            for e in pool:
+                f.write(np.int64(e.n_hits).tobytes())
+                for a in (e.x, e.y, e.z):
+                    f.write(np.ascontiguousarray(a, "<f4").tobytes())
+                f.write(np.ascontiguousarray(e.layer, np.uint8).tobytes())
+        gf = "-"
         if gate is not None:
-            srv.pt_server_set_gate(*gate)
-        for t in [srv.pt_submit(e.x, e.y, e.z, e.layer) for e in pool[:32]]:
-            srv.pt_poll(t, -1)
-        srv.pt_server_reset_stats()
-        per = max(1, int(rate * seconds) // threads)
-        t0 = time.perf_counter() + 0.05
-
-        def client(k):
-            rng = np.random.default_rng(100 + k)
-            nxt = t0
-            pending = []
-            for i in range(per):
-                nxt += rng.exponential(threads / rate)
-                d = nxt - time.perf_counter()
-                if d > 0:
-                    time.sleep(d)
-                e = pool[(k * per + i) % len(pool)]
-                pending.append(srv.pt_submit(e.x, e.y, e.z, e.layer))
-                while pending:
-                    try:
-                        srv.pt_poll(pending[0], 0)
-                        pending.pop(0)
-                    except pt.PtError as err:
-                        if err.status != pt.PT_ERR_NOT_READY:
-                            raise
-                        break
-            for t in pending:
-                srv.pt_poll(t, -1)
-
-        ths = [threading.Thread(target=client, args=(k,)) for k in range(threads)]
-        for th in ths:
-            th.start()
-        for th in ths:
-            th.join()
-        st = srv.pt_server_stats()
-    return {"offered_events_per_s": rate, "sustained_events_per_s": st["events_per_s"],
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "events": st["n_done"],
-            "clients": threads, "slots": slots, "budget_bytes": budget,
-            "workload": "PU uniform in [50, 200], 50 particles per unit, 2% noise"}
+            gf = os.path.join(td, "gate.bin")
+            np.concatenate([gate[0].astype("<f4"), np.array([gate[1]], "<f4")]).tofile(gf)
+        c = pt.default_cuts()
+        env = dict(os.environ, PT_CUTS=",".join(repr(float(np.float32(c[k]))) for k in
+                                                ("kmax", "z0max", "cotmax", "rz0", "rz1",
+                                                 "dca_b0", "dca_other")))
+        out = []
+        for rate in rates:
+            r = subprocess.run([pbuild.SERVE_LOAD, evf, str(rate), str(seconds), str(threads),
+                                str(slots), str(budget), gf, "11"], capture_output=True,
+                               text=True, env=env, timeout=600)
+            if r.returncode != 0:
+                raise RuntimeError(f"serve_load failed: {r.stderr.strip()[-300:]}")
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            d["p50_ms"], d["p99_ms"] = d["server_p50_ms"], d["server_p99_ms"]
+            d["budget_bytes"] = budget
+            d["workload"] = "PU uniform in [50, 200], 50 particles per unit, 2% noise"
+            out.append(d)
+    return out
 
 
 def run_ours(args):
@@ -799,10 +790,10 @@ def run_ours(args):
                 "clocks": clocks,
                 "gpu_launches": launches["plain"] * args.steps}
         if not args.no_serving:
+            rates = [float(r) for r in args.serve_rates.split(",")]
             line["serving"] = {
-                form: [_serving(pt, rate, args.serve_seconds,
-                                gate=(gw, gtau) if form == "gated" else None)
-                       for rate in (args.serve_rate_low, args.serve_rate)]
+                form: _serving(pt, rates, args.serve_seconds,
+                               gate=(gw, gtau) if form == "gated" else None)
                 for form in ("plain", "gated")}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
@@ -828,8 +819,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer rate (profiling)")
     ap.add_argument("--no-latency", action="store_true", help="skip the single-event latencies")
-    ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-rate-low", type=float, default=200.0)
+    ap.add_argument("--serve-rates", default="200,1000,2000,4000,6000,8000,10000,12000",
+                    help="offered events/s of the serving sweep")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.impl == "reference":

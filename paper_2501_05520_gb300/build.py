@@ -37,11 +37,12 @@ def sources() -> list[str]:
 
 def _deps() -> list[str]:
     return (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
-            + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
+            + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
+            + glob.glob(os.path.join(PKG, "tools", "*.cpp")))
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(os.path.join(LIBDIR, "serve_load")):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps())
@@ -75,7 +76,24 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
     os.replace(tmp, LIB)
+    build_tools()
     return LIB
+
+
+TOOLS = os.path.join(PKG, "tools")
+SERVE_LOAD = os.path.join(LIBDIR, "serve_load")
+
+
+def build_tools() -> str:
+    """The native open-loop load generator of the request server (lib/serve_load),
+    linked against libptca.so."""
+    cxx = os.environ.get("CXX", "g++")
+    tmp = SERVE_LOAD + f".tmp{os.getpid()}"
+    subprocess.check_call([cxx, "-std=c++17", "-O2", "-pthread", "-I", INCLUDE,
+                           os.path.join(TOOLS, "serve_load.cpp"), "-L", LIBDIR, "-lptca",
+                           "-Wl,-rpath,$ORIGIN", "-o", tmp])
+    os.replace(tmp, SERVE_LOAD)
+    return SERVE_LOAD
 
 
 if __name__ == "__main__":

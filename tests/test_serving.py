@@ -96,3 +96,29 @@ def test_poll_admission_and_errors(cuts):
         # the ticket is released after a successful poll
         with pytest.raises(pt.PtError):
             srv.pt_poll(t, 0)
+
+
+def test_native_load_generator(cuts, tmp_path):
+    """lib/serve_load (native client threads, open-loop arrivals): every submitted event
+    completes without error and the server's statistics count them all."""
+    import json
+    import os
+    import subprocess
+    from paper_2501_05520_gb300 import build as pbuild
+    pool = _events(12, 6100)
+    evf = tmp_path / "events.bin"
+    with open(evf, "wb") as f:
+        for e in pool:
+            f.write(np.int64(e.n_hits).tobytes())
+            for a in (e.x, e.y, e.z):
+                f.write(np.ascontiguousarray(a, "<f4").tobytes())
+            f.write(np.ascontiguousarray(e.layer, np.uint8).tobytes())
+    env = dict(os.environ, PT_CUTS=",".join(repr(float(np.float32(cuts[k]))) for k in
+                                            ("kmax", "z0max", "cotmax", "rz0", "rz1", "dca_b0",
+                                             "dca_other")))
+    r = subprocess.run([pbuild.SERVE_LOAD, str(evf), "300", "0.5", "4", "2", str(2 << 30), "-",
+                        "3"], capture_output=True, text=True, env=env, timeout=300)
+    assert r.returncode == 0, r.stderr
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["errors"] == 0 and d["submitted"] > 50 and d["completed"] == d["submitted"]
+    assert 0 < d["server_p50_ms"] <= d["server_p99_ms"]
