@@ -480,6 +480,14 @@ pt_status pt_poll(pt_server* s, uint64_t ticket, int64_t timeout_us, int32_t* hi
  * the time from the first submit to the last completion) since creation or reset. */
 pt_status pt_server_stats(pt_server* s, double* p50_ms, double* p99_ms, double* events_per_s,
                           int64_t* n_done);
+
+/* Batching counters since the server started or since pt_server_reset_stats: batches
+ * launched, batches whose cells overflowed their slot (the cell estimate of the
+ * admission was short) and were split, and the events those splits ran again alone
+ * (each such event pays for two launches).  Any pointer may be NULL.  The paper has no
+ * counterpart; it explains slow requests in the latency tail. */
+pt_status pt_server_counters(pt_server* server, int64_t* batches, int64_t* split_batches,
+                             int64_t* requeued_events);
 pt_status pt_server_reset_stats(pt_server* s);
 
 /* Stop accepting work, finish what is queued, free everything.  NULL ok. */

@@ -36,7 +36,8 @@ EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt
             "pt_gate_loss_grad", "pt_gate_adam", "pt_server_create", "pt_server_set_gate",
             "pt_submit", "pt_poll", "pt_server_stats", "pt_server_reset_stats",
             "pt_server_destroy", "pt_set_launch", "pt_autotune", "pt_set_tracing",
-            "pt_get_trace", "pt_set_layer_pairs", "pt_set_wait_limit", "pt_last_error")
+            "pt_get_trace", "pt_set_layer_pairs", "pt_set_wait_limit", "pt_server_counters",
+            "pt_last_error")
 
 
 # The chain's 13 (inner, outer) layer pairs, the library's default table (pt_set_layer_pairs).
@@ -140,6 +141,7 @@ def lib() -> ctypes.CDLL:
             "pt_server_stats": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), PI64],
             "pt_server_reset_stats": [P],
+            "pt_server_counters": [P, PI64, PI64, PI64],
             "pt_server_destroy": [P],
             "pt_set_launch": [P, I32, I32],
             "pt_set_layer_pairs": [P, I32, P, P],
@@ -639,6 +641,12 @@ class Server:
         _check(lib().pt_server_stats(self.handle, ctypes.byref(p50), ctypes.byref(p99),
                                      ctypes.byref(eps), ctypes.byref(n)))
         return dict(p50_ms=p50.value, p99_ms=p99.value, events_per_s=eps.value, n_done=n.value)
+
+    def pt_server_counters(self) -> dict:
+        b, s_, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().pt_server_counters(self.handle, ctypes.byref(b), ctypes.byref(s_),
+                                        ctypes.byref(r)))
+        return dict(batches=b.value, split_batches=s_.value, requeued_events=r.value)
 
     def pt_server_reset_stats(self):
         _check(lib().pt_server_reset_stats(self.handle))

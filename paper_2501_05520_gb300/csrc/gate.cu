@@ -70,10 +70,13 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
                : "memory");
 }
 
-// Bounded wait for the mbarrier phase `parity` to complete; false after `limit` cycles.
+// Bounded wait for the mbarrier phase `parity` to complete; false once `limit` cycles
+// have passed.  The limit is checked before every try (try_wait itself may suspend the
+// thread for a while), so even a limit of one cycle gives up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (true) {
+    if (clock64() - t0 >= limit) return false;
     uint32_t ok;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -82,7 +85,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long 
         : "r"(smem_u32(mbar)), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > limit) return false;
   }
 }
 

@@ -36,6 +36,7 @@ enum : int {
   CNT_SCAN_NT = 6,
   CNT_GATE_KEPT = 7,
   CNT_SV = 8,         // cleaned ntuplets
+  CNT_SCORE_STATUS = 9,  // status bits of the standalone gate scoring (pt_gate_score)
   CNT_CELLS_USED = 10,  // cells written (CNT_CELLS counts reserved slots incl. holes)
   CNT_LINKS_USED = 11,  // links written (CNT_LINKS counts reserved slots incl. holes)
   CNT_DBL_WORK = 12,    // doublet search: next chunk of 32 sorted hits

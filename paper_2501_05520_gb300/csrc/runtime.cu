@@ -1108,10 +1108,16 @@ pt_status pt_gate_score(pt_ctx* c, const float* feat, int64_t n, float* out) {
   if (n == 0) return PT_OK;
   if (!feat || !out) return fail(PT_ERR_INVALID, "feat and out must not be NULL");
   DeviceGuard guard(c->device);
-  launch_gate_score(c->gate, feat, n, out, c->B.gate_x, &c->B.cnt[CNT_STATUS], c->L.sms,
+  // a status word of its own, so that neither the loaded batch's status nor an earlier
+  // scoring call's leaks into the answer
+  PT_CUDA(cudaMemsetAsync(&c->B.cnt[CNT_SCORE_STATUS], 0, 8, c->stream));
+  launch_gate_score(c->gate, feat, n, out, c->B.gate_x, &c->B.cnt[CNT_SCORE_STATUS], c->L.sms,
                     c->P.wait_cycles, c->stream);
   PT_TRY(last_launch());
-  PT_TRY(sync_counters(c));
+  PT_CUDA(cudaMemcpyAsync(c->h_cnt, c->B.cnt, CNT_N * 8, cudaMemcpyDeviceToHost, c->stream));
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->h_cnt[CNT_SCORE_STATUS] & ST_GATE_TIMEOUT)
+    return fail(PT_ERR_TIMEOUT, "a bounded wait of the gate's tensor-core kernel expired");
   return PT_OK;
 }
 

@@ -83,6 +83,9 @@ struct pt_server {
   uint64_t next_ticket = 1;
   std::vector<double> lat_ms;
   int64_t completed = 0;
+  int64_t batches = 0;       // batches launched
+  int64_t split = 0;         // batches that overflowed their slot and were split
+  int64_t requeued = 0;      // events those splits sent back to run alone
   Clock::time_point t_first, t_last;
   bool any = false;
 };
@@ -133,6 +136,7 @@ bool dispatch(pt_server* s, Slot& sl) {
     std::memcpy(sl.hl + o, r.layer.data(), n);
     sl.hoff[e + 1] = o + n;
   }
+  s->batches += 1;
   pt_status st = pt_enqueue_batch(sl.ctx, E, sl.hoff, sl.hx, sl.hy, sl.hz, sl.hl, 0);
   if (st == PT_OK) st = ctx_counters_async(sl.ctx, sl.ev);
   if (st != PT_OK) {
@@ -164,6 +168,8 @@ bool advance(pt_server* s, Slot& sl) {
     pt_status st = ctx_read_counters(sl.ctx, &S);
     if (st == PT_ERR_CAPACITY && sl.batch.size() > 1) {
       // split the batch: every event runs alone, ahead of the rest of the queue
+      s->split += 1;
+      s->requeued += (int64_t)sl.batch.size();
       for (auto it = sl.batch.rbegin(); it != sl.batch.rend(); ++it) {
         (*it)->solo = true;
         s->queue.push_front(*it);
@@ -407,12 +413,24 @@ pt_status pt_server_stats(pt_server* s, double* p50_ms, double* p99_ms, double* 
   return PT_OK;
 }
 
+pt_status pt_server_counters(pt_server* s, int64_t* batches, int64_t* split_batches,
+                             int64_t* requeued_events) {
+  set_last_error("");
+  if (!s) return sfail(PT_ERR_INVALID, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (batches) *batches = s->batches;
+  if (split_batches) *split_batches = s->split;
+  if (requeued_events) *requeued_events = s->requeued;
+  return PT_OK;
+}
+
 pt_status pt_server_reset_stats(pt_server* s) {
   set_last_error("");
   if (!s) return sfail(PT_ERR_INVALID, "server is NULL");
   std::lock_guard<std::mutex> lk(s->mu);
   s->lat_ms.clear();
   s->completed = 0;
+  s->batches = s->split = s->requeued = 0;
   s->any = false;
   return PT_OK;
 }

@@ -224,8 +224,9 @@ int main(int argc, char** argv) {
   for (auto& t : th) t.join();
   const Clock::time_point t_last = Clock::now();
   double p50 = 0, p99 = 0, srv_rate = 0;
-  int64_t done = 0;
+  int64_t done = 0, batches = 0, split = 0, requeued = 0;
   pt_server_stats(srv, &p50, &p99, &srv_rate, &done);
+  pt_server_counters(srv, &batches, &split, &requeued);
   std::vector<double> all;
   int64_t errors = 0;
   for (auto& c : cl) {
@@ -233,15 +234,25 @@ int main(int argc, char** argv) {
     errors += c.errors;
   }
   const double drain_s = std::chrono::duration<double>(t_last - t_end).count();
+  const double med = pct(all, 0.5);
+  int64_t over3 = 0, over10ms = 0;
+  for (double v : all) {
+    over3 += v > 3.0 * med;
+    over10ms += v > 10.0;
+  }
   std::printf(
       "{\"offered_events_per_s\": %.1f, \"seconds\": %.3f, \"clients\": %d, \"slots\": %d, "
       "\"submitted\": %lld, \"completed\": %lld, \"errors\": %lld, "
       "\"sustained_events_per_s\": %.1f, \"drain_s\": %.4f, \"server_p50_ms\": %.4f, "
       "\"server_p99_ms\": %.4f, \"client_p50_ms\": %.4f, \"client_p99_ms\": %.4f, "
-      "\"client_max_ms\": %.4f}\n",
+      "\"client_max_ms\": %.4f, \"requests_over_3x_median\": %lld, "
+      "\"requests_over_10ms\": %lld, \"batches\": %lld, \"split_batches\": %lld, "
+      "\"requeued_events\": %lld}\n",
       rate, seconds, clients, slots, (long long)submitted.load(), (long long)done,
       (long long)errors, (double)done / seconds, drain_s, p50, p99, pct(all, 0.5),
-      pct(all, 0.99), all.empty() ? 0.0 : *std::max_element(all.begin(), all.end()));
+      pct(all, 0.99), all.empty() ? 0.0 : *std::max_element(all.begin(), all.end()),
+      (long long)over3, (long long)over10ms, (long long)batches, (long long)split,
+      (long long)requeued);
   pt_server_destroy(srv);
   return errors ? 1 : 0;
 }

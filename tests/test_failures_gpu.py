@@ -1,5 +1,5 @@
 """Failure detection in the forms that fault, trap or hang no GPU: a bounded device-side
-wait made to run out (the gate's tensor-core waits with a limit of a few cycles) comes
+wait made to run out (the gate's tensor-core waits with a limit of one cycle) comes
 back as PT_ERR_TIMEOUT and leaves the context usable; a workspace larger than the
 device is refused with PT_ERR_NOMEM and leaves the device usable; clients that abandon
 their tickets leave the server's other results and its shutdown intact."""
@@ -36,7 +36,7 @@ def test_gate_wait_runs_out(cuts):
     with pt.Context(cuts=cuts, capacity=CAP) as ctx:
         ctx.pt_set_gate(*pt.default_gate())
         n_ref, h_ref = _gated_run(ctx, ev)
-        ctx.pt_set_wait_limit(4)
+        ctx.pt_set_wait_limit(1)
         ctx.pt_load_hits(ev.x, ev.y, ev.z, ev.layer)
         ctx.pt_build_doublets()
         with pytest.raises(pt.PtError) as ei:
@@ -60,7 +60,7 @@ def test_gate_score_wait_runs_out(cuts):
         out = torch.empty(1000, device="cuda")
         ctx.pt_gate_score(feat, out)
         ref = out.clone()
-        ctx.pt_set_wait_limit(4)
+        ctx.pt_set_wait_limit(1)
         with pytest.raises(pt.PtError) as ei:
             ctx.pt_gate_score(feat, out)
         assert ei.value.status == pt.PT_ERR_TIMEOUT
