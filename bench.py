@@ -571,7 +571,7 @@ def _physics(ctx, host, events):
 
 
 def _serving(pt, rates, seconds: float, gate=None, threads: int = 16,
-             budget: int = 2 << 30, slots: int = 4) -> list:
+             budget: int = 2 << 30, slots: int = 4, instances: int = 1) -> list:
     """Open-loop Poisson arrivals of PU 50-200 events from `threads` native client threads
     (lib/serve_load: each client submits at its arrival times and never waits for its
     results; a collector thread per client polls them) into a pt_server with a
@@ -600,7 +600,8 @@ def _serving(pt, rates, seconds: float, gate=None, threads: int = 16,
         out = []
         for rate in rates:
             r = subprocess.run([pbuild.SERVE_LOAD, evf, str(rate), str(seconds), str(threads),
-                                str(slots), str(budget), gf, "11"], capture_output=True,
+                                str(slots), str(budget), gf, "11", str(instances)],
+                               capture_output=True,
                                text=True, env=env, timeout=600)
             if r.returncode != 0:
                 raise RuntimeError(f"serve_load failed: {r.stderr.strip()[-300:]}")
@@ -795,6 +796,11 @@ def run_ours(args):
                 form: _serving(pt, rates, args.serve_seconds,
                                gate=(gw, gtau) if form == "gated" else None)
                 for form in ("plain", "gated")}
+            # model-instance scaling on one GPU: 1, 2 and 4 server instances behind the
+            # router, offered more than one instance sustains
+            line["serving"]["instances"] = [
+                _serving(pt, [args.serve_instances_rate], args.serve_seconds, instances=k)[0]
+                for k in (1, 2, 4)]
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -822,6 +828,8 @@ def main():
     ap.add_argument("--serve-rates", default="200,1000,2000,4000,6000,8000,10000,12000",
                     help="offered events/s of the serving sweep")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-instances-rate", type=float, default=16000.0,
+                    help="offered events/s of the instance-scaling runs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

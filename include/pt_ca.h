@@ -488,6 +488,31 @@ pt_status pt_server_stats(pt_server* s, double* p50_ms, double* p99_ms, double* 
  * counterpart; it explains slow requests in the latency tail. */
 pt_status pt_server_counters(pt_server* server, int64_t* batches, int64_t* split_batches,
                              int64_t* requeued_events);
+
+/* Router over several server instances (Sec. 3.2, Sec. 4.2: the inference server
+ * balances requests over several instances of the model, on one GPU or on several).
+ * Instance i is a pt_server on devices[i] (host array of n_instances device ordinals,
+ * 1..255 instances) with its own dispatcher thread, budget_per_instance bytes and
+ * slots_per_instance slots.  A submission goes to the instance with the fewest requests
+ * submitted and not yet completed on the device; the returned ticket names the
+ * instance.  Submit and poll behave as pt_submit and pt_poll; the gate, statistics and
+ * reset apply to every instance (p50: the instances' medians weighted by their
+ * requests; p99: the largest instance p99; events_per_s: the sum; per_instance_done
+ * (NULL or n_instances int64) receives each instance's completed requests).
+ * Thread-safe. */
+typedef struct pt_router pt_router;
+pt_status pt_router_create(const pt_geometry* geom, const pt_cuts* cuts, const int* devices,
+                           int n_instances, size_t budget_per_instance, int slots_per_instance,
+                           pt_router** out);
+pt_status pt_router_set_gate(pt_router* router, const float* w, float tau);
+pt_status pt_router_submit(pt_router* router, int64_t n, const float* x, const float* y,
+                           const float* z, const uint8_t* layer, uint64_t* ticket);
+pt_status pt_router_poll(pt_router* router, uint64_t ticket, int64_t timeout_us, int32_t* hits,
+                         uint8_t* nhits, pt_track* tracks, int64_t cap, int64_t* n);
+pt_status pt_router_stats(pt_router* router, double* p50_ms, double* p99_ms,
+                          double* events_per_s, int64_t* n_done, int64_t* per_instance_done);
+pt_status pt_router_reset_stats(pt_router* router);
+pt_status pt_router_destroy(pt_router* router);
 pt_status pt_server_reset_stats(pt_server* s);
 
 /* Stop accepting work, finish what is queued, free everything.  NULL ok. */

@@ -37,7 +37,8 @@ EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt
             "pt_submit", "pt_poll", "pt_server_stats", "pt_server_reset_stats",
             "pt_server_destroy", "pt_set_launch", "pt_autotune", "pt_set_tracing",
             "pt_get_trace", "pt_set_layer_pairs", "pt_set_wait_limit", "pt_server_counters",
-            "pt_last_error")
+            "pt_router_create", "pt_router_set_gate", "pt_router_submit", "pt_router_poll",
+            "pt_router_stats", "pt_router_reset_stats", "pt_router_destroy", "pt_last_error")
 
 
 # The chain's 13 (inner, outer) layer pairs, the library's default table (pt_set_layer_pairs).
@@ -142,6 +143,15 @@ def lib() -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_double), PI64],
             "pt_server_reset_stats": [P],
             "pt_server_counters": [P, PI64, PI64, PI64],
+            "pt_router_create": [ctypes.POINTER(PtGeometry), ctypes.POINTER(PtCuts), P, I32,
+                                 ctypes.c_size_t, I32, ctypes.POINTER(ctypes.c_void_p)],
+            "pt_router_set_gate": [P, P, ctypes.c_float],
+            "pt_router_submit": [P, I64, P, P, P, P, ctypes.POINTER(ctypes.c_uint64)],
+            "pt_router_poll": [P, ctypes.c_uint64, I64, P, P, P, I64, PI64],
+            "pt_router_stats": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double), PI64, P],
+            "pt_router_reset_stats": [P],
+            "pt_router_destroy": [P],
             "pt_server_destroy": [P],
             "pt_set_launch": [P, I32, I32],
             "pt_set_layer_pairs": [P, I32, P, P],
@@ -578,6 +588,8 @@ def pt_gate_adam(w, m, v, grad, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stre
 class Server:
     """pt_server: continuous-batching request server (thread-safe)."""
 
+    _fn = dict(submit="pt_submit", poll="pt_poll")
+
     def __init__(self, cuts: dict | None = None, budget_bytes: int = 2 << 30, slots: int = 2,
                  bfield: float = 3.8, device: int = 0):
         self.cuts = dict(cuts or default_cuts())
@@ -614,15 +626,15 @@ class Server:
         xs = [np.ascontiguousarray(a, t) for a, t in ((x, np.float32), (y, np.float32),
                                                      (z, np.float32), (layer, np.uint8))]
         t = ctypes.c_uint64(0)
-        _check(lib().pt_submit(self.handle, xs[0].shape[0], *(_hptr(a) for a in xs),
-                               ctypes.byref(t)))
+        submit = getattr(lib(), self._fn["submit"])
+        _check(submit(self.handle, xs[0].shape[0], *(_hptr(a) for a in xs), ctypes.byref(t)))
         return int(t.value)
 
     def pt_poll(self, ticket: int, timeout_us: int = -1):
         """(hits [S,6], nhits [S], tracks [S]); raises PtError (e.g. PT_ERR_NOT_READY)."""
         n = ctypes.c_int64(0)
-        st = lib().pt_poll(self.handle, ticket, int(timeout_us), None, None, None, 0,
-                           ctypes.byref(n))
+        poll = getattr(lib(), self._fn["poll"])
+        st = poll(self.handle, ticket, int(timeout_us), None, None, None, 0, ctypes.byref(n))
         if st == PT_OK:  # empty result, ticket released
             return (np.empty((0, 6), np.int32), np.empty(0, np.uint8), np.zeros(0, TRACK_DTYPE))
         if st != PT_ERR_CAPACITY:
@@ -631,8 +643,7 @@ class Server:
         hits = np.empty((S, 6), np.int32)
         nh = np.empty(S, np.uint8)
         tr = np.zeros(S, TRACK_DTYPE)
-        _check(lib().pt_poll(self.handle, ticket, 0, _hptr(hits), _hptr(nh), _hptr(tr), S,
-                             ctypes.byref(n)))
+        _check(poll(self.handle, ticket, 0, _hptr(hits), _hptr(nh), _hptr(tr), S, ctypes.byref(n)))
         return hits, nh, tr
 
     def pt_server_stats(self) -> dict:
@@ -650,6 +661,49 @@ class Server:
 
     def pt_server_reset_stats(self):
         _check(lib().pt_server_reset_stats(self.handle))
+
+
+class Router(Server):
+    """pt_router: several server instances behind one submit/poll front end."""
+
+    _fn = dict(submit="pt_router_submit", poll="pt_router_poll")
+
+    def __init__(self, instances: int = 2, cuts: dict | None = None,
+                 budget_bytes_per_instance: int = 1 << 30, slots: int = 2, bfield: float = 3.8,
+                 devices=None):
+        self.cuts = dict(cuts or default_cuts())
+        self.instances = int(instances)
+        devs = np.ascontiguousarray(devices if devices is not None else [0] * self.instances,
+                                    np.int32)
+        h = ctypes.c_void_p(None)
+        _check(lib().pt_router_create(
+            ctypes.byref(PtGeometry(bfield)),
+            ctypes.byref(PtCuts(*(float(self.cuts[k]) for k, _ in PtCuts._fields_))),
+            _hptr(devs), self.instances, int(budget_bytes_per_instance), int(slots),
+            ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().pt_router_destroy(self.handle)
+            self.handle = ctypes.c_void_p(None)
+
+    def pt_server_set_gate(self, w, tau: float):
+        arr = None if w is None else np.ascontiguousarray(w, np.float32)
+        _check(lib().pt_router_set_gate(self.handle, None if arr is None else _hptr(arr),
+                                        float(tau)))
+
+    def pt_server_stats(self) -> dict:
+        p50, p99, eps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64(0)
+        per = np.zeros(self.instances, np.int64)
+        _check(lib().pt_router_stats(self.handle, ctypes.byref(p50), ctypes.byref(p99),
+                                     ctypes.byref(eps), ctypes.byref(n), _hptr(per)))
+        return dict(p50_ms=p50.value, p99_ms=p99.value, events_per_s=eps.value, n_done=n.value,
+                    per_instance=per.tolist())
+
+    def pt_server_reset_stats(self):
+        _check(lib().pt_router_reset_stats(self.handle))
 
 
 def pt_autotune(offsets, x, y, z, layer, capacity: dict, phi_bins=(256, 512, 1024, 2048),

@@ -238,6 +238,9 @@ struct Launch {
 // Sets the calling thread's pt_last_error() message.
 void set_last_error(const char* msg);
 
+// Requests a server has completed since it was created (for the router's balancing).
+int64_t server_finished(pt_server* s);
+
 // Asynchronous pieces of a batch for the request server (runtime.cu): read-back of the
 // counters, status check of that copy, and copies of the cleaned ntuplets, tracks and
 // per-event offsets into host memory, each completion recorded on `done`.

@@ -83,6 +83,7 @@ struct pt_server {
   uint64_t next_ticket = 1;
   std::vector<double> lat_ms;
   int64_t completed = 0;
+  int64_t finished = 0;      // requests completed since creation (never reset)
   int64_t batches = 0;       // batches launched
   int64_t split = 0;         // batches that overflowed their slot and were split
   int64_t requeued = 0;      // events those splits sent back to run alone
@@ -104,6 +105,7 @@ void finish(pt_server* s, const ReqPtr& r, pt_status st, const std::string& err)
   r->t_done = Clock::now();
   s->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
   s->completed += 1;
+  s->finished += 1;
   s->t_last = r->t_done;
 }
 
@@ -241,6 +243,13 @@ void free_slot(Slot& sl) {
 }
 
 }  // namespace
+
+namespace ptca {
+int64_t server_finished(pt_server* s) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  return s->finished;
+}
+}  // namespace ptca
 
 extern "C" {
 

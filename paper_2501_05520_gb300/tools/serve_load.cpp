@@ -1,7 +1,9 @@
 // Open-loop load generator for the request server (pt_server_*), native threads only.
 //
-//   serve_load EVENTS_FILE RATE SECONDS CLIENTS SLOTS BUDGET_BYTES GATE_FILE|- SEED
+//   serve_load EVENTS_FILE RATE SECONDS CLIENTS SLOTS BUDGET_BYTES GATE_FILE|- SEED [INSTANCES]
 //
+// INSTANCES > 1 serves through a pt_router of that many server instances on device 0,
+// each with SLOTS slots and BUDGET_BYTES; otherwise one pt_server.
 // EVENTS_FILE holds a pool of events, each as int64 n followed by float32 x[n], y[n],
 // z[n] and uint8 layer[n] (little-endian).  CLIENTS threads submit events from the pool
 // at Poisson arrival times (RATE events/s in all, for SECONDS), never waiting for their
@@ -87,11 +89,13 @@ double pct(std::vector<double> v, double p) {
 }  // namespace
 
 int main(int argc, char** argv) {
-  if (argc != 9) {
+  if (argc != 9 && argc != 10) {
     std::fprintf(stderr,
-                 "usage: %s EVENTS RATE SECONDS CLIENTS SLOTS BUDGET_BYTES GATE|- SEED\n", argv[0]);
+                 "usage: %s EVENTS RATE SECONDS CLIENTS SLOTS BUDGET_BYTES GATE|- SEED [INSTANCES]\n",
+                 argv[0]);
     return 2;
   }
+  const int instances = argc == 10 ? std::atoi(argv[9]) : 1;
   std::vector<Event> pool;
   if (!read_events(argv[1], &pool)) {
     std::fprintf(stderr, "cannot read events from %s\n", argv[1]);
@@ -101,7 +105,8 @@ int main(int argc, char** argv) {
   const int clients = std::atoi(argv[4]), slots = std::atoi(argv[5]);
   const size_t budget = (size_t)std::atoll(argv[6]);
   const unsigned seed = (unsigned)std::atoi(argv[8]);
-  if (!(rate > 0) || !(seconds > 0) || clients < 1 || clients > 256) {
+  if (!(rate > 0) || !(seconds > 0) || clients < 1 || clients > 256 || instances < 1 ||
+      instances > 64) {
     std::fprintf(stderr, "bad arguments\n");
     return 2;
   }
@@ -127,30 +132,49 @@ int main(int argc, char** argv) {
     }
   }
   pt_server* srv = nullptr;
-  if (pt_server_create(&geom, &cuts, 0, budget, slots, &srv) != PT_OK) {
+  pt_router* rtr = nullptr;
+  if (instances > 1) {
+    std::vector<int> devs(instances, 0);
+    if (pt_router_create(&geom, &cuts, devs.data(), instances, budget, slots, &rtr) != PT_OK) {
+      std::fprintf(stderr, "pt_router_create: %s\n", pt_last_error());
+      return 1;
+    }
+  } else if (pt_server_create(&geom, &cuts, 0, budget, slots, &srv) != PT_OK) {
     std::fprintf(stderr, "pt_server_create: %s\n", pt_last_error());
     return 1;
   }
-  if (!gate.empty() && pt_server_set_gate(srv, gate.data(), gate[5057]) != PT_OK) {
-    std::fprintf(stderr, "pt_server_set_gate: %s\n", pt_last_error());
+  auto submit = [&](int64_t n, const float* x, const float* y, const float* z, const uint8_t* l,
+                    uint64_t* t) {
+    return rtr ? pt_router_submit(rtr, n, x, y, z, l, t) : pt_submit(srv, n, x, y, z, l, t);
+  };
+  auto poll = [&](uint64_t t, int64_t us, int32_t* h, uint8_t* nh, pt_track* tr, int64_t cap,
+                  int64_t* n) {
+    return rtr ? pt_router_poll(rtr, t, us, h, nh, tr, cap, n)
+               : pt_poll(srv, t, us, h, nh, tr, cap, n);
+  };
+  if (!gate.empty() &&
+      (rtr ? pt_router_set_gate(rtr, gate.data(), gate[5057])
+           : pt_server_set_gate(srv, gate.data(), gate[5057])) != PT_OK) {
+    std::fprintf(stderr, "set_gate: %s\n", pt_last_error());
     return 1;
   }
   // warm-up: every slot's graph captured, every pool event once
   {
     std::vector<uint64_t> t(pool.size());
     for (size_t i = 0; i < pool.size(); ++i)
-      pt_submit(srv, (int64_t)pool[i].x.size(), pool[i].x.data(), pool[i].y.data(),
-                pool[i].z.data(), pool[i].layer.data(), &t[i]);
+      submit((int64_t)pool[i].x.size(), pool[i].x.data(), pool[i].y.data(), pool[i].z.data(),
+             pool[i].layer.data(), &t[i]);
     for (uint64_t k : t) {
       int64_t n = 0;
-      while (pt_poll(srv, k, -1, nullptr, nullptr, nullptr, 0, &n) == PT_ERR_CAPACITY) {
+      while (poll(k, -1, nullptr, nullptr, nullptr, 0, &n) == PT_ERR_CAPACITY) {
         std::vector<int32_t> h(6 * n);
         std::vector<uint8_t> nh(n);
         std::vector<pt_track> tr(n);
-        if (pt_poll(srv, k, -1, h.data(), nh.data(), tr.data(), n, &n) == PT_OK) break;
+        if (poll(k, -1, h.data(), nh.data(), tr.data(), n, &n) == PT_OK) break;
       }
     }
-    pt_server_reset_stats(srv);
+    if (rtr) pt_router_reset_stats(rtr);
+    else pt_server_reset_stats(srv);
   }
   std::vector<Client> cl(clients);
   std::atomic<int64_t> submitted{0};
@@ -170,8 +194,8 @@ int main(int argc, char** argv) {
       k += (size_t)clients;
       uint64_t ticket = 0;
       const Clock::time_point ts = Clock::now();
-      if (pt_submit(srv, (int64_t)e.x.size(), e.x.data(), e.y.data(), e.z.data(), e.layer.data(),
-                    &ticket) != PT_OK) {
+      if (submit((int64_t)e.x.size(), e.x.data(), e.y.data(), e.z.data(), e.layer.data(),
+                 &ticket) != PT_OK) {
         std::lock_guard<std::mutex> lk(cl[c].mu);
         cl[c].errors += 1;
         continue;
@@ -203,12 +227,12 @@ int main(int argc, char** argv) {
         cl[c].q.pop_front();
       }
       int64_t n = 0;
-      pt_status st = pt_poll(srv, p.ticket, -1, nullptr, nullptr, nullptr, 0, &n);
+      pt_status st = poll(p.ticket, -1, nullptr, nullptr, nullptr, 0, &n);
       if (st == PT_ERR_CAPACITY) {
         h.resize(6 * n);
         nh.resize(n);
         tr.resize(n);
-        st = pt_poll(srv, p.ticket, -1, h.data(), nh.data(), tr.data(), n, &n);
+        st = poll(p.ticket, -1, h.data(), nh.data(), tr.data(), n, &n);
       }
       const double ms = std::chrono::duration<double, std::milli>(Clock::now() - p.t_submit).count();
       std::lock_guard<std::mutex> lk(cl[c].mu);
@@ -225,8 +249,12 @@ int main(int argc, char** argv) {
   const Clock::time_point t_last = Clock::now();
   double p50 = 0, p99 = 0, srv_rate = 0;
   int64_t done = 0, batches = 0, split = 0, requeued = 0;
-  pt_server_stats(srv, &p50, &p99, &srv_rate, &done);
-  pt_server_counters(srv, &batches, &split, &requeued);
+  if (rtr) {
+    pt_router_stats(rtr, &p50, &p99, &srv_rate, &done, nullptr);
+  } else {
+    pt_server_stats(srv, &p50, &p99, &srv_rate, &done);
+    pt_server_counters(srv, &batches, &split, &requeued);
+  }
   std::vector<double> all;
   int64_t errors = 0;
   for (auto& c : cl) {
@@ -247,12 +275,13 @@ int main(int argc, char** argv) {
       "\"server_p99_ms\": %.4f, \"client_p50_ms\": %.4f, \"client_p99_ms\": %.4f, "
       "\"client_max_ms\": %.4f, \"requests_over_3x_median\": %lld, "
       "\"requests_over_10ms\": %lld, \"batches\": %lld, \"split_batches\": %lld, "
-      "\"requeued_events\": %lld}\n",
+      "\"requeued_events\": %lld, \"instances\": %d}\n",
       rate, seconds, clients, slots, (long long)submitted.load(), (long long)done,
       (long long)errors, (double)done / seconds, drain_s, p50, p99, pct(all, 0.5),
       pct(all, 0.99), all.empty() ? 0.0 : *std::max_element(all.begin(), all.end()),
       (long long)over3, (long long)over10ms, (long long)batches, (long long)split,
-      (long long)requeued);
-  pt_server_destroy(srv);
+      (long long)requeued, instances);
+  if (rtr) pt_router_destroy(rtr);
+  else pt_server_destroy(srv);
   return errors ? 1 : 0;
 }

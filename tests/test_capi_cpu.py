@@ -75,9 +75,13 @@ def test_null_handles_are_rejected_before_any_cuda_call():
         "pt_server_stats": (None, None, None, None, None),
         "pt_set_layer_pairs": (None, 0, None, None), "pt_set_wait_limit": (None, 1),
         "pt_server_counters": (None, None, None, None),
+        "pt_router_submit": (None, 0, None, None, None, None, None),
+        "pt_router_poll": (None, 0, 0, None, None, None, 0, None),
+        "pt_router_stats": (None, None, None, None, None, None),
     }
     for name, args in calls.items():
         assert getattr(L, name)(*args) == pt.PT_ERR_INVALID, name
         assert L.pt_last_error().decode(), name
     assert L.pt_destroy(None) == pt.PT_OK
     assert L.pt_server_destroy(None) == pt.PT_OK
+    assert L.pt_router_destroy(None) == pt.PT_OK

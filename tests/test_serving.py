@@ -122,3 +122,18 @@ def test_native_load_generator(cuts, tmp_path):
     d = json.loads(r.stdout.strip().splitlines()[-1])
     assert d["errors"] == 0 and d["submitted"] > 50 and d["completed"] == d["submitted"]
     assert 0 < d["server_p50_ms"] <= d["server_p99_ms"]
+
+
+def test_router_results_same_alone(cuts):
+    """Three server instances behind the router: every result equals the event alone,
+    and the requests spread over the instances."""
+    events = _events(30, 6200)
+    ref = _alone(events, cuts)
+    with pt.Router(instances=3, cuts=cuts, budget_bytes_per_instance=1 << 30, slots=2) as r:
+        got = _serve(r, events, threads=12)
+        st = r.pt_server_stats()
+    for (h, n, t), (h2, n2, t2) in zip(ref, got):
+        assert np.array_equal(h, h2) and np.array_equal(n, n2)
+        assert t.tobytes() == t2.tobytes()
+    assert st["n_done"] == len(events) and sum(st["per_instance"]) == len(events)
+    assert sum(1 for k in st["per_instance"] if k > 0) >= 2
