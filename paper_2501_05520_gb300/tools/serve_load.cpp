@@ -9,9 +9,10 @@
 // at Poisson arrival times (RATE events/s in all, for SECONDS), never waiting for their
 // results: each client has a collector thread that polls its tickets in submission
 // order.  GATE_FILE: 5057 float32 weights and a float32 threshold, or "-" for the plain
-// form.  Prints one JSON line: offered and achieved rates, completions over the offered
-// window, the server's latency percentiles (submit to result ready) and the client-side
-// latency (submit to poll returning).
+// form.  Prints one JSON line: the offered rate; sustained events/s = results returned
+// within the offered window over its length; throughput = all results over the window
+// plus the time the server took to drain the backlog after it; the server's latency
+// percentiles (submit to result ready) and the clients' (submit to poll returning).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -76,6 +77,7 @@ struct Client {
   std::deque<Pending> q;
   bool done = false;
   std::vector<double> lat_ms;
+  int64_t in_window = 0;  // results returned before the offered window closed
   int64_t errors = 0;
 };
 
@@ -234,10 +236,15 @@ int main(int argc, char** argv) {
         tr.resize(n);
         st = poll(p.ticket, -1, h.data(), nh.data(), tr.data(), n, &n);
       }
-      const double ms = std::chrono::duration<double, std::milli>(Clock::now() - p.t_submit).count();
+      const Clock::time_point tr_ = Clock::now();
+      const double ms = std::chrono::duration<double, std::milli>(tr_ - p.t_submit).count();
       std::lock_guard<std::mutex> lk(cl[c].mu);
-      if (st == PT_OK) cl[c].lat_ms.push_back(ms);
-      else cl[c].errors += 1;
+      if (st == PT_OK) {
+        cl[c].lat_ms.push_back(ms);
+        cl[c].in_window += tr_ <= t_end;
+      } else {
+        cl[c].errors += 1;
+      }
     }
   };
   std::vector<std::thread> th;
@@ -256,10 +263,11 @@ int main(int argc, char** argv) {
     pt_server_counters(srv, &batches, &split, &requeued);
   }
   std::vector<double> all;
-  int64_t errors = 0;
+  int64_t errors = 0, in_window = 0;
   for (auto& c : cl) {
     all.insert(all.end(), c.lat_ms.begin(), c.lat_ms.end());
     errors += c.errors;
+    in_window += c.in_window;
   }
   const double drain_s = std::chrono::duration<double>(t_last - t_end).count();
   const double med = pct(all, 0.5);
@@ -271,13 +279,15 @@ int main(int argc, char** argv) {
   std::printf(
       "{\"offered_events_per_s\": %.1f, \"seconds\": %.3f, \"clients\": %d, \"slots\": %d, "
       "\"submitted\": %lld, \"completed\": %lld, \"errors\": %lld, "
-      "\"sustained_events_per_s\": %.1f, \"drain_s\": %.4f, \"server_p50_ms\": %.4f, "
+      "\"sustained_events_per_s\": %.1f, \"throughput_events_per_s\": %.1f, "
+      "\"drain_s\": %.4f, \"server_p50_ms\": %.4f, "
       "\"server_p99_ms\": %.4f, \"client_p50_ms\": %.4f, \"client_p99_ms\": %.4f, "
       "\"client_max_ms\": %.4f, \"requests_over_3x_median\": %lld, "
       "\"requests_over_10ms\": %lld, \"batches\": %lld, \"split_batches\": %lld, "
       "\"requeued_events\": %lld, \"instances\": %d}\n",
       rate, seconds, clients, slots, (long long)submitted.load(), (long long)done,
-      (long long)errors, (double)done / seconds, drain_s, p50, p99, pct(all, 0.5),
+      (long long)errors, (double)in_window / seconds, (double)done / (seconds + drain_s),
+      drain_s, p50, p99, pct(all, 0.5),
       pct(all, 0.99), all.empty() ? 0.0 : *std::max_element(all.begin(), all.end()),
       (long long)over3, (long long)over10ms, (long long)batches, (long long)split,
       (long long)requeued, instances);
