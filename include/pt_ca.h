@@ -343,7 +343,7 @@ pt_status pt_enqueue_batch(pt_ctx* ctx, int n_events, const int64_t* hit_offsets
  * this entry point exists for callers that cannot allocate device memory -- code whose
  * process hands all device memory to another allocator (a framework's caching pool
  * that has reserved the GPU), or real-time loops that must not allocate after start-up
- * -- and so cannot create a context.  Its scratch is a fixed array of about 2.7 MB
+ * -- and so cannot create a context.  Its scratch is a fixed array of about 2.4 MB
  * compiled into the library, which every GPU that loads the library keeps until the
  * process exits.
  *   n <= 65536 hits, else PT_ERR_CAPACITY with no GPU work.  x, y, z (float32) and
