@@ -7,7 +7,7 @@
 // (written contiguously by the doublet stage).  The cells leaving h1 are found again
 // here by the doublet search towards its outer layers (the same window and exact cuts,
 // so exactly the cells the doublet stage made), staged in shared memory with their
-// outer hit and r-z slope, and ordered by slope with a counting sort into 64 buckets
+// outer hit and r-z slope, and ordered by slope with a counting sort into 128 buckets
 // spanning the staged slopes.  With d1 = r1-r0, d2 = r2-r1 and t_a, t_b the slopes of
 // a and b, C1 reads
 //   d1 d2 |t_a - t_b| <= rz0 (d1 + d2) + rz1 |t_a d1 + t_b d2|,
@@ -23,8 +23,8 @@
 // slope is a monotone function of it, evaluated the same way for the staged slopes and
 // for the window's ends, which are moved out by a further 0.1 % + 1e-5 so that rounding
 // of t_a -+ w cannot exclude a bucket); the staged cells there that fall inside the
-// window are tested with C1, and the pairs that pass are queued and tested with C2 and
-// C3 32 at a time, all lanes busy.
+// window are queued, and the queued pairs are tested with C1, C2 and C3 32 at a time,
+// all lanes busy.
 //
 // The target cell (h1, h2) of a link is found afterwards, one thread per link, in h2's
 // incoming segment from h1's layer (ordered by inner hit) by binary search: in the
@@ -47,7 +47,8 @@ constexpr float kHalfPi = 1.57079632679489661923f;
 constexpr int kConnWarps = 8;
 constexpr int kConnBlocksPerSm = 4;  // 64 registers per thread
 constexpr int kOut = 128;            // staged outgoing cells of one piece (<= 256)
-constexpr int kNb = 64;              // slope buckets of a piece (two per lane)
+constexpr int kNb = 128;             // slope buckets of a piece (a multiple of 32)
+static_assert(kNb % 32 == 0, "buckets are scanned kNb / 32 per lane");
 constexpr int kQueue = 64;           // pairs that passed C1, waiting for C2/C3 (power of two)
 constexpr int kFound = 64;           // links of one incoming group kept before writing
 static_assert(kOut <= 256 && kOut % 32 == 0, "staged index fits 8 bits");
@@ -109,7 +110,7 @@ struct ConnWarp {
   uint32_t bstart[kNb + 1];  // first bucket-ordered position of each slope bucket
   uint32_t lcnt[32];         // links found per incoming cell of the group
   uint32_t loff[32];         // first slot of each incoming cell's links
-  uint2 q[kQueue];           // C1 passes: (incoming lane, staged index)
+  uint2 q[kQueue];           // window passes: (incoming lane, bucket-order position)
   uint32_t fa[kFound];       // found links: incoming lane | rank << 5
   uint32_t fb[kFound];       //   target: outer hit | slot << 29
   float fq[kFound];          //   quality
@@ -312,11 +313,20 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
         }
         __syncwarp();
         {
-          const uint32_t c0 = W.bstart[2 * lane + 1], c1 = W.bstart[2 * lane + 2];
-          const uint32_t inc = warp_incl_scan(c0 + c1);
+          // bucket starts: kNb / 32 consecutive buckets per lane
+          uint32_t cb[kNb / 32], sum = 0;
+#pragma unroll
+          for (int u = 0; u < kNb / 32; ++u) {
+            cb[u] = W.bstart[(kNb / 32) * lane + u + 1];
+            sum += cb[u];
+          }
+          uint32_t run = warp_incl_scan(sum) - sum;
           __syncwarp();
-          W.bstart[2 * lane + 1] = inc - c1;
-          W.bstart[2 * lane + 2] = inc;
+#pragma unroll
+          for (int u = 0; u < kNb / 32; ++u) {
+            run += cb[u];
+            W.bstart[(kNb / 32) * lane + u + 1] = run;
+          }
         }
         __syncwarp();
 #pragma unroll
@@ -402,7 +412,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
               pend = W.bstart[slope_bucket(__fadd_rn(ta, w2), tmin, scale) + 1];
             }
             uint32_t head = 0, tail = 0;
-            // C2 and C3 on up to 32 queued pairs, all lanes busy
+            // C1, C2 and C3 on up to 32 queued pairs, all lanes busy
             auto process = [&](uint32_t nt) {
               __syncwarp();
               const bool v = (uint32_t)lane < nt;
@@ -417,10 +427,12 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
               float q = 0.0f;
               uint32_t cb = 0;
               if (v) {
-                ok = link_c23(cuts, q0, qb0, p1, W.p2[e.y], q);
+                const uint32_t st = W.perm[e.y];
+                const float4 q2 = W.p2[st];
+                ok = link_c1(cuts, q0, p1, q2) && link_c23(cuts, q0, qb0, p1, q2, q);
                 // the target cell, named by its outer hit and the slot of h1's layer
                 // among that hit's inner layers until k_link_targets finds it
-                cb = W.h2[e.y] | ((uint32_t)W.j2[e.y] << 29);
+                cb = W.h2[st] | ((uint32_t)W.j2[st] << 29);
               }
               uint32_t rk = 0;
               if (ok) rk = atomicAdd(&W.lcnt[il], 1u);
@@ -439,16 +451,13 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
               }
               nf += __popc(pm);
             };
-            // each lane walks its own bucket range; C1 passes are queued
+            // each lane walks its own bucket range; the staged cells inside its window
+            // are queued (bucket-order position) and tested with C1-C3 32 at a time
             while (__any_sync(kFull, pos < pend)) {
               bool pass = false;
-              uint32_t e = 0;
+              const uint32_t e = pos;
               if (pos < pend) {
-                const float tb = W.ts[pos];
-                if (fabsf(tb - ta) <= w) {
-                  e = W.perm[pos];
-                  pass = link_c1(cuts, p0, p1, W.p2[e]);
-                }
+                pass = fabsf(W.ts[pos] - ta) <= w;
                 ++pos;
               }
               const unsigned bal = __ballot_sync(kFull, pass);

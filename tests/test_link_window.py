@@ -88,14 +88,14 @@ def test_window_contains_c1_at_the_boundary(cuts):
     _check(cuts, *(v.astype(f32) for v in (r0, r1, r2, z0, z1, z2)))
 
 
-def _bucket(x, tmin, scale, nb=64):
+def _bucket(x, tmin, scale, nb=128):
     """The link kernel's slope bucket: trunc((x - tmin) * scale) in float32, clamped."""
     v = (x.astype(f32) - f32(tmin)).astype(f32) * f32(scale)
     return np.clip(np.trunc(v.astype(f32)), 0, nb - 1).astype(np.int64)
 
 
 def test_bucket_range_contains_window():
-    """Outgoing slopes are counting-sorted into 64 buckets spanning their range, and an
+    """Outgoing slopes are counting-sorted into 128 buckets spanning their range, and an
     incoming cell visits the buckets of t_a - w2 .. t_a + w2 with w2 = 1.001 w + 1e-5:
     every staged slope with |t_a - t_b| <= w (float32) lies in a visited bucket, for
     windows down to 1e-3 and slopes up to the largest |t| the cuts allow."""
@@ -105,7 +105,7 @@ def test_bucket_range_contains_window():
         t0 = rng.uniform(-7, 7 - spread)
         tb = (t0 + rng.uniform(0, spread, rng.integers(1, 129))).astype(f32)
         tmin, tmax = tb.min(), tb.max()
-        scale = f32(64) / f32(tmax - tmin) if tmax - tmin > 1e-6 else f32(0)
+        scale = f32(128) / f32(tmax - tmin) if tmax - tmin > 1e-6 else f32(0)
         kb = _bucket(tb, tmin, scale)
         ta = (rng.uniform(t0 - 0.1, t0 + spread + 0.1, 200)).astype(f32)
         w = f32(1e-3) + rng.choice([0.0, 1e-3, 0.05, 0.3], 200).astype(f32)
