@@ -472,30 +472,96 @@ def _gap_form(pt, dev, flush, steps: int, n_events: int = 64) -> dict:
     return out
 
 
-def _vertexing(ctx, dbat, stream, steps: int) -> dict:
-    """Primary vertices (pt_find_vertices, quadruplets and longer, 0.02 cm steps) of the
-    fitted tracks of one bench batch, timed with CUDA events on the library's stream; the
-    chain itself runs before the events."""
+def _fishbone_form(pt, dev, flush, steps: int, n_events: int = 64) -> dict:
+    """Fishbone step: PU200 events whose sensors overlap (a second hit on the same layer
+    for 20 % of the crossings, seeds 3600+i), through the whole-chain graph with device
+    inputs, with the step off and on; events/s, ntuplet candidates before cleaning, and
+    efficiency / fake / duplicate rate against generator truth."""
+    import dataclasses
     import torch
-    off, x, y, z, layer = dbat[0]
-    ctx.pt_load_batch(off, x, y, z, layer)
-    ctx.pt_build_doublets(sync=False)
-    ctx.pt_connect_cells(sync=False)
-    ctx.pt_find_ntuplets(sync=False)
-    ctx.pt_fit_tracks(sync=False)
-    nv = ctx.pt_find_vertices()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
-    for e0, e1 in ev:
-        e0.record(stream)
-        ctx.pt_find_vertices(sync=False)
-        e1.record(stream)
-    stream.synchronize()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    E = len(off) - 1
-    return {"ms_per_step": statistics.mean(ms), "events_per_step": E,
-            "vertices_per_event": nv / E, "tracks_per_event": ctx.pt_get_tracks().shape[0] / E,
-            "workload": "the bench batch's fitted tracks (its particles have independent z0)"}
+    from sim import truth
+    cfg = dataclasses.replace(sim.PU200, overlap=0.2)
+    evs = [sim.generate(cfg, 3600 + i) for i in range(n_events)]
+    off, *arrs = sim.concat(evs)
+    d = [torch.from_numpy(a).to(dev) for a in arrs]
+    cap = pt.default_capacity(max_events=n_events, hits_per_event=65536,
+                              cells_per_event=6_000_000, links_per_event=524_288,
+                              ntuplets_per_event=393_216, phi_bins=2048)
+    out = {"workload": f"{n_events} PU200 events, overlapping sensors on 20 % of the "
+                       "crossings, seeds 3600+i",
+           "path": "whole-chain CUDA graph, device inputs, L2 flushed per step"}
+    with pt.Context(capacity=cap, device=dev.index or 0) as c:
+        c.pt_set_launch(8, 8)
+        for name, on in (("off", False), ("on", True)):
+            c.pt_set_fishbone(on)
+            s_ = c.stream
+            with torch.cuda.stream(s_):
+                for _ in range(2):
+                    c.pt_enqueue_batch(off, *d)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(steps)]
+                for e0, e1 in ev:
+                    flush.zero_()
+                    e0.record(s_)
+                    c.pt_enqueue_batch(off, *d)
+                    e1.record(s_)
+            s_.synchronize()
+            hits, nh, eoff = c.pt_get_ntuplets()
+            n_cand = c.pt_get_candidates()[0].shape[0]
+            ms = [a.elapsed_time(b) for a, b in ev]
+            tot = dict(reco=0, matched=0.0, dup=0.0, fake=0, nt=0)
+            for e, evt in enumerate(evs):
+                r = truth.rates_fast(hits[eoff[e]:eoff[e + 1]], evt.pid, evt.layer)
+                tot["reco"] += r["n_reconstructable"]
+                tot["matched"] += r["efficiency"] * r["n_reconstructable"]
+                tot["dup"] += r["duplicate_rate"] * r["n_reconstructable"]
+                tot["fake"] += r["n_fake"]
+                tot["nt"] += r["n_ntuplets"]
+            out[name] = {"value": n_events * len(ms) / (sum(ms) / 1000.0), "unit": "events/s",
+                         "ms_per_step": float(np.mean(ms)),
+                         "efficiency": tot["matched"] / max(tot["reco"], 1),
+                         "fake_rate": tot["fake"] / max(tot["nt"], 1),
+                         "duplicate_rate": tot["dup"] / max(tot["reco"], 1),
+                         "candidates": int(n_cand), "n_ntuplets": tot["nt"]}
+    return out
+
+
+def _vertexing(ctx, dbat, stream, steps: int) -> dict:
+    """Primary vertices (pt_find_vertices, quadruplets and longer, 0.02 cm steps) timed
+    with CUDA events on the library's stream, the chain itself before the events: on 64
+    PU200 events with vertex structure (200 interactions of 50 particles sharing one z,
+    seeds 7300+i), and on the benchmark batch itself, whose particles each draw their own
+    z0 so that the 0.02 cm linking chains thousands of tracks into a few groups (a stress
+    case for the per-group sums)."""
+    import torch
+    out = {}
+    evs = [sim.vertex_event(7300 + i, 200) for i in range(len(dbat[0][0]) - 1)]
+    voff, *varrs = sim.concat(evs)
+    dev = dbat[0][1].device
+    vbat = (voff, *(torch.from_numpy(a).to(dev) for a in varrs))
+    for name, (off, x, y, z, layer) in (("vertex_events", vbat), ("bench_batch", dbat[0])):
+        ctx.pt_load_batch(off, x, y, z, layer)
+        ctx.pt_build_doublets(sync=False)
+        ctx.pt_connect_cells(sync=False)
+        ctx.pt_find_ntuplets(sync=False)
+        ctx.pt_fit_tracks(sync=False)
+        nv = ctx.pt_find_vertices()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for e0, e1 in ev:
+            e0.record(stream)
+            ctx.pt_find_vertices(sync=False)
+            e1.record(stream)
+        stream.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        E = len(off) - 1
+        out[name] = {"ms_per_step": statistics.mean(ms), "events_per_step": E,
+                     "vertices_per_event": nv / E,
+                     "tracks_per_event": ctx.pt_get_tracks().shape[0] / E}
+    out["ms_per_step"] = out["vertex_events"]["ms_per_step"]
+    out["workload"] = ("64 PU200 events of 200 interactions x 50 particles sharing z "
+                       "(seeds 7300+i); bench_batch: the benchmark's own batch")
+    return out
 
 
 def _broken_line(ctx, dbat, stream, steps: int) -> dict:
@@ -713,6 +779,7 @@ def run_ours(args):
         raw_input = _raw_input(ctx, dev, stream, min(args.steps, 20), B)
     latency = _latency(pt, dev) if not args.no_latency else None
     gap = _gap_form(pt, dev, flush, min(args.steps, 10)) if not args.no_physics else None
+    fishbone = _fishbone_form(pt, dev, flush, min(args.steps, 10)) if not args.no_physics else None
     config4 = {"plain": _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)}
     ctx.pt_set_gate(gw, gtau)
     config4["gated"] = _config4(ctx, dev, flush, stream, args.steps, args.warmup, B)
@@ -784,6 +851,7 @@ def run_ours(args):
                 "batch_workload": config4,
                 "latency": latency,
                 "gap_pairs": gap,
+                "fishbone": fishbone,
                 "vertexing": vertexing,
                 "broken_line": broken_line,
                 "raw_input": raw_input,

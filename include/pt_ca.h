@@ -411,6 +411,27 @@ pt_status pt_set_launch(pt_ctx* ctx, int blocks_per_sm, int search_blocks_per_sm
  * the next whole-batch call re-captures its graph. */
 pt_status pt_set_layer_pairs(pt_ctx* ctx, int n_pairs, const int32_t* inner, const int32_t* outer);
 
+/* Fishbone duplicate removal, off by default.  The paper does not describe this step;
+ * this is the library's reading of the overlap cleaning of the Patatrack chain
+ * (Sec. 2.2.1 names the chain's steps).  A track crossing two overlapping sensors of
+ * one layer leaves two hits there, and its cells from both to the next hit point the
+ * same way.  After the links (and the learned gate, when set), cells with at least one
+ * outgoing link that end on the same hit are compared two by two when their inner hits
+ * lie on different layers or on different sensors of one layer (r, barrel layers 0..3,
+ * or |z|, disks, more than 0.1 cm apart, as float32 r = sqrt(x x + y y) and |z|; the
+ * stand-in for a sensor identity, which the hit input does not carry): with u, v the
+ * float32 vectors from each cell's inner hit to the common outer hit, a pair is aligned when
+ * u.v > 0 and (u.v)^2 >= 0.99999 |u|^2 |v|^2 (evaluated as
+ * ((ux vx + uy vy) + uz vz)^2 >= 0.99999 (|u|^2 |v|^2), each |.|^2 as (x x + y y) + z z,
+ * correctly rounded, no FMA).  Of an aligned pair on the same inner layer the shorter
+ * cell loses, on different inner layers the longer one; at equal lengths the cell whose
+ * inner hit has the larger input index loses.  Every cell that loses to some aligned
+ * partner is removed with all its links before the ntuplet search; the link counts and
+ * link exports then list the remaining links.  on: 0 off, 1 on; PT_ERR_INVALID
+ * otherwise.  Synchronises the stream; the next whole-batch call re-captures its
+ * graph. */
+pt_status pt_set_fishbone(pt_ctx* ctx, int on);
+
 /* Limit, in SM clock cycles (>= 1; default 2^31, about 1 s at 2 GHz), of the context's
  * bounded device-side waits: the learned gate's waits for its tensor-core results
  * (pt_connect_cells in the gated form, pt_gate_score, the whole-batch graph).  A wait that

@@ -71,6 +71,10 @@ def _load():
         lib.orc_reconstruct_pairs.restype = P
         lib.orc_reconstruct_pairs.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.POINTER(Cuts),
                                               ctypes.c_double, ctypes.c_int, P, P]
+        lib.orc_reconstruct_ex.restype = P
+        lib.orc_reconstruct_ex.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.POINTER(Cuts),
+                                           ctypes.c_double, ctypes.c_int, P, P, P,
+                                           ctypes.c_int64, ctypes.c_int]
         for name in ("orc_sizes", "orc_get_radius", "orc_get_near"):
             getattr(lib, name).argtypes = [P, P]
         lib.orc_get_cells.argtypes = [P, P, P]
@@ -81,6 +85,8 @@ def _load():
         lib.orc_fit_hits.argtypes = [ctypes.c_int, P, P, P, ctypes.c_double, P]
         lib.orc_doublet_ok.argtypes = [ctypes.POINTER(Cuts), P, P, P]
         lib.orc_link_ok.argtypes = [ctypes.POINTER(Cuts), P, ctypes.c_int, P, P, P, P]
+        lib.orc_fb_loses.argtypes = [P, P, ctypes.c_int, ctypes.c_int64, P, ctypes.c_int,
+                                     ctypes.c_int64]
         lib.orc_dedup.restype = ctypes.c_int64
         lib.orc_dedup.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int64, ctypes.c_int64, P]
         _lib = lib
@@ -96,13 +102,15 @@ def make_cuts(d: dict) -> Cuts:
 
 
 def reconstruct(x, y, z, layer, cuts: dict, bfield: float = 3.8, link_keep=None,
-                pairs=None) -> dict:
+                pairs=None, fishbone: bool = False) -> dict:
     """Run the whole chain on one event.  Hit arrays are float32 / uint8, input order.
 
     link_keep: optional bool array, one entry per link of the plain run (its link order);
     links with False are removed before the ntuplet search (a gate decision).
     pairs: optional (inner, outer) layer-pair table replacing DEFAULT_PAIRS (e.g.
-    DEFAULT_PAIRS + gap_pairs()); not combined with link_keep.
+    DEFAULT_PAIRS + gap_pairs()).
+    fishbone: apply the fishbone step (aligned active cells sharing an outer hit) to the
+    links before the ntuplet search; the returned links are those that remain.
 
     Returns a dict of numpy arrays:
       r                      float32 [N]
@@ -122,22 +130,19 @@ def reconstruct(x, y, z, layer, cuts: dict, bfield: float = 3.8, link_keep=None,
     n = x.shape[0]
     c = make_cuts(cuts)
     if pairs is not None:
-        if link_keep is not None:
-            raise ValueError("pairs and link_keep are not combined")
         pt = np.ascontiguousarray(np.asarray(pairs, np.int32).reshape(-1, 2).T)
         pin, pout = np.ascontiguousarray(pt[0]), np.ascontiguousarray(pt[1])
-        h = lib.orc_reconstruct_pairs(n, _ptr(x), _ptr(y), _ptr(z), _ptr(layer),
-                                      ctypes.byref(c), float(bfield), int(pin.size), _ptr(pin),
-                                      _ptr(pout))
-        if not h:
+        if pin.size == 0:
             raise ValueError("invalid layer-pair table")
-    elif link_keep is None:
-        h = lib.orc_reconstruct(n, _ptr(x), _ptr(y), _ptr(z), _ptr(layer), ctypes.byref(c),
-                                float(bfield))
     else:
-        keep = np.ascontiguousarray(link_keep, np.uint8)
-        h = lib.orc_reconstruct_masked(n, _ptr(x), _ptr(y), _ptr(z), _ptr(layer),
-                                       ctypes.byref(c), float(bfield), _ptr(keep), keep.size)
+        pin = pout = np.zeros(0, np.int32)
+    keep = None if link_keep is None else np.ascontiguousarray(link_keep, np.uint8)
+    h = lib.orc_reconstruct_ex(n, _ptr(x), _ptr(y), _ptr(z), _ptr(layer), ctypes.byref(c),
+                               float(bfield), int(pin.size), _ptr(pin), _ptr(pout),
+                               _ptr(keep) if keep is not None else None,
+                               0 if keep is None else keep.size, int(bool(fishbone)))
+    if not h:
+        raise ValueError("invalid layer-pair table")
     try:
         sz = np.zeros(7, np.int64)
         lib.orc_sizes(h, _ptr(sz))
@@ -202,6 +207,15 @@ def link_ok(cuts: dict, h0, layer0: int, h1, h2):
     ok = lib.orc_link_ok(ctypes.byref(c), _ptr(a), int(layer0), _ptr(b), _ptr(d),
                          ctypes.byref(near), ctypes.byref(q))
     return bool(ok), bool(near.value), float(q.value)
+
+
+def fishbone_loses(h, i, layer_i: int, key_i: int, j, layer_j: int, key_j: int) -> bool:
+    """The fishbone comparison: does cell (i -> h) lose to cell (j -> h)?  h, i, j are
+    (x, y, z) points, rounded to float32."""
+    lib = _load()
+    a = [np.ascontiguousarray(v, np.float32) for v in (h, i, j)]
+    return bool(lib.orc_fb_loses(_ptr(a[0]), _ptr(a[1]), int(layer_i), int(key_i), _ptr(a[2]),
+                                 int(layer_j), int(key_j)))
 
 
 def dedup(hits, cells, nh, q, n_cells: int, n_hits: int) -> np.ndarray:

@@ -14,6 +14,7 @@
  *   r = sqrt(x*x + y*y)                                   (per hit, float32)
  *   doublet (i inner, o outer) on an allowed layer pair:   D0..D4
  *   link a=(h0,h1) -> b=(h1,h2):                           C1..C3
+ *   fishbone (optional) = of two aligned active cells ending on one hit, one is removed
  *   ntuplet = every root->leaf path of linked cells with 3..6 hits
  *   dedup   = best-key-per-cell, then triplets sharing a hit with a >=4-hit survivor
  *   fit     = closed-form circle (Karimaki, NIM A305 (1991) 187) + straight z(s) line
@@ -374,6 +375,81 @@ int64_t orc_dedup(int64_t T, const int32_t* hits, const int32_t* cells, const in
 }
 
 /* ------------------------------------------------------------------ whole chain */
+/* ---------------------------------------------------------------------- fishbone */
+/* Fishbone duplicate removal (optional).  The paper does not describe this step; this is
+ * the library's reading of the overlap cleaning of the Patatrack chain.  A track that
+ * crosses two overlapping sensors of one layer leaves two hits there, and the cells from
+ * both to the same outer hit point the same way.  Active cells are those with at least
+ * one outgoing link.  Two active cells i, j ending on the same hit h, with u = h - inner(i)
+ * and v = h - inner(j) (float32, outer minus inner), are compared when their inner hits
+ * lie on different layers or on different sensors of one layer: radii (barrel layers
+ * 0..3) or |z| (disks) more than 0.1 cm apart, the stand-in for a sensor identity,
+ * which the hit input does not carry.  They are aligned when u.v > 0 and
+ * (u.v)^2 >= 0.99999 |u|^2 |v|^2.  Of an aligned pair on the same inner layer the shorter
+ * cell loses (the longer lever arm stays); on different inner layers the longer one loses
+ * (the consecutive-layer cell stays); equal lengths: the cell whose inner hit has the
+ * larger input index loses.  A cell that loses to any aligned partner is removed with
+ * every link from or to it.  Activity is taken from the links before the removal, so the
+ * result does not depend on the order of the comparisons. */
+#define ORC_FB_COS2 0.99999f
+#define ORC_FB_SENSOR_GAP 0.1f
+
+static int fb_loses_at(float hx, float hy, float hz, float ix, float iy, float iz, int li,
+                       int64_t ki, float jx, float jy, float jz, int lj, int64_t kj) {
+  if (li == lj) {
+    /* one layer: only hits on different sensors (radius or |z| apart) are compared */
+    const float si = li < 4 ? sqrtf((ix * ix) + (iy * iy)) : fabsf(iz);
+    const float sj = lj < 4 ? sqrtf((jx * jx) + (jy * jy)) : fabsf(jz);
+    if (!(fabsf(si - sj) > ORC_FB_SENSOR_GAP)) return 0;
+  }
+  const float ux = hx - ix, uy = hy - iy, uz = hz - iz;
+  const float vx = hx - jx, vy = hy - jy, vz = hz - jz;
+  const float dot = ((ux * vx) + (uy * vy)) + (uz * vz);
+  const float nu = ((ux * ux) + (uy * uy)) + (uz * uz);
+  const float nv = ((vx * vx) + (vy * vy)) + (vz * vz);
+  if (!(dot > 0.0f) || !((dot * dot) >= (ORC_FB_COS2 * (nu * nv)))) return 0;
+  if (nu == nv) return ki > kj;
+  return li == lj ? nu < nv : nu > nv;
+}
+
+static int fb_loses(const float* x, const float* y, const float* z, const uint8_t* layer,
+                    int32_t h, int32_t hi, int32_t hj) {
+  return fb_loses_at(x[h], y[h], z[h], x[hi], y[hi], z[hi], layer[hi], hi, x[hj], y[hj], z[hj],
+                     layer[hj], hj);
+}
+
+/* The fishbone comparison alone (for checks): does the cell from inner hit i (layer li,
+ * input index ki) to outer hit h lose to the cell from inner hit j (lj, kj) to h?
+ * h, i, j: float32 (x, y, z). */
+int orc_fb_loses(const float* h, const float* i, int li, int64_t ki, const float* j, int lj,
+                 int64_t kj) {
+  return fb_loses_at(h[0], h[1], h[2], i[0], i[1], i[2], li, ki, j[0], j[1], j[2], lj, kj);
+}
+
+/* killed[c] = 1 for every removed cell (killed has C entries, zeroed by the caller). */
+static void fishbone(int64_t n, const float* x, const float* y, const float* z,
+                     const uint8_t* layer, int64_t C, const int32_t* cin, const int32_t* cout,
+                     const int32_t* link_off, uint8_t* killed) {
+  /* active cells grouped by outer hit (counting sort) */
+  int32_t* cnt = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+  for (int64_t c = 0; c < C; ++c)
+    if (link_off[c + 1] > link_off[c]) cnt[cout[c] + 1]++;
+  for (int64_t h = 0; h < n; ++h) cnt[h + 1] += cnt[h];
+  int32_t* grp = (int32_t*)malloc((size_t)(cnt[n] > 0 ? cnt[n] : 1) * sizeof(int32_t));
+  int32_t* fill = (int32_t*)malloc((size_t)(n + 1) * sizeof(int32_t));
+  memcpy(fill, cnt, (size_t)(n + 1) * sizeof(int32_t));
+  for (int64_t c = 0; c < C; ++c)
+    if (link_off[c + 1] > link_off[c]) grp[fill[cout[c]]++] = (int32_t)c;
+  for (int64_t h = 0; h < n; ++h)
+    for (int32_t a = cnt[h]; a < cnt[h + 1]; ++a)
+      for (int32_t b = cnt[h]; b < cnt[h + 1]; ++b)
+        if (a != b && fb_loses(x, y, z, layer, (int32_t)h, cin[grp[a]], cin[grp[b]])) {
+          killed[grp[a]] = 1;
+          break;
+        }
+  free(cnt); free(grp); free(fill);
+}
+
 /* link_keep (optional, may be NULL): one flag per link accepted by the cuts, in the
  * order the plain run lists them (cell a major); links with flag 0 are removed before
  * the ntuplet search (the learned gate's decision, computed by the caller). */
@@ -381,19 +457,23 @@ int64_t orc_dedup(int64_t T, const int32_t* hits, const int32_t* cells, const in
 static orc_result* reconstruct_pairs(int64_t n, const float* x, const float* y, const float* z,
                                      const uint8_t* layer, const orc_cuts* cuts, double bfield,
                                      int n_pairs, const int* pin, const int* pout,
-                                     const uint8_t* link_keep, int64_t n_keep);
+                                     const uint8_t* link_keep, int64_t n_keep, int fishbone_on);
+orc_result* orc_reconstruct_ex(int64_t n, const float* x, const float* y, const float* z,
+                               const uint8_t* layer, const orc_cuts* cuts, double bfield,
+                               int n_pairs, const int32_t* pin, const int32_t* pout,
+                               const uint8_t* link_keep, int64_t n_keep, int fishbone_on);
 
 orc_result* orc_reconstruct(int64_t n, const float* x, const float* y, const float* z,
                             const uint8_t* layer, const orc_cuts* cuts, double bfield) {
   return reconstruct_pairs(n, x, y, z, layer, cuts, bfield, ORC_N_PAIRS, PAIR_IN, PAIR_OUT,
-                           NULL, 0);
+                           NULL, 0, 0);
 }
 
 orc_result* orc_reconstruct_masked(int64_t n, const float* x, const float* y, const float* z,
                                    const uint8_t* layer, const orc_cuts* cuts, double bfield,
                                    const uint8_t* link_keep, int64_t n_keep) {
   return reconstruct_pairs(n, x, y, z, layer, cuts, bfield, ORC_N_PAIRS, PAIR_IN, PAIR_OUT,
-                           link_keep, n_keep);
+                           link_keep, n_keep, 0);
 }
 
 /* The chain over a caller's layer-pair table (at most ORC_MAX_PAIRS distinct pairs of
@@ -402,7 +482,22 @@ orc_result* orc_reconstruct_masked(int64_t n, const float* x, const float* y, co
 orc_result* orc_reconstruct_pairs(int64_t n, const float* x, const float* y, const float* z,
                                   const uint8_t* layer, const orc_cuts* cuts, double bfield,
                                   int n_pairs, const int32_t* pin, const int32_t* pout) {
+  if (n_pairs < 1) return NULL;
+  return orc_reconstruct_ex(n, x, y, z, layer, cuts, bfield, n_pairs, pin, pout, NULL, 0, 0);
+}
+
+/* The general entry: a layer-pair table (n_pairs = 0: the default table), an optional
+ * link mask (as orc_reconstruct_masked) and fishbone_on (the fishbone step after the
+ * links, applied to the links the mask keeps). */
+orc_result* orc_reconstruct_ex(int64_t n, const float* x, const float* y, const float* z,
+                               const uint8_t* layer, const orc_cuts* cuts, double bfield,
+                               int n_pairs, const int32_t* pin, const int32_t* pout,
+                               const uint8_t* link_keep, int64_t n_keep, int fishbone_on) {
   int ti[ORC_MAX_PAIRS], to[ORC_MAX_PAIRS];
+  if (n_pairs == 0) {
+    return reconstruct_pairs(n, x, y, z, layer, cuts, bfield, ORC_N_PAIRS, PAIR_IN, PAIR_OUT,
+                             link_keep, n_keep, fishbone_on);
+  }
   if (n_pairs < 1 || n_pairs > ORC_MAX_PAIRS) return NULL;
   for (int p = 0; p < n_pairs; ++p) {
     if (pin[p] < 0 || pin[p] >= ORC_N_LAYERS || pout[p] < 0 || pout[p] >= ORC_N_LAYERS ||
@@ -413,13 +508,14 @@ orc_result* orc_reconstruct_pairs(int64_t n, const float* x, const float* y, con
     ti[p] = pin[p];
     to[p] = pout[p];
   }
-  return reconstruct_pairs(n, x, y, z, layer, cuts, bfield, n_pairs, ti, to, NULL, 0);
+  return reconstruct_pairs(n, x, y, z, layer, cuts, bfield, n_pairs, ti, to, link_keep, n_keep,
+                           fishbone_on);
 }
 
 static orc_result* reconstruct_pairs(int64_t n, const float* x, const float* y, const float* z,
                                      const uint8_t* layer, const orc_cuts* cuts, double bfield,
                                      int n_pairs, const int* pin, const int* pout,
-                                     const uint8_t* link_keep, int64_t n_keep) {
+                                     const uint8_t* link_keep, int64_t n_keep, int fishbone_on) {
   int64_t lidx = 0; /* index among all links accepted by the cuts */
   orc_result* R = (orc_result*)calloc(1, sizeof(orc_result));
   R->n_hits = n;
@@ -490,6 +586,30 @@ static orc_result* reconstruct_pairs(int64_t n, const float* x, const float* y, 
     link_off[a + 1] = (int32_t)R->link_a.n;
   }
   free(out_cnt); free(by_inner); free(fill);
+
+  if (fishbone_on) {
+    /* remove the fishbone's cells with every link from or to them */
+    uint8_t* killed = (uint8_t*)calloc((size_t)(C > 0 ? C : 1), 1);
+    fishbone(n, x, y, z, layer, C, R->cell_in.v, R->cell_out.v, link_off, killed);
+    int64_t w = 0;
+    memset(has_in, 0, (size_t)(C > 0 ? C : 1));
+    for (int64_t a = 0; a < C; ++a) {
+      const int32_t lo = link_off[a], hi = link_off[a + 1];
+      link_off[a] = (int32_t)w;
+      for (int32_t l = lo; l < hi; ++l) {
+        const int32_t b = R->link_b.v[l];
+        if (killed[a] || killed[b]) continue;
+        R->link_a.v[w] = (int32_t)a;
+        R->link_b.v[w] = b;
+        R->link_q.v[w] = R->link_q.v[l];
+        has_in[b] = 1;
+        ++w;
+      }
+    }
+    link_off[C] = (int32_t)w;
+    R->link_a.n = R->link_b.n = R->link_q.n = w;
+    free(killed);
+  }
 
   /* ntuplets: every path from a root (no incoming link) to a leaf (no outgoing link) */
   dfs_ctx d = {link_off, R->link_b.v, R->link_q.v, R->cell_in.v, R->cell_out.v, R};

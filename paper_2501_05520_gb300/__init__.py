@@ -36,7 +36,8 @@ EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt
             "pt_gate_loss_grad", "pt_gate_adam", "pt_server_create", "pt_server_set_gate",
             "pt_submit", "pt_poll", "pt_server_stats", "pt_server_reset_stats",
             "pt_server_destroy", "pt_set_launch", "pt_autotune", "pt_set_tracing",
-            "pt_get_trace", "pt_set_layer_pairs", "pt_set_wait_limit", "pt_server_counters",
+            "pt_get_trace", "pt_set_layer_pairs", "pt_set_wait_limit", "pt_set_fishbone",
+            "pt_server_counters",
             "pt_router_create", "pt_router_set_gate", "pt_router_submit", "pt_router_poll",
             "pt_router_stats", "pt_router_reset_stats", "pt_router_destroy", "pt_last_error")
 
@@ -156,6 +157,7 @@ def lib() -> ctypes.CDLL:
             "pt_set_launch": [P, I32, I32],
             "pt_set_layer_pairs": [P, I32, P, P],
             "pt_set_wait_limit": [P, I64],
+            "pt_set_fishbone": [P, I32],
             "pt_set_tracing": [P, I32],
             "pt_get_trace": [P, P, I32, P],
             "pt_autotune": [ctypes.POINTER(PtGeometry), ctypes.POINTER(PtCuts),
@@ -468,6 +470,10 @@ class Context:
     def pt_set_wait_limit(self, cycles: int = 1 << 31):
         """Limit (SM cycles) of the context's bounded device-side waits."""
         _check(lib().pt_set_wait_limit(self.handle, int(cycles)))
+
+    def pt_set_fishbone(self, on: bool = True):
+        """Fishbone removal of aligned cells sharing an outer hit (off by default)."""
+        _check(lib().pt_set_fishbone(self.handle, 1 if on else 0))
 
     def pt_set_tracing(self, on: bool = True):
         _check(lib().pt_set_tracing(self.handle, 1 if on else 0))

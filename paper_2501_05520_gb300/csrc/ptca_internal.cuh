@@ -154,6 +154,12 @@ struct Buffers {
   uint32_t* cell_out;        // [max_cells]
   uint8_t* has_in;           // [max_cells] an accepted link ends on the cell
   uint8_t* has_out;          // [max_cells] an accepted link starts from the cell
+  uint8_t* fb_kill;          // [max_cells] removed by the fishbone step (zeroed for every
+                             //   cell when the step runs)
+  uint32_t* fb_cnt;          // [max_hits + 1] fishbone: active cells per outer hit
+  uint32_t* fb_start;        // [max_hits + 1]   and their first position in fb_list
+  float4* fb_rec;            // [max_links * 2] active cells grouped by outer hit: vector to
+                             //   the hit and |.|^2; cell, inner hit's input index, layer, sensor
   uint2* link_oc;            // [max_cells] first slot and number of the cell's links
                              //   (valid where it has links)
   unsigned long long* best;  // [max_cells] duplicate-cleaning key (cells on ntuplets)
@@ -258,6 +264,10 @@ void launch_doublets(const Buffers& b, const Params& p, const Launch& l, cudaStr
 // and leaves the in/out flags to the gate (launch_gate)
 void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
                     bool gated = false);
+// Fishbone step and the link filter after it (keep mask and link flags of the ntuplet
+// search); gated: the gate's keep mask is the starting point.
+void launch_fishbone(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
+                     bool gated);
 void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
                      bool gated = false);
 void launch_fit(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);

@@ -183,6 +183,10 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.cell_out = (uint32_t*)take(C * 4);
   t.has_in = (uint8_t*)take(C);
   t.has_out = (uint8_t*)take(C);
+  t.fb_kill = (uint8_t*)take(C);
+  t.fb_cnt = (uint32_t*)take((N + 1) * 4);
+  t.fb_start = (uint32_t*)take((N + 1) * 4);
+  t.fb_rec = (float4*)take(L * 32);
   t.link_oc = (uint2*)take(C * 8);
   t.best = (unsigned long long*)take(C * 8);
   t.link_dst = (uint32_t*)take(L * 4);
@@ -271,6 +275,9 @@ struct pt_ctx {
   // learned gate
   GateWeights* gate = nullptr;  // device, inside the workspace
   bool gate_on = false;
+  bool fishbone_on = false;
+  // the ntuplet search and the link exports follow a keep mask (gate and/or fishbone)
+  bool masked() const { return gate_on || fishbone_on; }
   // raw input: module table and scratch (allocated on first use)
   pt_module* modules = nullptr;
   int n_modules = 0;
@@ -398,7 +405,8 @@ void enqueue_pipeline(pt_ctx* c, cudaStream_t s) {
   launch_doublets(c->B, c->P, L, s);
   launch_connect(c->B, c->P, L, s, c->gate_on);
   if (c->gate_on) launch_gate(c->B, c->P, L, c->gate, s);
-  launch_ntuplets(c->B, c->P, L, s, c->gate_on);
+  if (c->fishbone_on) launch_fishbone(c->B, c->P, L, s, c->gate_on);
+  launch_ntuplets(c->B, c->P, L, s, c->masked());
   launch_fit(c->B, c->P, L, s);
   launch_export_ntuplets(c->B, L, s);
 }
@@ -682,10 +690,12 @@ pt_status pt_build_doublets(pt_ctx* c, int64_t* n_cells) {
 }
 
 pt_status pt_connect_cells(pt_ctx* c, int64_t* n_links) {
-  if (c && c->gate_on) {
+  if (c && c->masked()) {
     STAGE_BODY((reset_counters(c, {CNT_LINKS, CNT_LINKS_USED, CNT_GATE_KEPT}),
-                launch_connect(c->B, c->P, c->L, c->stream, true),
-                launch_gate(c->B, c->P, c->L, c->gate, c->stream)),
+                launch_connect(c->B, c->P, c->L, c->stream, c->gate_on),
+                c->gate_on ? launch_gate(c->B, c->P, c->L, c->gate, c->stream) : (void)0,
+                c->fishbone_on ? launch_fishbone(c->B, c->P, c->L, c->stream, c->gate_on)
+                               : (void)0),
                CNT_GATE_KEPT, n_links)
   }
   STAGE_BODY((reset_counters(c, {CNT_LINKS, CNT_LINKS_USED, CNT_GATE_KEPT}),
@@ -697,7 +707,7 @@ pt_status pt_find_ntuplets(pt_ctx* c, int64_t* n_ntuplets) {
   STAGE_BODY((reset_counters(c, {CNT_NT, CNT_SCAN_NT, CNT_SV}),
               cudaMemsetAsync(c->B.bucket_cnt, 0, (size_t)(loaded_hits(c) + 1) * 4, c->stream),
               cudaMemsetAsync(c->B.used, 0, (size_t)loaded_hits(c), c->stream),
-              launch_ntuplets(c->B, c->P, c->L, c->stream, c->gate_on)),
+              launch_ntuplets(c->B, c->P, c->L, c->stream, c->masked())),
              CNT_SV, n_ntuplets)
 }
 
@@ -956,7 +966,7 @@ pt_status pt_get_links(pt_ctx* c, int32_t* h0, int32_t* h1, int32_t* h2, float* 
   PT_TRY(need_loaded(c));
   DeviceGuard guard(c->device);
   PT_TRY(sync_counters(c));
-  const int64_t Lk = c->gate_on ? (int64_t)c->h_cnt[CNT_GATE_KEPT] : (int64_t)c->h_cnt[CNT_LINKS_USED];
+  const int64_t Lk = c->masked() ? (int64_t)c->h_cnt[CNT_GATE_KEPT] : (int64_t)c->h_cnt[CNT_LINKS_USED];
   int64_t slots = (int64_t)c->h_cnt[CNT_LINKS];
   if (slots > c->cap.max_links) slots = c->cap.max_links;
   if (n) *n = Lk;
@@ -967,7 +977,7 @@ pt_status pt_get_links(pt_ctx* c, int32_t* h0, int32_t* h1, int32_t* h2, float* 
   int32_t* o4 = (int32_t*)c->val;
   float* oq = (float*)(c->val + (size_t)slots * 16);
   PT_CUDA(cudaMemsetAsync(o4, 0xff, (size_t)slots * 16, c->stream));
-  launch_export_links(c->B, c->P, c->L, o4, oq, c->stream, c->gate_on);
+  launch_export_links(c->B, c->P, c->L, o4, oq, c->stream, c->masked());
   PT_TRY(last_launch());
   std::vector<int32_t> tmp((size_t)slots * 4);
   std::vector<float> tq((size_t)slots);
@@ -1056,13 +1066,27 @@ pt_status pt_set_gate(pt_ctx* c, const float* w, float tau) {
   return PT_OK;
 }
 
+pt_status pt_set_fishbone(pt_ctx* c, int on) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  if (on != 0 && on != 1) return fail(PT_ERR_INVALID, "on must be 0 or 1");
+  DeviceGuard guard(c->device);
+  PT_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->fishbone_on = on == 1;
+  return PT_OK;
+}
+
 pt_status pt_get_link_features(pt_ctx* c, float* feat, int32_t* h0, int32_t* h1, int32_t* h2,
                                int32_t* event, float* score, int64_t cap, int64_t* n) {
   g_err.clear();
   PT_TRY(need_loaded(c));
   DeviceGuard guard(c->device);
   PT_TRY(sync_counters(c));
-  const int64_t Lk = c->gate_on ? (int64_t)c->h_cnt[CNT_GATE_KEPT] : (int64_t)c->h_cnt[CNT_LINKS_USED];
+  const int64_t Lk = c->masked() ? (int64_t)c->h_cnt[CNT_GATE_KEPT] : (int64_t)c->h_cnt[CNT_LINKS_USED];
   int64_t slots = (int64_t)c->h_cnt[CNT_LINKS];
   if (slots > c->cap.max_links) slots = c->cap.max_links;
   if (n) *n = Lk;
@@ -1074,8 +1098,8 @@ pt_status pt_get_link_features(pt_ctx* c, float* feat, int32_t* h0, int32_t* h1,
   float* oq = (float*)(c->val + (size_t)slots * 16);
   float* of = (float*)(c->val + (size_t)slots * 20);
   PT_CUDA(cudaMemsetAsync(o4, 0xff, (size_t)slots * 16, c->stream));
-  launch_export_links(c->B, c->P, c->L, o4, oq, c->stream, c->gate_on);
-  launch_export_link_features(c->B, c->P, c->L, c->gate_on, of, c->stream);
+  launch_export_links(c->B, c->P, c->L, o4, oq, c->stream, c->masked());
+  launch_export_link_features(c->B, c->P, c->L, c->masked(), of, c->stream);
   PT_TRY(last_launch());
   std::vector<int32_t> t4((size_t)slots * 4);
   std::vector<float> tf((size_t)slots * 12), ts((size_t)slots);

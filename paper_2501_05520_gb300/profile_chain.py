@@ -7,7 +7,8 @@ the GPU, and prints the per-kernel times of the last repetition.  A kernel's n-t
 launch is its (n-1)-th repetition.
 
   python -m paper_2501_05520_gb300.profile_chain --events 8 --reps 3 [--gated]
-         [--extra] [--phi-bins 2048] [--blocks-per-sm 8] [--search-blocks-per-sm 8]
+         [--fishbone] [--overlap 0.2] [--extra] [--phi-bins 2048] [--blocks-per-sm 8]
+         [--search-blocks-per-sm 8]
 """
 
 from __future__ import annotations
@@ -23,6 +24,9 @@ def main(argv=None) -> int:
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed0", type=int, default=3000)
     ap.add_argument("--gated", action="store_true")
+    ap.add_argument("--fishbone", action="store_true")
+    ap.add_argument("--overlap", type=float, default=0.0,
+                    help="fraction of crossings that also cross an overlapping sensor")
     ap.add_argument("--extra", action="store_true",
                     help="also run the refit, the vertices and raw data -> hits")
     ap.add_argument("--phi-bins", type=int, default=2048)
@@ -38,17 +42,21 @@ def main(argv=None) -> int:
     import paper_2501_05520_gb300 as pt
     import sim
 
-    events = [sim.generate(sim.PU200, a.seed0 + i) for i in range(a.events)]
+    import dataclasses
+    cfg = dataclasses.replace(sim.PU200, overlap=a.overlap)
+    events = [sim.generate(cfg, a.seed0 + i) for i in range(a.events)]
     off, x, y, z, layer = sim.concat(events)
     dev = torch.device("cuda", 0)
     d = [torch.from_numpy(v).to(dev) for v in (x, y, z, layer)]
-    cap = pt.default_capacity(max_events=a.events, hits_per_event=49152,
-                              cells_per_event=3_500_000, links_per_event=262_144,
+    cap = pt.default_capacity(max_events=a.events, hits_per_event=65536,
+                              cells_per_event=6_000_000 if a.overlap > 0 else 3_500_000, links_per_event=262_144,
                               ntuplets_per_event=196_608, phi_bins=a.phi_bins)
     with pt.Context(capacity=cap, device=0) as ctx:
         ctx.pt_set_launch(a.blocks_per_sm, a.search_blocks_per_sm)
         if a.gated:
             ctx.pt_set_gate(*pt.default_gate())
+        if a.fishbone:
+            ctx.pt_set_fishbone(True)
         raw = None
         if a.extra:
             from sim import pixels

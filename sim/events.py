@@ -18,6 +18,11 @@ Detector (layer codes are part of the library's input contract):
   4..6  disks at z = +29.1 / +39.6 / +51.6 cm, 4.5 <= r <= 16 cm
   7..9  disks at z = -29.1 / -39.6 / -51.6 cm, same radial extent
 
+Overlapping sensors (off unless a configuration gives `overlap`): a crossing falls in the
+overlap of two neighbouring sensors of its layer with probability `overlap`, and the
+particle then also crosses the second sensor, which sits OVERLAP_DR further out (barrel)
+or OVERLAP_DZ further from z = 0 (disks), leaving a second hit with the same layer code.
+
 The paper's workloads are CMS HLT data and ACTS ttbar events at pileup 200
 (Sec. 2.2.2); neither is available, so these helices stand in for them.
 """
@@ -37,6 +42,9 @@ DISK_Z = (29.1, 39.6, 51.6)
 DISK_RMIN = 4.5
 DISK_RMAX = 16.0
 N_LAYERS = 10
+
+OVERLAP_DR = 0.5    # cm, radial offset of a barrel layer's overlapping sensors
+OVERLAP_DZ = 0.5    # cm, z offset of a disk's overlapping sensors
 
 SIGMA_RPHI = 10e-4  # 10 um
 SIGMA_Z = 20e-4     # 20 um (barrel z, disk r)
@@ -95,6 +103,7 @@ class GenConfig:
     x0_barrel: float = 0.0  # radiation lengths per barrel layer (0: no scattering)
     x0_disk: float = 0.0    # radiation lengths per disk
     hit_eff: float = 1.0    # probability that a crossing gives a hit (1: every crossing)
+    overlap: float = 0.0    # probability that a crossing also crosses an overlapping sensor
 
 
 # The five workloads.  Sizes and spectra follow the library's benchmark definitions.
@@ -156,6 +165,35 @@ def _crossings(p: dict, barrel_only: bool):
     y = np.concatenate([o[3] for o in out])
     z = np.concatenate([o[4] for o in out])
     return pid, lay, x, y, z
+
+
+def _overlap_crossings(p: dict, pid, lay):
+    """Noiseless crossings of the overlapping sensors behind the given crossings
+    (pid, layer): barrel radius + OVERLAP_DR, disk |z| + OVERLAP_DZ.  Returns
+    (pid, layer, x, y, z) of those that lie inside the sensor's acceptance."""
+    R, z0, q = p["R"][pid], p["z0"][pid], p["q"][pid]
+    sh, phi0 = np.sinh(p["eta"][pid]), p["phi0"][pid]
+    barrel = lay < 4
+    rl = np.asarray(BARREL_R + (0.0,) * 6)[lay] + OVERLAP_DR
+    ok_b = barrel & (rl < 2.0 * R)
+    alpha_b = 2.0 * np.arcsin(np.where(ok_b, rl / (2.0 * R), 0.0))
+    zb = z0 + R * alpha_b * sh
+    ok_b &= np.abs(zb) < BARREL_ZMAX
+    side = np.where(lay < 7, 1.0, -1.0)
+    zd = side * (np.asarray((0.0,) * 4 + DISK_Z + DISK_Z)[lay] + OVERLAP_DZ)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s_d = (zd - z0) / sh
+    alpha_d = np.where(np.isfinite(s_d), s_d / R, -1.0)
+    ok_d = ~barrel & np.isfinite(s_d) & (s_d > 0) & (alpha_d < np.pi)
+    rd = 2.0 * R * np.sin(np.where(ok_d, alpha_d, 0.0) / 2.0)
+    ok_d &= (rd >= DISK_RMIN) & (rd <= DISK_RMAX)
+    alpha = np.where(barrel, alpha_b, alpha_d)
+    r = np.where(barrel, rl, rd)
+    z = np.where(barrel, zb, zd)
+    phi = phi0 - q * alpha / 2.0
+    keep = ok_b | ok_d
+    return (pid[keep], lay[keep], r[keep] * np.cos(phi[keep]), r[keep] * np.sin(phi[keep]),
+            z[keep])
 
 
 def highland(p, t):
@@ -340,6 +378,12 @@ def generate(cfg: GenConfig, seed: int, n_particles: int | None = None,
                                                 cfg.x0_disk)
     else:
         pid, lay, xt, yt, zt = _crossings(p, cfg.barrel_only)
+    if cfg.overlap > 0.0:
+        if cfg.x0_barrel > 0.0 or cfg.x0_disk > 0.0:
+            raise ValueError("overlapping sensors are modelled without material only")
+        sel = rng.random(pid.shape[0]) < cfg.overlap
+        o = _overlap_crossings(p, pid[sel], lay[sel])
+        pid, lay, xt, yt, zt = (np.concatenate([a, b]) for a, b in zip((pid, lay, xt, yt, zt), o))
     if cfg.hit_eff < 1.0:  # inefficient sensors: each crossing kept independently
         keep = rng.random(pid.shape[0]) < cfg.hit_eff
         pid, lay, xt, yt, zt = pid[keep], lay[keep], xt[keep], yt[keep], zt[keep]
