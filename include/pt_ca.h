@@ -47,7 +47,9 @@ typedef enum {
   PT_ERR_CUDA = 3,      /* a CUDA runtime call failed; message has the CUDA error string */
   PT_ERR_TIMEOUT = 4,   /* a bounded wait expired (pt_poll) */
   PT_ERR_NOT_READY = 5, /* result not ready yet (pt_poll with timeout 0) */
-  PT_ERR_NOMEM = 6      /* device or host allocation failed, or the budget is exhausted */
+  PT_ERR_NOMEM = 6,     /* device or host allocation failed, or the budget is exhausted */
+  PT_ERR_INTERNAL = 7   /* debug build only: a device-side bounds check failed (a library
+                         * fault, reported instead of made; the message names the check) */
 } pt_status;
 
 typedef struct pt_ctx pt_ctx;
@@ -431,6 +433,20 @@ pt_status pt_set_layer_pairs(pt_ctx* ctx, int n_pairs, const int32_t* inner, con
  * otherwise.  Synchronises the stream; the next whole-batch call re-captures its
  * graph. */
 pt_status pt_set_fishbone(pt_ctx* ctx, int on);
+
+/* 1 when this library is the debug build (libptca_debug.so, compiled with PT_DEBUG):
+ * its kernels check the indexes of their main array accesses against the sizes they
+ * hold, and a failing check sets a status bit and skips the access; the next call that
+ * reads the device counters then returns PT_ERR_INTERNAL naming the first failing
+ * check.  0 for the normal build, whose kernels carry no checks.  Touches no GPU. */
+int pt_debug_build(void);
+
+/* Debug build only: records a failure of bounds check `site` (1..13) on the context's
+ * stream the way a failing check does, touching no array, so that the reporting path can
+ * be tested: the next call that reads the device counters returns PT_ERR_INTERNAL
+ * naming the site, until the next pt_load_hits / pt_load_batch clears the status.
+ * PT_ERR_INVALID in the normal build, for a NULL context or a site out of range. */
+pt_status pt_debug_inject(pt_ctx* ctx, int site);
 
 /* Limit, in SM clock cycles (>= 1; default 2^31, about 1 s at 2 GHz), of the context's
  * bounded device-side waits: the learned gate's waits for its tensor-core results

@@ -17,12 +17,15 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "lib", "libptca.so")
+# PT_DEBUG=1 in the environment selects the debug build (bounds-checked kernels,
+# build.build(debug=True)).
+LIB_PATH = os.path.join(_PKG, "lib", "libptca_debug.so" if os.environ.get("PT_DEBUG") == "1"
+                        else "libptca.so")
 CUTS_FILE = os.path.join(_PKG, "params", "cuts_v1.json")
 _lib = None
 
 PT_OK, PT_ERR_INVALID, PT_ERR_CAPACITY, PT_ERR_CUDA, PT_ERR_TIMEOUT, PT_ERR_NOT_READY, \
-    PT_ERR_NOMEM = range(7)
+    PT_ERR_NOMEM, PT_ERR_INTERNAL = range(8)
 
 # Every symbol include/pt_ca.h declares.
 EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt_load_hits",
@@ -36,7 +39,8 @@ EXPORTED = ("pt_workspace_size", "pt_create", "pt_destroy", "pt_set_stream", "pt
             "pt_gate_loss_grad", "pt_gate_adam", "pt_server_create", "pt_server_set_gate",
             "pt_submit", "pt_poll", "pt_server_stats", "pt_server_reset_stats",
             "pt_server_destroy", "pt_set_launch", "pt_autotune", "pt_set_tracing",
-            "pt_get_trace", "pt_set_layer_pairs", "pt_set_wait_limit", "pt_set_fishbone",
+            "pt_get_trace", "pt_set_layer_pairs", "pt_set_wait_limit", "pt_set_fishbone", "pt_debug_build",
+            "pt_debug_inject",
             "pt_server_counters",
             "pt_router_create", "pt_router_set_gate", "pt_router_submit", "pt_router_poll",
             "pt_router_stats", "pt_router_reset_stats", "pt_router_destroy", "pt_last_error")
@@ -158,6 +162,8 @@ def lib() -> ctypes.CDLL:
             "pt_set_layer_pairs": [P, I32, P, P],
             "pt_set_wait_limit": [P, I64],
             "pt_set_fishbone": [P, I32],
+            "pt_debug_build": [],
+            "pt_debug_inject": [P, I32],
             "pt_set_tracing": [P, I32],
             "pt_get_trace": [P, P, I32, P],
             "pt_autotune": [ctypes.POINTER(PtGeometry), ctypes.POINTER(PtCuts),
@@ -474,6 +480,10 @@ class Context:
     def pt_set_fishbone(self, on: bool = True):
         """Fishbone removal of aligned cells sharing an outer hit (off by default)."""
         _check(lib().pt_set_fishbone(self.handle, 1 if on else 0))
+
+    def pt_debug_inject(self, site: int):
+        """Debug build only: record a failure of bounds check `site` (reporting test)."""
+        _check(lib().pt_debug_inject(self.handle, int(site)))
 
     def pt_set_tracing(self, on: bool = True):
         _check(lib().pt_set_tracing(self.handle, 1 if on else 0))

@@ -20,6 +20,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libptca.so")
+# The debug build: the same sources compiled with PT_DEBUG (device-side bounds checks
+# that report a failing index through a status bit instead of making the access).
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(LIBDIR, "libptca_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
@@ -41,24 +45,31 @@ def _deps() -> list[str]:
             + glob.glob(os.path.join(PKG, "tools", "*.cpp")))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB) or not os.path.exists(os.path.join(LIBDIR, "serve_load")):
+def up_to_date(debug: bool = False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    if not debug and not os.path.exists(os.path.join(LIBDIR, "serve_load")):
+        return False
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Build libptca.so; returns its path.  Raises CalledProcessError on compile errors."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          debug: bool = False) -> str:
+    """Build libptca.so (debug: libptca_debug.so, compiled with PT_DEBUG); returns its
+    path.  Raises RuntimeError on compile errors."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and up_to_date(debug):
+        return lib
+    bdir = BUILD_DEBUG if debug else BUILD
+    os.makedirs(bdir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     nvcc = _nvcc()
-    flags = NVCC_FLAGS + (extra_flags or [])
+    flags = NVCC_FLAGS + (["-DPT_DEBUG"] if debug else []) + (extra_flags or [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
@@ -73,11 +84,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             objs = list(ex.map(compile_one, srcs))
         except subprocess.CalledProcessError as e:
             raise RuntimeError(f"nvcc failed:\n{' '.join(e.cmd)}\n{e.stdout}\n{e.stderr}") from None
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
-    os.replace(tmp, LIB)
-    build_tools()
-    return LIB
+    os.replace(tmp, lib)
+    if not debug:
+        build_tools()
+    return lib
 
 
 TOOLS = os.path.join(PKG, "tools")
@@ -98,4 +110,4 @@ def build_tools() -> str:
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

@@ -29,6 +29,7 @@ __global__ void k_clear(Buffers b, int32_t phi_bins) {
     b.cnt[CNT_LINKS] = 0;
     b.cnt[CNT_NT] = 0;
     b.cnt[CNT_STATUS] = 0;
+    b.cnt[CNT_DEBUG_SITE] = 0;
     b.cnt[CNT_GATE_KEPT] = 0;
     b.cnt[CNT_SCAN_NT] = 0;
     b.cnt[CNT_SV] = 0;
@@ -98,6 +99,7 @@ __global__ void k_bin_scatter(Buffers b, float kmax) {
     const uint32_t gb = b.in_bin[g];
     if (gb == 0xffffffffu) continue;
     const uint32_t s = b.bin_start[gb] + b.in_rank[g];
+    if (!PT_CHECK(b.cnt, s < (uint32_t)N, DBG_BIN_SCATTER)) continue;
     const float x = b.in_x[g], y = b.in_y[g], z = b.in_z[g];
     b.hit4[s] = make_float4(x, y, z, hit_radius(x, y));
     b.perm[s] = (uint32_t)g;
@@ -190,6 +192,19 @@ void launch_bin_hits(const Buffers& b, const Params& p, const Launch& l, cudaStr
   PT_TRACE(l, s, "k_bin_count", k_bin_count<<<l.grid, 256, 0, s>>>(b, p.phi_bins));
   PT_TRACE(l, s, "scan", launch_scan(b.bin_cnt, b.bin_start, &b.cnt[CNT_SCAN_BINS], b.scan_part, s));
   PT_TRACE(l, s, "k_bin_scatter", k_bin_scatter<<<l.grid, 256, 0, s>>>(b, p.cuts.kmax));
+}
+
+namespace {
+__global__ void k_debug_inject(Buffers b, unsigned site) {
+#ifdef PT_DEBUG
+  debug_fail(b.cnt, site);
+#endif
+}
+}  // namespace
+
+cudaError_t launch_debug_inject(const Buffers& b, unsigned site, cudaStream_t s) {
+  k_debug_inject<<<1, 1, 0, s>>>(b, site);
+  return cudaGetLastError();
 }
 
 }  // namespace ptca

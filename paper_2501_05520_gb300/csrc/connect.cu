@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
     for (unsigned long long i = lo + lane; i < hi; i += 32) b.link_src[i] = kHole;
   };
   auto write_link = [&](uint64_t slot, uint32_t a, uint32_t t, float q) {
+    if (!PT_CHECK(b.cnt, slot < cap_links, DBG_CON_LINK)) return;
     b.link_src[slot] = a;
     b.link_dst[slot] = t;  // outer hit | slot << 29, made a cell id by k_link_targets
     b.link_q[slot] = q;
@@ -232,9 +233,14 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
         if (lane == kMaxInner) W.sb[kMaxInner] = inc;
       }
       // forward windows, one outer slot per lane
-      if (lane < kMaxOuter)
-        W.rg[lane] = forward_window(b, pt, B, bins_per_rad, gb, p1,
-                                    asinf(0.5f * cuts.kmax * p1.w), lane);
+      if (lane < kMaxOuter) {
+        uint4 rg = forward_window(b, pt, B, bins_per_rad, gb, p1, asinf(0.5f * cuts.kmax * p1.w),
+                                  lane);
+        if (!PT_CHECK(b.cnt, rg.x <= rg.y && rg.y <= n_sorted && rg.z <= rg.w && rg.w <= n_sorted,
+                      DBG_CON_WINDOW))
+          rg = make_uint4(0u, 0u, 0u, 0u);
+        W.rg[lane] = rg;
+      }
       if (lane == 0) {
         W.p1 = p1;
         W.piece = -1;
@@ -359,7 +365,9 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
       float4 p0_next = make_float4(0.f, 0.f, 0.f, 0.f);
       if ((uint32_t)lane < nin) {
         int kin;
-        p0_next = b.hit4[b.cell_in[incoming(lane, kin)]];
+        const uint32_t c0 = incoming(lane, kin);
+        if (PT_CHECK(b.cnt, c0 < b.cnt[CNT_CELLS], DBG_CON_INCOMING))
+          p0_next = b.hit4[b.cell_in[c0]];
       }
       const uint32_t nout = stage_piece(0);
       if (nout == 0) continue;
@@ -369,16 +377,20 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
       for (uint32_t g0 = 0; g0 < nin; g0 += 32) {
         // the lane's incoming cell
         const uint32_t i = g0 + lane;
-        const bool valid = i < nin;
+        bool valid = i < nin;
         uint32_t c = 0;
         int kin = 0;
-        if (valid) c = incoming(i, kin);
+        if (valid) {
+          c = incoming(i, kin);
+          valid = PT_CHECK(b.cnt, c < b.cnt[CNT_CELLS], DBG_CON_INCOMING);
+        }
         const float4 p0 = p0_next;
         uint32_t h0_next = 0;
         const bool valid_next = i + 32 < nin;
         if (valid_next) {
           int kn;
-          h0_next = b.cell_in[incoming(i + 32, kn)];
+          const uint32_t cn = incoming(i + 32, kn);
+          if (PT_CHECK(b.cnt, cn < b.cnt[CNT_CELLS], DBG_CON_INCOMING)) h0_next = b.cell_in[cn];
         }
         const bool first_b0 = valid && pt.inner[L1][kin] == 0;
         const float ta = __fdividef(p1.z - p0.z, p1.w - p0.w);  // the cell's slope dz/dr
@@ -410,6 +422,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
               const float w2 = w * 1.001f + 1e-5f;
               pos = W.bstart[slope_bucket(__fsub_rn(ta, w2), tmin, scale)];
               pend = W.bstart[slope_bucket(__fadd_rn(ta, w2), tmin, scale) + 1];
+              if (!PT_CHECK(b.cnt, pos <= pend && pend <= (uint32_t)kOut, DBG_CON_BUCKET))
+                pend = pos;
             }
             uint32_t head = 0, tail = 0;
             // C1, C2 and C3 on up to 32 queued pairs, all lanes busy
@@ -461,6 +475,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
                 ++pos;
               }
               const unsigned bal = __ballot_sync(kFull, pass);
+              PT_CHECK(b.cnt, tail + __popc(bal) - head <= (uint32_t)kQueue, DBG_CON_QUEUE);
               if (pass) W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2((uint32_t)lane, e);
               tail += __popc(bal);
               if (tail - head >= 32u) process(32u);
@@ -523,7 +538,9 @@ __global__ void k_link_targets(Buffers b, pt_cuts cuts, int32_t B, int max_inner
     if (a == kHole) continue;
     const uint32_t t = b.link_dst[l];
     const uint32_t h1 = b.cell_out[a];
-    const uint2 sg = b.seg[(uint64_t)(t & 0x1fffffffu) * max_inner + (t >> 29)];
+    uint2 sg = b.seg[(uint64_t)(t & 0x1fffffffu) * max_inner + (t >> 29)];
+    if (!PT_CHECK(b.cnt, (uint64_t)sg.x + sg.y <= b.cnt[CNT_CELLS], DBG_TGT_SEGMENT))
+      sg = make_uint2(0u, 0u);
     uint32_t lo = sg.x, hi = sg.x + sg.y;
     while (lo < hi) {
       const uint32_t mid = (lo + hi) >> 1;

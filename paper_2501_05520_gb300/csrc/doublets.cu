@@ -116,8 +116,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
       const float a = 0.5f * cuts.kmax * ho.w;
       const float asin_o = a >= 0.7f ? __int_as_float(0x7f800000) : asinf(a);
       st_hit[wib][lane] = ho;
-      for (int k = 0; k < pt.max_inner; ++k)
-        st_rng[wib][lane][k] = reverse_window(b, pt, B, bins_per_rad, gb, ho, asin_o, k);
+      for (int k = 0; k < pt.max_inner; ++k) {
+        uint4 rg = reverse_window(b, pt, B, bins_per_rad, gb, ho, asin_o, k);
+        if (!PT_CHECK(b.cnt, rg.x <= rg.y && rg.y <= n_sorted && rg.z <= rg.w && rg.w <= n_sorted,
+                      DBG_DBL_WINDOW))
+          rg = make_uint4(0u, 0u, 0u, 0u);
+        st_rng[wib][lane][k] = rg;
+      }
     }
     __syncwarp();
 
@@ -163,7 +168,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
             mark_hole(base, base + cnt);  // slots below the capacity stay readable
           } else if (cnt <= (uint32_t)kStage) {
             __syncwarp();
-            for (uint32_t i = lane; i < cnt; i += 32) write_cell(b, base + i, sval[i], s);
+            for (uint32_t i = lane; i < cnt; i += 32)
+              if (PT_CHECK(b.cnt, base + i < cap_cells, DBG_DBL_CELL))
+                write_cell(b, base + i, sval[i], s);
             seg_off = (uint32_t)base;
             seg_cnt = cnt;
           } else {
@@ -175,7 +182,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
                 const uint32_t i = i0 + lane;
                 const bool pass = i < end && doublet_pass(cuts, b.hit4[i], ho);
                 const unsigned bal = __ballot_sync(kFull, pass);
-                if (pass) write_cell(b, base + pos0 + __popc(bal & lt_mask), i, s);
+                if (pass && PT_CHECK(b.cnt, base + pos0 + __popc(bal & lt_mask) < cap_cells,
+                                     DBG_DBL_CELL))
+                  write_cell(b, base + pos0 + __popc(bal & lt_mask), i, s);
                 pos0 += __popc(bal);
               }
             }

@@ -97,6 +97,7 @@ __global__ void k_fb_scatter(Buffers b, int32_t B, uint64_t cap_links, bool gate
     if (a == kHole) continue;
     const uint32_t h = b.cell_out[a];
     const uint32_t pos = b.fb_start[h] + atomicSub(&b.fb_cnt[h], 1u) - 1u;
+    if (!PT_CHECK(b.cnt, pos < cap_links, DBG_FB_RECORD)) continue;
     reinterpret_cast<FbCell*>(b.fb_rec)[pos] = fb_cell(b, b.hit4[h], a, B);
   }
 }

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(256) k_fit(Buffers b, float bfield) {
     if (active) {
       t = b.ord[b.sv[j]];
       n = b.nt_n[t];
+      if (!PT_CHECK(b.cnt, n >= 3 && n <= kMaxHits, DBG_FIT_HITS)) n = 3;
       if (sub < n) {
         const int32_t g = b.nt_hits[(uint64_t)t * kMaxHits + sub];
         x = b.in_x[g];

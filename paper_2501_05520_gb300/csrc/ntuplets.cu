@@ -79,6 +79,7 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
     if (depth == kMaxCellsPerNt) continue;  // deeper than the layer graph allows
     if (GATED && !b.gate_keep[l]) continue;  // removed by the learned gate
     const uint32_t c = b.link_dst[l];
+    if (!PT_CHECK(b.cnt, c < b.cnt[CNT_CELLS], DBG_NT_CELL)) continue;
     const float q = fadd(qs[d], b.link_q[l]);
     // everything c may need is loaded at once: its flag, its link list (stale and
     // unused when c has no links) and its outer hit
@@ -129,7 +130,8 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
     }
     path[depth] = c;
     it[depth] = oc.x;
-    end[depth] = oc.x + oc.y;
+    end[depth] = PT_CHECK(b.cnt, (uint64_t)oc.x + oc.y <= b.cnt[CNT_LINKS], DBG_NT_LINKS)
+                     ? oc.x + oc.y : oc.x;
     qs[depth] = q;
     if (EMIT) gh[depth] = gc;
     ++depth;

@@ -48,6 +48,7 @@ enum : int {
   CNT_RAW_HITS = 18,    // raw input: hits made from the digis
   CNT_RAW_BIG = 19,     // raw input: long module runs listed for the block-per-run launch
   CNT_LNK_WORK = 20,    // link search: next chunk of 32 sorted middle hits
+  CNT_DEBUG_SITE = 22,  // debug build: the first failing bounds check (DebugSite)
   CNT_N = 24
 };
 // raw-input status bits (cnt[CNT_RAW_STATUS])
@@ -65,6 +66,24 @@ enum : unsigned long long {
   ST_LAYER = 8ull,
   ST_GATE_TIMEOUT = 16ull,  // a bounded wait in the gate kernel expired
   ST_VTX = 32ull,           // an event has more tracks for vertexing than a block sorts
+  ST_DEBUG = 64ull,         // a bounds check of the debug build failed (cnt[CNT_DEBUG_SITE])
+};
+
+// Sites of the debug build's bounds checks (the first one that fails is recorded).
+enum DebugSite : unsigned {
+  DBG_BIN_SCATTER = 1,   // sorted position of a hit < hits
+  DBG_DBL_WINDOW = 2,    // a doublet window inside the sorted hits
+  DBG_DBL_CELL = 3,      // a cell slot < max_cells
+  DBG_CON_WINDOW = 4,    // a forward window inside the sorted hits
+  DBG_CON_INCOMING = 5,  // an incoming cell id < cell slots
+  DBG_CON_BUCKET = 6,    // a bucket range inside the staged piece
+  DBG_CON_QUEUE = 7,     // queued pairs <= queue size
+  DBG_CON_LINK = 8,      // a link slot < max_links
+  DBG_TGT_SEGMENT = 9,   // a target's incoming segment inside the cell slots
+  DBG_NT_LINKS = 10,     // a cell's link run inside the link slots
+  DBG_NT_CELL = 11,      // a link target < cell slots
+  DBG_FIT_HITS = 12,     // 3..6 hits per fitted ntuplet
+  DBG_FB_RECORD = 13,    // a fishbone record position < max_links
 };
 
 // Gate parameters on the device: W1 and W2 as bf16 in the tensor-core operand layout,
@@ -268,6 +287,8 @@ void launch_connect(const Buffers& b, const Params& p, const Launch& l, cudaStre
 // search); gated: the gate's keep mask is the starting point.
 void launch_fishbone(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
                      bool gated);
+// Debug build: records a failure of bounds check `site` as a failing check does.
+cudaError_t launch_debug_inject(const Buffers& b, unsigned site, cudaStream_t s);
 void launch_ntuplets(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s,
                      bool gated = false);
 void launch_fit(const Buffers& b, const Params& p, const Launch& l, cudaStream_t s);
@@ -371,6 +392,20 @@ __device__ __forceinline__ bool link_c23(const pt_cuts& c, float4 p0, bool first
 }
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Bounds checks of the debug build (compiled with -DPT_DEBUG, libptca_debug.so): a
+// failing check sets the status bit ST_DEBUG and records the first failing site, and the
+// access it guards is skipped, so that the kernel reports the fault instead of making
+// it.  In the normal build every check is the constant true and costs nothing.
+#ifdef PT_DEBUG
+__device__ __noinline__ inline void debug_fail(unsigned long long* cnt, unsigned site) {
+  atomicOr(&cnt[CNT_STATUS], ST_DEBUG);
+  atomicCAS(&cnt[CNT_DEBUG_SITE], 0ull, (unsigned long long)site);
+}
+#define PT_CHECK(cnt, cond, site) ((cond) ? true : (::ptca::debug_fail((cnt), (site)), false))
+#else
+#define PT_CHECK(cnt, cond, site) true
+#endif
 
 // Learned-gate features of link (h0 -> h1 -> h2) from the hit coordinates (x, y, z, r)
 // and layers: C1, C2, C3 cut ratios, t_a/cotmax, 10 (t_b - t_a), r0/16, r1/16, r2/16,

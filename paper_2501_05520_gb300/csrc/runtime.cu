@@ -319,6 +319,9 @@ pt_status sync_counters(pt_ctx* c) {
 // Status bits of the host copy of the counters -> error.
 pt_status check_status(pt_ctx* c) {
   const unsigned long long st = c->h_cnt[CNT_STATUS];
+  if (st & ST_DEBUG)
+    return fail(PT_ERR_INTERNAL, "debug build: device bounds check %llu failed",
+                c->h_cnt[CNT_DEBUG_SITE]);
   if (st & ST_LAYER) return fail(PT_ERR_INVALID, "input contains a layer code > 9");
   const unsigned long long raw = c->h_cnt[CNT_RAW_STATUS];
   if (raw & RAW_INVALID)
@@ -1063,6 +1066,24 @@ pt_status pt_set_gate(pt_ctx* c, const float* w, float tau) {
   PT_CUDA(gate_prepare());
   PT_CUDA(cudaMemcpy(c->gate, &h, sizeof(h), cudaMemcpyHostToDevice));
   c->gate_on = true;
+  return PT_OK;
+}
+
+int pt_debug_build(void) {
+#ifdef PT_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+pt_status pt_debug_inject(pt_ctx* c, int site) {
+  g_err.clear();
+  if (!c) return fail(PT_ERR_INVALID, "context is NULL");
+  if (!pt_debug_build()) return fail(PT_ERR_INVALID, "not the debug build");
+  if (site < 1 || site > DBG_FB_RECORD) return fail(PT_ERR_INVALID, "site out of range");
+  DeviceGuard guard(c->device);
+  PT_CUDA(launch_debug_inject(c->B, (unsigned)site, c->stream));
   return PT_OK;
 }
 

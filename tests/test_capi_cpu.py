@@ -18,7 +18,7 @@ def _declared():
     for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
         if h.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", h)).read()
-            names += re.findall(r"^\s*(?:pt_status|const char\*)\s+(pt_\w+)\s*\(", txt, re.M)
+            names += re.findall(r"^\s*(?:pt_status|const char\*|int)\s+(pt_\w+)\s*\(", txt, re.M)
     return names
 
 
@@ -74,7 +74,7 @@ def test_null_handles_are_rejected_before_any_cuda_call():
         "pt_poll": (None, 0, 0, None, None, None, 0, None),
         "pt_server_stats": (None, None, None, None, None),
         "pt_set_layer_pairs": (None, 0, None, None), "pt_set_wait_limit": (None, 1),
-        "pt_set_fishbone": (None, 1),
+        "pt_set_fishbone": (None, 1), "pt_debug_inject": (None, 1),
         "pt_server_counters": (None, None, None, None),
         "pt_router_submit": (None, 0, None, None, None, None, None),
         "pt_router_poll": (None, 0, 0, None, None, None, 0, None),
