@@ -104,7 +104,7 @@ def kernel_layout_bytes(kernel: str, c: dict) -> int | None:
         # their two link flags 2 C
         "k_doublets": 20 * N + 24 * N + 10 * C,
         # hit and bin 20 N, incoming segments 24 N; inner hit of each incoming cell 4 C;
-        # links (source, target, quality) 12 Lk, per-cell lists (8) and out flag <= 9 Lk
+        # links (source, target, quality, next) 16 Lk, list heads and out flags <= 5 Lk
         "k_connect": 44 * N + 4 * C + 21 * Lk,
         # link source and target 8 Lk (read), the source's outer hit and the target's
         # segment 12 Lk, target (write) and in flag 5 Lk

@@ -23,19 +23,19 @@
 // slope is a monotone function of it, evaluated the same way for the staged slopes and
 // for the window's ends, which are moved out by a further 0.1 % + 1e-5 so that rounding
 // of t_a -+ w cannot exclude a bucket); the staged cells there that fall inside the
-// window are queued, and the queued pairs are tested with C1, C2 and C3 32 at a time,
-// all lanes busy.
+// window are queued as (source cell, target) pairs.  A queued pair carries all it needs,
+// so the queue runs on across incoming groups and middle hits, and C1, C2 and C3 are
+// tested only once 32 pairs are waiting, all lanes busy (about six pairs fall in the
+// windows of a group of 32 incoming cells).  A link takes the next slot of the warp's
+// reservation and is pushed onto its source's out-link list (cell_head, link_next),
+// the list the ntuplet search walks; a cell's list head is cleared by the lane that
+// holds the cell before any of its pairs is queued.
 //
 // The target cell (h1, h2) of a link is found afterwards, one thread per link, in h2's
 // incoming segment from h1's layer (ordered by inner hit) by binary search: in the
-// warp's own path those dependent loads would hold up the search.  Every link of a
-// source cell is found by the
-// lane that holds the cell, so a group of 32 incoming cells is finalised at once: each
-// cell's links take consecutive slots of one reservation (the out-link list the
-// ntuplet search walks, one run of equal link_src values per source).  If a group finds
-// more links than the shared buffer holds, its search runs again and writes them
-// straight to their slots.  A middle hit with more outgoing cells than the stage holds
-// is handled piece by piece, every incoming group visiting every piece.
+// warp's own path those dependent loads would hold up the search.  A middle hit with
+// more outgoing cells than the stage holds is handled piece by piece, every incoming
+// group visiting every piece.
 #include "ptca_internal.cuh"
 
 namespace ptca {
@@ -49,8 +49,7 @@ constexpr int kConnBlocksPerSm = 4;  // 64 registers per thread
 constexpr int kOut = 128;            // staged outgoing cells of one piece (<= 256)
 constexpr int kNb = 128;             // slope buckets of a piece (a multiple of 32)
 static_assert(kNb % 32 == 0, "buckets are scanned kNb / 32 per lane");
-constexpr int kQueue = 64;           // pairs that passed C1, waiting for C2/C3 (power of two)
-constexpr int kFound = 64;           // links of one incoming group kept before writing
+constexpr int kQueue = 64;           // window pairs waiting for C1-C3 (power of two)
 static_assert(kOut <= 256 && kOut % 32 == 0, "staged index fits 8 bits");
 static_assert(kQueue >= 63 && (kQueue & (kQueue - 1)) == 0, "queue holds 31 + 32 entries");
 
@@ -108,12 +107,7 @@ struct ConnWarp {
   uint8_t perm[kOut];        // bucket order -> staged index
   float ts[kOut];            // slopes in bucket order
   uint32_t bstart[kNb + 1];  // first bucket-ordered position of each slope bucket
-  uint32_t lcnt[32];         // links found per incoming cell of the group
-  uint32_t loff[32];         // first slot of each incoming cell's links
-  uint2 q[kQueue];           // window passes: (incoming lane, bucket-order position)
-  uint32_t fa[kFound];       // found links: incoming lane | rank << 5
-  uint32_t fb[kFound];       //   target: outer hit | slot << 29
-  float fq[kFound];          //   quality
+  uint2 q[kQueue];           // window pairs: (source cell, target: outer hit | slot << 29)
   float4 p1;                 // middle hit
   uint4 rg[kMaxOuter];       //   its forward windows, one per outer slot
   uint32_t so[kMaxInner];    //   its incoming segments: first cell
@@ -183,12 +177,47 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
     hi = min(hi, (unsigned long long)cap_links);
     for (unsigned long long i = lo + lane; i < hi; i += 32) b.link_src[i] = kHole;
   };
-  auto write_link = [&](uint64_t slot, uint32_t a, uint32_t t, float q) {
-    if (!PT_CHECK(b.cnt, slot < cap_links, DBG_CON_LINK)) return;
-    b.link_src[slot] = a;
-    b.link_dst[slot] = t;  // outer hit | slot << 29, made a cell id by k_link_targets
-    b.link_q[slot] = q;
-    if (!GATE) b.has_out[a] = 1;  // gated form: the gate sets the flags of the links it keeps
+  // C1, C2 and C3 on nt queued pairs, one per lane, all of them carrying what they need
+  // (the source cell and the target's outer hit and slot), so that pairs of different
+  // incoming groups and middle hits share one pass; a link is appended to its source's
+  // out-link list.
+  uint32_t qhead = 0, qtail = 0;  // warp-uniform queue positions
+  auto process = [&](uint32_t nt) {
+    __syncwarp();
+    const bool v = (uint32_t)lane < nt;
+    const uint2 e = v ? W.q[(qhead + lane) & (kQueue - 1)] : make_uint2(0u, 0u);
+    qhead += nt;
+    __syncwarp();
+    bool ok = false;
+    float q = 0.0f;
+    if (v) {
+      const uint32_t h0 = b.cell_in[e.x], h1 = b.cell_out[e.x];
+      const float4 q0 = b.hit4[h0], q1 = b.hit4[h1], q2 = b.hit4[e.y & 0x1fffffffu];
+      const bool b0 = (b.hbin[h0] / (uint32_t)B) % kLayers == 0;
+      ok = link_c1(cuts, q0, q1, q2) && link_c23(cuts, q0, b0, q1, q2, q);
+    }
+    const unsigned pm = __ballot_sync(kFull, ok);
+    const uint32_t n = __popc(pm);
+    if (n) {
+      unsigned long long hlo, hhi;
+      const unsigned long long base = chunk_take_shared(W, &b.cnt[CNT_LINKS], n, &hlo, &hhi);
+      mark_link_hole(hlo, hhi);
+      if (lane == 0) W.used += n;
+      if (base + n > cap_links) {
+        if (lane == 0) atomicOr(&b.cnt[CNT_STATUS], ST_LINKS);
+        mark_link_hole(base, base + n);  // slots below the capacity stay readable
+      } else if (ok) {
+        const uint64_t slot = base + __popc(pm & lt_mask);
+        if (PT_CHECK(b.cnt, slot < cap_links, DBG_CON_LINK)) {
+          b.link_src[slot] = e.x;
+          b.link_dst[slot] = e.y;  // outer hit | slot << 29, made a cell id by k_link_targets
+          b.link_q[slot] = q;
+          b.link_next[slot] = atomicExch(&b.cell_head[e.x], (uint32_t)slot);
+          if (!GATE) b.has_out[e.x] = 1;  // gated form: the gate sets the flags of kept links
+        }
+      }
+    }
+    __syncwarp();
   };
 
   for (;;) {
@@ -392,129 +421,61 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
           const uint32_t cn = incoming(i + 32, kn);
           if (PT_CHECK(b.cnt, cn < b.cnt[CNT_CELLS], DBG_CON_INCOMING)) h0_next = b.cell_in[cn];
         }
-        const bool first_b0 = valid && pt.inner[L1][kin] == 0;
         const float ta = __fdividef(p1.z - p0.z, p1.w - p0.w);  // the cell's slope dz/dr
         const float id1 = __fdividef(1.0f, p1.w - p0.w);
         const float wa = (cuts.rz0 + cuts.rz1 * cuts.cotmax) * id1;
         const float ua = cuts.rz0 + cuts.rz1 * fabsf(ta);
         const float shrink = 1.0f - cuts.rz1 * id1;
 
-        // mode 0: links buffered in shared memory; mode 1: written straight to their
-        // slots (the group found more than the buffer holds)
-        unsigned long long lbase = 0;
+        bool inited = false;  // the lane's cell had its out-link list cleared
 #pragma unroll 1
-        for (int mode = 0; mode < 2; ++mode) {
-          __syncwarp();
-          W.lcnt[lane] = 0;
-          uint32_t nf = 0;  // links found by the group (mode 0)
-          __syncwarp();
-#pragma unroll 1
-          for (int piece = 0; piece < npieces; ++piece) {
-            if (W.piece != piece) stage_piece(piece);
-            const float m = W.m, tmin = W.tmin, scale = W.scale;
-            float w = 0.0f;
-            uint32_t pos = 0, pend = 0;
-            if (valid) {
-              const float im = __fdividef(1.0f, m);
-              float wk = fmaf(ua, im, wa);
-              if (shrink > 0.0f) wk = fminf(wk, __fdividef(ua * (id1 + im), shrink));
-              w = wk * 1.01f + 1e-3f;
-              const float w2 = w * 1.001f + 1e-5f;
-              pos = W.bstart[slope_bucket(__fsub_rn(ta, w2), tmin, scale)];
-              pend = W.bstart[slope_bucket(__fadd_rn(ta, w2), tmin, scale) + 1];
-              if (!PT_CHECK(b.cnt, pos <= pend && pend <= (uint32_t)kOut, DBG_CON_BUCKET))
-                pend = pos;
-            }
-            uint32_t head = 0, tail = 0;
-            // C1, C2 and C3 on up to 32 queued pairs, all lanes busy
-            auto process = [&](uint32_t nt) {
-              __syncwarp();
-              const bool v = (uint32_t)lane < nt;
-              const uint2 e = v ? W.q[(head + lane) & (kQueue - 1)] : make_uint2(0u, 0u);
-              head += nt;
-              const int il = (int)e.x;
-              const float4 q0 = make_float4(__shfl_sync(kFull, p0.x, il), __shfl_sync(kFull, p0.y, il),
-                                            __shfl_sync(kFull, p0.z, il), __shfl_sync(kFull, p0.w, il));
-              const bool qb0 = __shfl_sync(kFull, first_b0, il);
-              const uint32_t ca = __shfl_sync(kFull, c, il);
-              bool ok = false;
-              float q = 0.0f;
-              uint32_t cb = 0;
-              if (v) {
-                const uint32_t st = W.perm[e.y];
-                const float4 q2 = W.p2[st];
-                ok = link_c1(cuts, q0, p1, q2) && link_c23(cuts, q0, qb0, p1, q2, q);
+        for (int piece = 0; piece < npieces; ++piece) {
+          if (W.piece != piece) stage_piece(piece);
+          const float m = W.m, tmin = W.tmin, scale = W.scale;
+          float w = 0.0f;
+          uint32_t pos = 0, pend = 0;
+          if (valid) {
+            const float im = __fdividef(1.0f, m);
+            float wk = fmaf(ua, im, wa);
+            if (shrink > 0.0f) wk = fminf(wk, __fdividef(ua * (id1 + im), shrink));
+            w = wk * 1.01f + 1e-3f;
+            const float w2 = w * 1.001f + 1e-5f;
+            pos = W.bstart[slope_bucket(__fsub_rn(ta, w2), tmin, scale)];
+            pend = W.bstart[slope_bucket(__fadd_rn(ta, w2), tmin, scale) + 1];
+            if (!PT_CHECK(b.cnt, pos <= pend && pend <= (uint32_t)kOut, DBG_CON_BUCKET))
+              pend = pos;
+          }
+          // each lane walks its own bucket range; the staged cells inside its window are
+          // queued with their target and tested with C1-C3 once 32 are waiting
+          while (__any_sync(kFull, pos < pend)) {
+            bool pass = false;
+            uint32_t code = 0;
+            if (pos < pend) {
+              pass = fabsf(W.ts[pos] - ta) <= w;
+              if (pass) {
                 // the target cell, named by its outer hit and the slot of h1's layer
                 // among that hit's inner layers until k_link_targets finds it
-                cb = W.h2[st] | ((uint32_t)W.j2[st] << 29);
-              }
-              uint32_t rk = 0;
-              if (ok) rk = atomicAdd(&W.lcnt[il], 1u);
-              const unsigned pm = __ballot_sync(kFull, ok);
-              if (ok) {
-                if (mode == 0) {
-                  const uint32_t seq = nf + __popc(pm & lt_mask);
-                  if (seq < (uint32_t)kFound) {
-                    W.fa[seq] = (uint32_t)il | (rk << 5);
-                    W.fb[seq] = cb;
-                    W.fq[seq] = q;
-                  }
-                } else {
-                  write_link(lbase + W.loff[il] + rk, ca, cb, q);
+                const uint32_t st = W.perm[pos];
+                code = W.h2[st] | ((uint32_t)W.j2[st] << 29);
+                if (!inited) {
+                  b.cell_head[c] = kHole;  // before any of its pairs is tested
+                  inited = true;
                 }
               }
-              nf += __popc(pm);
-            };
-            // each lane walks its own bucket range; the staged cells inside its window
-            // are queued (bucket-order position) and tested with C1-C3 32 at a time
-            while (__any_sync(kFull, pos < pend)) {
-              bool pass = false;
-              const uint32_t e = pos;
-              if (pos < pend) {
-                pass = fabsf(W.ts[pos] - ta) <= w;
-                ++pos;
-              }
-              const unsigned bal = __ballot_sync(kFull, pass);
-              PT_CHECK(b.cnt, tail + __popc(bal) - head <= (uint32_t)kQueue, DBG_CON_QUEUE);
-              if (pass) W.q[(tail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2((uint32_t)lane, e);
-              tail += __popc(bal);
-              if (tail - head >= 32u) process(32u);
+              ++pos;
             }
-            while (tail != head) process(min(32u, tail - head));
+            const unsigned bal = __ballot_sync(kFull, pass);
+            (void)PT_CHECK(b.cnt, qtail + __popc(bal) - qhead <= (uint32_t)kQueue, DBG_CON_QUEUE);
+            if (pass) W.q[(qtail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2(c, code);
+            qtail += __popc(bal);
+            if (qtail - qhead >= 32u) process(32u);
           }
-          __syncwarp();
-          if (mode == 1) break;
-          // finalise the group: one reservation, each cell's links consecutive
-          const uint32_t nl = valid ? W.lcnt[lane] : 0u;
-          const uint32_t inc = warp_incl_scan(nl);
-          const uint32_t tot = __shfl_sync(kFull, inc, 31);
-          if (tot == 0) break;
-          unsigned long long hlo, hhi;
-          lbase = chunk_take_shared(W, &b.cnt[CNT_LINKS], tot, &hlo, &hhi);
-          mark_link_hole(hlo, hhi);
-          if (lane == 0) W.used += tot;
-          if (lbase + tot > cap_links) {
-            if (lane == 0) atomicOr(&b.cnt[CNT_STATUS], ST_LINKS);
-            mark_link_hole(lbase, lbase + tot);  // slots below the capacity stay readable
-            break;
-          }
-          W.loff[lane] = inc - nl;
-          if (nl) b.link_oc[c] = make_uint2((uint32_t)(lbase + inc - nl), nl);
-          __syncwarp();
-          if (tot > (uint32_t)kFound) continue;  // search again, writing directly
-          for (uint32_t f0 = 0; f0 < tot; f0 += 32) {
-            const uint32_t f = f0 + lane;
-            const uint32_t fa = f < tot ? W.fa[f] : 0u;
-            const int il = (int)(fa & 31u);
-            const uint32_t ca = __shfl_sync(kFull, c, il);
-            if (f < tot) write_link(lbase + W.loff[il] + (fa >> 5), ca, W.fb[f], W.fq[f]);
-          }
-          break;
         }
         if (valid_next) p0_next = b.hit4[h0_next];
       }
     }
   }
+  while (qtail != qhead) process(min(32u, qtail - qhead));
   __syncwarp();
   mark_link_hole(W.chunk_next, W.chunk_end);
   if (lane == 0 && W.used) atomicAdd(&b.cnt[CNT_LINKS_USED], W.used);

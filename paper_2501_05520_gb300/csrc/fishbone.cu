@@ -17,8 +17,8 @@
 // comparisons: each cell decides only its own fate.
 //
 // The active cells are the sources of the links (with the gate: of the kept links), so
-// they are found from the link list, which holds each source's links in consecutive
-// slots: the first slot of each run stands for its source.  They are grouped by outer
+// they are found from the link slots: the slot that heads a source's out-link list
+// stands for its source.  They are grouped by outer
 // hit with a counting sort (k_fb_count, a scan, k_fb_scatter, which also writes each
 // cell's comparison record), and k_fb_compare takes one active cell per thread and
 // compares it with the other records of its group.  The removal
@@ -71,11 +71,10 @@ __device__ __forceinline__ FbCell fb_cell(const Buffers& b, float4 ph, uint32_t 
   return f;
 }
 
-// The source of link slot l when l is the first slot of an active source's run, else
-// kHole.
+// The source of link slot l when l heads an active source's out-link list, else kHole.
 __device__ __forceinline__ uint32_t run_source(const Buffers& b, uint64_t l, bool gated) {
   const uint32_t a = b.link_src[l];
-  if (a == kHole || (l > 0 && b.link_src[l - 1] == a)) return kHole;
+  if (a == kHole || b.cell_head[a] != (uint32_t)l) return kHole;
   if (gated && !b.has_out[a]) return kHole;  // no link of the run passed the gate
   return a;
 }

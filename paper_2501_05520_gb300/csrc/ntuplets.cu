@@ -44,23 +44,23 @@ enum WalkMode { kCount = 0, kEmit = 1, kBuffer = 2 };
 // Depth-first walk from root a.  kCount: returns the number of ntuplets; kEmit: also
 // writes them at slots t0, t0 + 1, ... (slots >= cap_nt are dropped); kBuffer: also
 // writes them to the warp's shared buffer (entries >= kNtBuf are dropped; the caller
-// then walks again with kEmit).  A cell's links are one (offset, count) read; when
-// writing, the batch index of each cell's outer hit is looked up once, when the cell is
-// pushed.
+// then walks again with kEmit).  A cell's links are a list (its head, then each link's
+// next slot); when writing, the batch index of each cell's outer hit is looked up once,
+// when the cell is pushed.
 template <int MODE, bool GATED>
 __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, uint64_t cap_nt,
                          NtWarp* W) {
   constexpr bool EMIT = MODE != kCount;
   uint32_t path[kMaxCellsPerNt];
-  uint32_t it[kMaxCellsPerNt], end[kMaxCellsPerNt];
+  uint32_t it[kMaxCellsPerNt];  // next out-link slot of path[k] (kHole: none left)
   float qs[kMaxCellsPerNt];
   int32_t gh[kMaxCellsPerNt];  // batch index of the outer hit of path[k] (EMIT)
+  // a link slot read from the lists (debug build: kHole unless inside the link slots)
+  auto slot = [&](uint32_t x) -> uint32_t {
+    return (x == kHole || PT_CHECK(b.cnt, x < b.cnt[CNT_LINKS], DBG_NT_LINKS)) ? x : kHole;
+  };
   path[0] = a;
-  {
-    const uint2 oc = b.link_oc[a];
-    it[0] = oc.x;
-    end[0] = oc.x + oc.y;
-  }
+  it[0] = slot(b.cell_head[a]);
   qs[0] = 0.0f;
   int32_t g0 = 0;
   if (EMIT) {
@@ -71,20 +71,21 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
   int depth = 1;
   while (depth > 0) {
     const int d = depth - 1;
-    if (it[d] == end[d]) {
+    if (it[d] == kHole) {
       --depth;
       continue;
     }
-    const uint32_t l = it[d]++;
+    const uint32_t l = it[d];
+    it[d] = slot(b.link_next[l]);
     if (depth == kMaxCellsPerNt) continue;  // deeper than the layer graph allows
     if (GATED && !b.gate_keep[l]) continue;  // removed by the learned gate
     const uint32_t c = b.link_dst[l];
     if (!PT_CHECK(b.cnt, c < b.cnt[CNT_CELLS], DBG_NT_CELL)) continue;
     const float q = fadd(qs[d], b.link_q[l]);
-    // everything c may need is loaded at once: its flag, its link list (stale and
+    // everything c may need is loaded at once: its flag, its list head (stale and
     // unused when c has no links) and its outer hit
     const bool leaf = !b.has_out[c];
-    const uint2 oc = b.link_oc[c];
+    const uint32_t hc = b.cell_head[c];
     const int32_t gc = EMIT ? (int32_t)b.perm[b.cell_out[c]] : 0;
     if (leaf) {
       // leaf: path[0..d] + c, i.e. depth + 1 cells, depth + 2 hits
@@ -129,9 +130,7 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
       continue;
     }
     path[depth] = c;
-    it[depth] = oc.x;
-    end[depth] = PT_CHECK(b.cnt, (uint64_t)oc.x + oc.y <= b.cnt[CNT_LINKS], DBG_NT_LINKS)
-                     ? oc.x + oc.y : oc.x;
+    it[depth] = slot(hc);
     qs[depth] = q;
     if (EMIT) gh[depth] = gc;
     ++depth;
@@ -139,9 +138,8 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
   return found;
 }
 
-// The slot that starts a source cell's run of links (its predecessor holds another
-// source or a hole) names a candidate root, which is a root when the cell has a kept
-// outgoing link and no incoming one.  Each warp queues the roots of its link slots in
+// The slot that heads a source cell's out-link list names a candidate root, which is a
+// root when the cell has a kept outgoing link and no incoming one.  Each warp queues the roots of its link slots in
 // shared memory and walks them 32 at a time, one per lane, writing the ntuplets to its
 // shared buffer; one atomic then reserves them and the warp copies them out.  If a
 // batch finds more than the buffer holds, it is walked again and written directly.
@@ -160,9 +158,7 @@ __global__ void __launch_bounds__(kNtWarps * 32, kNtBlocksPerSm)
     const uint64_t i = i0 + lane;
     uint32_t a = kHole;
     if (i < nl) a = b.link_src[i];
-    uint32_t prev = __shfl_up_sync(kFull, a, 1);
-    if (lane == 0) prev = i0 > 0 ? b.link_src[i0 - 1] : kHole;
-    const bool root = a != kHole && a != prev && b.has_out[a] && !b.has_in[a];
+    const bool root = a != kHole && b.cell_head[a] == (uint32_t)i && b.has_out[a] && !b.has_in[a];
     const unsigned rm = __ballot_sync(kFull, root);
     if (root) W.roots[nq + __popc(rm & lt_mask)] = a;
     nq += __popc(rm);

@@ -179,11 +179,12 @@ struct Buffers {
   uint32_t* fb_start;        // [max_hits + 1]   and their first position in fb_list
   float4* fb_rec;            // [max_links * 2] active cells grouped by outer hit: vector to
                              //   the hit and |.|^2; cell, inner hit's input index, layer, sensor
-  uint2* link_oc;            // [max_cells] first slot and number of the cell's links
-                             //   (valid where it has links)
+  uint32_t* cell_head;       // [max_cells] the cell's latest out-link slot, the head of
+                             //   its out-link list (valid where it has links)
   unsigned long long* best;  // [max_cells] duplicate-cleaning key (cells on ntuplets)
   // links
   uint32_t* link_dst;        // [max_links]
+  uint32_t* link_next;       // [max_links] the source's next out-link slot (kHole: last)
   float* link_q;             // [max_links]
   // ntuplets before cleaning
   int32_t* nt_hits;          // [max_ntuplets*6] batch input index, -1 pad

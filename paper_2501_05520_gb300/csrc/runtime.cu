@@ -187,9 +187,10 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.fb_cnt = (uint32_t*)take((N + 1) * 4);
   t.fb_start = (uint32_t*)take((N + 1) * 4);
   t.fb_rec = (float4*)take(L * 32);
-  t.link_oc = (uint2*)take(C * 8);
+  t.cell_head = (uint32_t*)take(C * 4);
   t.best = (unsigned long long*)take(C * 8);
   t.link_dst = (uint32_t*)take(L * 4);
+  t.link_next = (uint32_t*)take(L * 4);
   t.link_q = (float*)take(L * 4);
   t.nt_hits = (int32_t*)take(T * kMaxHits * 4);
   t.nt_cells = (uint32_t*)take(T * kMaxCellsPerNt * 4);
