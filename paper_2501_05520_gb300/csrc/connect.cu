@@ -107,7 +107,9 @@ struct ConnWarp {
   uint8_t perm[kOut];        // bucket order -> staged index
   float ts[kOut];            // slopes in bucket order
   uint32_t bstart[kNb + 1];  // first bucket-ordered position of each slope bucket
-  uint2 q[kQueue];           // window pairs: (source cell, target: outer hit | slot << 29)
+  float4 qp0[kQueue];        // window pairs: the source's inner hit (x, y, z, r)
+  uint4 q[kQueue];           //   source cell, target (outer hit | slot << 29), middle hit,
+                             //   inner hit on layer 0
   float4 p1;                 // middle hit
   uint4 rg[kMaxOuter];       //   its forward windows, one per outer slot
   uint32_t so[kMaxInner];    //   its incoming segments: first cell
@@ -185,16 +187,21 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
   auto process = [&](uint32_t nt) {
     __syncwarp();
     const bool v = (uint32_t)lane < nt;
-    const uint2 e = v ? W.q[(qhead + lane) & (kQueue - 1)] : make_uint2(0u, 0u);
+    const uint32_t qi = (qhead + lane) & (kQueue - 1);
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (v) {
+      e = W.q[qi];
+      q0 = W.qp0[qi];
+    }
     qhead += nt;
     __syncwarp();
     bool ok = false;
     float q = 0.0f;
+    const uint32_t src = e.x;
     if (v) {
-      const uint32_t h0 = b.cell_in[e.x], h1 = b.cell_out[e.x];
-      const float4 q0 = b.hit4[h0], q1 = b.hit4[h1], q2 = b.hit4[e.y & 0x1fffffffu];
-      const bool b0 = (b.hbin[h0] / (uint32_t)B) % kLayers == 0;
-      ok = link_c1(cuts, q0, q1, q2) && link_c23(cuts, q0, b0, q1, q2, q);
+      const float4 q1 = b.hit4[e.z], q2 = b.hit4[e.y & 0x1fffffffu];
+      ok = link_c1(cuts, q0, q1, q2) && link_c23(cuts, q0, e.w != 0, q1, q2, q);
     }
     const unsigned pm = __ballot_sync(kFull, ok);
     const uint32_t n = __popc(pm);
@@ -209,11 +216,11 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
       } else if (ok) {
         const uint64_t slot = base + __popc(pm & lt_mask);
         if (PT_CHECK(b.cnt, slot < cap_links, DBG_CON_LINK)) {
-          b.link_src[slot] = e.x;
+          b.link_src[slot] = src;
           b.link_dst[slot] = e.y;  // outer hit | slot << 29, made a cell id by k_link_targets
           b.link_q[slot] = q;
-          b.link_next[slot] = atomicExch(&b.cell_head[e.x], (uint32_t)slot);
-          if (!GATE) b.has_out[e.x] = 1;  // gated form: the gate sets the flags of kept links
+          b.link_next[slot] = atomicExch(&b.cell_head[src], (uint32_t)slot);
+          if (!GATE) b.has_out[src] = 1;  // gated form: the gate sets the flags of kept links
         }
       }
     }
@@ -414,6 +421,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
           valid = PT_CHECK(b.cnt, c < b.cnt[CNT_CELLS], DBG_CON_INCOMING);
         }
         const float4 p0 = p0_next;
+        const bool first_b0 = valid && pt.inner[L1][kin] == 0;
         uint32_t h0_next = 0;
         const bool valid_next = i + 32 < nin;
         if (valid_next) {
@@ -466,7 +474,11 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
             }
             const unsigned bal = __ballot_sync(kFull, pass);
             (void)PT_CHECK(b.cnt, qtail + __popc(bal) - qhead <= (uint32_t)kQueue, DBG_CON_QUEUE);
-            if (pass) W.q[(qtail + __popc(bal & lt_mask)) & (kQueue - 1)] = make_uint2(c, code);
+            if (pass) {
+              const uint32_t qi = (qtail + __popc(bal & lt_mask)) & (kQueue - 1);
+              W.q[qi] = make_uint4(c, code, h1, first_b0 ? 1u : 0u);
+              W.qp0[qi] = p0;
+            }
             qtail += __popc(bal);
             if (qtail - qhead >= 32u) process(32u);
           }
