@@ -242,6 +242,7 @@ __global__ void k_bucket_sort(Buffers b) {
       }
       b.ord[j] = v;
     }
+    for (uint32_t i = lo; i < hi; ++i) b.nt_rank[b.ord[i]] = i;  // sorted position
   }
 }
 
@@ -250,12 +251,14 @@ __device__ __forceinline__ unsigned long long dedup_key(const Buffers& b, uint32
          ((unsigned long long)__float_as_uint(b.nt_q[t]) << kRankBits) | i;
 }
 
+// The two key kernels take the candidates in their own order (their arrays read
+// contiguously) and find each one's sorted position in nt_rank.
 __global__ void k_dedup_min(Buffers b) {
   const uint64_t T = b.cnt[CNT_SCAN_NT];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += stride) {
-    const uint32_t t = b.ord[i];
-    const unsigned long long key = dedup_key(b, t, i);
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += stride) {
+    const uint32_t i = b.nt_rank[t];
+    const unsigned long long key = dedup_key(b, (uint32_t)t, i);
     const int nc = b.nt_n[t] - 1;
     for (int k = 0; k < nc; ++k) atomicMin(&b.best[b.nt_cells[(uint64_t)t * kMaxCellsPerNt + k]], key);
   }
@@ -264,9 +267,9 @@ __global__ void k_dedup_min(Buffers b) {
 __global__ void k_dedup_alive(Buffers b) {
   const uint64_t T = b.cnt[CNT_SCAN_NT];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += stride) {
-    const uint32_t t = b.ord[i];
-    const unsigned long long key = dedup_key(b, t, i);
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += stride) {
+    const uint32_t i = b.nt_rank[t];
+    const unsigned long long key = dedup_key(b, (uint32_t)t, i);
     const int n = b.nt_n[t];
     bool ok = true;
     for (int k = 0; k < n - 1; ++k)

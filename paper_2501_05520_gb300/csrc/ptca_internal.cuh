@@ -191,7 +191,8 @@ struct Buffers {
   uint32_t* nt_cells;        // [max_ntuplets*5]
   uint8_t* nt_n;             // [max_ntuplets]
   float* nt_q;               // [max_ntuplets]
-  uint32_t* nt_rank;         // [max_ntuplets] rank within its first-hit bucket
+  uint32_t* nt_rank;         // [max_ntuplets] rank within its first-hit bucket, then (after
+                             //   the canonical sort) its sorted position
   // canonical order
   uint32_t* bucket_cnt;      // [max_hits + 1]
   uint32_t* bucket_start;    // [max_hits + 1]
