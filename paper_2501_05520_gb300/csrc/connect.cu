@@ -99,11 +99,9 @@ __device__ __forceinline__ uint4 forward_window(const Buffers& b, const PairTabl
 
 // Per-warp shared state.
 struct ConnWarp {
-  float4 p2[kOut];           // staged outgoing cells: outer hit (x, y, z, r)
-  float t[kOut];             //   r-z slope
-  uint32_t h2[kOut];         //   outer hit (sorted index)
-  uint8_t j2[kOut];          //   slot of the middle hit's layer among the outer hit's
-                             //   inner layers
+  float t[kOut];             // staged outgoing cells: r-z slope
+  uint32_t code[kOut];       //   outer hit (sorted index) | slot of the middle hit's layer
+                             //   among the outer hit's inner layers << 29
   uint8_t perm[kOut];        // bucket order -> staged index
   float ts[kOut];            // slopes in bucket order
   uint32_t bstart[kNb + 1];  // first bucket-ordered position of each slope bucket
@@ -315,10 +313,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
                   if (pos >= lo_ord && pos < lo_ord + kOut) {
                     const uint32_t st = pos - lo_ord;
                     const float t = __fdividef(ho.z - p1.z, ho.w - p1.w);
-                    W.p2[st] = ho;
                     W.t[st] = t;
-                    W.h2[st] = o;
-                    W.j2[st] = j2;
+                    W.code[st] = o | ((uint32_t)j2 << 29);
                     m = fminf(m, fsub(ho.w, p1.w));
                     tlo = fminf(tlo, t);
                     thi = fmaxf(thi, t);
@@ -464,7 +460,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
                 // the target cell, named by its outer hit and the slot of h1's layer
                 // among that hit's inner layers until k_link_targets finds it
                 const uint32_t st = W.perm[pos];
-                code = W.h2[st] | ((uint32_t)W.j2[st] << 29);
+                code = W.code[st];
                 if (!inited) {
                   b.cell_head[c] = kHole;  // before any of its pairs is tested
                   inited = true;
