@@ -11,10 +11,12 @@
 //   C1, C2 and C3 cut ratios, t_a / cotmax, 10 (t_b - t_a), r0/16, r1/16, r2/16,
 //   (z0 - r0 t_a) / z0max, layer0/9, layer1/9, layer2/9; padded with 4 zeros to K = 16.
 //
-// Tensor-core MLP (one 128-thread CTA per SM slot, persistent over 128-link tiles):
+// Tensor-core MLP (128-thread CTAs, six per SM, persistent over 128-link tiles; each
+// tile's rows are loaded into registers while the tile before it is computed):
 //   D1[128x64] = X[128x16] * W1^T      one tcgen05.mma (M=128, N=64, K=16), TMEM cols 0..63
 //   H1 = bf16(relu(D1 + b1))           tcgen05.ld by each warp's 32 TMEM lanes -> smem
-//   D2[128x64] = H1[128x64] * W2^T     four tcgen05.mma (K=16 each), TMEM cols 64..127
+//   D2[128x64] = H1[128x64] * W2^T     four tcgen05.mma (K=16 each), the same TMEM columns
+//                                      (D1 has been read by then)
 //   score = relu(D2 + b2) . w3 + b3    tcgen05.ld + float32 dot in registers
 // Operands are bf16 in shared memory in the no-swizzle K-major layout of 8x8 core
 // matrices (16 bytes per row, 128 bytes per core matrix; LBO = 128 bytes between core
@@ -116,13 +118,17 @@ constexpr int kOffF = 30720;          // b1, b2, w3 (64 each), b3, tau
 constexpr int kOffBar = 31744;        // mbarrier
 constexpr int kOffTmem = 31752;       // TMEM base address
 constexpr int kOffFlag = 31756;       // wait status
-constexpr int kMlpSmem = 48 * 1024;   // requested: at most 4 CTAs per SM (TMEM 4 x 128 cols)
+constexpr int kMlpSmem = 32 * 1024;   // requested: six CTAs per SM by shared memory
+constexpr int kMlpCtasPerSm = 6;
+constexpr int kMlpTmemCols = 64;      // D1, then D2
+static_assert(kMlpCtasPerSm * kMlpTmemCols <= 512, "every resident CTA gets its TMEM columns");
+static_assert(kMlpCtasPerSm * (kMlpSmem + 1024) <= 228 * 1024, "six CTAs fit an SM");
 
 // PIPE = true: rows are link slots of the batch, whose bf16 feature rows the link stage
 // wrote to gate_x; kept links set the flags the ntuplet search reads.
 // PIPE = false: rows are given bf16 feature rows X (standalone scoring).
 template <bool PIPE>
-__global__ void __launch_bounds__(kTileM, 1)
+__global__ void __launch_bounds__(kTileM, kMlpCtasPerSm)
     k_gate_mlp(const GateWeights* gw, Buffers b, pt_cuts cuts, int32_t B, const uint16_t* X,
                const unsigned long long* n_dev, int64_t n_max, float* score, uint8_t* keep,
                unsigned long long* status, unsigned long long* kept, long long wait_limit) {
@@ -159,7 +165,7 @@ __global__ void __launch_bounds__(kTileM, 1)
     }
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
                      smem_u32(tslot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -176,33 +182,32 @@ __global__ void __launch_bounds__(kTileM, 1)
   bool pending = false;  // an MMA group was committed and not yet seen complete
   const uint64_t n_tiles = (n + kTileM - 1) / kTileM;
 
+  // this thread's row of tile tt: its source cell (pipeline form) and bf16 feature row
+  auto load_row = [&](uint64_t tt, uint4& lo, uint4& hi, uint32_t& src) {
+    const uint64_t r = tt * kTileM + tid;
+    lo = make_uint4(0, 0, 0, 0);
+    hi = lo;
+    src = kHole;
+    if (tt >= n_tiles || r >= n) return;
+    if (PIPE) {
+      src = b.link_src[r];
+      if (src == kHole) return;
+    }
+    const uint4* srcp = (const uint4*)((PIPE ? b.gate_x : X) + r * kGateK1);
+    lo = srcp[0];
+    hi = srcp[1];
+  };
+  uint4 nlo, nhi;
+  uint32_t nsrc;
+  load_row(blockIdx.x, nlo, nhi, nsrc);
   for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const uint64_t row = t * kTileM + tid;
     // X row -> core-matrix layout: k 0..7 at +0, k 8..15 at +128 within the row group
     unsigned char* xr = sm + kOffX + (tid >> 3) * 256 + (tid & 7) * 16;
-    uint32_t src_cell = kHole;
-    if (PIPE) {
-      uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
-      if (row < n) {
-        src_cell = b.link_src[row];
-        if (src_cell != kHole) {
-          const uint4* srcp = (const uint4*)(b.gate_x + row * kGateK1);
-          lo = srcp[0];
-          hi = srcp[1];
-        }
-      }
-      *(uint4*)xr = lo;
-      *(uint4*)(xr + 128) = hi;
-    } else {
-      uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
-      if (row < n) {
-        const uint4* srcp = (const uint4*)(X + row * kGateK1);
-        lo = srcp[0];
-        hi = srcp[1];
-      }
-      *(uint4*)xr = lo;
-      *(uint4*)(xr + 128) = hi;
-    }
+    const uint32_t src_cell = nsrc;
+    *(uint4*)xr = nlo;
+    *(uint4*)(xr + 128) = nhi;
+    load_row(t + gridDim.x, nlo, nhi, nsrc);  // in flight while this tile is computed
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(kTileM, 1)
     if (tid == 0) {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        mma_bf16(tmem + 64, smem_desc(ah1 + 256 * j, 128, 1024), smem_desc(aw2 + 256 * j, 128, 1024),
+        mma_bf16(tmem, smem_desc(ah1 + 256 * j, 128, 1024), smem_desc(aw2 + 256 * j, 128, 1024),
                  j > 0 ? 1u : 0u);
       mma_commit(mbar);
       pending = true;
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(kTileM, 1)
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       float v[32];
-      tmem_ld32(tmem + lane_base + 64 + 32 * half, v);
+      tmem_ld32(tmem + lane_base + 32 * half, v);
 #pragma unroll
       for (int i = 0; i < 32; ++i) acc += fmaxf(v[i] + sb2[32 * half + i], 0.f) * sw3[32 * half + i];
     }
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(kTileM, 1)
   __syncthreads();
   tc_after_sync();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
 // float32 features of every current link (gated form: kept links only), row = link slot.
@@ -343,7 +348,7 @@ cudaError_t gate_prepare() {
 void launch_gate(const Buffers& b, const Params& p, const Launch& l, const GateWeights* w,
                  cudaStream_t s) {
   PT_TRACE(l, s, "k_gate_mlp",
-           k_gate_mlp<true><<<l.sms * 4, kTileM, kMlpSmem, s>>>(
+           k_gate_mlp<true><<<l.sms * kMlpCtasPerSm, kTileM, kMlpSmem, s>>>(
                w, b, p.cuts, p.phi_bins, nullptr, &b.cnt[CNT_LINKS], p.max_links, b.gate_score,
                b.gate_keep, &b.cnt[CNT_STATUS], &b.cnt[CNT_GATE_KEPT], p.wait_cycles));
 }
@@ -352,7 +357,7 @@ void launch_gate_score(const GateWeights* w, const float* feat, int64_t n, float
                        uint16_t* xbuf, unsigned long long* status, int sms, long long wait_cycles,
                        cudaStream_t s) {
   k_gate_pack<<<sms * 4, 256, 0, s>>>(feat, n, xbuf);
-  k_gate_mlp<false><<<sms * 4, kTileM, kMlpSmem, s>>>(w, Buffers{}, pt_cuts{}, 1, xbuf, nullptr, n,
+  k_gate_mlp<false><<<sms * kMlpCtasPerSm, kTileM, kMlpSmem, s>>>(w, Buffers{}, pt_cuts{}, 1, xbuf, nullptr, n,
                                                         out, nullptr, status, nullptr, wait_cycles);
 }
 
