@@ -7,7 +7,9 @@ import concurrent.futures as cf
 import numpy as np
 import pytest
 
+import oracle
 import sim
+from parity import assert_fits_close, assert_ntuplets_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +58,13 @@ def test_results_same_alone_and_in_the_mix(cuts):
         assert t.tobytes() == t2.tobytes()
     assert st["n_done"] == len(events)
     assert 0 < st["p50_ms"] <= st["p99_ms"] and st["events_per_s"] > 0
+    # served results against the oracle directly, on a sample of the mix
+    for i in (0, 7, 19, 33):
+        ev = events[i]
+        ref_o = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts)
+        h, n, t = got[i]
+        assert_ntuplets_equal(h, oracle.survivors_hits(ref_o), ref_o)
+        assert_fits_close(t, ref_o["fit"])
 
 
 def test_gated_serving_same_as_gated_alone(cuts):
