@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
   __shared__ uint32_t st_val[kWarpsPerBlock][kStage];
   __shared__ uint4 st_rng[kWarpsPerBlock][32][kMaxInner];
   __shared__ float4 st_hit[kWarpsPerBlock][32];
+  __shared__ uint8_t st_nin[kWarpsPerBlock][32];  // inner layers of each hit's layer
   const int lane = lane_id(), wib = threadIdx.x >> 5;
   uint32_t* sval = st_val[wib];
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -116,7 +117,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
       const float a = 0.5f * cuts.kmax * ho.w;
       const float asin_o = a >= 0.7f ? __int_as_float(0x7f800000) : asinf(a);
       st_hit[wib][lane] = ho;
-      for (int k = 0; k < pt.max_inner; ++k) {
+      const int nin = pt.n_inner[(gb / (uint32_t)B) % kLayers];
+      st_nin[wib][lane] = (uint8_t)nin;
+      for (int k = 0; k < nin; ++k) {
         uint4 rg = reverse_window(b, pt, B, bins_per_rad, gb, ho, asin_o, k);
         if (!PT_CHECK(b.cnt, rg.x <= rg.y && rg.y <= n_sorted && rg.z <= rg.w && rg.w <= n_sorted,
                       DBG_DBL_WINDOW))
@@ -129,7 +132,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
     for (uint32_t j = 0; j < nh; ++j) {
       const uint32_t s = (uint32_t)s0 + j;
       const float4 ho = st_hit[wib][j];
-      for (int k = 0; k < pt.max_inner; ++k) {
+      const int nin = st_nin[wib][j];
+      // the slots the hit's layer does not use are written empty, so readers need not
+      // know the hit's layer
+      if (lane >= nin && lane < pt.max_inner)
+        b.seg[(uint64_t)s * pt.max_inner + lane] = make_uint2(0u, 0u);
+      for (int k = 0; k < nin; ++k) {
         const uint4 rg = st_rng[wib][j][k];
         uint32_t cnt = 0;
         // pass 1: test, stage up to kStage passing hits, count all; two candidates per
@@ -192,8 +200,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
             seg_cnt = cnt;
           }
         }
-        // every slot is written (empty where the layer has fewer inner layers), so
-        // readers need not know the hit's layer
         if (lane == 0) b.seg[(uint64_t)s * pt.max_inner + k] = make_uint2(seg_off, seg_cnt);
         __syncwarp();
       }
