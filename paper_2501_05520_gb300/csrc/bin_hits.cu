@@ -21,6 +21,8 @@ __global__ void k_clear(Buffers b, int32_t phi_bins) {
   for (int i = t0; i < E * kLayers; i += stride) {
     b.layer_rmax[i] = 0u;
     b.layer_rmin[i] = 0x7f800000u;  // +inf
+    b.layer_zmin[i] = 0xffffffffu;
+    b.layer_zmax[i] = 0u;
   }
   for (int i = t0; i <= N; i += stride) b.bucket_cnt[i] = 0;
   for (int i = t0; i < N; i += stride) b.used[i] = 0;
@@ -44,8 +46,8 @@ __device__ __forceinline__ float hit_radius(float x, float y) {
   return fsqrt(fadd(fmul(x, x), fmul(y, y)));
 }
 
-// Histogram: global bin of every input hit and its rank inside the bin; max and min r
-// per (event, layer), reduced within the warp before the atomics.
+// Histogram: global bin of every input hit and its rank inside the bin; the r and z
+// ranges per (event, layer), reduced within the warp before the atomics.
 __global__ void k_bin_count(Buffers b, int32_t B) {
   const int E = b.hdr->n_events, N = b.hdr->n_hits;
   const float scale = (float)B / (2.0f * kPi);
@@ -55,6 +57,7 @@ __global__ void k_bin_count(Buffers b, int32_t B) {
     const bool valid = g < N;
     uint32_t key = 0xffffffffu;  // event*10 + layer
     float r = 0.0f;
+    uint32_t zk = 0;
     if (valid) {
       const int L = b.in_layer[g];
       if (L >= kLayers) {
@@ -64,6 +67,7 @@ __global__ void k_bin_count(Buffers b, int32_t B) {
         const int e = find_event(b.hit_off, E, g);
         const float x = b.in_x[g], y = b.in_y[g];
         r = hit_radius(x, y);
+        zk = float_order_key(b.in_z[g]);
         int bin = (int)floorf((atan2f(y, x) + kPi) * scale);
         bin = bin < 0 ? 0 : (bin >= B ? B - 1 : bin);
         key = (uint32_t)(e * kLayers + L);
@@ -77,9 +81,13 @@ __global__ void k_bin_count(Buffers b, int32_t B) {
     // r >= 0, so the integer order of the bit patterns is the float order
     const unsigned m = __reduce_max_sync(peers, __float_as_uint(r));
     const unsigned mn = __reduce_min_sync(peers, __float_as_uint(r));
+    const unsigned zmx = __reduce_max_sync(peers, zk);
+    const unsigned zmn = __reduce_min_sync(peers, zk);
     if (key != 0xffffffffu && (__ffs(peers) - 1) == lane_id()) {
       atomicMax(&b.layer_rmax[key], m);
       atomicMin(&b.layer_rmin[key], mn);
+      atomicMax(&b.layer_zmax[key], zmx);
+      atomicMin(&b.layer_zmin[key], zmn);
     }
   }
 }

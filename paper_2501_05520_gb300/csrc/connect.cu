@@ -56,9 +56,11 @@ static_assert(kQueue >= 63 && (kQueue & (kQueue - 1)) == 0, "queue holds 31 + 32
 // Azimuthal window of inner hit `hi` (global bin gb, asin_i = asin(kmax*ri/2)) towards
 // outer slot k, the doublet search's window from the inner side: the outer layer's
 // asin(kmax*ro_max/2) - asin_i (+1e-4 rad, +1 bin); up to two ranges [r.x, r.y) and
-// [r.z, r.w) of the sorted hits; empty where the slot is unused or the outer layer ends
-// inside the inner hit's radius.
-__device__ __forceinline__ uint4 forward_window(const Buffers& b, const PairTable& pt, int32_t B,
+// [r.z, r.w) of the sorted hits; empty where the slot is unused, the outer layer ends
+// inside the inner hit's radius, or none of its r-z extent can pass D2 and D3 with the
+// inner hit.
+__device__ __forceinline__ uint4 forward_window(const Buffers& b, const pt_cuts& cuts,
+                                                const PairTable& pt, int32_t B,
                                                 float bins_per_rad, uint32_t gb, float4 hi,
                                                 float asin_i, int k) {
   const int el = gb / B;  // event*10 + layer
@@ -69,6 +71,10 @@ __device__ __forceinline__ uint4 forward_window(const Buffers& b, const PairTabl
   const int Lo = pt.outer[L][k];
   const float ro_max = __uint_as_float(b.layer_rmax[e * kLayers + Lo]);
   if (!(ro_max > hi.w)) return r;
+  if (!rz_box_reachable(cuts, hi.w, hi.z, __uint_as_float(b.layer_rmin[e * kLayers + Lo]), ro_max,
+                        float_from_order_key(b.layer_zmin[e * kLayers + Lo]),
+                        float_from_order_key(b.layer_zmax[e * kLayers + Lo]), true))
+    return r;
   const float asin_o = b.layer_asin[e * kLayers + Lo];
   float win = kHalfPi + 1e-3f;
   if (asin_o != __int_as_float(0x7f800000)) win = fminf(asin_o - asin_i + 1e-4f, win);
@@ -240,7 +246,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
         const int L = (my_gb / (uint32_t)B) % kLayers;
         if (pt.n_outer[L] > 0) {
           uint32_t any = 0;
-          for (int k = 0; k < pt.max_inner; ++k) any |= b.seg[s * pt.max_inner + k].y;
+          // slots past the layer's own inner layers are written empty
+          for (int k = 0; k < pt.n_inner[L]; ++k) any |= b.seg[s * pt.max_inner + k].y;
           work = any != 0;
         }
       }
@@ -256,7 +263,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
       __syncwarp();
       {
         // h1's incoming segments, one slot per lane, and the cells before each
-        const uint2 sgl = lane < pt.max_inner ? b.seg[(uint64_t)h1 * pt.max_inner + lane]
+        const uint2 sgl = lane < pt.n_inner[L1] ? b.seg[(uint64_t)h1 * pt.max_inner + lane]
                                               : make_uint2(0u, 0u);
         const uint32_t inc = warp_incl_scan(sgl.y);
         if (lane < kMaxInner) {
@@ -268,8 +275,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
       }
       // forward windows, one outer slot per lane
       if (lane < kMaxOuter) {
-        uint4 rg = forward_window(b, pt, B, bins_per_rad, gb, p1, asinf(0.5f * cuts.kmax * p1.w),
-                                  lane);
+        uint4 rg = forward_window(b, cuts, pt, B, bins_per_rad, gb, p1,
+                                  asinf(0.5f * cuts.kmax * p1.w), lane);
         if (!PT_CHECK(b.cnt, rg.x <= rg.y && rg.y <= n_sorted && rg.z <= rg.w && rg.w <= n_sorted,
                       DBG_CON_WINDOW))
           rg = make_uint4(0u, 0u, 0u, 0u);

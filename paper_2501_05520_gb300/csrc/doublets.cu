@@ -39,9 +39,11 @@ __device__ __forceinline__ void write_cell(const Buffers& b, uint64_t c, uint32_
 
 // Azimuthal window of outer hit `ho` (global bin gb, asin_o = asin(kmax*ro/2), +inf where
 // kmax*ro/2 >= 0.7) towards inner slot k: up to two ranges [r.x, r.y) and [r.z, r.w) of
-// the sorted hits, the first below the second; empty where the slot is unused or the
-// inner layer has no hit inside the outer hit's radius.
-__device__ __forceinline__ uint4 reverse_window(const Buffers& b, const PairTable& pt, int32_t B,
+// the sorted hits, the first below the second; empty where the slot is unused, the
+// inner layer has no hit inside the outer hit's radius, or none of its r-z extent can
+// pass D2 and D3 with the outer hit.
+__device__ __forceinline__ uint4 reverse_window(const Buffers& b, const pt_cuts& cuts,
+                                                const PairTable& pt, int32_t B,
                                                 float bins_per_rad, uint32_t gb, float4 ho,
                                                 float asin_o, int k) {
   const int el = gb / B;  // event*10 + layer
@@ -52,6 +54,10 @@ __device__ __forceinline__ uint4 reverse_window(const Buffers& b, const PairTabl
   const int Li = pt.inner[L][k];
   const float ri_min = __uint_as_float(b.layer_rmin[e * kLayers + Li]);
   if (!(ho.w > ri_min)) return r;  // D0 fails for every hit of the inner layer
+  if (!rz_box_reachable(cuts, ho.w, ho.z, ri_min, __uint_as_float(b.layer_rmax[e * kLayers + Li]),
+                        float_from_order_key(b.layer_zmin[e * kLayers + Li]),
+                        float_from_order_key(b.layer_zmax[e * kLayers + Li]), false))
+    return r;
   float win = kHalfPi + 1e-3f;     // where the curvature bound is void, D1's
   if (asin_o != __int_as_float(0x7f800000))
     win = fminf(asin_o - b.layer_asin_lo[e * kLayers + Li] + 1e-4f, win);
@@ -120,7 +126,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5)
       const int nin = pt.n_inner[(gb / (uint32_t)B) % kLayers];
       st_nin[wib][lane] = (uint8_t)nin;
       for (int k = 0; k < nin; ++k) {
-        uint4 rg = reverse_window(b, pt, B, bins_per_rad, gb, ho, asin_o, k);
+        uint4 rg = reverse_window(b, cuts, pt, B, bins_per_rad, gb, ho, asin_o, k);
         if (!PT_CHECK(b.cnt, rg.x <= rg.y && rg.y <= n_sorted && rg.z <= rg.w && rg.w <= n_sorted,
                       DBG_DBL_WINDOW))
           rg = make_uint4(0u, 0u, 0u, 0u);

@@ -20,7 +20,8 @@ constexpr size_t kNaNb = (size_t)kLayers * kNaBins + 1;
 // Bytes of each scratch buffer, in the order na_layout carves them.
 enum NaPart {
   NA_HDR, NA_CNT, NA_OFF, NA_IN_BIN, NA_IN_RANK, NA_HIT4, NA_PERM, NA_HBIN, NA_BIN_CNT,
-  NA_BIN_START, NA_RMAX, NA_ASIN, NA_RMIN, NA_ASIN_LO, NA_BUCKET_CNT, NA_USED, NA_SCAN,
+  NA_BIN_START, NA_RMAX, NA_ASIN, NA_RMIN, NA_ASIN_LO, NA_ZMIN, NA_ZMAX, NA_BUCKET_CNT, NA_USED,
+  NA_SCAN,
   NA_PARTS
 };
 constexpr size_t kNaPart[NA_PARTS] = {
@@ -29,6 +30,7 @@ constexpr size_t kNaPart[NA_PARTS] = {
     kNaMaxHits * 16, kNaMaxHits * 4, kNaMaxHits * 4,         // hit4, perm, hbin
     kNaNb * 4, kNaNb * 4, kLayers * 4, kLayers * 4,          // bins, layer r max, layer asin
     kLayers * 4, kLayers * 4,                                // layer r min, its asin
+    kLayers * 4, kLayers * 4,                                // layer z min, max
     (kNaMaxHits + 1) * 4, kNaMaxHits,                        // cleared: bucket, used
     (kScanBlocks + 1) * 4};                                  // scan partials
 constexpr size_t na_offset(int part) {
@@ -60,6 +62,8 @@ Buffers na_layout(char* base, const float* x, const float* y, const float* z,
   b.layer_asin = (float*)at(NA_ASIN);
   b.layer_rmin = (uint32_t*)at(NA_RMIN);
   b.layer_asin_lo = (float*)at(NA_ASIN_LO);
+  b.layer_zmin = (uint32_t*)at(NA_ZMIN);
+  b.layer_zmax = (uint32_t*)at(NA_ZMAX);
   b.bucket_cnt = (uint32_t*)at(NA_BUCKET_CNT);
   b.used = (uint8_t*)at(NA_USED);
   b.scan_part = (uint32_t*)at(NA_SCAN);

@@ -164,6 +164,8 @@ struct Buffers {
                              //   for an empty layer)
   float* layer_asin_lo;      // [max_events*10] asin(kmax r_min / 2) (0 where that is >= 0.7
                              //   or the layer is empty)
+  uint32_t* layer_zmin;      // [max_events*10] order keys (float_order_key) of min and max
+  uint32_t* layer_zmax;      //   z per event layer (~0 and 0 for an empty layer)
   // incoming segments: per sorted (outer) hit and inner-layer slot, the cells ending on
   // the hit from that layer, cells [x, x + y), ordered by inner hit; the table's
   // max_inner slots per hit, all written
@@ -340,6 +342,45 @@ __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// Order-preserving map of a float to an unsigned key (for atomicMin / atomicMax), and
+// back.
+__device__ __forceinline__ uint32_t float_order_key(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float float_from_order_key(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Whether a layer whose hits lie in the r-z box [rlo, rhi] x [zlo, zhi] can hold a
+// partner of the hit (r, z), outward (larger r) or inward, that passes D2 and D3.  Both
+// cuts bound the r-z slope s of the cell: |s| <= cotmax, and the line's z at r = 0,
+// which is z - r s from either hit, within +-z0max.  Seen from the hit, the slopes of
+// the box's points with a positive radial step fill the interval between its corners'
+// slopes; the layer is ruled out only when that interval lies wholly beyond the allowed
+// one, compared in multiplied form with margins (1e-3 on slopes, 1e-3 cm on z) far above
+// float32 rounding.  Boxes reaching to the hit's radius or inside it are kept (D0
+// decides them).
+__device__ __forceinline__ bool rz_box_reachable(const pt_cuts& c, float r, float z, float rlo,
+                                                 float rhi, float zlo, float zhi, bool outward) {
+  float d0, d1, e0, e1;  // radial steps and z steps (towards the partner) over the box
+  if (outward) {
+    d0 = fmaxf(rlo - r, 0.0f), d1 = rhi - r, e0 = zlo - z, e1 = zhi - z;
+  } else {
+    d0 = fmaxf(r - rhi, 0.0f), d1 = r - rlo, e0 = z - zhi, e1 = z - zlo;
+  }
+  if (!(d1 > 0.0f) || !(r > 0.0f)) return true;
+  const float lo = fmaxf((z - c.z0max) / r, -c.cotmax);
+  const float hi = fminf((z + c.z0max) / r, c.cotmax);
+  const float slo = lo - 1e-3f * (1.0f + fabsf(lo)), shi = hi + 1e-3f * (1.0f + fabsf(hi));
+  e0 -= 1e-3f;
+  e1 += 1e-3f;
+  // largest slope of the box below slo, or its smallest above shi
+  const bool below = e1 >= 0.0f ? e1 < slo * d0 : e1 < slo * d1;
+  const bool above = e0 <= 0.0f ? e0 > shi * d0 : e0 > shi * d1;
+  return !(below || above);
+}
 
 // Doublet cuts D0..D4 on (x, y, z, r) of the inner and outer hit, in the library's
 // fixed evaluation order (see pt_cuts in pt_ca.h).

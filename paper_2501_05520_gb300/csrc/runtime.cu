@@ -178,6 +178,8 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.layer_asin = (float*)take(E * kLayers * 4);
   t.layer_rmin = (uint32_t*)take(E * kLayers * 4);
   t.layer_asin_lo = (float*)take(E * kLayers * 4);
+  t.layer_zmin = (uint32_t*)take(E * kLayers * 4);
+  t.layer_zmax = (uint32_t*)take(E * kLayers * 4);
   t.seg = (uint2*)take(N * kMaxInner * sizeof(uint2));  // the table's max_inner slots used
   t.cell_in = (uint32_t*)take(C * 4);
   t.cell_out = (uint32_t*)take(C * 4);
