@@ -26,13 +26,21 @@ namespace ptca {
 
 namespace {
 
-// Ntuplets buffered per warp in shared memory before one global reservation.
-constexpr int kNtBuf = 64;
+// Ntuplets buffered per warp in shared memory before one global reservation, and the
+// search's blocks per SM (more walks in flight hide more of their load latency; the
+// build may set both for tuning sweeps).
+#ifndef PT_NT_BUF
+#define PT_NT_BUF 64
+#endif
+#ifndef PT_NT_BLOCKS_PER_SM
+#define PT_NT_BLOCKS_PER_SM 6
+#endif
+constexpr int kNtBuf = PT_NT_BUF;
 constexpr int kNtWarps = 8;  // warps per block of the ntuplet search
-constexpr int kNtBlocksPerSm = 6;  // more walks in flight hide more of their load latency
+constexpr int kNtBlocksPerSm = PT_NT_BLOCKS_PER_SM;
 struct NtWarp {
   uint32_t roots[64];                        // queued roots (< 32 + 32)
-  int32_t hits[kNtBuf][kMaxHits];            // buffered ntuplets
+  int32_t hits[kNtBuf][kMaxHits];            // buffered ntuplets (sorted hit indices)
   uint32_t cells[kNtBuf][kMaxCellsPerNt];
   float q[kNtBuf];
   uint32_t n[kNtBuf];
@@ -45,8 +53,10 @@ enum WalkMode { kCount = 0, kEmit = 1, kBuffer = 2 };
 // writes them at slots t0, t0 + 1, ... (slots >= cap_nt are dropped); kBuffer: also
 // writes them to the warp's shared buffer (entries >= kNtBuf are dropped; the caller
 // then walks again with kEmit).  A cell's links are a list (its head, then each link's
-// next slot); when writing, the batch index of each cell's outer hit is looked up once,
-// when the cell is pushed.
+// next slot).  The walk keeps the sorted index of each cell's outer hit, read beside
+// the cell's flag and list head when the cell is pushed, so that no step waits on a
+// third dependent load; the batch index (perm) is looked up when a path is written
+// (kEmit) or when the warp copies its buffer out (kBuffer holds sorted indices).
 template <int MODE, bool GATED>
 __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, uint64_t cap_nt,
                          NtWarp* W) {
@@ -54,7 +64,7 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
   uint32_t path[kMaxCellsPerNt];
   uint32_t it[kMaxCellsPerNt];  // next out-link slot of path[k] (kHole: none left)
   float qs[kMaxCellsPerNt];
-  int32_t gh[kMaxCellsPerNt];  // batch index of the outer hit of path[k] (EMIT)
+  int32_t gh[kMaxCellsPerNt];  // sorted index of the outer hit of path[k] (EMIT)
   // a link slot read from the lists (debug build: kHole unless inside the link slots)
   auto slot = [&](uint32_t x) -> uint32_t {
     return (x == kHole || PT_CHECK(b.cnt, x < b.cnt[CNT_LINKS], DBG_NT_LINKS)) ? x : kHole;
@@ -64,8 +74,8 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
   qs[0] = 0.0f;
   int32_t g0 = 0;
   if (EMIT) {
-    g0 = (int32_t)b.perm[b.cell_in[a]];
-    gh[0] = (int32_t)b.perm[b.cell_out[a]];
+    g0 = (int32_t)b.cell_in[a];
+    gh[0] = (int32_t)b.cell_out[a];
   }
   uint32_t found = 0;
   int depth = 1;
@@ -86,7 +96,7 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
     // unused when c has no links) and its outer hit
     const bool leaf = !b.has_out[c];
     const uint32_t hc = b.cell_head[c];
-    const int32_t gc = EMIT ? (int32_t)b.perm[b.cell_out[c]] : 0;
+    const int32_t gc = EMIT ? (int32_t)b.cell_out[c] : 0;
     if (leaf) {
       // leaf: path[0..d] + c, i.e. depth + 1 cells, depth + 2 hits
       if (EMIT) {
@@ -117,9 +127,13 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
         for (int k = 0; k < ncell; ++k)
           b.best[k < depth ? path[k] : c] = ~0ull;  // initial duplicate-cleaning key
         if (keep) {
-          hp[0] = g0;
+          // batch indices when written out, sorted ones in the warp's buffer
+          auto hit = [&](int32_t sorted) -> int32_t {
+            return MODE == kEmit ? (int32_t)b.perm[sorted] : sorted;
+          };
+          hp[0] = hit(g0);
           for (int k = 0; k < ncell; ++k) {
-            hp[k + 1] = k < depth ? gh[k] : gl;
+            hp[k + 1] = hit(k < depth ? gh[k] : gl);
             cp[k] = k < depth ? path[k] : c;
           }
           for (int k = ncell + 1; k < kMaxHits; ++k) hp[k] = -1;
@@ -188,7 +202,10 @@ __global__ void __launch_bounds__(kNtWarps * 32, kNtBlocksPerSm)
           const unsigned long long t = base + e;
           if (t < cap_nt) {
 #pragma unroll
-            for (int k = 0; k < kMaxHits; ++k) b.nt_hits[t * kMaxHits + k] = W.hits[e][k];
+            for (int k = 0; k < kMaxHits; ++k) {
+              const int32_t sh = W.hits[e][k];  // sorted index, -1 pad
+              b.nt_hits[t * kMaxHits + k] = sh >= 0 ? (int32_t)b.perm[sh] : -1;
+            }
 #pragma unroll
             for (int k = 0; k < kMaxCellsPerNt; ++k)
               b.nt_cells[t * kMaxCellsPerNt + k] = W.cells[e][k];
