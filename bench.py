@@ -50,10 +50,10 @@ CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped
 # DRAM traffic per event of the main kernels from one ncu capture (8 PU200 events per
 # launch, profiles/), valid only while the kernel's sources hash to the recorded value.
 NCU_TRAFFIC = {
-    "k_doublets": {"bytes_per_event": 24579200, "issue_active_pct": 58.6, "sha": "b400f2b7270c"},
-    "k_connect": {"bytes_per_event": 22545536, "issue_active_pct": 57.5, "sha": "c130ad467d8f"},
+    "k_doublets": {"bytes_per_event": 24625984, "issue_active_pct": 58.0, "sha": "1af3652c4cc5"},
+    "k_connect": {"bytes_per_event": 22262848, "issue_active_pct": 57.9, "sha": "69724970cad8"},
     "k_link_targets": {"bytes_per_event": 10708576, "issue_active_pct": 12.1, "sha": "c130ad467d8f"},
-    "k_find_ntuplets": {"bytes_per_event": 43480992, "issue_active_pct": 17.2, "sha": "d502d1bde289"},
+    "k_find_ntuplets": {"bytes_per_event": 44179488, "issue_active_pct": 16.5, "sha": "45ab37becb1c"},
 }
 
 
