@@ -317,3 +317,46 @@ def test_poisson_batch_sampled(cuts):
         sl = slice(evoff[e], evoff[e + 1])
         assert_ntuplets_equal(hits[sl], oracle.survivors_hits(ref), ref)
         assert_fits_close(tracks[sl], ref["fit"])
+
+
+def _edge_event(rng, n_lines, cuts):
+    """Straight lines from z0 = +-z0max and with |slope| = cotmax, each nudged by a few
+    float32 ulp either way, through the barrel layers and the disks (hits only where a
+    line meets a layer inside its extent): the cells sit on the D2 and D3 edges, and with
+    a few lines per event most layers' r-z extents are a point or a thin box, the cases
+    where the search windows' r-z reachability test has the least room."""
+    z0max, cot = float(cuts["z0max"]), float(cuts["cotmax"])
+    x, y, z, lay = [], [], [], []
+    for _ in range(n_lines):
+        phi = rng.uniform(-np.pi, np.pi)
+        if rng.random() < 0.5:
+            z0 = rng.choice([-1.0, 1.0]) * z0max * (1 + rng.choice([-3, -1, 0, 1, 3]) * 6e-8)
+            s = rng.uniform(-2.0, 2.0)
+        else:
+            z0 = rng.uniform(-z0max, z0max)
+            s = rng.choice([-1.0, 1.0]) * cot * (1 + rng.choice([-3, -1, 0, 1, 3]) * 6e-8)
+        for L, rl in enumerate(sim.events.BARREL_R):
+            zz = z0 + s * rl
+            if abs(zz) < sim.events.BARREL_ZMAX:
+                x.append(rl * np.cos(phi)), y.append(rl * np.sin(phi)), z.append(zz), lay.append(L)
+        for k, zd in enumerate(sim.events.DISK_Z):
+            for side, base in ((1.0, 4), (-1.0, 7)):
+                if s * side <= 0:
+                    continue
+                r = (side * zd - z0) / s
+                if sim.events.DISK_RMIN <= r <= sim.events.DISK_RMAX:
+                    x.append(r * np.cos(phi)), y.append(r * np.sin(phi))
+                    z.append(side * zd), lay.append(base + k)
+    return _Hits(x, y, z, lay)
+
+
+def test_cut_edge_lines_and_point_layers_match_oracle(small_ctx, cuts):
+    rng = np.random.default_rng(606)
+    events = [_edge_event(rng, n, cuts) for n in (1, 2, 3, 5, 8, 13, 40, 120)]
+    out = run_stages(small_ctx, events)
+    n_cells = 0
+    for e, ev in enumerate(events):
+        ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts)
+        n_cells += ref["cell_inner"].size
+        check_event(out, e, ev, ref)
+    assert n_cells > 100
