@@ -51,7 +51,9 @@ def run_stages(ctx, events):
     return out
 
 
-def check_event(out, e, ev, ref):
+def check_event(out, e, ev, ref, edge_cases=False):
+    """edge_cases: the event was built on the cuts' edges, so the bound on ntuplets near a
+    threshold does not apply; the full sets must still be equal."""
     ci, co, ce = out["cells"]
     m = ce == e
     assert cell_set(ci[m], co[m]) == cell_set(ref["cell_inner"], ref["cell_outer"])
@@ -69,7 +71,10 @@ def check_event(out, e, ev, ref):
     assert int(m.sum()) == ref["nt_n"].size  # no duplicate candidates
     nth, ntn, evoff = out["nt"]
     sl = slice(evoff[e], evoff[e + 1])
-    assert_ntuplets_equal(nth[sl], oracle.survivors_hits(ref), ref)
+    if edge_cases:
+        assert np.array_equal(nth[sl], oracle.survivors_hits(ref))
+    else:
+        assert_ntuplets_equal(nth[sl], oracle.survivors_hits(ref), ref)
     assert np.array_equal(ntn[sl], ref["nt_n"][ref["survivors"]].astype(np.uint8))
     assert_fits_close(out["tracks"][sl], ref["fit"])
 
@@ -320,15 +325,19 @@ def test_poisson_batch_sampled(cuts):
 
 
 def _edge_event(rng, n_lines, cuts):
-    """Straight lines from z0 = +-z0max and with |slope| = cotmax, each nudged by a few
-    float32 ulp either way, through the barrel layers and the disks (hits only where a
-    line meets a layer inside its extent): the cells sit on the D2 and D3 edges, and with
-    a few lines per event most layers' r-z extents are a point or a thin box, the cases
-    where the search windows' r-z reachability test has the least room."""
+    """Tracks whose r-z lines start at z0 = +-z0max or have |slope| = cotmax, each nudged
+    by a few float32 ulp either way, through the barrel layers and the disks (hits only
+    where a line meets a layer inside its extent), on circles through the beam line with
+    0.15 to 0.8 of the largest curvature (so the fitted charge is defined): the cells sit
+    on the D2 and D3 edges, and with a few tracks per event most layers' r-z extents are
+    a point or a thin box, the cases where the search windows' r-z reachability test has
+    the least room."""
     z0max, cot = float(cuts["z0max"]), float(cuts["cotmax"])
     x, y, z, lay = [], [], [], []
     for _ in range(n_lines):
         phi = rng.uniform(-np.pi, np.pi)
+        kap = rng.choice([-1.0, 1.0]) * rng.uniform(0.15, 0.8) * float(cuts["kmax"])
+        turn = lambda r: phi + np.arcsin(0.5 * kap * r)  # noqa: E731
         if rng.random() < 0.5:
             z0 = rng.choice([-1.0, 1.0]) * z0max * (1 + rng.choice([-3, -1, 0, 1, 3]) * 6e-8)
             s = rng.uniform(-2.0, 2.0)
@@ -338,15 +347,16 @@ def _edge_event(rng, n_lines, cuts):
         for L, rl in enumerate(sim.events.BARREL_R):
             zz = z0 + s * rl
             if abs(zz) < sim.events.BARREL_ZMAX:
-                x.append(rl * np.cos(phi)), y.append(rl * np.sin(phi)), z.append(zz), lay.append(L)
-        for k, zd in enumerate(sim.events.DISK_Z):
+                x.append(rl * np.cos(turn(rl))), y.append(rl * np.sin(turn(rl)))
+                z.append(zz), lay.append(L)
+        for j, zd in enumerate(sim.events.DISK_Z):
             for side, base in ((1.0, 4), (-1.0, 7)):
                 if s * side <= 0:
                     continue
                 r = (side * zd - z0) / s
                 if sim.events.DISK_RMIN <= r <= sim.events.DISK_RMAX:
-                    x.append(r * np.cos(phi)), y.append(r * np.sin(phi))
-                    z.append(side * zd), lay.append(base + k)
+                    x.append(r * np.cos(turn(r))), y.append(r * np.sin(turn(r)))
+                    z.append(side * zd), lay.append(base + j)
     return _Hits(x, y, z, lay)
 
 
@@ -358,5 +368,5 @@ def test_cut_edge_lines_and_point_layers_match_oracle(small_ctx, cuts):
     for e, ev in enumerate(events):
         ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts)
         n_cells += ref["cell_inner"].size
-        check_event(out, e, ev, ref)
+        check_event(out, e, ev, ref, edge_cases=True)
     assert n_cells > 100
