@@ -52,7 +52,7 @@ CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped
 NCU_TRAFFIC = {
     "k_doublets": {"bytes_per_event": 24625984, "issue_active_pct": 58.0, "sha": "1af3652c4cc5"},
     "k_connect": {"bytes_per_event": 22262848, "issue_active_pct": 57.9, "sha": "69724970cad8"},
-    "k_link_targets": {"bytes_per_event": 10708576, "issue_active_pct": 12.1, "sha": "c130ad467d8f"},
+    "k_link_targets": {"bytes_per_event": 10678208, "issue_active_pct": 11.9, "sha": "69724970cad8"},
     "k_find_ntuplets": {"bytes_per_event": 44179488, "issue_active_pct": 16.5, "sha": "45ab37becb1c"},
 }
 
