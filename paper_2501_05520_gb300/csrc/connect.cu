@@ -498,7 +498,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
 
 // The target cell (h1, h2) of every link: h1 (the outer hit of the source cell) in h2's
 // incoming segment from h1's layer, which is ordered by inner hit, by binary search;
-// one thread per link slot.  Plain form: the target's incoming-link flag is set.  Gated
+// one thread per link slot.  Plain form: the target's incoming-link flag is set and the
+// link records the target's out-link list head and outer hit.  Gated
 // form: the link's bf16 feature row for the gate's MLP is computed here, one thread per
 // link with every lane busy, from the three hits (mostly still in L2).  A
 // target can be missing only when the doublet stage ran out of cell slots (its status
@@ -525,7 +526,13 @@ __global__ void k_link_targets(Buffers b, pt_cuts cuts, int32_t B, int max_inner
     const bool found = lo < sg.x + sg.y && b.cell_in[lo] == h1;
     const uint32_t c = found ? lo : a;
     b.link_dst[l] = c;
-    if (!GATE && found) b.has_in[c] = 1;
+    if (!GATE) {
+      if (found) b.has_in[c] = 1;
+      // the target's list (complete: every link was pushed by the link kernel; kHole
+      // when the target has none) and outer hit, for the ntuplet walk
+      b.link_walk[l] = make_uint2(b.has_out[c] ? b.cell_head[c] : kHole,
+                                  found ? (t & 0x1fffffffu) : b.cell_out[c]);
+    }
     if (GATE) {
       const uint32_t h0 = b.cell_in[a], h2 = t & 0x1fffffffu;
       float f[kGateFeat];

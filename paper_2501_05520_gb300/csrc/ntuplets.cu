@@ -92,11 +92,24 @@ __device__ uint32_t walk(const Buffers& b, uint32_t a, unsigned long long t0, ui
     const uint32_t c = b.link_dst[l];
     if (!PT_CHECK(b.cnt, c < b.cnt[CNT_CELLS], DBG_NT_CELL)) continue;
     const float q = fadd(qs[d], b.link_q[l]);
-    // everything c may need is loaded at once: its flag, its list head (stale and
-    // unused when c has no links) and its outer hit
-    const bool leaf = !b.has_out[c];
-    const uint32_t hc = b.cell_head[c];
-    const int32_t gc = EMIT ? (int32_t)b.cell_out[c] : 0;
+    bool leaf;
+    uint32_t hc;
+    int32_t gc;
+    if (!GATED) {
+      // the link carries c's list head (kHole: c is a leaf) and outer hit, so a step
+      // waits on one level of loads
+      const uint2 w = b.link_walk[l];
+      leaf = w.x == kHole;
+      hc = w.x;
+      gc = (int32_t)w.y;
+    } else {
+      // everything c may need is loaded at once: its flag, its list head (stale and
+      // unused when c has no links; it also holds the links the mask removed) and its
+      // outer hit
+      leaf = !b.has_out[c];
+      hc = b.cell_head[c];
+      gc = EMIT ? (int32_t)b.cell_out[c] : 0;
+    }
     if (leaf) {
       // leaf: path[0..d] + c, i.e. depth + 1 cells, depth + 2 hits
       if (EMIT) {

@@ -187,6 +187,10 @@ struct Buffers {
   // links
   uint32_t* link_dst;        // [max_links]
   uint32_t* link_next;       // [max_links] the source's next out-link slot (kHole: last)
+  uint2* link_walk;          // [max_links] plain form: the target cell's out-link list head
+                             //   (kHole: a leaf) and its outer hit (sorted index), written
+                             //   with the target so that the ntuplet walk reads each step
+                             //   from the link alone
   float* link_q;             // [max_links]
   // ntuplets before cleaning
   int32_t* nt_hits;          // [max_ntuplets*6] batch input index, -1 pad

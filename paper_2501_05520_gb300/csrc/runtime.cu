@@ -193,6 +193,7 @@ size_t layout(const pt_capacity& c, char* base, Buffers* b, GateWeights** gate =
   t.best = (unsigned long long*)take(C * 8);
   t.link_dst = (uint32_t*)take(L * 4);
   t.link_next = (uint32_t*)take(L * 4);
+  t.link_walk = (uint2*)take(L * 8);
   t.link_q = (float*)take(L * 4);
   t.nt_hits = (int32_t*)take(T * kMaxHits * 4);
   t.nt_cells = (uint32_t*)take(T * kMaxCellsPerNt * 4);
@@ -281,6 +282,10 @@ struct pt_ctx {
   bool fishbone_on = false;
   // the ntuplet search and the link exports follow a keep mask (gate and/or fishbone)
   bool masked() const { return gate_on || fishbone_on; }
+  // whether the stage path's last link stage ran masked: the stage-path ntuplet search
+  // follows the links as that stage left them (plain: each link records its target's
+  // list head; masked: the keep mask and flags)
+  bool links_masked = false;
   // raw input: module table and scratch (allocated on first use)
   pt_module* modules = nullptr;
   int n_modules = 0;
@@ -696,6 +701,7 @@ pt_status pt_build_doublets(pt_ctx* c, int64_t* n_cells) {
 }
 
 pt_status pt_connect_cells(pt_ctx* c, int64_t* n_links) {
+  if (c) c->links_masked = c->masked();
   if (c && c->masked()) {
     STAGE_BODY((reset_counters(c, {CNT_LINKS, CNT_LINKS_USED, CNT_GATE_KEPT}),
                 launch_connect(c->B, c->P, c->L, c->stream, c->gate_on),
@@ -713,7 +719,7 @@ pt_status pt_find_ntuplets(pt_ctx* c, int64_t* n_ntuplets) {
   STAGE_BODY((reset_counters(c, {CNT_NT, CNT_SCAN_NT, CNT_SV}),
               cudaMemsetAsync(c->B.bucket_cnt, 0, (size_t)(loaded_hits(c) + 1) * 4, c->stream),
               cudaMemsetAsync(c->B.used, 0, (size_t)loaded_hits(c), c->stream),
-              launch_ntuplets(c->B, c->P, c->L, c->stream, c->masked())),
+              launch_ntuplets(c->B, c->P, c->L, c->stream, c->links_masked)),
              CNT_SV, n_ntuplets)
 }
 
