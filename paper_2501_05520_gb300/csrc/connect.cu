@@ -496,8 +496,57 @@ __global__ void __launch_bounds__(kConnWarps * 32, kConnBlocksPerSm)
   if (lane == 0 && W.used) atomicAdd(&b.cnt[CNT_LINKS_USED], W.used);
 }
 
+// Position of inner hit h in the cells [lo, hi) of one segment (ordered by inner hit, each
+// inner hit once): the first cell whose inner hit is >= h (hi if none), `found` telling
+// whether it is h.  The segment's inner hits spread over the outer hit's window in the
+// inner layer, so h's position is guessed from the first and last of them and the eight
+// cells around the guess are read at once; a guess that misses leaves a bisection of the
+// side beyond it.  Segments of up to eight cells are read whole.  Dependent loads: two or
+// three levels for most links, against about seven for a bisection of the whole segment.
+__device__ __forceinline__ uint32_t find_inner(const Buffers& b, uint32_t lo, uint32_t hi,
+                                               uint32_t h, bool& found) {
+  const uint32_t end = hi;
+  uint32_t w0 = lo;
+  if (hi - lo > 8) {
+    const uint32_t f = b.cell_in[lo], la = b.cell_in[hi - 1];
+    if (h <= f) {
+      found = h == f;
+      return lo;
+    }
+    if (h > la) {
+      found = false;
+      return hi;
+    }
+    // f < h <= la
+    const uint32_t g =
+        lo + (uint32_t)((uint64_t)(h - f) * (uint64_t)(hi - 1 - lo) / (uint64_t)(la - f));
+    w0 = min(max(g, lo + 3u) - 3u, hi - 8u);
+  }
+  // the (up to) eight cells from w0
+  uint32_t less = 0;
+  bool eq = false;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t v = w0 + k < hi ? b.cell_in[w0 + k] : 0xffffffffu;
+    less += v < h ? 1u : 0u;
+    eq |= v == h;
+  }
+  if (hi - lo <= 8 || (less > 0 && less < 8)) {
+    found = eq;
+    return w0 + less;
+  }
+  // the guess missed: the position lies before w0 (less == 0) or after w0 + 7
+  if (less == 0) hi = w0; else lo = w0 + 8;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (b.cell_in[mid] < h) lo = mid + 1; else hi = mid;
+  }
+  found = lo < end && b.cell_in[lo] == h;
+  return lo;
+}
+
 // The target cell (h1, h2) of every link: h1 (the outer hit of the source cell) in h2's
-// incoming segment from h1's layer, which is ordered by inner hit, by binary search;
+// incoming segment from h1's layer, which is ordered by inner hit (find_inner);
 // one thread per link slot.  Plain form: the target's incoming-link flag is set and the
 // link records the target's out-link list head and outer hit.  Gated
 // form: the link's bf16 feature row for the gate's MLP is computed here, one thread per
@@ -518,13 +567,9 @@ __global__ void k_link_targets(Buffers b, pt_cuts cuts, int32_t B, int max_inner
     uint2 sg = b.seg[(uint64_t)(t & 0x1fffffffu) * max_inner + (t >> 29)];
     if (!PT_CHECK(b.cnt, (uint64_t)sg.x + sg.y <= b.cnt[CNT_CELLS], DBG_TGT_SEGMENT))
       sg = make_uint2(0u, 0u);
-    uint32_t lo = sg.x, hi = sg.x + sg.y;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (b.cell_in[mid] < h1) lo = mid + 1; else hi = mid;
-    }
-    const bool found = lo < sg.x + sg.y && b.cell_in[lo] == h1;
-    const uint32_t c = found ? lo : a;
+    bool found;
+    const uint32_t pos = find_inner(b, sg.x, sg.x + sg.y, h1, found);
+    const uint32_t c = found ? pos : a;
     b.link_dst[l] = c;
     if (!GATE) {
       if (found) b.has_in[c] = 1;
