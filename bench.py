@@ -50,10 +50,10 @@ CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped
 # DRAM traffic per event of the main kernels from one ncu capture (8 PU200 events per
 # launch, profiles/), valid only while the kernel's sources hash to the recorded value.
 NCU_TRAFFIC = {
-    "k_doublets": {"bytes_per_event": 24625984, "issue_active_pct": 58.0, "sha": "1af3652c4cc5"},
-    "k_connect": {"bytes_per_event": 22262848, "issue_active_pct": 57.9, "sha": "69724970cad8"},
-    "k_link_targets": {"bytes_per_event": 10678208, "issue_active_pct": 11.9, "sha": "69724970cad8"},
-    "k_find_ntuplets": {"bytes_per_event": 44179488, "issue_active_pct": 16.5, "sha": "45ab37becb1c"},
+    "k_doublets": {"bytes_per_event": 24503712, "issue_active_pct": 58.4, "sha": "2a8aa9a0d737"},
+    "k_connect": {"bytes_per_event": 22363520, "issue_active_pct": 57.7, "sha": "0d56a924773e"},
+    "k_link_targets": {"bytes_per_event": 14528864, "issue_active_pct": 19.2, "sha": "0d56a924773e"},
+    "k_find_ntuplets": {"bytes_per_event": 35716608, "issue_active_pct": 19.5, "sha": "e73b2d03adb5"},
 }
 
 
