@@ -212,7 +212,9 @@ pt_status pt_connect_cells(pt_ctx* ctx, int64_t* n_links);
 /* Ntuplets: every path of linked cells from a cell without an incoming link to a cell
  * without an outgoing link, 3..6 hits (Sec. 2.2.1: the chain selects candidate sets of
  * hits), then duplicate cleaning and canonical ordering.  n_ntuplets
- * receives the number of cleaned ntuplets. */
+ * receives the number of cleaned ntuplets.  The links are taken as the last
+ * pt_connect_cells left them: with the gate's and fishbone step's keep mask if either was
+ * on then, whatever pt_set_gate or pt_set_fishbone were called with since. */
 pt_status pt_find_ntuplets(pt_ctx* ctx, int64_t* n_ntuplets);
 
 /* Circle + line fit of every cleaned ntuplet (Sec. 2.2.1: a fit determines the track

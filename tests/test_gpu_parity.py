@@ -370,3 +370,29 @@ def test_cut_edge_lines_and_point_layers_match_oracle(small_ctx, cuts):
         n_cells += ref["cell_inner"].size
         check_event(out, e, ev, ref, edge_cases=True)
     assert n_cells > 100
+
+
+def test_stage_ntuplets_follow_the_link_stage_form(cuts):
+    """The stage-path ntuplet search follows the links as the last link stage left them:
+    a gate switched on after a plain link stage does not change the plain result, and
+    one switched off after a gated link stage does not change the gated result."""
+    ev = sim.generate(sim.PU50, 2030, n_particles=600)
+    batch = sim.concat([ev])
+    ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts)
+    with pt.Context(cuts=cuts, capacity=PU_CAP) as ctx:
+        ctx.pt_load_batch(*batch)
+        ctx.pt_build_doublets()
+        ctx.pt_connect_cells()
+        ctx.pt_set_gate(*pt.default_gate())
+        ctx.pt_find_ntuplets()
+        plain = ctx.pt_get_ntuplets()[0]
+        gated_graph = ctx.pt_reconstruct_batch(*batch)[0]
+        ctx.pt_load_batch(*batch)
+        ctx.pt_build_doublets()
+        ctx.pt_connect_cells()
+        ctx.pt_set_gate(None, 0.0)
+        ctx.pt_find_ntuplets()
+        gated_stage = ctx.pt_get_ntuplets()[0]
+    assert_ntuplets_equal(plain, oracle.survivors_hits(ref), ref)
+    assert np.array_equal(gated_stage, gated_graph)
+    assert not np.array_equal(gated_graph, plain)
