@@ -50,11 +50,16 @@ CONFIG4_SEED0 = 5000  # batch workload: 64 events, pileup ~ Poisson(140) clipped
 # DRAM traffic per event of the main kernels from one ncu capture (8 PU200 events per
 # launch, profiles/), valid only while the kernel's sources hash to the recorded value.
 NCU_TRAFFIC = {
-    "k_doublets": {"bytes_per_event": 24503712, "issue_active_pct": 58.4, "sha": "2a8aa9a0d737"},
-    "k_connect": {"bytes_per_event": 22363520, "issue_active_pct": 57.7, "sha": "0d56a924773e"},
-    "k_link_targets": {"bytes_per_event": 14528864, "issue_active_pct": 19.2, "sha": "0d56a924773e"},
-    "k_find_ntuplets": {"bytes_per_event": 35716608, "issue_active_pct": 19.5, "sha": "e73b2d03adb5"},
+    "k_doublets": {"bytes_per_event": 24503712, "issue_active_pct": 58.4,
+                   "warp_inst_per_event": 25200120, "sha": "2a8aa9a0d737"},
+    "k_connect": {"bytes_per_event": 22363520, "issue_active_pct": 57.7,
+                  "warp_inst_per_event": 45554002, "sha": "0d56a924773e"},
+    "k_link_targets": {"bytes_per_event": 14528864, "issue_active_pct": 19.2,
+                       "warp_inst_per_event": 840076, "sha": "0d56a924773e"},
+    "k_find_ntuplets": {"bytes_per_event": 35716608, "issue_active_pct": 19.5,
+                        "warp_inst_per_event": 2328577, "sha": "e73b2d03adb5"},
 }
+SMS, SCHEDULERS_PER_SM = 152, 4  # GB300: each scheduler issues one warp instruction a cycle
 
 
 def make_events(n: int, seed0: int = SEED0):
@@ -176,6 +181,21 @@ class Clocks:
         reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def _issue_roof(rec, events: int, launch_ms: float, clocks) -> dict | None:
+    """The kernel against the instruction-issue roof: its warp instructions per launch
+    (ncu count per event x events) over the launch time, against 152 SMs x 4 schedulers x
+    one warp instruction per cycle at the SM clock seen during the timed steps (the
+    largest, 2070 MHz, when none was sampled)."""
+    if rec is None:
+        return None
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    inst = rec["warp_inst_per_event"] * events
+    achieved = inst / (launch_ms / 1000.0) / 1e9
+    peak = SMS * SCHEDULERS_PER_SM * mhz / 1000.0
+    return {"warp_inst": inst, "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "Ginst/s", "frac": round(achieved / peak, 4), "sm_mhz": mhz}
 
 
 def _peaks() -> dict:
@@ -823,6 +843,7 @@ def run_ours(args):
                 "traffic_over_algorithmic": round(traffic / ab, 3) if traffic else None,
                 "layout_bytes": kernel_layout_bytes(dom, counts),
                 "issue_active_pct": rec["issue_active_pct"] if fresh else None,
+                "issue": _issue_roof(rec if fresh else None, B, km[dom], clocks),
                 "stage": {"name": dstage, "ms": sms_,
                           "frac": round(ab / (sms_ / 1000.0) / 1e9 / pk, 4) if sms_ else None},
                 "graph_stages_A1_A6": {"bytes": gby, "ms": round(gms, 4),
