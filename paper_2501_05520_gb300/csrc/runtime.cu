@@ -1315,6 +1315,7 @@ pt_status pt_enqueue_batch(pt_ctx* c, int n_events, const int64_t* hit_offsets, 
   PT_TRY(ensure_graph(c));
   PT_CUDA(cudaGraphLaunch(c->graph, c->stream));
   c->fitted = true;
+  c->links_masked = c->masked();  // the graph's link stage ran in the current form
   return PT_OK;
 }
 
@@ -1331,6 +1332,7 @@ pt_status pt_reconstruct_batch(pt_ctx* c, int n_events, const int64_t* hit_offse
   PT_TRY(ensure_graph(c));
   PT_CUDA(cudaGraphLaunch(c->graph, c->stream));
   c->fitted = true;
+  c->links_masked = c->masked();  // the graph's link stage ran in the current form
   PT_TRY(sync_counters(c));
   const int64_t S = (int64_t)c->h_cnt[CNT_SV];
   if (n) *n = S;
