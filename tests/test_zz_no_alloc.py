@@ -1,10 +1,11 @@
 """pt_find_doublets_noalloc: the allocation-free doublet search for callers that cannot
-allocate device memory, checked against the context-based entry point.
+allocate device memory, checked against the oracle and the context-based entry point.
 
-Two calls in a row on different events: each call must return exactly the doublet set
-that pt_build_doublets + pt_get_cells returns for the same event and cuts (integer
-output, so the comparison is exact).  The calls go through the C ABI with device
-buffers the test owns; the function itself allocates nothing.
+Two calls in a row on different events: each call must return exactly the oracle's
+doublet set for the same event and cuts, which is also what pt_build_doublets +
+pt_get_cells return (integer output, so the comparison is exact).  The calls go
+through the C ABI with device buffers the test owns; the function itself allocates
+nothing.
 """
 
 import ctypes
@@ -12,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import sim
 
 pytestmark = pytest.mark.gpu
@@ -64,6 +66,8 @@ def test_noalloc_doublets_match_context_entry_point(cuts):
         assert n == len(exp)
         got = set(zip(inner[:n].tolist(), outer[:n].tolist()))
         assert len(got) == n and got == exp
+        ref = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, cuts)
+        assert got == set(zip(ref["cell_inner"].tolist(), ref["cell_outer"].tolist()))
 
 
 def test_noalloc_limits(cuts):
